@@ -1,0 +1,10 @@
+"""FP64 CPU oracle of the volumetric path-graph hot path.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``, never by the product path. It
+shares no code with the CUDA library.
+"""
+from .pathgraph import (  # noqa: F401
+    adjoint, aggregate, dense_fixed_point, forward, gather, hg, hg_dg, image_loss,
+    knn, knn_brute, path_values, propagate, quantize, sweep, vertex_arrays,
+)

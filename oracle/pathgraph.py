@@ -1,0 +1,481 @@
+"""FP64 CPU oracle for the volumetric path-graph hot path.
+
+TEST INFRASTRUCTURE ONLY. Nothing in the product path imports this module:
+only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may use it. It shares no code with the CUDA library.
+
+It computes the path-graph estimator of "Rendering Participating Media Using
+Path Graphs" (Hu et al.) step by step, in float64 with numpy, in the paper's
+own form: the indirect radiance vector L+ indexed by vertex (Section 3.5,
+Eq. rte-mff), the aggregation matrix A+ (Eq. ag-indirect / its matrix form),
+the direct term A°L° (Eq. ag-direct), the propagation matrix P
+(Eq. volume-propagation / rte-pg) and the per-path output (Section 4,
+"Final output", "Handling direct light").
+
+Readings where the paper is silent or garbled (each listed in the design
+notes):
+  * neighbourhoods are exact k-nearest-neighbour sets (self first, then the
+    k-1 nearest others by squared integer distance, ties by smaller index) on
+    21-bit quantised coordinates; the paper's clusters (Section 3.1) are the
+    special case where every point's neighbourhood is its cluster;
+  * the marginal density of a sample (Eq. indirect-weight) is taken over the
+    receiver's own neighbourhood;
+  * the "K p_E(omega_j)" inside the direct marginal (Eq. ag-direct, the
+    definition of p_m after it) is read as K p_e of the same direction;
+  * a delta-light emitter sample cannot be produced by phase sampling, so its
+    balance-heuristic weight reduces to an average over the K emitter samples;
+  * Jacobi iteration (double-buffered), starting from the path tracer's
+    estimate (Section 4, "Path graph solver"); sweep t=1 is the first
+    aggregation + propagation;
+  * "non-aggregated direct light" at output is the K=1 form of Eq. ag-direct.
+
+Parity status of each function is stated in its docstring; the pins live in
+``tests/test_oracle_pins.py``. The whole-pipeline bias against the exact RTE
+solution is parity unpinned (the method is biased by design, Section 5).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+FOUR_PI = 4.0 * np.pi
+QBITS = 21
+QMAX = (1 << QBITS) - 1
+
+
+# --------------------------------------------------------------------------
+# Graph build: quantisation and exact k nearest neighbours
+# --------------------------------------------------------------------------
+def quantize(px, py, pz, lo, hi):
+    """21-bit integer coordinates of the vertices.
+
+    q_a = min(2^21 - 1, max(0, floor((x_a - lo_a) * s))) with
+    s = 2^21 / max_a(hi_a - lo_a). Every operation is one float32 operation
+    with round-to-nearest (this is the single float32 step of the oracle, so
+    that the integer coordinates, and with them the neighbour lists, are
+    identical on every machine). Pinned by hand-computed cases.
+    """
+    lo = np.asarray(lo, np.float32)
+    hi = np.asarray(hi, np.float32)
+    span = np.float32(max(hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]))
+    scale = np.float32(np.float32(1 << QBITS) / span)
+    q = np.empty((len(px), 3), np.int64)
+    for a, x in enumerate((px, py, pz)):
+        t = (np.asarray(x, np.float32) - lo[a]) * scale  # float32 ops
+        assert t.dtype == np.float32
+        qa = np.floor(t).astype(np.int64)
+        q[:, a] = np.clip(qa, 0, QMAX)
+    return q
+
+
+def knn_brute(q, k, r2_max=None):
+    """Definition of the neighbourhood N(s), by brute force (O(n^2)).
+
+    Row s: entry 0 is s itself; entries 1..k-1 are the other vertices with the
+    smallest squared distance |q_s - q_j|^2 (exact int64), ties broken by the
+    smaller index; with r2_max, entries farther than r2_max are dropped.
+    Missing entries are -1. Pinned against a pure-Python loop.
+    """
+    n = len(q)
+    nbr = -np.ones((n, k), np.int64)
+    if n == 0 or k == 0:
+        return nbr
+    idx = np.arange(n)
+    for s in range(n):
+        d2 = ((q - q[s]) ** 2).sum(axis=1)
+        order = np.lexsort((idx, d2))  # by d2, then index
+        order = order[order != s][: k - 1]
+        if r2_max is not None:
+            order = order[d2[order] <= r2_max]
+        nbr[s, 0] = s
+        nbr[s, 1:1 + len(order)] = order
+    return nbr
+
+
+def knn(q, k, r2_max=None, workers=1):
+    """Same neighbourhoods as :func:`knn_brute`, found with a k-d tree.
+
+    scipy's cKDTree (a library kNN primitive) proposes candidate sets; each is
+    re-ordered with exact int64 squared distances and index ties, and widened
+    until the candidate set provably holds every point that can tie with the
+    last kept entry. Pinned against :func:`knn_brute`.
+    """
+    from scipy.spatial import cKDTree
+
+    n = len(q)
+    nbr = -np.ones((n, k), np.int64)
+    if n == 0 or k == 0:
+        return nbr
+    nbr[:, 0] = np.arange(n)
+    if k == 1 or n == 1:
+        return nbr
+    tree = cKDTree(q.astype(np.float64))
+    todo = np.arange(n)
+    kk = min(n, k + 8)
+    while todo.size:
+        _, cand = tree.query(q[todo].astype(np.float64), k=kk, workers=workers)
+        cand = np.asarray(cand, np.int64).reshape(len(todo), kk)
+        d2 = ((q[cand] - q[todo][:, None, :]) ** 2).sum(axis=2)
+        self_mask = cand == todo[:, None]
+        d2s = np.where(self_mask, np.iinfo(np.int64).max, d2)
+        # sort candidates by (d2, index), self last
+        order = np.lexsort((cand, d2s), axis=1)
+        cand_sorted = np.take_along_axis(cand, order, axis=1)
+        d2_sorted = np.take_along_axis(d2s, order, axis=1)
+        d2_far = d2.max(axis=1)  # every point outside the set is at least this far
+        m = min(k - 1, n - 1)  # others wanted (all of them when n <= k-1)
+        last = d2_sorted[:, m - 1]
+        ok = (kk == n) | (last < d2_far)
+        rows = todo[ok]
+        take = cand_sorted[ok, :m]
+        dt = d2_sorted[ok, :m]
+        take = np.where(dt == np.iinfo(np.int64).max, -1, take)  # never self
+        if r2_max is not None:
+            take = np.where(dt <= r2_max, take, -1)
+        ncols = take.shape[1]
+        nbr[rows, 1:1 + ncols] = take
+        todo = todo[~ok]
+        kk = min(n, kk * 2)
+    return nbr
+
+
+# --------------------------------------------------------------------------
+# Henyey-Greenstein phase function (Eq. standard-RTE's rho)
+# --------------------------------------------------------------------------
+def hg(o, d, g):
+    """rho(o, d) = (1 - g^2) / (4 pi (1 + g^2 - 2 g mu)^(3/2)), mu = -o.d.
+
+    o: outgoing direction (toward the previous vertex / camera), d: direction
+    the light arrives from; g > 0 scatters forward. Arrays broadcast over the
+    leading axes; the last axis of o and d is xyz. Pinned by normalisation
+    and the closed forms at mu = +-1.
+    """
+    o = np.asarray(o, np.float64)
+    d = np.asarray(d, np.float64)
+    g = np.asarray(g, np.float64)
+    mu = -(o * d).sum(axis=-1)
+    den = 1.0 + g * g - 2.0 * g * mu
+    return (1.0 - g * g) / (FOUR_PI * den ** 1.5)
+
+
+def hg_dg(o, d, g):
+    """d rho / d g of :func:`hg` (for the adjoint). Pinned by finite differences."""
+    o = np.asarray(o, np.float64)
+    d = np.asarray(d, np.float64)
+    g = np.asarray(g, np.float64)
+    mu = -(o * d).sum(axis=-1)
+    den = 1.0 + g * g - 2.0 * g * mu
+    return (-2.0 * g) / (FOUR_PI * den ** 1.5) - 1.5 * (1.0 - g * g) * (2.0 * g - 2.0 * mu) / (FOUR_PI * den ** 2.5)
+
+
+# --------------------------------------------------------------------------
+# Vertex records
+# --------------------------------------------------------------------------
+def vertex_arrays(V):
+    """float64 views of the recorded per-vertex quantities (caller order)."""
+    f = lambda k: np.asarray(V[k], np.float64)  # noqa: E731
+    return dict(
+        o=np.stack([f("ox"), f("oy"), f("oz")], axis=1),
+        d=np.stack([f("dx"), f("dy"), f("dz")], axis=1),
+        e=np.stack([f("ex"), f("ey"), f("ez")], axis=1),
+        g=f("g"), sigma_s=f("sigma_s"), sigma_t=f("sigma_t"), w=f("w_prop"),
+        Le=f("Le"), pe_e=f("pe_e"), Lph=f("Lph"), pe_ph=f("pe_ph"),
+        delta=np.asarray(V["e_delta"]).astype(bool),
+        succ=np.asarray(V["succ"], np.int64),
+    )
+
+
+# --------------------------------------------------------------------------
+# Aggregation (Section 3.5)
+# --------------------------------------------------------------------------
+def aggregate(V, nbr, chunk=8192, sigma_s=None, g=None):
+    """Aggregation weights of every row s with neighbourhood N(s) = nbr[s].
+
+    Returns a dict (all float64, caller order):
+      A   (n,k): A+_{s,j} = sigma_s(s) rho_s(o_s, d_j) / p_m(d_j),
+                 p_m(d_j) = sum_{l in N(s)} rho_l(o_l, d_j)
+                 (Eq. ag-indirect with the marginal of Eq. indirect-weight)
+      Ae  (n,k): A°_{s,2j}: emitter sample of j (Eq. ag-direct, first sum),
+                 sigma_s rho_s(o_s,e_j) / (sum_l rho_l(o_l,e_j) + K pe_e_j), or
+                 sigma_s rho_s(o_s,e_j) / K for a delta light
+      Aph (n,k): A°_{s,2j+1}: phase sample of j (Eq. ag-direct, second sum),
+                 sigma_s rho_s(o_s,d_j) / (sum_l rho_l(o_l,d_j) + K pe_ph_j)
+      c   (n):   (A°L°)_s = sum_j Ae_{s,j} Le_j + Aph_{s,j} Lph_j
+      D   (n):   the same with N(s) = {s} (non-aggregated direct, Section 4)
+      K   (n):   |N(s)|
+    Entries for missing neighbours (-1) are 0. ``sigma_s``/``g`` override the
+    recorded per-vertex values (used by finite differences).
+    Parity: pinned by the MIS column sums (Eq. indirect-weight), the isotropic
+    closed form, and the K=1 reduction to the path tracer.
+    """
+    X = vertex_arrays(V)
+    if sigma_s is not None:
+        X["sigma_s"] = np.asarray(sigma_s, np.float64)
+    if g is not None:
+        X["g"] = np.asarray(g, np.float64)
+    n, k = nbr.shape
+    out = {name: np.zeros((n, k)) for name in ("A", "Ae", "Aph")}
+    out["c"] = np.zeros(n)
+    out["D"] = np.zeros(n)
+    out["K"] = (nbr >= 0).sum(axis=1)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        nb = nbr[a:b]
+        valid = nb >= 0
+        j = np.where(valid, nb, 0)
+        K = valid.sum(axis=1).astype(np.float64)
+        o_l, g_l = X["o"][j], X["g"][j]              # (m,k,3), (m,k): strategies l
+        d_j, e_j = X["d"][j], X["e"][j]               # (m,k,3): samples j
+        s_idx = np.arange(a, b)
+        o_s, g_s, sig_s = X["o"][s_idx], X["g"][s_idx], X["sigma_s"][s_idx]
+        # rho_l(o_l, d_j) for all l (axis 1) and j (axis 2)
+        rho_ld = hg(o_l[:, :, None, :], d_j[:, None, :, :], g_l[:, :, None])
+        rho_le = hg(o_l[:, :, None, :], e_j[:, None, :, :], g_l[:, :, None])
+        vl = valid[:, :, None]
+        pm_d = np.where(vl, rho_ld, 0.0).sum(axis=1)  # sum over l -> (m,k)
+        pm_e = np.where(vl, rho_le, 0.0).sum(axis=1)
+        rho_sd = hg(o_s[:, None, :], d_j, g_s[:, None])
+        rho_se = hg(o_s[:, None, :], e_j, g_s[:, None])
+        A = sig_s[:, None] * rho_sd / pm_d
+        delta = X["delta"][j]
+        Ae_cont = sig_s[:, None] * rho_se / (pm_e + K[:, None] * X["pe_e"][j])
+        Ae_delta = sig_s[:, None] * rho_se / K[:, None]
+        Ae = np.where(delta, Ae_delta, Ae_cont)
+        Aph = sig_s[:, None] * rho_sd / (pm_d + K[:, None] * X["pe_ph"][j])
+        A, Ae, Aph = (np.where(valid, M, 0.0) for M in (A, Ae, Aph))
+        out["A"][a:b], out["Ae"][a:b], out["Aph"][a:b] = A, Ae, Aph
+        out["c"][a:b] = (Ae * X["Le"][j] + Aph * X["Lph"][j]).sum(axis=1)
+    # non-aggregated direct: K = 1, N(s) = {s}
+    rho_e = hg(X["o"], X["e"], X["g"])
+    rho_d = hg(X["o"], X["d"], X["g"])
+    De = np.where(X["delta"], rho_e * X["Le"], rho_e * X["Le"] / (rho_e + X["pe_e"]))
+    Dp = rho_d * X["Lph"] / (rho_d + X["pe_ph"])
+    out["D"] = X["sigma_s"] * (De + Dp)
+    return out
+
+
+# --------------------------------------------------------------------------
+# Propagation (Eq. volume-propagation, Eq. rte-mff) and output
+# --------------------------------------------------------------------------
+def sweep(V, nbr, A, c, L):
+    """One Jacobi sweep of L+ <- P (A+ L+ + A°L°).
+
+    For a vertex v with successor s = succ(v):
+    L+_v = (tau/p_t)_s * (sum_{j in N(s)} A+_{s,j} L+_j + c_s); 0 if v ends
+    its path. (tau/p_t)_s is the weight of the segment from v to s.
+    """
+    succ = np.asarray(V["succ"], np.int64)
+    w = np.asarray(V["w_prop"], np.float64)
+    Lj = np.where(nbr >= 0, L[np.where(nbr >= 0, nbr, 0)], 0.0)
+    Lbar = (A * Lj).sum(axis=1) + c              # scattered radiance at every s
+    s = np.where(succ >= 0, succ, 0)
+    return np.where(succ >= 0, w[s] * Lbar[s], 0.0)
+
+
+def propagate(V, nbr, A, c, L0, iters, keep_history=False):
+    """iters Jacobi sweeps from L0 (the path tracer's estimate, Section 4).
+
+    Returns (L, history, residuals): history[t] = L after t sweeps
+    (history[0] = L0); residuals[t-1] = ||L_t - L_{t-1}||_2 / ||L_t||_2.
+    Parity: pinned by the dense solve (I - P A+)^-1 P A°L° on tiny graphs,
+    the isotropic geometric series, and the K=1 path-tracing fixed point.
+    """
+    L = np.asarray(L0, np.float64).copy()
+    hist = [L.copy()] if keep_history else None
+    res = []
+    for _ in range(iters):
+        Ln = sweep(V, nbr, A, c, L)
+        num = np.sqrt(((Ln - L) ** 2).sum())
+        den = np.sqrt((Ln ** 2).sum())
+        res.append(num / den if den > 0 else 0.0)
+        L = Ln
+        if keep_history:
+            hist.append(L.copy())
+    return L, hist, np.array(res)
+
+
+def path_values(V, nbr, A, L, D, first, bg):
+    """Radiance each path carries into the camera (Section 4, "Final output").
+
+    For a path whose first vertex is f: (tau/p_t)_f * (sum_{j in N(f)} A+_{f,j} L+_j + D_f),
+    with the non-aggregated direct D_f ("Handling direct light"); plus the
+    background seen by a camera ray that left the medium (bg, 0 otherwise).
+    """
+    first = np.asarray(first, np.int64)
+    bg = np.asarray(bg, np.float64)
+    w = np.asarray(V["w_prop"], np.float64)
+    Lj = np.where(nbr >= 0, L[np.where(nbr >= 0, nbr, 0)], 0.0)
+    Lbar = (A * Lj).sum(axis=1) + D
+    f = np.where(first >= 0, first, 0)
+    return bg + np.where(first >= 0, w[f] * Lbar[f], 0.0)
+
+
+def gather(V, nbr, A, L, D, first, bg, spp, width, height):
+    """Pixel = mean of its spp path values (box filter, one pixel per path)."""
+    vals = path_values(V, nbr, A, L, D, first, bg)
+    return vals.reshape(height, width, spp).mean(axis=2)
+
+
+def forward(V, first, bg, spp, width, height, k, iters, lo=(0, 0, 0), hi=(1, 1, 1),
+            r2_max=None, L0=None, nbr=None, keep_history=False, sigma_s=None, g=None):
+    """Whole hot path: graph, aggregation, iters sweeps, image."""
+    if nbr is None:
+        q = quantize(V["px"], V["py"], V["pz"], lo, hi)
+        nbr = knn(q, k, r2_max)
+    agg = aggregate(V, nbr, sigma_s=sigma_s, g=g)
+    if L0 is None:
+        L0 = V["L0"]
+    L, hist, res = propagate(V, nbr, agg["A"], agg["c"], L0, iters, keep_history)
+    img = gather(V, nbr, agg["A"], L, agg["D"], first, bg, spp, width, height)
+    return dict(nbr=nbr, L=L, history=hist, residuals=res, image=img, **agg)
+
+
+def dense_fixed_point(V, nbr, A, c):
+    """L+ = (I - P A+)^-1 P A°L° (Eq. rte-mff) by a dense LU solve, for tiny n.
+
+    A+ and P are assembled as the paper's matrices: A+[s, nbr[s,j]] = A[s,j]
+    (Eq. ag-indireect-mf) and P[v, succ(v)] = (tau/p_t)_{succ(v)} (Eq. rte-pg).
+    """
+    n = len(c)
+    Ap = np.zeros((n, n))
+    for s in range(n):
+        for jj in range(nbr.shape[1]):
+            if nbr[s, jj] >= 0:
+                Ap[s, nbr[s, jj]] += A[s, jj]
+    P = np.zeros((n, n))
+    succ = np.asarray(V["succ"], np.int64)
+    w = np.asarray(V["w_prop"], np.float64)
+    for v in range(n):
+        if succ[v] >= 0:
+            P[v, succ[v]] = w[succ[v]]
+    return np.linalg.solve(np.eye(n) - P @ Ap, P @ np.asarray(c, np.float64))
+
+
+# --------------------------------------------------------------------------
+# Adjoint: image-loss gradients through the fixed graph
+# --------------------------------------------------------------------------
+def adjoint(V, nbr, iters, L0, dI, first, bg, spp, width, height, voxel=None, n_vox=0, chunk=4096):
+    """Reverse-mode derivative of the image w.r.t. per-vertex sigma_s and g.
+
+    The differentiated map is theta -> image with theta = (sigma_s, g) per
+    vertex; held fixed are positions, directions, light records, tau/p_t,
+    L0 and the graph (weights are re-evaluated as functions of theta).
+    ``dI`` is dLoss/dImage (height x width). Returns dict with grad_sigma_s,
+    grad_g (per vertex) and, when ``voxel`` is given, grad_albedo per voxel
+    (sigma_s = albedo * sigma_t, so d/dalbedo = sum over the voxel's vertices
+    of sigma_t * d/dsigma_s).
+
+    It is written as the chain rule through each weight formula: adjoints of
+    A+, c and D first (reverse sweeps), then the explicit derivatives of the
+    aggregation formulas. Parity: pinned by central finite differences of
+    :func:`forward`.
+    """
+    X = vertex_arrays(V)
+    n, k = nbr.shape
+    agg = aggregate(V, nbr)
+    A, c, D = agg["A"], agg["c"], agg["D"]
+    L, hist, _ = propagate(V, nbr, A, c, L0, iters, keep_history=True)
+    succ, w = X["succ"], X["w"]
+    first = np.asarray(first, np.int64)
+    valid = nbr >= 0
+    j_idx = np.where(valid, nbr, 0)
+    # path adjoints: nu_pi = dI[pixel]/spp
+    nu_path = np.repeat(np.asarray(dI, np.float64).reshape(-1), spp) / spp
+    hasf = first >= 0
+    f = first[hasf]
+    # adjoint of the per-row output weight w_f and of the quantities of row f
+    gA = np.zeros((n, k))   # dLoss/dA+_{s,j}
+    gc = np.zeros(n)        # dLoss/dc_s
+    gD = np.zeros(n)        # dLoss/dD_s
+    nu_row = np.zeros(n)
+    np.add.at(nu_row, f, nu_path[hasf])
+    gD += nu_row * w
+    # lambda = dLoss/dL^(T) from the output
+    lam = np.zeros(n)
+    contrib = (nu_row * w)[:, None] * A
+    np.add.at(lam, j_idx[valid], contrib[valid])
+    gA += (nu_row * w)[:, None] * np.where(valid, hist[iters][j_idx], 0.0)
+    # reverse sweeps t = iters .. 1: L^(t)_v = w_s (sum_j A_sj L^(t-1)_j + c_s)
+    has_succ = succ >= 0
+    v_rows = np.nonzero(has_succ)[0]
+    s_rows = succ[v_rows]
+    for t in range(iters, 0, -1):
+        mu = np.zeros(n)                       # dLoss/d(scattered radiance at s)
+        mu[s_rows] = lam[v_rows] * w[s_rows]
+        gc += mu
+        Lprev = hist[t - 1]
+        gA += mu[:, None] * np.where(valid, Lprev[j_idx], 0.0)
+        lam_prev = np.zeros(n)
+        np.add.at(lam_prev, j_idx[valid], (mu[:, None] * A)[valid])
+        lam = lam_prev
+    # explicit derivatives of the aggregation formulas
+    grad_sig = np.zeros(n)
+    grad_g = np.zeros(n)
+    sig = X["sigma_s"]
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        nb = nbr[a:b]
+        vm = nb >= 0
+        j = np.where(vm, nb, 0)
+        K = vm.sum(axis=1).astype(np.float64)[:, None]
+        s_idx = np.arange(a, b)
+        o_l, g_l = X["o"][j], X["g"][j]
+        d_j, e_j = X["d"][j], X["e"][j]
+        o_s, g_s = X["o"][s_idx], X["g"][s_idx]
+        sg = sig[s_idx][:, None]
+        rho_ld = hg(o_l[:, :, None, :], d_j[:, None, :, :], g_l[:, :, None])
+        rho_le = hg(o_l[:, :, None, :], e_j[:, None, :, :], g_l[:, :, None])
+        drho_ld = hg_dg(o_l[:, :, None, :], d_j[:, None, :, :], g_l[:, :, None])
+        drho_le = hg_dg(o_l[:, :, None, :], e_j[:, None, :, :], g_l[:, :, None])
+        vl = vm[:, :, None]
+        rho_ld, rho_le = np.where(vl, rho_ld, 0.0), np.where(vl, rho_le, 0.0)
+        drho_ld, drho_le = np.where(vl, drho_ld, 0.0), np.where(vl, drho_le, 0.0)
+        pm_d, pm_e = rho_ld.sum(axis=1), rho_le.sum(axis=1)
+        rho_sd = hg(o_s[:, None, :], d_j, g_s[:, None])
+        rho_se = hg(o_s[:, None, :], e_j, g_s[:, None])
+        drho_sd = hg_dg(o_s[:, None, :], d_j, g_s[:, None])
+        drho_se = hg_dg(o_s[:, None, :], e_j, g_s[:, None])
+        delta = X["delta"][j]
+        Le, Lph = X["Le"][j], X["Lph"][j]
+        me = pm_e + K * X["pe_e"][j]
+        mph = pm_d + K * X["pe_ph"][j]
+        gAc, gcc = gA[a:b], gc[a:b][:, None]
+        # d/dsigma_s(s): every weight of row s is sigma_s(s) times a factor
+        fA = np.where(vm, rho_sd / pm_d, 0.0)
+        fe = np.where(vm, np.where(delta, rho_se / K, rho_se / me), 0.0)
+        fph = np.where(vm, rho_sd / mph, 0.0)
+        grad_sig[a:b] += (gAc * fA).sum(axis=1) + gcc[:, 0] * (fe * Le + fph * Lph).sum(axis=1)
+        # d/dg_l through the marginals (l ranges over N(s), axis 1)
+        # A_sj = sg rho_sd / pm_d -> dA/dg_l = -sg rho_sd drho_ld[l,j] / pm_d^2
+        coefA = np.where(vm, -sg * rho_sd / pm_d ** 2, 0.0) * gAc                        # (m,j)
+        coefE = np.where(vm & ~delta, -sg * rho_se * Le / me ** 2, 0.0) * gcc           # (m,j)
+        coefP = np.where(vm, -sg * rho_sd * Lph / mph ** 2, 0.0) * gcc
+        g_l_contrib = (drho_ld * (coefA + coefP)[:, None, :]).sum(axis=2) + (drho_le * coefE[:, None, :]).sum(axis=2)
+        np.add.at(grad_g, j[vm], g_l_contrib[vm])
+        # d/dg_s through the numerators rho_s(o_s, .)
+        numA = np.where(vm, sg * drho_sd / pm_d, 0.0) * gAc
+        numE = np.where(vm, np.where(delta, sg * drho_se * Le / K, sg * drho_se * Le / me), 0.0) * gcc
+        numP = np.where(vm, sg * drho_sd * Lph / mph, 0.0) * gcc
+        grad_g[a:b] += (numA + numE + numP).sum(axis=1)
+    # D_s = sigma_s (De + Dp) with K = 1
+    rho_e = hg(X["o"], X["e"], X["g"])
+    rho_d = hg(X["o"], X["d"], X["g"])
+    drho_e = hg_dg(X["o"], X["e"], X["g"])
+    drho_d = hg_dg(X["o"], X["d"], X["g"])
+    De = np.where(X["delta"], rho_e * X["Le"], rho_e * X["Le"] / (rho_e + X["pe_e"]))
+    Dp = rho_d * X["Lph"] / (rho_d + X["pe_ph"])
+    grad_sig += gD * (De + Dp)
+    dDe = np.where(X["delta"], drho_e * X["Le"], drho_e * X["Le"] * X["pe_e"] / (rho_e + X["pe_e"]) ** 2)
+    dDp = drho_d * X["Lph"] * X["pe_ph"] / (rho_d + X["pe_ph"]) ** 2
+    grad_g += gD * sig * (dDe + dDp)
+    out = dict(grad_sigma_s=grad_sig, grad_g=grad_g)
+    if voxel is not None:
+        ga = np.zeros(n_vox)
+        np.add.at(ga, np.asarray(voxel, np.int64), X["sigma_t"] * grad_sig)
+        out["grad_albedo"] = ga
+    return out
+
+
+def image_loss(img, target):
+    """L = 1/2 sum_p (I_p - I*_p)^2 and its gradient dL/dI."""
+    diff = np.asarray(img, np.float64) - np.asarray(target, np.float64)
+    return 0.5 * float((diff ** 2).sum()), diff

@@ -1,0 +1,607 @@
+/*
+ * pgrec: seeded synthetic scenes and an instrumented volumetric path tracer
+ * that records path-graph inputs.
+ *
+ * This is the input generator shared by the FP64 oracle and the CUDA path.
+ * It plays the role of the paper's instrumented path tracer (Section 4,
+ * "Instrumented path tracer"; Section 3.4 "Volume Path Tracing"): it traces
+ * camera paths through a voxel medium with delta tracking, takes one emitter
+ * (next-event) sample and one phase-function sample at every scattering
+ * vertex, and records every vertex in one global array in path order.
+ *
+ * It computes its own path-tracing estimate (the image and, per vertex, the
+ * incoming indirect radiance along the phase-sampled direction) the way a
+ * path tracer does, by walking each path; it does not evaluate any
+ * path-graph aggregation or propagation operator.
+ *
+ * Conventions (all directions unit length):
+ *   o_v  direction from x_v toward the previous vertex (or the camera)
+ *   d_v  phase-sampled direction at x_v (light arrives from x_v + t d_v)
+ *   e_v  emitter-sample direction at x_v
+ *   Henyey-Greenstein phase with mu = -o.d, so g > 0 scatters forward.
+ * Light model: an optional directional "sun" (a delta light, sampled with
+ * probability p_sun) and continuous emitters (a constant environment and an
+ * optional one-sided rectangular area light), treated together as one
+ * emitter-sampling strategy whose pdf is the selection-weighted mixture.
+ * The area light does not occlude the environment (their radiance adds).
+ *
+ * Randomness: every path draws from its own counter-based splitmix64 stream
+ * keyed by (seed, path index), so the output does not depend on the number
+ * of threads.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define PI_D 3.14159265358979323846
+
+typedef struct {
+    /* medium: [0,1]^3 voxel grid, nearest-voxel lookup */
+    int32_t grid_res;       /* voxels per axis */
+    int32_t medium_kind;    /* 0 = constant sigma_t, 1 = fBm cloud */
+    float sigma_t_max;      /* constant value, or the cloud's maximum */
+    float albedo;           /* used when no albedo grid is given */
+    float g;                /* Henyey-Greenstein asymmetry */
+    int32_t fbm_octaves;
+    float fbm_base_freq;
+    float fbm_lacunarity;
+    float fbm_gain;
+    float cloud_threshold;  /* fBm level mapped to zero density */
+    float cloud_radius;     /* spherical falloff radius around (0.5,0.5,0.5) */
+    uint64_t seed;
+    /* lights */
+    float sun_dir[3];       /* direction the sunlight travels */
+    float sun_irradiance;   /* 0 = no sun */
+    float sky_radiance;     /* constant environment, 0 = none */
+    float area_radiance;    /* 0 = no area light */
+    float area_center[3];
+    float area_u[3];        /* half-edge vectors; emits toward +(u x v) */
+    float area_v[3];
+    float p_sun;            /* probability of picking the sun in NEE */
+    float p_area;           /* share of the area light among continuous lights */
+    /* camera */
+    int32_t width, height, spp, max_depth;
+    float cam_pos[3];
+    float cam_target[3];
+    float cam_fov_deg;      /* vertical field of view */
+} pgrec_config;
+
+typedef struct {
+    /* per-thread growable vertex buffers */
+    int64_t n, cap;
+    float *px, *py, *pz, *ox, *oy, *oz, *dx, *dy, *dz, *ex, *ey, *ez;
+    float *g, *sigma_s, *sigma_t, *w_prop, *Le, *pe_e, *Lph, *pe_ph, *L0;
+    double *L0_f64;
+    uint8_t *e_delta;
+    int32_t *succ_local; /* -1 or offset within the path */
+    int32_t *voxel;
+} vbuf;
+
+typedef struct {
+    pgrec_config cfg;
+    float *density;      /* grid_res^3 sigma_t */
+    float *albedo_grid;  /* grid_res^3 albedo */
+    int64_t n_paths;
+    int nthreads;
+    vbuf *bufs;
+    int64_t *path_first_local; /* per path: local vertex index in its thread buffer or -1 */
+    int32_t *path_thread;
+    float *bg;
+    double *val;
+    int64_t n_vertices;
+    int64_t *thread_offset;
+    double majorant;     /* max sigma_t over the grid (delta-tracking bound) */
+    double p_sun;        /* probability that the emitter sample picks the sun */
+} pgrec_state;
+
+/* ---------------- random numbers ---------------- */
+typedef struct { uint64_t s; } rng_t;
+static inline uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+static inline double rnd(rng_t *r) {
+    r->s += 0x9E3779B97F4A7C15ULL;
+    return (double)(mix64(r->s) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* ---------------- value noise ---------------- */
+static inline double lattice(int64_t x, int64_t y, int64_t z, uint64_t seed) {
+    uint64_t h = seed;
+    h = mix64(h ^ (uint64_t)(x * 0x8DA6B343LL));
+    h = mix64(h ^ (uint64_t)(y * 0xD8163841LL));
+    h = mix64(h ^ (uint64_t)(z * 0xCB1AB31FLL));
+    return (double)(h >> 11) * (1.0 / 9007199254740992.0);
+}
+static double value_noise(double x, double y, double z, uint64_t seed) {
+    double fx = floor(x), fy = floor(y), fz = floor(z);
+    int64_t ix = (int64_t)fx, iy = (int64_t)fy, iz = (int64_t)fz;
+    double tx = x - fx, ty = y - fy, tz = z - fz;
+    double c[2][2][2];
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++)
+            for (int e = 0; e < 2; e++) c[a][b][e] = lattice(ix + a, iy + b, iz + e, seed);
+    double x00 = c[0][0][0] * (1 - tx) + c[1][0][0] * tx;
+    double x10 = c[0][1][0] * (1 - tx) + c[1][1][0] * tx;
+    double x01 = c[0][0][1] * (1 - tx) + c[1][0][1] * tx;
+    double x11 = c[0][1][1] * (1 - tx) + c[1][1][1] * tx;
+    double y0 = x00 * (1 - ty) + x10 * ty;
+    double y1 = x01 * (1 - ty) + x11 * ty;
+    return y0 * (1 - tz) + y1 * tz;
+}
+static double fbm(const pgrec_config *c, double x, double y, double z) {
+    double amp = 1.0, freq = c->fbm_base_freq, sum = 0.0, norm = 0.0;
+    for (int o = 0; o < c->fbm_octaves; o++) {
+        sum += amp * value_noise(x * freq, y * freq, z * freq, c->seed * 131ULL + (uint64_t)o);
+        norm += amp;
+        amp *= c->fbm_gain;
+        freq *= c->fbm_lacunarity;
+    }
+    return sum / norm;
+}
+
+static void build_medium(pgrec_state *st, const float *albedo_grid) {
+    const pgrec_config *c = &st->cfg;
+    int64_t G = c->grid_res, nv = G * G * G;
+    st->density = (float *)malloc(sizeof(float) * nv);
+    st->albedo_grid = (float *)malloc(sizeof(float) * nv);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nv; i++) {
+        int64_t ix = i % G, iy = (i / G) % G, iz = i / (G * G);
+        double x = (ix + 0.5) / G, y = (iy + 0.5) / G, z = (iz + 0.5) / G;
+        double s;
+        if (c->medium_kind == 0) {
+            s = c->sigma_t_max;
+        } else {
+            double rx = x - 0.5, ry = y - 0.5, rz = z - 0.5;
+            double r = sqrt(rx * rx + ry * ry + rz * rz) / c->cloud_radius;
+            double shape = 1.0 - r * r;
+            if (shape < 0) shape = 0;
+            double v = fbm(c, x, y, z) * shape;
+            double t = (v - c->cloud_threshold) / (1.0 - c->cloud_threshold);
+            if (t < 0) t = 0;
+            t = t * 3.0;
+            if (t > 1) t = 1;
+            s = c->sigma_t_max * t;
+        }
+        st->density[i] = (float)s;
+        st->albedo_grid[i] = albedo_grid ? albedo_grid[i] : c->albedo;
+    }
+}
+
+static inline int64_t voxel_of(const pgrec_config *c, double x, double y, double z) {
+    int64_t G = c->grid_res;
+    int64_t ix = (int64_t)floor(x * G), iy = (int64_t)floor(y * G), iz = (int64_t)floor(z * G);
+    if (ix < 0) ix = 0;
+    if (iy < 0) iy = 0;
+    if (iz < 0) iz = 0;
+    if (ix >= G) ix = G - 1;
+    if (iy >= G) iy = G - 1;
+    if (iz >= G) iz = G - 1;
+    return ix + G * (iy + G * iz);
+}
+
+/* ray / unit-box slab test; returns 0 if missed */
+static int box_hit(const double o[3], const double d[3], double *t0, double *t1) {
+    double tn = -1e300, tf = 1e300;
+    for (int a = 0; a < 3; a++) {
+        if (fabs(d[a]) < 1e-300) {
+            if (o[a] < 0.0 || o[a] > 1.0) return 0;
+            continue;
+        }
+        double inv = 1.0 / d[a];
+        double ta = (0.0 - o[a]) * inv, tb = (1.0 - o[a]) * inv;
+        if (ta > tb) { double tmp = ta; ta = tb; tb = tmp; }
+        if (ta > tn) tn = ta;
+        if (tb < tf) tf = tb;
+    }
+    if (tn > tf) return 0;
+    *t0 = tn;
+    *t1 = tf;
+    return tf > 0.0;
+}
+
+static inline double sigma_t_at(const pgrec_state *st, double x, double y, double z) {
+    return st->density[voxel_of(&st->cfg, x, y, z)];
+}
+
+/* delta tracking from p along d (p inside or outside the box).
+ * Returns 1 and the collision point if a real collision happens. */
+static int delta_track(const pgrec_state *st, rng_t *r, const double p[3], const double d[3], double out[3]) {
+    double t0, t1;
+    double majorant = st->majorant;
+    if (majorant <= 0.0) return 0;
+    if (!box_hit(p, d, &t0, &t1)) return 0;
+    double t = t0 > 0.0 ? t0 : 0.0;
+    for (;;) {
+        t -= log(1.0 - rnd(r)) / majorant;
+        if (t >= t1) return 0;
+        double x = p[0] + t * d[0], y = p[1] + t * d[1], z = p[2] + t * d[2];
+        double s = sigma_t_at(st, x, y, z);
+        if (rnd(r) * majorant < s) {
+            out[0] = x; out[1] = y; out[2] = z;
+            return 1;
+        }
+    }
+}
+
+/* ratio-tracking transmittance estimate from p along d up to distance tmax */
+static double ratio_track(const pgrec_state *st, rng_t *r, const double p[3], const double d[3], double tmax) {
+    double t0, t1;
+    double majorant = st->majorant;
+    if (majorant <= 0.0) return 1.0;
+    if (!box_hit(p, d, &t0, &t1)) return 1.0;
+    if (t1 > tmax) t1 = tmax;
+    double t = t0 > 0.0 ? t0 : 0.0, T = 1.0;
+    for (;;) {
+        t -= log(1.0 - rnd(r)) / majorant;
+        if (t >= t1) return T;
+        double s = sigma_t_at(st, p[0] + t * d[0], p[1] + t * d[1], p[2] + t * d[2]);
+        T *= 1.0 - s / majorant;
+    }
+}
+
+static inline void normalize3(double v[3]) {
+    double l = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    v[0] /= l; v[1] /= l; v[2] /= l;
+}
+static inline void cross3(const double a[3], const double b[3], double c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Henyey-Greenstein density for outgoing direction o and light direction d */
+static inline double hg_eval(double g, const double o[3], const double d[3]) {
+    double od = o[0] * d[0] + o[1] * d[1] + o[2] * d[2];
+    double den = 1.0 + g * g + 2.0 * g * od;
+    return (1.0 - g * g) / (4.0 * PI_D * den * sqrt(den));
+}
+
+/* sample d ~ HG around the travel direction w = -o */
+static void hg_sample(double g, const double o[3], rng_t *r, double d[3]) {
+    double u1 = rnd(r), u2 = rnd(r), ct;
+    if (fabs(g) < 1e-6) {
+        ct = 1.0 - 2.0 * u1;
+    } else {
+        double s = (1.0 - g * g) / (1.0 - g + 2.0 * g * u1);
+        ct = (1.0 + g * g - s * s) / (2.0 * g);
+    }
+    if (ct > 1.0) ct = 1.0;
+    if (ct < -1.0) ct = -1.0;
+    double st_ = sqrt(1.0 - ct * ct), ph = 2.0 * PI_D * u2;
+    double w[3] = {-o[0], -o[1], -o[2]}, a[3], u[3], v[3];
+    if (fabs(w[0]) > 0.9) { a[0] = 0; a[1] = 1; a[2] = 0; } else { a[0] = 1; a[1] = 0; a[2] = 0; }
+    cross3(w, a, u); normalize3(u);
+    cross3(w, u, v);
+    for (int i = 0; i < 3; i++) d[i] = st_ * cos(ph) * u[i] + st_ * sin(ph) * v[i] + ct * w[i];
+    normalize3(d);
+}
+
+/* area light: ray from p along d; returns distance to the rectangle or -1 */
+static double area_hit(const pgrec_config *c, const double p[3], const double d[3], double *cos_l) {
+    double u[3] = {c->area_u[0], c->area_u[1], c->area_u[2]};
+    double v[3] = {c->area_v[0], c->area_v[1], c->area_v[2]};
+    double n[3];
+    cross3(u, v, n);
+    normalize3(n);
+    double dn = d[0] * n[0] + d[1] * n[1] + d[2] * n[2];
+    if (dn >= 0.0) return -1.0; /* one-sided: visible only from its +n side */
+    double q[3] = {c->area_center[0] - p[0], c->area_center[1] - p[1], c->area_center[2] - p[2]};
+    double t = (q[0] * n[0] + q[1] * n[1] + q[2] * n[2]) / dn;
+    if (t <= 0.0) return -1.0;
+    double h[3] = {p[0] + t * d[0] - c->area_center[0], p[1] + t * d[1] - c->area_center[1],
+                   p[2] + t * d[2] - c->area_center[2]};
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2], vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    double a = (h[0] * u[0] + h[1] * u[1] + h[2] * u[2]) / uu;
+    double b = (h[0] * v[0] + h[1] * v[1] + h[2] * v[2]) / vv;
+    if (fabs(a) > 1.0 || fabs(b) > 1.0) return -1.0;
+    *cos_l = -dn;
+    return t;
+}
+
+static double area_size(const pgrec_config *c) {
+    double u[3] = {c->area_u[0], c->area_u[1], c->area_u[2]};
+    double v[3] = {c->area_v[0], c->area_v[1], c->area_v[2]}, n[3];
+    cross3(u, v, n);
+    return 4.0 * sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+}
+
+/* continuous-emitter radiance seen from p along d (ignoring the medium) and
+ * the selection-weighted solid-angle pdf of the continuous strategy */
+static void continuous_emission(const pgrec_config *c, double p_cont, const double p[3], const double d[3], double *L,
+                                double *pdf) {
+    int has_area = c->area_radiance > 0, has_sky = c->sky_radiance > 0;
+    double pa = has_area ? (has_sky ? c->p_area : 1.0) : 0.0;
+    double L_ = 0.0, pdf_ = 0.0;
+    if (has_sky) {
+        L_ += c->sky_radiance;
+        pdf_ += (1.0 - pa) / (4.0 * PI_D);
+    }
+    if (has_area) {
+        double cl;
+        double t = area_hit(c, p, d, &cl);
+        if (t > 0) {
+            L_ += c->area_radiance;
+            pdf_ += pa * t * t / (area_size(c) * cl);
+        }
+    }
+    *L = L_;
+    *pdf = p_cont * pdf_;
+}
+
+static void vbuf_grow(vbuf *b) {
+    int64_t nc = b->cap ? b->cap * 2 : 4096;
+#define GROW(f, T) b->f = (T *)realloc(b->f, sizeof(T) * nc)
+    GROW(px, float); GROW(py, float); GROW(pz, float);
+    GROW(ox, float); GROW(oy, float); GROW(oz, float);
+    GROW(dx, float); GROW(dy, float); GROW(dz, float);
+    GROW(ex, float); GROW(ey, float); GROW(ez, float);
+    GROW(g, float); GROW(sigma_s, float); GROW(sigma_t, float); GROW(w_prop, float);
+    GROW(Le, float); GROW(pe_e, float); GROW(Lph, float); GROW(pe_ph, float); GROW(L0, float);
+    GROW(L0_f64, double);
+    GROW(e_delta, uint8_t); GROW(succ_local, int32_t); GROW(voxel, int32_t);
+#undef GROW
+    b->cap = nc;
+}
+
+static inline double f32(double x) { return (double)(float)x; }
+
+/* trace one camera path; appends its vertices to b; returns the path value */
+static double trace_path(pgrec_state *st, int64_t pi, vbuf *b, int64_t *first_local, float *bg_out) {
+    const pgrec_config *c = &st->cfg;
+    rng_t r;
+    r.s = mix64(c->seed ^ mix64((uint64_t)pi + 0x632BE59BD9B4E019ULL));
+    int64_t pix = pi / c->spp;
+    int64_t px_ = pix % c->width, py_ = pix / c->width;
+    /* pinhole camera */
+    double fwd[3] = {c->cam_target[0] - c->cam_pos[0], c->cam_target[1] - c->cam_pos[1], c->cam_target[2] - c->cam_pos[2]};
+    normalize3(fwd);
+    double up0[3] = {0, 1, 0}, right[3], up[3];
+    cross3(fwd, up0, right); normalize3(right);
+    cross3(right, fwd, up);
+    double th = tan(0.5 * c->cam_fov_deg * PI_D / 180.0);
+    double aspect = (double)c->width / c->height;
+    double sx = ((px_ + rnd(&r)) / c->width * 2.0 - 1.0) * th * aspect;
+    double sy = (1.0 - (py_ + rnd(&r)) / c->height * 2.0) * th;
+    double dir[3];
+    for (int i = 0; i < 3; i++) dir[i] = fwd[i] + sx * right[i] + sy * up[i];
+    normalize3(dir);
+    double pos[3] = {c->cam_pos[0], c->cam_pos[1], c->cam_pos[2]}, x[3];
+
+    *first_local = -1;
+    *bg_out = 0.0f;
+    if (!delta_track(st, &r, pos, dir, x)) {
+        double L, pdf;
+        continuous_emission(c, 1.0 - st->p_sun, pos, dir, &L, &pdf);
+        *bg_out = (float)L;
+        return (double)(float)L;
+    }
+    int64_t start = b->n;
+    double p_sun = st->p_sun;
+    int has_cont = c->sky_radiance > 0 || c->area_radiance > 0;
+    double sun_to[3] = {-c->sun_dir[0], -c->sun_dir[1], -c->sun_dir[2]};
+    normalize3(sun_to);
+    double o[3] = {-dir[0], -dir[1], -dir[2]};
+    for (int depth = 0; depth < c->max_depth; depth++) {
+        if (b->n == b->cap) vbuf_grow(b);
+        int64_t v = b->n++;
+        int64_t vox = voxel_of(c, x[0], x[1], x[2]);
+        double sig_t = st->density[vox];
+        double alb = st->albedo_grid[vox];
+        b->px[v] = (float)x[0]; b->py[v] = (float)x[1]; b->pz[v] = (float)x[2];
+        b->ox[v] = (float)o[0]; b->oy[v] = (float)o[1]; b->oz[v] = (float)o[2];
+        b->g[v] = c->g;
+        b->sigma_t[v] = (float)sig_t;
+        b->sigma_s[v] = (float)(alb * sig_t);
+        b->w_prop[v] = (float)(1.0 / sig_t); /* tau / p_t under delta tracking */
+        b->voxel[v] = (int32_t)vox;
+        /* emitter sample */
+        double e[3], Le = 0.0, pe = 0.0;
+        int delta = 0;
+        double u = rnd(&r);
+        if (u < p_sun) {
+            e[0] = sun_to[0]; e[1] = sun_to[1]; e[2] = sun_to[2];
+            delta = 1;
+            Le = c->sun_irradiance / p_sun * ratio_track(st, &r, x, e, 1e300);
+        } else if (has_cont) {
+            int has_area = c->area_radiance > 0, has_sky = c->sky_radiance > 0;
+            double pa = has_area ? (has_sky ? c->p_area : 1.0) : 0.0;
+            if (rnd(&r) < pa) {
+                double a = 2.0 * rnd(&r) - 1.0, bb = 2.0 * rnd(&r) - 1.0, y[3];
+                for (int i = 0; i < 3; i++) y[i] = c->area_center[i] + a * c->area_u[i] + bb * c->area_v[i];
+                for (int i = 0; i < 3; i++) e[i] = y[i] - x[i];
+                normalize3(e);
+            } else {
+                double z = 1.0 - 2.0 * rnd(&r), ph = 2.0 * PI_D * rnd(&r), s = sqrt(fmax(0.0, 1.0 - z * z));
+                e[0] = s * cos(ph); e[1] = s * sin(ph); e[2] = z;
+            }
+            double Lc, pc;
+            continuous_emission(c, 1.0 - st->p_sun, x, e, &Lc, &pc);
+            pe = pc;
+            /* the lights sit outside the medium box: transmittance to the box exit */
+            Le = Lc > 0 ? Lc * ratio_track(st, &r, x, e, 1e300) : 0.0;
+        } else {
+            e[0] = sun_to[0]; e[1] = sun_to[1]; e[2] = sun_to[2];
+        }
+        b->ex[v] = (float)e[0]; b->ey[v] = (float)e[1]; b->ez[v] = (float)e[2];
+        b->Le[v] = (float)Le;
+        b->pe_e[v] = (float)pe;
+        b->e_delta[v] = (uint8_t)delta;
+        /* phase sample and the continuation */
+        double d[3], xn[3];
+        hg_sample(c->g, o, &r, d);
+        b->dx[v] = (float)d[0]; b->dy[v] = (float)d[1]; b->dz[v] = (float)d[2];
+        b->succ_local[v] = -1;
+        b->Lph[v] = 0.0f;
+        b->pe_ph[v] = 0.0f;
+        int hit = delta_track(st, &r, x, d, xn);
+        if (!hit) {
+            if (has_cont) {
+                double Lc, pc;
+                continuous_emission(c, 1.0 - st->p_sun, x, d, &Lc, &pc);
+                b->Lph[v] = (float)Lc;
+                b->pe_ph[v] = (float)pc;
+            }
+            break;
+        }
+        if (depth + 1 >= c->max_depth) break; /* truncated: the collision is dropped */
+        b->succ_local[v] = (int32_t)(v + 1 - start);
+        x[0] = xn[0]; x[1] = xn[1]; x[2] = xn[2];
+        o[0] = -d[0]; o[1] = -d[1]; o[2] = -d[2];
+    }
+    *first_local = start;
+
+    /* Path-tracing estimate from the stored (float32) records, in double:
+     * scattered direct radiance per vertex by one-sample balance-heuristic
+     * MIS of the emitter and phase samples, then the path throughput. */
+    int64_t end = b->n;
+    double val = 0.0, beta = f32(b->w_prop[start]);
+    for (int64_t v = start; v < end; v++) {
+        double ov[3] = {b->ox[v], b->oy[v], b->oz[v]};
+        double ev[3] = {b->ex[v], b->ey[v], b->ez[v]};
+        double dv[3] = {b->dx[v], b->dy[v], b->dz[v]};
+        double gg = b->g[v], ss = b->sigma_s[v];
+        double rho_e = hg_eval(gg, ov, ev), rho_d = hg_eval(gg, ov, dv);
+        double direct;
+        if (b->e_delta[v]) direct = rho_e * (double)b->Le[v];
+        else direct = rho_e * (double)b->Le[v] / (rho_e + (double)b->pe_e[v]);
+        direct += rho_d * (double)b->Lph[v] / (rho_d + (double)b->pe_ph[v]);
+        direct *= ss;
+        val += beta * direct;
+        if (v + 1 < end) beta *= ss * (double)b->w_prop[v + 1];
+        /* store direct temporarily in L0_f64 */
+        b->L0_f64[v] = direct;
+    }
+    /* incoming indirect radiance along d_v: what the rest of the path returns */
+    double Lin = 0.0;
+    for (int64_t v = end - 1; v >= start; v--) {
+        double direct = b->L0_f64[v];
+        b->L0_f64[v] = Lin;
+        b->L0[v] = (float)Lin;
+        if (v > start) Lin = (double)b->w_prop[v] * (direct + (double)b->sigma_s[v] * Lin);
+    }
+    return val;
+}
+
+/* ---------------- public API ---------------- */
+void *pgrec_trace(const pgrec_config *cfg, const float *albedo_grid, int32_t nthreads) {
+    pgrec_state *st = (pgrec_state *)calloc(1, sizeof(pgrec_state));
+    st->cfg = *cfg;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+    omp_set_num_threads(nthreads);
+#else
+    nthreads = 1;
+#endif
+    build_medium(st, albedo_grid);
+    int64_t G = cfg->grid_res, nv = G * G * G;
+    double mx = 0.0;
+    for (int64_t i = 0; i < nv; i++) mx = st->density[i] > mx ? st->density[i] : mx;
+    st->majorant = mx;
+    {
+        int has_cont = cfg->sky_radiance > 0 || cfg->area_radiance > 0;
+        if (cfg->sun_irradiance <= 0) st->p_sun = 0.0;
+        else if (!has_cont) st->p_sun = 1.0;
+        else st->p_sun = cfg->p_sun;
+    }
+    st->n_paths = (int64_t)cfg->width * cfg->height * cfg->spp;
+    st->nthreads = nthreads;
+    st->bufs = (vbuf *)calloc(nthreads, sizeof(vbuf));
+    st->path_first_local = (int64_t *)malloc(sizeof(int64_t) * st->n_paths);
+    st->path_thread = (int32_t *)malloc(sizeof(int32_t) * st->n_paths);
+    st->bg = (float *)malloc(sizeof(float) * st->n_paths);
+    st->val = (double *)malloc(sizeof(double) * st->n_paths);
+    int64_t np = st->n_paths;
+#pragma omp parallel num_threads(nthreads)
+    {
+        int t = 0, nt = 1;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+        nt = omp_get_num_threads();
+#endif
+        int64_t a = np * t / nt, bnd = np * (t + 1) / nt;
+        for (int64_t pi = a; pi < bnd; pi++) {
+            st->val[pi] = trace_path(st, pi, &st->bufs[t], &st->path_first_local[pi], &st->bg[pi]);
+            st->path_thread[pi] = t;
+        }
+    }
+    st->thread_offset = (int64_t *)malloc(sizeof(int64_t) * (nthreads + 1));
+    st->thread_offset[0] = 0;
+    for (int t = 0; t < nthreads; t++) st->thread_offset[t + 1] = st->thread_offset[t] + st->bufs[t].n;
+    st->n_vertices = st->thread_offset[nthreads];
+    return st;
+}
+
+int64_t pgrec_num_vertices(void *h) { return ((pgrec_state *)h)->n_vertices; }
+int64_t pgrec_num_paths(void *h) { return ((pgrec_state *)h)->n_paths; }
+double pgrec_majorant(void *h) { return ((pgrec_state *)h)->majorant; }
+
+/* Copy the records out. Float arrays in the order of `names` below; any
+ * pointer may be NULL to skip it. */
+void pgrec_copy_vertices(void *h, float **f32_out /* 21 */, double *L0_f64, uint8_t *e_delta, int32_t *succ,
+                         int32_t *voxel) {
+    pgrec_state *st = (pgrec_state *)h;
+#pragma omp parallel for schedule(static, 1)
+    for (int t = 0; t < st->nthreads; t++) {
+        vbuf *b = &st->bufs[t];
+        int64_t off = st->thread_offset[t];
+        float *src[21] = {b->px, b->py, b->pz, b->ox, b->oy, b->oz, b->dx, b->dy, b->dz, b->ex, b->ey,
+                          b->ez, b->g, b->sigma_s, b->sigma_t, b->w_prop, b->Le, b->pe_e, b->Lph, b->pe_ph, b->L0};
+        for (int f = 0; f < 21; f++)
+            if (f32_out[f]) memcpy(f32_out[f] + off, src[f], sizeof(float) * b->n);
+        if (L0_f64) memcpy(L0_f64 + off, b->L0_f64, sizeof(double) * b->n);
+        if (e_delta) memcpy(e_delta + off, b->e_delta, b->n);
+        if (voxel) memcpy(voxel + off, b->voxel, sizeof(int32_t) * b->n);
+        if (succ) {
+            /* succ_local is an offset within the path; each vertex's path start is
+             * recovered by walking: vertex v has succ v+1 inside the same buffer */
+            for (int64_t v = 0; v < b->n; v++)
+                succ[off + v] = b->succ_local[v] < 0 ? -1 : (int32_t)(off + v + 1);
+        }
+    }
+}
+
+void pgrec_copy_paths(void *h, int32_t *first, float *bg, double *val) {
+    pgrec_state *st = (pgrec_state *)h;
+#pragma omp parallel for schedule(static)
+    for (int64_t pi = 0; pi < st->n_paths; pi++) {
+        int64_t fl = st->path_first_local[pi];
+        if (first) first[pi] = fl < 0 ? -1 : (int32_t)(st->thread_offset[st->path_thread[pi]] + fl);
+        if (bg) bg[pi] = st->bg[pi];
+        if (val) val[pi] = st->val[pi];
+    }
+}
+
+void pgrec_copy_medium(void *h, float *density, float *albedo) {
+    pgrec_state *st = (pgrec_state *)h;
+    int64_t G = st->cfg.grid_res, nv = G * G * G;
+    if (density) memcpy(density, st->density, sizeof(float) * nv);
+    if (albedo) memcpy(albedo, st->albedo_grid, sizeof(float) * nv);
+}
+
+void pgrec_free(void *h) {
+    pgrec_state *st = (pgrec_state *)h;
+    if (!st) return;
+    for (int t = 0; t < st->nthreads; t++) {
+        vbuf *b = &st->bufs[t];
+        void *ptrs[] = {b->px, b->py, b->pz, b->ox, b->oy, b->oz, b->dx, b->dy, b->dz, b->ex, b->ey, b->ez,
+                        b->g, b->sigma_s, b->sigma_t, b->w_prop, b->Le, b->pe_e, b->Lph, b->pe_ph, b->L0,
+                        b->L0_f64, b->e_delta, b->succ_local, b->voxel};
+        for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); i++) free(ptrs[i]);
+    }
+    free(st->bufs);
+    free(st->path_first_local);
+    free(st->path_thread);
+    free(st->bg);
+    free(st->val);
+    free(st->thread_offset);
+    free(st->density);
+    free(st->albedo_grid);
+    free(st);
+}

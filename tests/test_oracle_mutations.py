@@ -1,0 +1,80 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that a pin fails.
+
+Each mutation replaces one oracle function for the duration of a test with a
+copy that has one deliberate error; the pin that should catch it must then
+raise. This shows the pins constrain the oracle, not just re-run it.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.pathgraph as opg
+import pgrec
+
+from test_oracle_pins import SMALL_SCENES, _cluster_graph, test_hg_forward_convention
+
+
+def _k1_image(scene):
+    rec = pgrec.trace(scene, nthreads=2)
+    n = rec["n"]
+    nbr = np.arange(n, dtype=np.int64)[:, None]
+    agg = opg.aggregate(rec, nbr)
+    L, _, _ = opg.propagate(rec, nbr, agg["A"], agg["c"], np.zeros(n), scene.max_depth)
+    img = opg.gather(rec, nbr, agg["A"], L, agg["D"], rec["first"], rec["bg"], scene.spp, scene.width, scene.height)
+    return img, rec["pt_image"]
+
+
+def test_flipped_scattering_cosine_is_caught(monkeypatch):
+    good = opg.hg
+
+    def bad_hg(o, d, g):  # mu = +o.d instead of -o.d
+        return good(o, -np.asarray(d, np.float64), g)
+
+    monkeypatch.setattr(opg, "hg", bad_hg)
+    monkeypatch.setattr(oracle, "hg", bad_hg)
+    with pytest.raises(AssertionError):
+        test_hg_forward_convention()
+    img, pt = _k1_image(SMALL_SCENES[1])  # sun + sky: continuous-light MIS
+    assert not np.allclose(img, pt, rtol=1e-12, atol=1e-15)
+
+
+def test_wrong_propagation_weight_is_caught(monkeypatch):
+    def bad_sweep(V, nbr, A, c, L):  # weight of the segment into v, not into succ(v)
+        succ = np.asarray(V["succ"], np.int64)
+        w = np.asarray(V["w_prop"], np.float64)
+        Lj = np.where(nbr >= 0, L[np.where(nbr >= 0, nbr, 0)], 0.0)
+        Lbar = (A * Lj).sum(axis=1) + c
+        s = np.where(succ >= 0, succ, 0)
+        return np.where(succ >= 0, w * Lbar[s], 0.0)
+
+    monkeypatch.setattr(opg, "sweep", bad_sweep)
+    img, pt = _k1_image(SMALL_SCENES[1])
+    assert not np.allclose(img, pt, rtol=1e-12, atol=1e-15)
+
+
+def test_transposed_numerator_is_caught():
+    """Using the sample's own pdf rho_j(o_j, d_j) in the numerator instead of
+    the receiver's rho_s(o_s, d_j) breaks the MIS identity of Eq. indirect-weight."""
+    V, nbr = _cluster_graph(random_g=True, random_sigma=True, pe_e=0.0, pe_ph=0.0, Lph=1.0)
+    X = opg.vertex_arrays(V)
+
+    def col_sums(M):
+        out = []
+        for c in range(20):
+            rows = np.nonzero(V["cluster"] == c)[0]
+            col = {}
+            for s in rows:
+                for jj in range(nbr.shape[1]):
+                    col[nbr[s, jj]] = col.get(nbr[s, jj], 0.0) + M[s, jj]
+            out += list(col.values())
+        return np.array(out)
+
+    good = oracle.aggregate(V, nbr)["A"] / X["sigma_s"][:, None]
+    np.testing.assert_allclose(col_sums(good), 1.0, rtol=1e-13)
+    n, k = nbr.shape
+    bad = np.zeros((n, k))
+    for s in range(n):
+        js = nbr[s]
+        pm = opg.hg(X["o"][js][:, None, :], X["d"][js][None, :, :], X["g"][js][:, None]).sum(axis=0)
+        bad[s] = opg.hg(X["o"][js], X["d"][js], X["g"][js]) / pm  # rho_j(o_j, d_j): wrong operand
+    assert not np.allclose(col_sums(bad), 1.0, rtol=1e-6)
