@@ -1,0 +1,222 @@
+/*
+ * pg.h -- C ABI of the GB300 volumetric path-graph library (libpg.so).
+ *
+ * The library computes the path-graph estimator of "Rendering Participating
+ * Media Using Path Graphs" (Hu, Deng, Luan, Hasan, Marschner) on one GPU:
+ *
+ *   pg_build_graph        neighbour edges E_N of the path graph (Section 3.1)
+ *   pg_aggregate          aggregation weights A+ (Eq. ag-indirect) and the
+ *                         direct term A°L° (Eq. ag-direct) per vertex
+ *   pg_propagate          Jacobi sweeps of L+ = P A+ L+ + P A°L° (Eq. rte-mff)
+ *                         with P from Eq. volume-propagation
+ *   pg_gather             per-path output into pixels (Section 4, "Final
+ *                         output", "Handling direct light")
+ *   pg_propagate_adjoint  reverse-mode gradients of an image loss through the
+ *                         fixed graph (the paper has no adjoint; this follows
+ *                         from differentiating the maps above)
+ *
+ * Conventions for every call:
+ *  - Vertex arrays are indexed in CALLER order: the recorder's path order, a
+ *    path's vertices contiguous from first to last (Section 4, "Instrumented
+ *    path tracer"). All array pointers are DEVICE pointers allocated and owned
+ *    by the caller unless a parameter says "host".
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream) unless documented to synchronise. Work stays in flight
+ *    after return; keep inputs alive until the stream has passed the call.
+ *  - Nothing aborts the process. Errors are returned as pg_status; device
+ *    errors of earlier asynchronous work surface at the next synchronising
+ *    call as PG_ERR_CUDA.
+ *  - n = 0 is valid (empty outputs, PG_OK).
+ *  - The library allocates its own device memory (stream-ordered allocator)
+ *    for the graph object and temporaries; PG_ERR_OOM when that fails.
+ */
+#ifndef PG_H
+#define PG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *pg_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+    PG_OK = 0,
+    PG_ERR_INVALID_ARG = 1,  /* bad size, NULL pointer, out-of-range index */
+    PG_ERR_OOM = 2,          /* device allocation failed */
+    PG_ERR_CUDA = 3,         /* CUDA runtime / launch error */
+    PG_ERR_NONFINITE = 4,    /* NaN or Inf in an input array */
+    PG_ERR_TIMEOUT = 5,      /* reserved: a bounded device wait ran out */
+    PG_ERR_UNSUPPORTED = 6,  /* parameter outside what this build supports */
+    PG_ERR_STATE = 7         /* call order: e.g. propagate before aggregate */
+} pg_status;
+
+/* Storage type of the edge weights in the propagation sweep. 16-bit types
+ * store each row as an FP32 scale times a 16-bit payload; accumulation is
+ * FP32 in every case. */
+typedef enum { PG_W_F32 = 0, PG_W_BF16 = 1, PG_W_F16 = 2 } pg_wdtype;
+
+typedef struct pg_graph pg_graph; /* opaque; owns its device buffers */
+
+/* Per-vertex records (caller order, length n, device pointers). They are the
+ * quantities the instrumented path tracer records (Section 4):
+ *   p     position x_v
+ *   o     unit direction from x_v toward the previous vertex / the camera
+ *   d     unit phase-sampled direction omega_v (light arrives from x_v + t d)
+ *   e     unit emitter-sample direction omega^e_v
+ *   g     Henyey-Greenstein asymmetry (|g| < 1), rho(o,d) with mu = -o.d
+ *   sigma_s, sigma_t  scattering / extinction coefficient at x_v
+ *   w_prop  tau/p_t of the segment that ENTERS x_v (Eq. volume-propagation;
+ *           1/sigma_t under delta tracking); for a path's first vertex this
+ *           is the camera segment
+ *   Le    radiance returned by the emitter sample (transmittance included;
+ *         for a delta light already divided by its selection probability)
+ *   pe_e  pdf of the emitter-sampling strategy for e (selection included);
+ *         ignored for delta lights
+ *   e_delta  1 if the emitter sample is a delta light (cannot be hit by
+ *            phase sampling), else 0
+ *   Lph   emitted radiance found along d when the phase-sampled flight left
+ *         the medium (0 otherwise); pe_ph its emitter-strategy pdf
+ *   succ  caller index of the next vertex on the same path, or -1 at the
+ *         end of a path. Every vertex has at most one predecessor.
+ * pg_build_graph reads only px, py, pz; pg_aggregate reads the rest. */
+typedef struct {
+    const float *px, *py, *pz;
+    const float *ox, *oy, *oz;
+    const float *dx, *dy, *dz;
+    const float *ex, *ey, *ez;
+    const float *g, *sigma_s, *sigma_t, *w_prop;
+    const float *Le, *pe_e, *Lph, *pe_ph;
+    const uint8_t *e_delta;
+    const int32_t *succ;
+} pg_vertices;
+
+typedef struct {
+    int32_t k;          /* neighbours per vertex INCLUDING itself, 1..32 */
+    float bbox_lo[3];   /* quantisation box; points outside are clamped */
+    float bbox_hi[3];
+    int64_t r2_max;     /* drop neighbours with squared quantised distance
+                           > r2_max; negative = no radius limit */
+    int32_t grid_level; /* hash-grid cells per axis = 2^grid_level (1..10);
+                           0 = chosen from n and k */
+} pg_build_params;
+
+/* Neighbour edges E_N (Section 3.1: points exchange information with their
+ * spatial neighbourhood). Each vertex s gets N(s): itself first, then the
+ * k-1 other vertices with the smallest squared distance between 21-bit
+ * quantised coordinates q = min(2^21-1, floor((p - lo) * 2^21 / max_extent)),
+ * ties broken by the smaller caller index; entries beyond r2_max are
+ * dropped. Exact (bit-identical to brute force).
+ * Synchronises `stream` once (to report non-finite positions).
+ * Errors: PG_ERR_INVALID_ARG (NULL, n < 0, n >= 2^31-1, bad box),
+ * PG_ERR_UNSUPPORTED (k outside 1..32, grid_level > 10), PG_ERR_NONFINITE.
+ * *out is freed with pg_graph_destroy. */
+pg_status pg_build_graph(const pg_vertices *v, int64_t n, const pg_build_params *params, pg_stream_t stream,
+                         pg_graph **out);
+
+/* Copy N(s) out: nbr[s*k + i] (caller indices, row s in caller order, -1 for
+ * a missing neighbour when n < k or beyond r2_max). nbr: device, n*k int32. */
+pg_status pg_graph_neighbors(const pg_graph *g, int32_t *nbr, pg_stream_t stream);
+
+typedef struct {
+    int64_t n;           /* vertices */
+    int32_t k;           /* neighbours per row requested */
+    int32_t row_width;   /* stored row width (k rounded up to 4, 8, 16, 32) */
+    int32_t grid_level;
+    int32_t aggregated;  /* 1 after pg_aggregate */
+    int64_t n_active;    /* vertices with a predecessor (rows a sweep updates) */
+    int64_t nnz_swept;   /* edge updates per sweep: entries (s, j) with j in
+                            N(s), s having a predecessor and j a successor */
+    int64_t device_bytes;/* device memory held by the graph */
+    int32_t weight_dtype;
+    int32_t history_iters; /* sweeps stored by the last pg_propagate, -1 none */
+} pg_graph_info;
+
+pg_status pg_graph_get_info(const pg_graph *g, pg_graph_info *info);
+
+/* Aggregation (Section 3.5). For every vertex s with K = |N(s)|:
+ *   A+_{s,j} = sigma_s(s) rho_s(o_s, d_j) / sum_{l in N(s)} rho_l(o_l, d_j)
+ *     (Eq. ag-indirect with the marginal density of Eq. indirect-weight)
+ *   c_s = sum_{j in N(s)} A°_{s,2j} Le_j + A°_{s,2j+1} Lph_j   (Eq. ag-direct)
+ *     A°_{s,2j}   = sigma_s rho_s(o_s,e_j) / (sum_l rho_l(o_l,e_j) + K pe_e_j),
+ *                   or sigma_s rho_s(o_s,e_j) / K for a delta light
+ *     A°_{s,2j+1} = sigma_s rho_s(o_s,d_j) / (sum_l rho_l(o_l,d_j) + K pe_ph_j)
+ *   D_s = the same direct term with N(s) = {s} (the non-aggregated direct
+ *     light used at output, Section 4 "Handling direct light").
+ * The graph keeps the propagation matrix (P A+, Eq. rte-mff) in `wdtype` and
+ * P c. c and D (caller order, n floats each, device) are written for the
+ * caller; either may be NULL. Synchronises `stream` once.
+ * Errors: PG_ERR_NONFINITE, PG_ERR_INVALID_ARG (succ out of range, a vertex
+ * with two predecessors, |g| >= 1, negative coefficients or pdfs). */
+pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype wdtype, float *c, float *D, pg_stream_t stream);
+
+/* Propagation (Eq. rte-mff, P from Eq. volume-propagation): `iters` Jacobi
+ * sweeps of
+ *   L+_v <- (tau/p_t)_s * ( sum_{j in N(s)} A+_{s,j} L+_j + c_s ),  s = succ(v),
+ * and L+_v = 0 at the end of a path, starting from L0 (the path tracer's
+ * incoming-indirect estimate, Section 4 "Path graph solver").
+ *   c      caller order, n floats; NULL = the c of the last pg_aggregate
+ *   L0     caller order, n floats
+ *   L      out, caller order, n floats: L+ after the last sweep run
+ *   tol    > 0: stop after the first sweep whose relative change
+ *          ||L_t - L_{t-1}||_2 / ||L_t||_2 (accumulated in FP64) is < tol;
+ *          later sweeps return at once on the device (no host round trip)
+ *   keep_history  1: the graph keeps every iterate for pg_propagate_adjoint
+ *   residual      HOST, `iters` doubles, or NULL (entries past the stop are 0)
+ *   iters_done    HOST int32 or NULL
+ * Asynchronous unless `residual` or `iters_done` is non-NULL (then it
+ * synchronises to copy them). Errors: PG_ERR_STATE (no pg_aggregate),
+ * PG_ERR_INVALID_ARG (iters < 0, NULL L0/L). */
+pg_status pg_propagate(pg_graph *g, const float *c, const float *L0, int32_t iters, double tol, int32_t keep_history,
+                       float *L, double *residual, int32_t *iters_done, pg_stream_t stream);
+
+/* Output (Section 4, "Final output" and "Handling direct light"). Path p
+ * with first vertex f carries
+ *   val_p = bg_p + (tau/p_t)_f * ( sum_{j in N(f)} A+_{f,j} L_j + D_f )
+ * (val_p = bg_p when first[p] = -1, the camera ray left the medium), and
+ * pixel i averages its spp paths p = i*spp .. i*spp+spp-1:
+ *   image[i] = (1/spp) sum_p val_p,   i = y*width + x.
+ * L, D: caller order, n floats; first: n_paths int32 (caller vertex index
+ * or -1); bg: n_paths floats; image: width*height floats (out).
+ * n_paths must equal width*height*spp. Errors: PG_ERR_STATE, PG_ERR_INVALID_ARG. */
+pg_status pg_gather(const pg_graph *g, const float *L, const float *D, const int32_t *first, const float *bg,
+                    int64_t n_paths, int32_t spp, int32_t width, int32_t height, float *image, pg_stream_t stream);
+
+/* Adjoint of pg_aggregate -> pg_propagate -> pg_gather for a fixed graph,
+ * fixed samples, fixed tau/p_t and a detached L0. Needs the last
+ * pg_propagate to have run with keep_history = 1 (its iteration count is
+ * used) and the gather to have used that call's L.
+ *   dI        dLoss/dImage, width*height floats (device)
+ *   first     as in pg_gather
+ *   grad_sigma_s, grad_g  out, caller order, n floats each, or NULL:
+ *             dLoss/dsigma_s(v) and dLoss/dg(v) (weights re-evaluated as
+ *             functions of sigma_s and g, marginals included)
+ *   voxel, sigma_t, grad_albedo_vox, n_vox: optional per-voxel albedo
+ *             gradient, sigma_s = albedo[voxel(v)] * sigma_t(v):
+ *             grad_albedo_vox[x] = sum_{v: voxel(v)=x} sigma_t(v) dLoss/dsigma_s(v)
+ *             (overwritten, n_vox floats); pass NULL to skip
+ *   recompute_weights  0: use the stored weights and a transposed copy kept
+ *             in the graph (fast, nnz*(4+weight bytes) extra memory);
+ *             1: re-evaluate every edge weight from the vertex records in
+ *             each reverse sweep (no weight memory; summation order of the
+ *             reverse sweep is not deterministic).
+ * Gradients of vertices with sigma_s = 0 are reported as 0.
+ * Errors: PG_ERR_STATE (no history), PG_ERR_INVALID_ARG. */
+pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const int32_t *first, int64_t n_paths, int32_t spp,
+                               int32_t width, int32_t height, float *grad_sigma_s, float *grad_g,
+                               const int32_t *voxel, const float *sigma_t, float *grad_albedo_vox, int64_t n_vox,
+                               int32_t recompute_weights, pg_stream_t stream);
+
+/* Free the stored edge weights and the transposed copy (after the forward
+ * pass, when memory is tight); pg_propagate then returns PG_ERR_STATE and
+ * pg_propagate_adjoint needs recompute_weights = 1. */
+pg_status pg_graph_release_weights(pg_graph *g);
+
+void pg_graph_destroy(pg_graph *g);
+const char *pg_status_string(pg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PG_H */

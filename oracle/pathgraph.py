@@ -187,8 +187,11 @@ def vertex_arrays(V):
 # --------------------------------------------------------------------------
 # Aggregation (Section 3.5)
 # --------------------------------------------------------------------------
-def aggregate(V, nbr, chunk=8192, sigma_s=None, g=None):
+def aggregate(V, nbr, chunk=8192, sigma_s=None, g=None, rows=None):
     """Aggregation weights of every row s with neighbourhood N(s) = nbr[s].
+
+    With ``rows``, nbr[i] is the neighbourhood of vertex rows[i] and the
+    outputs are for those vertices only (sampled rows of a large graph).
 
     Returns a dict (all float64, caller order):
       A   (n,k): A+_{s,j} = sigma_s(s) rho_s(o_s, d_j) / p_m(d_j),
@@ -213,9 +216,9 @@ def aggregate(V, nbr, chunk=8192, sigma_s=None, g=None):
     if g is not None:
         X["g"] = np.asarray(g, np.float64)
     n, k = nbr.shape
+    recv = np.arange(n) if rows is None else np.asarray(rows, np.int64)
     out = {name: np.zeros((n, k)) for name in ("A", "Ae", "Aph")}
     out["c"] = np.zeros(n)
-    out["D"] = np.zeros(n)
     out["K"] = (nbr >= 0).sum(axis=1)
     for a in range(0, n, chunk):
         b = min(n, a + chunk)
@@ -225,7 +228,7 @@ def aggregate(V, nbr, chunk=8192, sigma_s=None, g=None):
         K = valid.sum(axis=1).astype(np.float64)
         o_l, g_l = X["o"][j], X["g"][j]              # (m,k,3), (m,k): strategies l
         d_j, e_j = X["d"][j], X["e"][j]               # (m,k,3): samples j
-        s_idx = np.arange(a, b)
+        s_idx = recv[a:b]
         o_s, g_s, sig_s = X["o"][s_idx], X["g"][s_idx], X["sigma_s"][s_idx]
         # rho_l(o_l, d_j) for all l (axis 1) and j (axis 2)
         rho_ld = hg(o_l[:, :, None, :], d_j[:, None, :, :], g_l[:, :, None])
@@ -245,11 +248,13 @@ def aggregate(V, nbr, chunk=8192, sigma_s=None, g=None):
         out["A"][a:b], out["Ae"][a:b], out["Aph"][a:b] = A, Ae, Aph
         out["c"][a:b] = (Ae * X["Le"][j] + Aph * X["Lph"][j]).sum(axis=1)
     # non-aggregated direct: K = 1, N(s) = {s}
-    rho_e = hg(X["o"], X["e"], X["g"])
-    rho_d = hg(X["o"], X["d"], X["g"])
-    De = np.where(X["delta"], rho_e * X["Le"], rho_e * X["Le"] / (rho_e + X["pe_e"]))
-    Dp = rho_d * X["Lph"] / (rho_d + X["pe_ph"])
-    out["D"] = X["sigma_s"] * (De + Dp)
+    o, e, d, gg = X["o"][recv], X["e"][recv], X["d"][recv], X["g"][recv]
+    rho_e = hg(o, e, gg)
+    rho_d = hg(o, d, gg)
+    Le, pe, Lph, pph = X["Le"][recv], X["pe_e"][recv], X["Lph"][recv], X["pe_ph"][recv]
+    De = np.where(X["delta"][recv], rho_e * Le, rho_e * Le / (rho_e + pe))
+    Dp = rho_d * Lph / (rho_d + pph)
+    out["D"] = X["sigma_s"][recv] * (De + Dp)
     return out
 
 

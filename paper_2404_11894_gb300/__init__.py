@@ -1,0 +1,155 @@
+"""GB300 volumetric path-graph hot path: Python binding of libpg (include/pg.h).
+
+The functions below carry the C names and only marshal arguments: torch
+tensors provide device memory and the current CUDA stream; every step of the
+path runs in the library's CUDA kernels. There is no CPU fallback: importing
+the binding fails when libpg.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import PgBuildParams, PgError, PgGraphInfo, PgVertices, W_DTYPES, check
+
+VERTEX_F32 = ("px", "py", "pz", "ox", "oy", "oz", "dx", "dy", "dz", "ex", "ey", "ez",
+              "g", "sigma_s", "sigma_t", "w_prop", "Le", "pe_e", "Lph", "pe_ph")
+
+_LIB = _lib.load()
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensors must be contiguous CUDA tensors"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Vertices:
+    """Per-vertex records on the device (caller order), see pg_vertices."""
+
+    def __init__(self, tensors: dict):
+        self.t = tensors
+        self.n = int(tensors["px"].numel())
+        self._struct = PgVertices(**{k: (tensors[k].data_ptr() if k in tensors else None)
+                                     for k, _ in PgVertices._fields_})
+
+    @staticmethod
+    def from_records(rec: dict, device="cuda", non_blocking=False, overrides: dict | None = None) -> "Vertices":
+        """Copy recorder output (numpy or host tensors) to the device."""
+        t = {}
+        for k in VERTEX_F32 + ("e_delta", "succ"):
+            src = (overrides or {}).get(k, rec[k])
+            if isinstance(src, np.ndarray):
+                src = torch.from_numpy(np.ascontiguousarray(src))
+            t[k] = src.to(device, non_blocking=non_blocking)
+        return Vertices(t)
+
+    @property
+    def struct(self) -> PgVertices:
+        return self._struct
+
+
+class Graph:
+    """Owns a pg_graph handle; destroyed with the object."""
+
+    def __init__(self, handle: ctypes.c_void_p, n: int, k: int):
+        self.handle = handle
+        self.n = n
+        self.k = k
+
+    def info(self) -> dict:
+        inf = PgGraphInfo()
+        check(_LIB.pg_graph_get_info(self.handle, ctypes.byref(inf)), "pg_graph_get_info")
+        return {f: getattr(inf, f) for f, _ in PgGraphInfo._fields_}
+
+    def neighbors(self, stream=None) -> torch.Tensor:
+        out = torch.empty((self.n, self.k), dtype=torch.int32, device="cuda")
+        check(_LIB.pg_graph_neighbors(self.handle, _ptr(out), _stream_ptr(stream)), "pg_graph_neighbors")
+        return out
+
+    def release_weights(self):
+        check(_LIB.pg_graph_release_weights(self.handle), "pg_graph_release_weights")
+
+    def close(self):
+        if self.handle:
+            _LIB.pg_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pg_build_graph(verts: Vertices, k: int, bbox_lo=(0.0, 0.0, 0.0), bbox_hi=(1.0, 1.0, 1.0), r2_max: int = -1,
+                   grid_level: int = 0, stream=None) -> Graph:
+    p = PgBuildParams()
+    p.k = k
+    for a in range(3):
+        p.bbox_lo[a] = bbox_lo[a]
+        p.bbox_hi[a] = bbox_hi[a]
+    p.r2_max = r2_max
+    p.grid_level = grid_level
+    h = ctypes.c_void_p()
+    check(_LIB.pg_build_graph(ctypes.byref(verts.struct), verts.n, ctypes.byref(p), _stream_ptr(stream),
+                              ctypes.byref(h)), "pg_build_graph")
+    return Graph(h, verts.n, k)
+
+
+def pg_aggregate(graph: Graph, verts: Vertices, wdtype: str = "f32", stream=None):
+    """Returns (c, D), caller order, float32 device tensors."""
+    c = torch.empty(graph.n, dtype=torch.float32, device="cuda")
+    D = torch.empty(graph.n, dtype=torch.float32, device="cuda")
+    check(_LIB.pg_aggregate(graph.handle, ctypes.byref(verts.struct), W_DTYPES[wdtype], _ptr(c), _ptr(D),
+                            _stream_ptr(stream)), "pg_aggregate")
+    return c, D
+
+
+def pg_propagate(graph: Graph, L0: torch.Tensor, iters: int, c: torch.Tensor | None = None, tol: float = 0.0,
+                 keep_history: bool = False, want_residual: bool = False, out: torch.Tensor | None = None,
+                 stream=None):
+    """Returns L (caller order); with want_residual also (residuals, iters_done)."""
+    L = out if out is not None else torch.empty(graph.n, dtype=torch.float32, device="cuda")
+    res = (ctypes.c_double * max(iters, 1))() if want_residual else None
+    done = ctypes.c_int32(0) if want_residual else None
+    check(_LIB.pg_propagate(graph.handle, _ptr(c), _ptr(L0), iters, tol, int(keep_history), _ptr(L),
+                            res, ctypes.byref(done) if done is not None else None, _stream_ptr(stream)),
+          "pg_propagate")
+    if want_residual:
+        return L, np.array(res[:iters]), done.value
+    return L
+
+
+def pg_gather(graph: Graph, L: torch.Tensor, D: torch.Tensor, first: torch.Tensor, bg: torch.Tensor, spp: int,
+              width: int, height: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    img = out if out is not None else torch.empty((height, width), dtype=torch.float32, device="cuda")
+    check(_LIB.pg_gather(graph.handle, _ptr(L), _ptr(D), _ptr(first), _ptr(bg), first.numel(), spp, width, height,
+                         _ptr(img), _stream_ptr(stream)), "pg_gather")
+    return img
+
+
+def pg_propagate_adjoint(graph: Graph, dI: torch.Tensor, first: torch.Tensor, spp: int, width: int, height: int,
+                         want_sigma_s: bool = True, want_g: bool = True, voxel: torch.Tensor | None = None,
+                         sigma_t: torch.Tensor | None = None, n_vox: int = 0, recompute_weights: bool = False,
+                         stream=None) -> dict:
+    gs = torch.empty(graph.n, dtype=torch.float32, device="cuda") if want_sigma_s else None
+    gg = torch.empty(graph.n, dtype=torch.float32, device="cuda") if want_g else None
+    ga = torch.empty(n_vox, dtype=torch.float32, device="cuda") if voxel is not None else None
+    check(_LIB.pg_propagate_adjoint(graph.handle, _ptr(dI), _ptr(first), first.numel(), spp, width, height,
+                                    _ptr(gs), _ptr(gg), _ptr(voxel), _ptr(sigma_t), _ptr(ga), n_vox,
+                                    int(recompute_weights), _stream_ptr(stream)), "pg_propagate_adjoint")
+    return {"grad_sigma_s": gs, "grad_g": gg, "grad_albedo": ga}
+
+
+__all__ = ["Vertices", "Graph", "PgError", "pg_build_graph", "pg_aggregate", "pg_propagate", "pg_gather",
+           "pg_propagate_adjoint"]

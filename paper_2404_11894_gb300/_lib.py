@@ -1,0 +1,81 @@
+"""ctypes declarations of the libpg C ABI (include/pg.h)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpg.so")
+
+PG_STATUS = {
+    0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
+    4: "non-finite input", 5: "device wait timed out", 6: "unsupported parameter", 7: "invalid call order",
+}
+W_DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
+
+c_float_p = ctypes.POINTER(ctypes.c_float)
+
+
+class PgVertices(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_void_p) for name in (
+        "px", "py", "pz", "ox", "oy", "oz", "dx", "dy", "dz", "ex", "ey", "ez",
+        "g", "sigma_s", "sigma_t", "w_prop", "Le", "pe_e", "Lph", "pe_ph", "e_delta", "succ")]
+
+
+class PgBuildParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("bbox_lo", ctypes.c_float * 3), ("bbox_hi", ctypes.c_float * 3),
+                ("r2_max", ctypes.c_int64), ("grid_level", ctypes.c_int32)]
+
+
+class PgGraphInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("k", ctypes.c_int32), ("row_width", ctypes.c_int32),
+                ("grid_level", ctypes.c_int32), ("aggregated", ctypes.c_int32), ("n_active", ctypes.c_int64),
+                ("nnz_swept", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("weight_dtype", ctypes.c_int32),
+                ("history_iters", ctypes.c_int32)]
+
+
+EXPORTS = ("pg_build_graph", "pg_graph_neighbors", "pg_graph_get_info", "pg_aggregate", "pg_propagate",
+           "pg_gather", "pg_propagate_adjoint", "pg_graph_release_weights", "pg_graph_destroy",
+           "pg_status_string")
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpg.so; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libpg.so not found at {path}: run paper_2404_11894_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.pg_build_graph.argtypes = [ctypes.POINTER(PgVertices), i64, ctypes.POINTER(PgBuildParams), vp,
+                                   ctypes.POINTER(vp)]
+    lib.pg_graph_neighbors.argtypes = [vp, vp, vp]
+    lib.pg_graph_get_info.argtypes = [vp, ctypes.POINTER(PgGraphInfo)]
+    lib.pg_aggregate.argtypes = [vp, ctypes.POINTER(PgVertices), ctypes.c_int, vp, vp, vp]
+    lib.pg_propagate.argtypes = [vp, vp, vp, i32, f64, i32, vp, vp, vp, vp]
+    lib.pg_gather.argtypes = [vp, vp, vp, vp, vp, i64, i32, i32, i32, vp, vp]
+    lib.pg_propagate_adjoint.argtypes = [vp, vp, vp, i64, i32, i32, i32, vp, vp, vp, vp, vp, i64, i32, vp]
+    lib.pg_graph_release_weights.argtypes = [vp]
+    lib.pg_graph_destroy.argtypes = [vp]
+    lib.pg_graph_destroy.restype = None
+    lib.pg_status_string.argtypes = [ctypes.c_int]
+    lib.pg_status_string.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("pg_graph_destroy", "pg_status_string"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class PgError(RuntimeError):
+    def __init__(self, status: int, call: str):
+        self.status = status
+        super().__init__(f"{call}: {PG_STATUS.get(status, status)} (status {status})")
+
+
+def check(status: int, call: str):
+    if status != 0:
+        raise PgError(status, call)

@@ -1,0 +1,319 @@
+// Aggregation (Section 3.5): the MIS edge weights A+ of Eq. ag-indirect, the
+// direct term A°L° of Eq. ag-direct, and the non-aggregated direct light D
+// used at output (Section 4, "Handling direct light").
+//
+// Layout produced for the propagation sweep (Eq. rte-mff, L+ = P A+ L+ + P c):
+// the sweep works on y_s = (tau/p_t)_s (A+ L+ + c)_s, the radiance that s
+// sends to its predecessor, so L+_v = y_{succ(v)} and
+//   y_s <- sum_{j in N(s)} W_{s,j} y_{succ(j)} + b_s,
+//   W_{s,j} = (tau/p_t)_s A+_{s,j},  b_s = (tau/p_t)_s c_s.
+// Rows are stored in "sweep order" r: vertices that have a predecessor first
+// (in Morton order), then the paths' first vertices, whose y is never read
+// by a sweep. Column ids are sweep rows of succ(j); j at the end of its path
+// (or a missing neighbour) points at the zero slot n.
+#include "pg_internal.cuh"
+
+__global__ void pack_kernel(pg_vertices v, int64_t n, const int32_t *__restrict__ c2m, float4 *__restrict__ OG,
+                            float4 *__restrict__ DP, float4 *__restrict__ EP, float4 *__restrict__ LV,
+                            int32_t *__restrict__ succ_m, int32_t *__restrict__ predcnt, int32_t *__restrict__ flags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t m = c2m[i];
+    float ox = v.ox[i], oy = v.oy[i], oz = v.oz[i], g = v.g[i];
+    float dx = v.dx[i], dy = v.dy[i], dz = v.dz[i], pph = v.pe_ph[i];
+    float ex = v.ex[i], ey = v.ey[i], ez = v.ez[i], pe = v.pe_e[i];
+    float Le = v.Le[i], Lph = v.Lph[i], ss = v.sigma_s[i], w = v.w_prop[i];
+    int delta = v.e_delta[i] != 0;
+    int32_t sc = v.succ[i];
+    bool fin = isfinite(ox) && isfinite(oy) && isfinite(oz) && isfinite(g) && isfinite(dx) && isfinite(dy) &&
+               isfinite(dz) && isfinite(pph) && isfinite(ex) && isfinite(ey) && isfinite(ez) && isfinite(pe) &&
+               isfinite(Le) && isfinite(Lph) && isfinite(ss) && isfinite(w);
+    int f = 0;
+    if (!fin) f |= PG_FLAG_NONFINITE;
+    if (!(fabsf(g) < 1.0f) || ss < 0.0f || w < 0.0f || pph < 0.0f || (!delta && pe < 0.0f)) f |= PG_FLAG_BAD_RANGE;
+    int32_t sm = -1;
+    if (sc >= 0) {
+        if (sc >= n || sc == i) {
+            f |= PG_FLAG_BAD_INDEX;
+        } else {
+            sm = c2m[sc];
+            if (atomicAdd(&predcnt[sm], 1) != 0) f |= PG_FLAG_TWO_PREDS;
+        }
+    } else if (sc != -1) {
+        f |= PG_FLAG_BAD_INDEX;
+    }
+    if (f) atomicOr(flags, f);
+    OG[m] = make_float4(ox, oy, oz, g);
+    DP[m] = make_float4(dx, dy, dz, pph);
+    EP[m] = make_float4(ex, ey, ez, delta ? -1.0f : pe);
+    LV[m] = make_float4(Le, Lph, ss, w);
+    succ_m[m] = sm;
+}
+
+__global__ void active_flag_kernel(const int32_t *__restrict__ predcnt, int64_t n, int32_t *__restrict__ act) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    act[m] = predcnt[m] > 0 ? 1 : 0;
+}
+
+// act holds the exclusive prefix of the active flags; predcnt the flags' source
+__global__ void row_order_kernel(const int32_t *__restrict__ predcnt, const int32_t *__restrict__ act_prefix,
+                                 const int32_t *__restrict__ d_n_active, int64_t n, int32_t *__restrict__ m2r,
+                                 int32_t *__restrict__ r2m) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    int32_t pre = act_prefix[m];
+    int32_t r = predcnt[m] > 0 ? pre : (*d_n_active + (int32_t)(m - pre));
+    m2r[m] = r;
+    r2m[r] = (int32_t)m;
+}
+
+template <typename WT>
+__device__ __forceinline__ WT to_w(float x);
+template <>
+__device__ __forceinline__ float to_w<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_w<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <>
+__device__ __forceinline__ __half to_w<__half>(float x) { return __float2half_rn(x); }
+
+// One group of KP lanes per row s (Morton order m); lane j owns neighbour
+// slot j of N(s). Strategy data (o_l, HG constants of g_l) of the row's
+// neighbours are shared through shared memory; each lane sums the k pdfs
+// rho_l(o_l, d_j) and rho_l(o_l, e_j) for its own samples (the two marginal
+// densities), then forms its weights.
+template <int KP, typename WT>
+__global__ void __launch_bounds__(256) aggregate_kernel(
+    const int32_t *__restrict__ nbr, const float4 *__restrict__ OG, const float4 *__restrict__ DP,
+    const float4 *__restrict__ EP, const float4 *__restrict__ LV, const int32_t *__restrict__ succ_m,
+    const int32_t *__restrict__ m2r, const int32_t *__restrict__ m2c, int64_t n, int64_t n_active,
+    WT *__restrict__ W, float *__restrict__ rscale, int32_t *__restrict__ col, float *__restrict__ b,
+    float *__restrict__ c_m, float *__restrict__ D_m, float *__restrict__ c_out, float *__restrict__ D_out,
+    unsigned long long *__restrict__ nnz_counter) {
+    __shared__ float4 s_o[256];   // (ox, oy, oz, C)
+    __shared__ float2 s_ab[256];  // ((1-g)^2, 2g)
+    const int lane = threadIdx.x & 31;
+    const int j = lane & (KP - 1);
+    const int gbase = threadIdx.x - j; // first thread of this row's group
+    const int64_t m = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / KP;
+    const bool row_ok = m < n;
+    int32_t nj = row_ok ? nbr[m * KP + j] : -1;
+    const bool valid = nj >= 0;
+    float4 og = make_float4(0.f, 0.f, 1.f, 0.f), dp = make_float4(0.f, 0.f, 1.f, 0.f),
+           ep = make_float4(0.f, 0.f, 1.f, 0.f), lv = make_float4(0.f, 0.f, 0.f, 0.f);
+    int32_t sj = -1;
+    if (valid) {
+        og = OG[nj];
+        dp = DP[nj];
+        ep = EP[nj];
+        lv = LV[nj];
+        sj = succ_m[nj];
+    }
+    HGc hc = hg_consts(og.w);
+    s_o[threadIdx.x] = make_float4(og.x, og.y, og.z, valid ? hc.C : 0.0f);
+    s_ab[threadIdx.x] = make_float2(valid ? hc.a : 1.0f, valid ? hc.b2 : 0.0f);
+    __syncwarp();
+    const unsigned gmask = (KP == 32) ? 0xffffffffu : (((1u << KP) - 1u) << (lane & ~(KP - 1)));
+    const float K = (float)__popc(__ballot_sync(0xffffffffu, valid) & gmask);
+
+    // marginal densities of this lane's two samples over the row's strategies
+    float pm_d = 0.0f, pm_e = 0.0f;
+#pragma unroll 4
+    for (int l = 0; l < KP; l++) {
+        float4 so = s_o[gbase + l];
+        float2 ab = s_ab[gbase + l];
+        HGc h;
+        h.C = so.w;
+        h.a = ab.x;
+        h.b2 = ab.y;
+        pm_d += hg_eval(h, dot3(so.x, so.y, so.z, dp.x, dp.y, dp.z));
+        pm_e += hg_eval(h, dot3(so.x, so.y, so.z, ep.x, ep.y, ep.z));
+    }
+    // receiver s = slot 0 of the group
+    const float4 so = s_o[gbase];
+    const float2 sab = s_ab[gbase];
+    HGc hs;
+    hs.C = so.w;
+    hs.a = sab.x;
+    hs.b2 = sab.y;
+    const int src = lane & ~(KP - 1);
+    const float sig_s = __shfl_sync(0xffffffffu, lv.z, src);
+    const float w_s = __shfl_sync(0xffffffffu, lv.w, src);
+    float rho_sd = hg_eval(hs, dot3(so.x, so.y, so.z, dp.x, dp.y, dp.z));
+    float rho_se = hg_eval(hs, dot3(so.x, so.y, so.z, ep.x, ep.y, ep.z));
+    float A = 0.0f, term = 0.0f;
+    if (valid) {
+        A = sig_s * rho_sd / pm_d;
+        bool delta = ep.w < 0.0f;
+        float Ae = delta ? sig_s * rho_se / K : sig_s * rho_se / fmaf(K, ep.w, pm_e);
+        float Aph = sig_s * rho_sd / fmaf(K, dp.w, pm_d);
+        term = fmaf(Ae, lv.x, Aph * lv.y);
+    }
+    // c_s: sum over the group's lanes (fixed butterfly order)
+    float c = term;
+#pragma unroll
+    for (int o = KP / 2; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    // D_s from slot 0's own samples (K = 1)
+    float Dterm = 0.0f;
+    if (j == 0 && valid) {
+        bool delta = ep.w < 0.0f;
+        float De = delta ? rho_se * lv.x : rho_se * lv.x / (rho_se + ep.w);
+        float Dp = rho_sd * lv.y / (rho_sd + dp.w);
+        Dterm = sig_s * (De + Dp);
+    }
+    float Wt = w_s * A;
+    int32_t r = row_ok ? m2r[m] : 0;
+    int32_t cl = (valid && sj >= 0) ? m2r[sj] : (int32_t)n;
+    float scale = 1.0f;
+    if (WTraits<WT>::id != PG_W_F32) {
+        float mx = Wt;
+#pragma unroll
+        for (int o = KP / 2; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        scale = mx > 0.0f ? mx : 1.0f;
+    }
+    if (row_ok) {
+        W[(int64_t)r * KP + j] = to_w<WT>(WTraits<WT>::id == PG_W_F32 ? Wt : Wt / scale);
+        col[(int64_t)r * KP + j] = cl;
+        if (j == 0) {
+            b[r] = w_s * c;
+            if (WTraits<WT>::id != PG_W_F32) rscale[r] = scale;
+            c_m[m] = c;
+            D_m[m] = Dterm;
+            int32_t ci = m2c[m];
+            if (c_out) c_out[ci] = c;
+            if (D_out) D_out[ci] = Dterm;
+        }
+    }
+    // edge updates per sweep: real entries of rows that have a predecessor
+    bool counted = row_ok && valid && sj >= 0 && r < n_active;
+    unsigned cnt = __popc(__ballot_sync(0xffffffffu, counted));
+    if (lane == 0 && cnt) atomicAdd(nnz_counter, (unsigned long long)cnt);
+}
+
+template <int KP, typename WT>
+static pg_status launch_agg(pg_graph *g, float *c_out, float *D_out, unsigned long long *cnt, cudaStream_t s) {
+    int64_t threads = g->n * KP;
+    aggregate_kernel<KP, WT><<<pg_blocks(threads, 256), 256, 0, s>>>(
+        g->nbr, g->OG, g->DP, g->EP, g->LV, g->succ_m, g->m2r, g->m2c, g->n, g->n_active, (WT *)g->W, g->rscale,
+        g->col, g->b, g->c_m, g->D_m, c_out, D_out, cnt);
+    PG_LAUNCH_CHECK();
+    return PG_OK;
+}
+
+template <typename WT>
+static pg_status launch_agg_k(pg_graph *g, float *c_out, float *D_out, unsigned long long *cnt, cudaStream_t s) {
+    switch (g->kp) {
+        case 4: return launch_agg<4, WT>(g, c_out, D_out, cnt, s);
+        case 8: return launch_agg<8, WT>(g, c_out, D_out, cnt, s);
+        case 16: return launch_agg<16, WT>(g, c_out, D_out, cnt, s);
+        case 32: return launch_agg<32, WT>(g, c_out, D_out, cnt, s);
+        default: return PG_ERR_UNSUPPORTED;
+    }
+}
+
+static bool verts_ok(const pg_vertices *v) {
+    return v->ox && v->oy && v->oz && v->dx && v->dy && v->dz && v->ex && v->ey && v->ez && v->g && v->sigma_s &&
+           v->w_prop && v->Le && v->pe_e && v->Lph && v->pe_ph && v->e_delta && v->succ;
+}
+
+extern "C" pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype wdtype, float *c, float *D,
+                                  pg_stream_t stream) {
+    if (!g) return PG_ERR_INVALID_ARG;
+    if (wdtype != PG_W_F32 && wdtype != PG_W_BF16 && wdtype != PG_W_F16) return PG_ERR_INVALID_ARG;
+    if (g->n > 0 && (!v || !verts_ok(v))) return PG_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->stream = s;
+    const int64_t n = g->n;
+    const size_t kp = (size_t)g->kp;
+    // (re)allocate the aggregation buffers
+    size_t wb_old = pg_wbytes(g->wdtype);
+    pg_free(g, (void **)&g->W, wb_old * n * kp);
+    pg_free(g, (void **)&g->t_W, wb_old * (size_t)g->nnz_t);
+    pg_free(g, (void **)&g->t_row, 4 * (size_t)g->nnz_t);
+    pg_free(g, (void **)&g->t_ptr, 4 * (size_t)(n + 1));
+    g->nnz_t = 0;
+    g->aggregated = 0;
+    g->hist_iters = -1;
+    g->wdtype = wdtype;
+    pg_status st = PG_OK;
+#define A(ptr, bytes) \
+    if (st == PG_OK && !(ptr)) st = pg_alloc(g, (void **)&(ptr), (bytes), s)
+    A(g->m2r, 4 * (size_t)n);
+    A(g->r2m, 4 * (size_t)n);
+    A(g->OG, 16 * (size_t)n);
+    A(g->DP, 16 * (size_t)n);
+    A(g->EP, 16 * (size_t)n);
+    A(g->LV, 16 * (size_t)n);
+    A(g->succ_m, 4 * (size_t)n);
+    A(g->W, pg_wbytes(wdtype) * n * kp);
+    A(g->rscale, 4 * (size_t)n);
+    A(g->col, 4 * n * kp);
+    A(g->b, 4 * (size_t)(n + 1));
+    A(g->c_m, 4 * (size_t)n);
+    A(g->D_m, 4 * (size_t)n);
+#undef A
+    if (st != PG_OK) return st;
+    if (n == 0) {
+        g->aggregated = 1;
+        g->n_active = 0;
+        g->nnz_swept = 0;
+        return PG_OK;
+    }
+    int32_t *predcnt = nullptr, *act = nullptr, *d_nact = nullptr;
+    unsigned long long *d_cnt = nullptr;
+    st = pg_alloc(nullptr, (void **)&predcnt, 4 * (size_t)n, s);
+    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&act, 4 * (size_t)n, s);
+    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&d_nact, 16, s);
+    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&d_cnt, 16, s);
+    if (st == PG_OK && (cudaMemsetAsync(predcnt, 0, 4 * (size_t)n, s) != cudaSuccess ||
+                        cudaMemsetAsync(d_cnt, 0, 16, s) != cudaSuccess ||
+                        cudaMemsetAsync(g->flags, 0, 16, s) != cudaSuccess))
+        st = PG_ERR_CUDA;
+    if (st == PG_OK) {
+        pack_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(*v, n, g->c2m, g->OG, g->DP, g->EP, g->LV, g->succ_m, predcnt,
+                                                      g->flags);
+        active_flag_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(predcnt, n, act);
+        if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+    }
+    if (st == PG_OK) st = pg_scan_exclusive(g, act, n, d_nact, s);
+    int32_t h_nact = 0;
+    if (st == PG_OK) {
+        row_order_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(predcnt, act, d_nact, n, g->m2r, g->r2m);
+        if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+    }
+    if (st == PG_OK && (cudaMemcpyAsync(&h_nact, d_nact, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess))
+        st = PG_ERR_CUDA;
+    int32_t hflags = 0;
+    if (st == PG_OK && (cudaMemcpyAsync(&hflags, g->flags, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess))
+        st = PG_ERR_CUDA;
+    if (st == PG_OK && (hflags & PG_FLAG_NONFINITE)) st = PG_ERR_NONFINITE;
+    if (st == PG_OK && hflags) st = PG_ERR_INVALID_ARG;
+    if (st == PG_OK) {
+        g->n_active = h_nact;
+        if (cudaMemsetAsync(g->b + n, 0, 4, s) != cudaSuccess) st = PG_ERR_CUDA;
+    }
+    if (st == PG_OK) {
+        switch (wdtype) {
+            case PG_W_F32: st = launch_agg_k<float>(g, c, D, d_cnt, s); break;
+            case PG_W_BF16: st = launch_agg_k<__nv_bfloat16>(g, c, D, d_cnt, s); break;
+            case PG_W_F16: st = launch_agg_k<__half>(g, c, D, d_cnt, s); break;
+        }
+    }
+    unsigned long long h_cnt = 0;
+    if (st == PG_OK && (cudaMemcpyAsync(&h_cnt, d_cnt, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess))
+        st = PG_ERR_CUDA;
+    if (predcnt) cudaFreeAsync(predcnt, s);
+    if (act) cudaFreeAsync(act, s);
+    if (d_nact) cudaFreeAsync(d_nact, s);
+    if (d_cnt) cudaFreeAsync(d_cnt, s);
+    if (st != PG_OK) {
+        (void)cudaGetLastError();
+        return st;
+    }
+    g->nnz_swept = (int64_t)h_cnt;
+    g->aggregated = 1;
+    return PG_OK;
+}

@@ -1,0 +1,384 @@
+// Graph build: neighbour edges E_N of the path graph (Section 3.1).
+//
+// Vertices are quantised to 21-bit integer coordinates, bucketed into a
+// uniform grid of 2^L cells per axis whose cells are numbered in Morton
+// order, and stably sorted by cell (so a cell is a contiguous range of the
+// sorted "Morton order" m, and spatially close vertices are close in m).
+// Each query then scans rings of cells around its own and keeps its k-1
+// nearest others in registers, ordered by (squared integer distance, caller
+// index), until the k-1-th distance is provably below any unscanned cell.
+#include <stdio.h>
+#include <stdlib.h>
+
+#include "pg_internal.cuh"
+
+__global__ void quantize_kernel(const float *__restrict__ px, const float *__restrict__ py,
+                                const float *__restrict__ pz, int64_t n, float lo0, float lo1, float lo2,
+                                float scale, int level, uint32_t *__restrict__ cellkey, int32_t *__restrict__ idx,
+                                uint64_t *__restrict__ qpk_c, int32_t *__restrict__ flags) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    float p[3] = {px[v], py[v], pz[v]};
+    float lo[3] = {lo0, lo1, lo2};
+    uint32_t q[3];
+    bool finite = true;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        finite &= isfinite(p[a]);
+        // float32 round-to-nearest steps, never contracted into an FMA
+        float t = __fmul_rn(__fsub_rn(p[a], lo[a]), scale);
+        float f = floorf(t);
+        int32_t qi;
+        if (!(f > 0.0f)) qi = 0;                       // negative, zero or NaN
+        else if (f >= (float)PG_QMASK) qi = (int32_t)PG_QMASK;
+        else qi = (int32_t)f;
+        q[a] = (uint32_t)qi;
+    }
+    if (!finite) atomicOr(flags, PG_FLAG_NONFINITE);
+    int sh = PG_QBITS - level;
+    cellkey[v] = morton3(q[0] >> sh, q[1] >> sh, q[2] >> sh);
+    idx[v] = (int32_t)v;
+    qpk_c[v] = (uint64_t)q[0] | ((uint64_t)q[1] << 21) | ((uint64_t)q[2] << 42);
+}
+
+__global__ void permute_build_kernel(const int32_t *__restrict__ m2c, const uint64_t *__restrict__ qpk_c,
+                                     int64_t n, uint64_t *__restrict__ qpk, int32_t *__restrict__ c2m) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    int32_t c = m2c[m];
+    qpk[m] = qpk_c[c];
+    c2m[c] = (int32_t)m;
+}
+
+__global__ void cell_count_kernel(const uint32_t *__restrict__ sorted_keys, int64_t n, int32_t *__restrict__ counts) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    atomicAdd(&counts[sorted_keys[m]], 1);
+}
+
+// (d2, id) lexicographic order
+__device__ __forceinline__ bool knn_less(int64_t da, int32_t ia, int64_t db, int32_t ib) {
+    return da < db || (da == db && ia < ib);
+}
+
+template <int KP>
+__global__ void __launch_bounds__(128) knn_kernel(const uint64_t *__restrict__ qpk, const int32_t *__restrict__ cell_start,
+                                                  const int32_t *__restrict__ m2c, const int32_t *__restrict__ c2m,
+                                                  int64_t n, int k, int level, int64_t r2_max,
+                                                  int32_t *__restrict__ nbr) {
+    constexpr int M = KP - 1;
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const uint64_t qq = qpk[m];
+    const int32_t qx = (int32_t)(qq & PG_QMASK), qy = (int32_t)((qq >> 21) & PG_QMASK),
+                  qz = (int32_t)((qq >> 42) & PG_QMASK);
+    const int sh = PG_QBITS - level;
+    const int G = 1 << level;
+    const int64_t cs = (int64_t)1 << sh;
+    const int cx = qx >> sh, cy = qy >> sh, cz = qz >> sh;
+    const int km1 = k - 1;
+
+    // Ascending list of M slots. The lowest M - (k-1) slots hold a sentinel
+    // below every real entry, so the k-1 real entries occupy the top slots
+    // and the current worst one is always slot M-1 (constant register index).
+    const int pad = M - km1;
+    int64_t bd[M > 0 ? M : 1];
+    int32_t bi[M > 0 ? M : 1];
+#pragma unroll
+    for (int i = 0; i < M; i++) {
+        bd[i] = i < pad ? (int64_t)-1 : INT64_MAX;
+        bi[i] = i < pad ? -1 : INT32_MAX;
+    }
+    int64_t worst_d = INT64_MAX;
+    int32_t worst_i = INT32_MAX;
+    int found = 0;
+
+    if (km1 > 0) {
+        for (int r = 0;; r++) {
+            for (int dz = -r; dz <= r; dz++) {
+                int z = cz + dz;
+                if (z < 0 || z >= G) continue;
+                for (int dy = -r; dy <= r; dy++) {
+                    int y = cy + dy;
+                    if (y < 0 || y >= G) continue;
+                    bool edge = (dz == -r || dz == r || dy == -r || dy == r);
+                    int step = edge ? 1 : (2 * r > 0 ? 2 * r : 1);
+                    for (int dx = -r; dx <= r; dx += step) {
+                        int x = cx + dx;
+                        if (x < 0 || x >= G) continue;
+                        uint32_t cell = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
+                        int32_t p0 = cell_start[cell], p1 = cell_start[cell + 1];
+                        for (int32_t p = p0; p < p1; p++) {
+                            if (p == m) continue;
+                            uint64_t cq = qpk[p];
+                            int32_t ex = (int32_t)(cq & PG_QMASK) - qx;
+                            int32_t ey = (int32_t)((cq >> 21) & PG_QMASK) - qy;
+                            int32_t ez = (int32_t)((cq >> 42) & PG_QMASK) - qz;
+                            int64_t d2 = (int64_t)ex * ex + (int64_t)ey * ey + (int64_t)ez * ez;
+                            if (d2 > worst_d) continue;
+                            if (r2_max >= 0 && d2 > r2_max) continue;
+                            int32_t id = m2c[p];
+                            if (!knn_less(d2, id, worst_d, worst_i)) continue;
+                            // insert into the sorted list, shifting larger entries up
+#pragma unroll
+                            for (int i = M - 1; i > 0; --i) {
+                                if (knn_less(d2, id, bd[i], bi[i])) {
+                                    if (knn_less(d2, id, bd[i - 1], bi[i - 1])) {
+                                        bd[i] = bd[i - 1];
+                                        bi[i] = bi[i - 1];
+                                    } else {
+                                        bd[i] = d2;
+                                        bi[i] = id;
+                                    }
+                                }
+                            }
+                            if (knn_less(d2, id, bd[0], bi[0])) {
+                                bd[0] = d2;
+                                bi[0] = id;
+                            }
+                            found++;
+                            worst_d = bd[M - 1];
+                            worst_i = bi[M - 1];
+                        }
+                    }
+                }
+            }
+            // lower bound on the distance to any vertex outside the scanned
+            // block of cells [c - r, c + r]^3
+            int64_t bnd = INT64_MAX;
+            {
+                int c[3] = {cx, cy, cz};
+                int32_t q[3] = {qx, qy, qz};
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    int lo_c = c[a] - r, hi_c = c[a] + r;
+                    if (lo_c > 0) {
+                        int64_t dlo = (int64_t)q[a] - (int64_t)lo_c * cs + 1;
+                        bnd = dlo < bnd ? dlo : bnd;
+                    }
+                    if (hi_c < G - 1) {
+                        int64_t dhi = (int64_t)(hi_c + 1) * cs - q[a];
+                        bnd = dhi < bnd ? dhi : bnd;
+                    }
+                }
+            }
+            if (bnd == INT64_MAX) break;                       // whole grid scanned
+            int64_t bnd2 = bnd * bnd;
+            if (found >= km1 && worst_d < bnd2) break;          // nothing outside can enter
+            if (r2_max >= 0 && bnd2 > r2_max) break;            // nothing outside is in range
+        }
+    }
+    int32_t *row = nbr + m * KP;
+    row[0] = (int32_t)m;
+#pragma unroll
+    for (int i = 0; i < M; i++) {
+        int pos = i - pad; // rank among the k-1 others
+        if (pos >= 0) row[1 + pos] = bi[i] != INT32_MAX ? c2m[bi[i]] : -1;
+    }
+    for (int pos = km1; pos < M; pos++) row[1 + pos] = -1;
+}
+
+template <int KP>
+static pg_status launch_knn_t(pg_graph *g, cudaStream_t s) {
+    knn_kernel<KP><<<pg_blocks(g->n, 128), 128, 0, s>>>(g->qpk, g->cell_start, g->m2c, g->c2m, g->n, g->k, g->level,
+                                                        g->r2_max, g->nbr);
+    PG_LAUNCH_CHECK();
+    return PG_OK;
+}
+
+pg_status pg_launch_knn(pg_graph *g, cudaStream_t s) {
+    switch (g->kp) {
+        case 4: return launch_knn_t<4>(g, s);
+        case 8: return launch_knn_t<8>(g, s);
+        case 16: return launch_knn_t<16>(g, s);
+        case 32: return launch_knn_t<32>(g, s);
+        default: return PG_ERR_UNSUPPORTED;
+    }
+}
+
+static int auto_level(int64_t n, int k) {
+    // about four vertices per cell over the whole box
+    double cells = (double)n * 4.0 / (double)(k > 0 ? k : 1);
+    int L = (int)(log2(cells > 1.0 ? cells : 1.0) / 3.0 + 0.5);
+    if (L < 1) L = 1;
+    if (L > 10) L = 10;
+    return L;
+}
+
+static pg_status graph_free_all(pg_graph *g);
+
+extern "C" pg_status pg_build_graph(const pg_vertices *v, int64_t n, const pg_build_params *p, pg_stream_t stream,
+                                    pg_graph **out) {
+    if (!out || !p) return PG_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 0 || n >= INT32_MAX) return PG_ERR_INVALID_ARG;
+    if (p->k < 1 || p->k > PG_MAX_K) return PG_ERR_UNSUPPORTED;
+    if (p->grid_level < 0 || p->grid_level > 10) return PG_ERR_UNSUPPORTED;
+    if (n > 0 && (!v || !v->px || !v->py || !v->pz)) return PG_ERR_INVALID_ARG;
+    float span = 0.0f;
+    for (int a = 0; a < 3; a++) {
+        if (!isfinite(p->bbox_lo[a]) || !isfinite(p->bbox_hi[a])) return PG_ERR_INVALID_ARG;
+        float e = p->bbox_hi[a] - p->bbox_lo[a];
+        if (!(e > 0.0f)) return PG_ERR_INVALID_ARG;
+        span = e > span ? e : span;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    pg_graph *g = new pg_graph();
+    g->stream = s;
+    g->n = n;
+    g->k = p->k;
+    g->kp = p->k <= 4 ? 4 : p->k <= 8 ? 8 : p->k <= 16 ? 16 : 32;
+    g->level = p->grid_level ? p->grid_level : auto_level(n, p->k);
+    for (int a = 0; a < 3; a++) g->lo[a] = p->bbox_lo[a];
+    {
+        volatile float two21 = (float)(1u << PG_QBITS);
+        volatile float sp = span;
+        g->scale = two21 / sp; // float32 division, as the quantisation step defines it
+    }
+    g->r2_max = p->r2_max;
+
+    pg_status st = PG_OK;
+    int64_t ncells = (int64_t)1 << (3 * g->level);
+    uint32_t *keys = nullptr;
+    uint64_t *qpk_c = nullptr;
+#define A(ptr, bytes) \
+    if (st == PG_OK) st = pg_alloc(g, (void **)&(ptr), (bytes), s)
+    A(g->flags, sizeof(int32_t) * 4);
+    A(g->m2c, sizeof(int32_t) * n);
+    A(g->c2m, sizeof(int32_t) * n);
+    A(g->qpk, sizeof(uint64_t) * n);
+    A(g->cell_start, sizeof(int32_t) * (ncells + 1));
+    A(g->nbr, sizeof(int32_t) * n * g->kp);
+    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&keys, sizeof(uint32_t) * (n > 0 ? n : 1), s);
+    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&qpk_c, sizeof(uint64_t) * (n > 0 ? n : 1), s);
+#undef A
+    if (st == PG_OK) {
+        if (cudaMemsetAsync(g->flags, 0, sizeof(int32_t) * 4, s) != cudaSuccess) st = PG_ERR_CUDA;
+    }
+    if (st == PG_OK && n > 0) {
+        quantize_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(v->px, v->py, v->pz, n, g->lo[0], g->lo[1], g->lo[2],
+                                                          g->scale, g->level, keys, g->m2c, qpk_c, g->flags);
+        if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+        if (st == PG_OK) st = pg_radix_sort(g, keys, g->m2c, n, 3 * g->level, s);
+        if (st == PG_OK) {
+            permute_build_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(g->m2c, qpk_c, n, g->qpk, g->c2m);
+            if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+        }
+        if (st == PG_OK && cudaMemsetAsync(g->cell_start, 0, sizeof(int32_t) * (ncells + 1), s) != cudaSuccess)
+            st = PG_ERR_CUDA;
+        if (st == PG_OK) {
+            cell_count_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(keys, n, g->cell_start);
+            if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+        }
+        if (st == PG_OK) st = pg_scan_exclusive(g, g->cell_start, ncells + 1, nullptr, s);
+        if (st == PG_OK) st = pg_launch_knn(g, s);
+    }
+    if (keys) cudaFreeAsync(keys, s);
+    if (qpk_c) cudaFreeAsync(qpk_c, s);
+    int32_t hflags = 0;
+    if (st == PG_OK) {
+        if (cudaMemcpyAsync(&hflags, g->flags, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            st = PG_ERR_CUDA;
+    }
+    if (st == PG_OK && (hflags & PG_FLAG_NONFINITE)) st = PG_ERR_NONFINITE;
+    if (st != PG_OK) {
+        (void)cudaGetLastError();
+        graph_free_all(g);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return PG_OK;
+}
+
+__global__ void neighbors_out_kernel(const int32_t *__restrict__ nbr, const int32_t *__restrict__ m2c, int64_t n,
+                                     int kp, int k, int32_t *__restrict__ out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * k) return;
+    int64_t m = t / k;
+    int i = (int)(t - m * k);
+    int32_t j = nbr[m * kp + i];
+    out[(int64_t)m2c[m] * k + i] = j >= 0 ? m2c[j] : -1;
+}
+
+extern "C" pg_status pg_graph_neighbors(const pg_graph *g, int32_t *nbr, pg_stream_t stream) {
+    if (!g || (!nbr && g->n > 0)) return PG_ERR_INVALID_ARG;
+    if (g->n == 0) return PG_OK;
+    neighbors_out_kernel<<<pg_blocks(g->n * g->k, 256), 256, 0, (cudaStream_t)stream>>>(g->nbr, g->m2c, g->n, g->kp,
+                                                                                         g->k, nbr);
+    PG_LAUNCH_CHECK();
+    return PG_OK;
+}
+
+extern "C" pg_status pg_graph_get_info(const pg_graph *g, pg_graph_info *info) {
+    if (!g || !info) return PG_ERR_INVALID_ARG;
+    info->n = g->n;
+    info->k = g->k;
+    info->row_width = g->kp;
+    info->grid_level = g->level;
+    info->aggregated = g->aggregated;
+    info->n_active = g->n_active;
+    info->nnz_swept = g->nnz_swept;
+    info->device_bytes = g->bytes;
+    info->weight_dtype = (int32_t)g->wdtype;
+    info->history_iters = g->hist_iters;
+    return PG_OK;
+}
+
+static pg_status graph_free_all(pg_graph *g) {
+    size_t n = (size_t)g->n, kp = (size_t)g->kp;
+    size_t ncells = ((size_t)1 << (3 * g->level)) + 1;
+    size_t wb = pg_wbytes(g->wdtype);
+    pg_free(g, (void **)&g->flags, sizeof(int32_t) * 4);
+    pg_free(g, (void **)&g->m2c, 4 * n);
+    pg_free(g, (void **)&g->c2m, 4 * n);
+    pg_free(g, (void **)&g->qpk, 8 * n);
+    pg_free(g, (void **)&g->cell_start, 4 * ncells);
+    pg_free(g, (void **)&g->nbr, 4 * n * kp);
+    pg_free(g, (void **)&g->m2r, 4 * n);
+    pg_free(g, (void **)&g->r2m, 4 * n);
+    pg_free(g, (void **)&g->OG, 16 * n);
+    pg_free(g, (void **)&g->DP, 16 * n);
+    pg_free(g, (void **)&g->EP, 16 * n);
+    pg_free(g, (void **)&g->LV, 16 * n);
+    pg_free(g, (void **)&g->succ_m, 4 * n);
+    pg_free(g, (void **)&g->W, wb * n * kp);
+    pg_free(g, (void **)&g->rscale, 4 * n);
+    pg_free(g, (void **)&g->col, 4 * n * kp);
+    pg_free(g, (void **)&g->b, 4 * (n + 1));
+    pg_free(g, (void **)&g->c_m, 4 * n);
+    pg_free(g, (void **)&g->D_m, 4 * n);
+    pg_free(g, (void **)&g->ybuf[0], 4 * (n + 1));
+    pg_free(g, (void **)&g->ybuf[1], 4 * (n + 1));
+    pg_free(g, (void **)&g->hist, 4 * (n + 1) * (size_t)(g->hist_cap + 1));
+    pg_free(g, (void **)&g->d_resid, 8 * (size_t)g->resid_cap);
+    pg_free(g, (void **)&g->d_ctrl, 16);
+    pg_free(g, (void **)&g->d_partials, 16 * (size_t)g->partials_cap);
+    pg_free(g, (void **)&g->t_ptr, 4 * (n + 1));
+    pg_free(g, (void **)&g->t_row, 4 * (size_t)g->nnz_t);
+    pg_free(g, (void **)&g->t_W, wb * (size_t)g->nnz_t);
+    return PG_OK;
+}
+
+extern "C" void pg_graph_destroy(pg_graph *g) {
+    if (!g) return;
+    graph_free_all(g);
+    cudaStreamSynchronize(g->stream);
+    (void)cudaGetLastError();
+    delete g;
+}
+
+extern "C" const char *pg_status_string(pg_status s) {
+    switch (s) {
+        case PG_OK: return "ok";
+        case PG_ERR_INVALID_ARG: return "invalid argument";
+        case PG_ERR_OOM: return "out of device memory";
+        case PG_ERR_CUDA: return "CUDA error";
+        case PG_ERR_NONFINITE: return "non-finite input";
+        case PG_ERR_TIMEOUT: return "device wait timed out";
+        case PG_ERR_UNSUPPORTED: return "unsupported parameter";
+        case PG_ERR_STATE: return "invalid call order";
+        default: return "unknown status";
+    }
+}

@@ -1,0 +1,180 @@
+// Internal definitions shared by the libpg translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pg.h"
+
+#define PG_QBITS 21
+#define PG_QMASK ((1u << PG_QBITS) - 1u)
+#define PG_MAX_K 32
+
+// Bit flags raised by validation kernels (read back at synchronising calls).
+enum : int {
+    PG_FLAG_NONFINITE = 1,
+    PG_FLAG_BAD_INDEX = 2,
+    PG_FLAG_TWO_PREDS = 4,
+    PG_FLAG_BAD_RANGE = 8,
+};
+
+struct pg_graph {
+    int64_t n = 0;
+    int32_t k = 0;
+    int32_t kp = 0;        // stored row width: 4, 8, 16 or 32
+    int32_t level = 0;     // hash-grid level L: 2^L cells per axis
+    float lo[3] = {0, 0, 0};
+    float scale = 0;       // 2^21 / max extent, float32
+    int64_t r2_max = -1;
+    cudaStream_t stream = nullptr; // stream of the most recent call (frees go here)
+    int64_t bytes = 0;
+
+    // ---- graph build (Morton order m) ----
+    int32_t *m2c = nullptr;        // m -> caller index
+    int32_t *c2m = nullptr;        // caller -> m
+    uint64_t *qpk = nullptr;       // packed quantised coordinates (x | y<<21 | z<<42), m order
+    int32_t *cell_start = nullptr; // 8^L + 1 offsets into m order
+    int32_t *nbr = nullptr;        // [n][kp], m-space neighbour ids, -1 padded; slot 0 = self
+
+    // ---- aggregation ----
+    int aggregated = 0;
+    pg_wdtype wdtype = PG_W_F32;
+    int64_t n_active = 0;          // rows with a predecessor: sweep rows [0, n_active)
+    int64_t nnz_swept = 0;
+    int32_t *m2r = nullptr;        // m -> sweep row r
+    int32_t *r2m = nullptr;        // r -> m
+    float4 *OG = nullptr;          // (o, g)           m order
+    float4 *DP = nullptr;          // (d, pe_ph)       m order
+    float4 *EP = nullptr;          // (e, pe_e or -1 for a delta light) m order
+    float4 *LV = nullptr;          // (Le, Lph, sigma_s, w_prop) m order
+    int32_t *succ_m = nullptr;     // m-space successor or -1
+    void *W = nullptr;             // [n][kp] weights (tau/p_t)_s * A+_{s,j}, sweep-row order
+    float *rscale = nullptr;       // [n] per-row scale (16-bit weights)
+    int32_t *col = nullptr;        // [n][kp] sweep-row index of succ(j); n = zero slot
+    float *b = nullptr;            // [n] (tau/p_t)_s * c_s, sweep-row order
+    float *c_m = nullptr;          // [n] c_s, m order
+    float *D_m = nullptr;          // [n] D_s, m order
+
+    // ---- propagation ----
+    float *ybuf[2] = {nullptr, nullptr}; // (n+1) floats each; [n] stays 0
+    float *hist = nullptr;               // (hist_iters+1) x (n+1), sweep-row order
+    int32_t hist_iters = -1;
+    int32_t hist_cap = -1;
+    double *d_resid = nullptr;           // residual per sweep
+    int32_t resid_cap = 0;
+    int32_t *d_ctrl = nullptr;           // [0] iters_done, [1] stop flag, [2] block counter
+    double *d_partials = nullptr;        // per-block residual partials
+    int32_t partials_cap = 0;
+
+    // ---- adjoint (lazily built) ----
+    int32_t *t_ptr = nullptr;     // [n+1] transposed row pointers (by column)
+    int32_t *t_row = nullptr;     // [nnz_t] source row of each transposed entry
+    void *t_W = nullptr;          // [nnz_t] weight in transposed order (same dtype)
+    int64_t nnz_t = 0;
+    int32_t *flags = nullptr;     // validation flags (device)
+};
+
+// ------------------------------------------------------------------ helpers
+#define PG_TRY(expr)                                   \
+    do {                                               \
+        pg_status _s = (expr);                         \
+        if (_s != PG_OK) return _s;                    \
+    } while (0)
+
+#define PG_CUDA(expr)                                  \
+    do {                                               \
+        cudaError_t _e = (expr);                       \
+        if (_e != cudaSuccess) {                       \
+            (void)cudaGetLastError();                  \
+            return _e == cudaErrorMemoryAllocation ? PG_ERR_OOM : PG_ERR_CUDA; \
+        }                                              \
+    } while (0)
+
+#define PG_LAUNCH_CHECK() PG_CUDA(cudaGetLastError())
+
+static inline int pg_blocks(int64_t work, int threads) {
+    int64_t b = (work + threads - 1) / threads;
+    return (int)(b < 1 ? 1 : b);
+}
+
+pg_status pg_alloc(pg_graph *g, void **p, size_t bytes, cudaStream_t s);
+void pg_free(pg_graph *g, void **p, size_t bytes);
+int pg_num_sms();
+
+// Stable LSD radix sort of (key, value) pairs by key bits [0, nbits).
+pg_status pg_radix_sort(pg_graph *g, uint32_t *keys, int32_t *vals, int64_t n, int nbits, cudaStream_t s);
+// Exclusive prefix sum of n int32 counts (in place); total written to *d_total if non-NULL.
+pg_status pg_scan_exclusive(pg_graph *g, int32_t *data, int64_t n, int32_t *d_total, cudaStream_t s);
+
+// ------------------------------------------------------------------ device math
+// Henyey-Greenstein rho(o, d) with mu = -o.d, written as
+//   (1-g^2)/(4 pi) * den^(-3/2),  den = (1-g)^2 + 2 g (1 + o.d)
+// (equal to 1 + g^2 - 2 g mu); this form keeps the forward peak accurate in
+// float32. hgc holds (C = (1-g^2)/(4 pi), (1-g)^2, 2g) for the strategy.
+struct HGc {
+    float C, a, b2;
+};
+__device__ __forceinline__ HGc hg_consts(float g) {
+    const float inv4pi = 0.0795774715459476679f;
+    HGc h;
+    h.C = (1.0f - g * g) * inv4pi;
+    float omg = 1.0f - g;
+    h.a = omg * omg;
+    h.b2 = 2.0f * g;
+    return h;
+}
+__device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, float by, float bz) {
+    return fmaf(az, bz, fmaf(ay, by, ax * bx));
+}
+__device__ __forceinline__ float hg_eval(const HGc &h, float od) {
+    float den = fmaf(h.b2, 1.0f + od, h.a);
+    float r = rsqrtf(den);
+    return h.C * r * r * r;
+}
+// d rho / d g = rho * ( -2g/(1-g^2) - 3 (g - mu) / den ),  mu = -o.d
+__device__ __forceinline__ float hg_eval_dg(float g, float od, float *rho_out) {
+    const float inv4pi = 0.0795774715459476679f;
+    float omg = 1.0f - g;
+    float den = fmaf(2.0f * g, 1.0f + od, omg * omg);
+    float r = rsqrtf(den);
+    float rho = (1.0f - g * g) * inv4pi * r * r * r;
+    *rho_out = rho;
+    // -2g/(4pi) den^-3/2 - 1.5 (1-g^2)/(4pi) (2g + 2 od) den^-5/2
+    float r3 = r * r * r;
+    return -2.0f * g * inv4pi * r3 - 3.0f * (1.0f - g * g) * inv4pi * (g + od) * r3 * r * r;
+}
+
+__device__ __forceinline__ uint32_t part1by2(uint32_t x) {
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+__device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+    return part1by2(x) | (part1by2(y) << 1) | (part1by2(z) << 2);
+}
+
+template <typename T>
+struct WTraits;
+template <>
+struct WTraits<float> {
+    static constexpr pg_wdtype id = PG_W_F32;
+};
+template <>
+struct WTraits<__nv_bfloat16> {
+    static constexpr pg_wdtype id = PG_W_BF16;
+};
+template <>
+struct WTraits<__half> {
+    static constexpr pg_wdtype id = PG_W_F16;
+};
+
+static inline size_t pg_wbytes(pg_wdtype t) { return t == PG_W_F32 ? 4 : 2; }
+
+// Launchers implemented in the per-stage translation units.
+pg_status pg_launch_knn(pg_graph *g, cudaStream_t s);
+pg_status pg_launch_aggregate(pg_graph *g, float *c_out, float *D_out, cudaStream_t s);

@@ -1,0 +1,351 @@
+// Propagation (Eq. rte-mff with P from Eq. volume-propagation) and the
+// per-path output (Section 4, "Final output").
+//
+// One Jacobi sweep, in sweep-row order r over the rows that have a
+// predecessor:   y'_r = scale_r * sum_i W[r][i] * y[col[r][i]] + b_r
+// The matrix rows are streamed once per sweep (coalesced 16-byte loads,
+// evict-first so the gathered vector y stays in L2); KP/4 lanes share a row
+// and combine their four products with shuffles. The relative change of the
+// sweep is reduced in FP64 (per-block partials, then the last block), and a
+// sweep that finds the previous one converged returns at once.
+#include "pg_internal.cuh"
+
+template <typename WT>
+struct W4;
+template <>
+struct W4<float> {
+    static __device__ __forceinline__ float4 load(const float *p) { return __ldcs(reinterpret_cast<const float4 *>(p)); }
+};
+template <>
+struct W4<__nv_bfloat16> {
+    static __device__ __forceinline__ float4 load(const __nv_bfloat16 *p) {
+        uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
+        __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162 *>(&u.x), b = *reinterpret_cast<__nv_bfloat162 *>(&u.y);
+        float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+};
+template <>
+struct W4<__half> {
+    static __device__ __forceinline__ float4 load(const __half *p) {
+        uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
+        __half2 a = *reinterpret_cast<__half2 *>(&u.x), b = *reinterpret_cast<__half2 *>(&u.y);
+        float2 fa = __half22float2(a), fb = __half22float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+};
+
+template <typename WT>
+__device__ __forceinline__ float wdec(const WT *W, int64_t i);
+template <>
+__device__ __forceinline__ float wdec<float>(const float *W, int64_t i) { return W[i]; }
+template <>
+__device__ __forceinline__ float wdec<__nv_bfloat16>(const __nv_bfloat16 *W, int64_t i) { return __bfloat162float(W[i]); }
+template <>
+__device__ __forceinline__ float wdec<__half>(const __half *W, int64_t i) { return __half2float(W[i]); }
+
+static constexpr int SWEEP_THREADS = 256;
+
+// Sum (a, b) over the block in FP64; result valid in thread 0.
+__device__ __forceinline__ void block_sum2(double &a, double &b) {
+    __shared__ double sa[SWEEP_THREADS / 32], sb[SWEEP_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+        sa[wid] = a;
+        sb[wid] = b;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        a = lane < SWEEP_THREADS / 32 ? sa[lane] : 0.0;
+        b = lane < SWEEP_THREADS / 32 ? sb[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+    }
+}
+
+template <int KP, typename WT>
+__global__ void __launch_bounds__(SWEEP_THREADS) sweep_kernel(
+    const int32_t *__restrict__ col, const WT *__restrict__ W, const float *__restrict__ rscale,
+    const float *__restrict__ b, const float *__restrict__ yin, float *__restrict__ yout, int64_t n_active,
+    int32_t *__restrict__ ctrl, double2 *__restrict__ partials, double *__restrict__ resid, int t, double tol) {
+    if (*(volatile int32_t *)&ctrl[1]) return; // converged in an earlier sweep
+    constexpr int LPR = KP / 4;
+    const int lane = threadIdx.x & 31;
+    const int q = lane & (LPR - 1);
+    const int64_t total = n_active * LPR;
+    const int64_t total_w = (total + 31) & ~(int64_t)31; // whole warps iterate together
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    float rd = 0.0f, rn = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total_w; i += stride) {
+        const int64_t row = i / LPR;
+        const bool ok = i < total;
+        float acc = 0.0f;
+        if (ok) {
+            const int4 c4 = __ldcs(reinterpret_cast<const int4 *>(col + row * KP) + q);
+            const float4 w4 = W4<WT>::load(W + row * KP + q * 4);
+            acc = w4.x * __ldg(yin + c4.x);
+            acc = fmaf(w4.y, __ldg(yin + c4.y), acc);
+            acc = fmaf(w4.z, __ldg(yin + c4.z), acc);
+            acc = fmaf(w4.w, __ldg(yin + c4.w), acc);
+        }
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (ok && q == 0) {
+            const float s = WTraits<WT>::id == PG_W_F32 ? 1.0f : rscale[row];
+            const float yn = fmaf(acc, s, b[row]);
+            const float d = yn - yin[row];
+            yout[row] = yn;
+            rd = fmaf(d, d, rd);
+            rn = fmaf(yn, yn, rn);
+        }
+    }
+    double a = rd, bb = rn;
+    block_sum2(a, bb);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = make_double2(a, bb);
+        __threadfence();
+        last = atomicAdd(&ctrl[2], 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double sa = 0.0, sb = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        const volatile double *pv = reinterpret_cast<const volatile double *>(partials + i);
+        sa += pv[0];
+        sb += pv[1];
+    }
+    block_sum2(sa, sb);
+    if (threadIdx.x == 0) {
+        double r = sb > 0.0 ? sqrt(sa) / sqrt(sb) : 0.0;
+        resid[t - 1] = r;
+        ctrl[0] = t;
+        ctrl[2] = 0;
+        if (tol > 0.0 && r < tol) ctrl[1] = 1;
+    }
+}
+
+// y0[row of succ(v)] = L0[v]  (L+_v is the radiance that succ(v) sends back)
+__global__ void init_y_kernel(const float *__restrict__ L0, const int32_t *__restrict__ c2m,
+                              const int32_t *__restrict__ succ_m, const int32_t *__restrict__ m2r, int64_t n,
+                              float *__restrict__ y0) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int32_t s = succ_m[c2m[v]];
+    if (s >= 0) y0[m2r[s]] = L0[v];
+}
+
+__global__ void b_from_c_kernel(const float *__restrict__ c, const int32_t *__restrict__ c2m,
+                                const int32_t *__restrict__ m2r, const float4 *__restrict__ LV, int64_t n,
+                                float *__restrict__ b) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int32_t m = c2m[v];
+    b[m2r[m]] = LV[m].w * c[v];
+}
+
+// L[v] = y_T[row of succ(v)], 0 at the end of a path. The final iterate is
+// the one of the last sweep that ran (ctrl[0]); with a history it is slice
+// ctrl[0], otherwise ping-pong buffer ctrl[0] % 2.
+__global__ void finish_L_kernel(const int32_t *__restrict__ c2m, const int32_t *__restrict__ succ_m,
+                                const int32_t *__restrict__ m2r, int64_t n, const float *__restrict__ y_a,
+                                const float *__restrict__ y_b, const float *__restrict__ hist,
+                                const int32_t *__restrict__ ctrl, float *__restrict__ L) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int32_t it = ctrl[0];
+    const float *y = hist ? hist + (int64_t)it * (n + 1) : ((it & 1) ? y_b : y_a);
+    int32_t s = succ_m[c2m[v]];
+    L[v] = s >= 0 ? y[m2r[s]] : 0.0f;
+}
+
+template <int KP, typename WT>
+static pg_status launch_sweep(pg_graph *g, const float *b, const float *yin, float *yout, int t, double tol,
+                              int blocks, cudaStream_t s) {
+    sweep_kernel<KP, WT><<<blocks, SWEEP_THREADS, 0, s>>>(g->col, (const WT *)g->W, g->rscale, b, yin, yout,
+                                                          g->n_active, g->d_ctrl, (double2 *)g->d_partials,
+                                                          g->d_resid, t, tol);
+    PG_LAUNCH_CHECK();
+    return PG_OK;
+}
+
+template <typename WT>
+static pg_status launch_sweep_k(pg_graph *g, const float *b, const float *yin, float *yout, int t, double tol,
+                                int blocks, cudaStream_t s) {
+    switch (g->kp) {
+        case 4: return launch_sweep<4, WT>(g, b, yin, yout, t, tol, blocks, s);
+        case 8: return launch_sweep<8, WT>(g, b, yin, yout, t, tol, blocks, s);
+        case 16: return launch_sweep<16, WT>(g, b, yin, yout, t, tol, blocks, s);
+        case 32: return launch_sweep<32, WT>(g, b, yin, yout, t, tol, blocks, s);
+        default: return PG_ERR_UNSUPPORTED;
+    }
+}
+
+int pg_sweep_blocks(const pg_graph *g) {
+    int64_t lanes = g->n_active * (g->kp / 4);
+    int64_t need = (lanes + SWEEP_THREADS - 1) / SWEEP_THREADS;
+    int64_t cap = (int64_t)pg_num_sms() * 8; // 8 x 256 threads = 2048 per SM
+    int64_t bl = need < cap ? need : cap;
+    return (int)(bl < 1 ? 1 : bl);
+}
+
+extern "C" pg_status pg_propagate(pg_graph *g, const float *c, const float *L0, int32_t iters, double tol,
+                                  int32_t keep_history, float *L, double *residual, int32_t *iters_done,
+                                  pg_stream_t stream) {
+    if (!g || iters < 0) return PG_ERR_INVALID_ARG;
+    if (!g->aggregated) return PG_ERR_STATE;
+    if (!g->W) return PG_ERR_STATE;
+    const int64_t n = g->n;
+    if (n > 0 && (!L0 || !L)) return PG_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->stream = s;
+    pg_status st = PG_OK;
+    // buffers
+    if (!g->ybuf[0]) {
+        PG_TRY(pg_alloc(g, (void **)&g->ybuf[0], 4 * (size_t)(n + 1), s));
+        PG_TRY(pg_alloc(g, (void **)&g->ybuf[1], 4 * (size_t)(n + 1), s));
+        PG_CUDA(cudaMemsetAsync(g->ybuf[0], 0, 4 * (size_t)(n + 1), s));
+        PG_CUDA(cudaMemsetAsync(g->ybuf[1], 0, 4 * (size_t)(n + 1), s));
+    }
+    if (!g->d_ctrl) PG_TRY(pg_alloc(g, (void **)&g->d_ctrl, 16, s));
+    int blocks = pg_sweep_blocks(g);
+    if (g->partials_cap < blocks) {
+        pg_free(g, (void **)&g->d_partials, 16 * (size_t)g->partials_cap);
+        g->partials_cap = 0;
+        PG_TRY(pg_alloc(g, (void **)&g->d_partials, 16 * (size_t)blocks, s));
+        g->partials_cap = blocks;
+    }
+    int rcap = iters > 0 ? iters : 1;
+    if (g->resid_cap < rcap) {
+        pg_free(g, (void **)&g->d_resid, 8 * (size_t)g->resid_cap);
+        g->resid_cap = 0;
+        PG_TRY(pg_alloc(g, (void **)&g->d_resid, 8 * (size_t)rcap, s));
+        g->resid_cap = rcap;
+    }
+    if (keep_history && g->hist_cap < iters) {
+        pg_free(g, (void **)&g->hist, 4 * (size_t)(n + 1) * (size_t)(g->hist_cap + 1));
+        g->hist_cap = -1;
+        PG_TRY(pg_alloc(g, (void **)&g->hist, 4 * (size_t)(n + 1) * (size_t)(iters + 1), s));
+        PG_CUDA(cudaMemsetAsync(g->hist, 0, 4 * (size_t)(n + 1) * (size_t)(iters + 1), s));
+        g->hist_cap = iters;
+    }
+    g->hist_iters = -1;
+    PG_CUDA(cudaMemsetAsync(g->d_ctrl, 0, 16, s));
+    PG_CUDA(cudaMemsetAsync(g->d_resid, 0, 8 * (size_t)rcap, s));
+    if (n == 0) {
+        if (residual && iters > 0) for (int i = 0; i < iters; i++) residual[i] = 0.0;
+        if (iters_done) *iters_done = 0;
+        return PG_OK;
+    }
+    const float *b = g->b;
+    float *buser = nullptr;
+    if (c) {
+        PG_TRY(pg_alloc(nullptr, (void **)&buser, 4 * (size_t)(n + 1), s));
+        cudaMemsetAsync(buser, 0, 4 * (size_t)(n + 1), s);
+        b_from_c_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(c, g->c2m, g->m2r, g->LV, n, buser);
+        b = buser;
+    }
+    const int64_t stride = n + 1;
+    float *y0 = keep_history ? g->hist : g->ybuf[0];
+    init_y_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(L0, g->c2m, g->succ_m, g->m2r, n, y0);
+    if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+    for (int t = 1; t <= iters && st == PG_OK; t++) {
+        const float *yin = keep_history ? g->hist + (int64_t)(t - 1) * stride : g->ybuf[(t - 1) & 1];
+        float *yout = keep_history ? g->hist + (int64_t)t * stride : g->ybuf[t & 1];
+        switch (g->wdtype) {
+            case PG_W_F32: st = launch_sweep_k<float>(g, b, yin, yout, t, tol, blocks, s); break;
+            case PG_W_BF16: st = launch_sweep_k<__nv_bfloat16>(g, b, yin, yout, t, tol, blocks, s); break;
+            case PG_W_F16: st = launch_sweep_k<__half>(g, b, yin, yout, t, tol, blocks, s); break;
+        }
+    }
+    if (st == PG_OK) {
+        finish_L_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(g->c2m, g->succ_m, g->m2r, n, g->ybuf[0], g->ybuf[1],
+                                                          keep_history ? g->hist : nullptr, g->d_ctrl, L);
+        if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+    }
+    if (buser) cudaFreeAsync(buser, s);
+    if (st != PG_OK) return st;
+    if (keep_history) g->hist_iters = iters;
+    if (residual || iters_done) {
+        int32_t ctrl[4] = {0, 0, 0, 0};
+        PG_CUDA(cudaMemcpyAsync(ctrl, g->d_ctrl, 16, cudaMemcpyDeviceToHost, s));
+        if (residual && iters > 0)
+            PG_CUDA(cudaMemcpyAsync(residual, g->d_resid, 8 * (size_t)iters, cudaMemcpyDeviceToHost, s));
+        PG_CUDA(cudaStreamSynchronize(s));
+        if (iters_done) *iters_done = ctrl[0];
+        if (keep_history) g->hist_iters = ctrl[0];
+    }
+    return PG_OK;
+}
+
+// ------------------------------------------------------------------ gather
+template <typename WT>
+__global__ void gather_kernel(const int32_t *__restrict__ first, const float *__restrict__ bg,
+                              const float *__restrict__ L, const float *__restrict__ D,
+                              const int32_t *__restrict__ c2m, const int32_t *__restrict__ m2c,
+                              const int32_t *__restrict__ m2r, const int32_t *__restrict__ nbr,
+                              const WT *__restrict__ W, const float *__restrict__ rscale,
+                              const float4 *__restrict__ LV, int kp, int spp, int64_t npix, int64_t n,
+                              float *__restrict__ image) {
+    int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= npix) return;
+    float acc = 0.0f;
+    for (int sidx = 0; sidx < spp; sidx++) {
+        int64_t p = pix * spp + sidx;
+        float val = bg[p];
+        int32_t f = first[p];
+        if (f >= 0 && f < n) { // out-of-range entries are treated as -1
+            int32_t m = c2m[f];
+            int64_t r = m2r[m];
+            float sc = WTraits<WT>::id == PG_W_F32 ? 1.0f : rscale[r];
+            float sum = 0.0f;
+            for (int i = 0; i < kp; i++) {
+                int32_t j = nbr[(int64_t)m * kp + i];
+                if (j >= 0) sum = fmaf(wdec<WT>(W, r * kp + i), L[m2c[j]], sum);
+            }
+            val += fmaf(sum, sc, LV[m].w * D[f]);
+        }
+        acc += val;
+    }
+    image[pix] = acc / (float)spp;
+}
+
+extern "C" pg_status pg_gather(const pg_graph *g, const float *L, const float *D, const int32_t *first,
+                               const float *bg, int64_t n_paths, int32_t spp, int32_t width, int32_t height,
+                               float *image, pg_stream_t stream) {
+    if (!g || spp <= 0 || width < 0 || height < 0) return PG_ERR_INVALID_ARG;
+    if (n_paths != (int64_t)width * height * spp) return PG_ERR_INVALID_ARG;
+    if (!g->aggregated || !g->W) return PG_ERR_STATE;
+    int64_t npix = (int64_t)width * height;
+    if (npix == 0) return PG_OK;
+    if (!first || !bg || !image || (g->n > 0 && (!L || !D))) return PG_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (g->wdtype) {
+        case PG_W_F32:
+            gather_kernel<float><<<pg_blocks(npix, 128), 128, 0, s>>>(first, bg, L, D, g->c2m, g->m2c, g->m2r, g->nbr,
+                                                                     (const float *)g->W, g->rscale, g->LV, g->kp,
+                                                                     spp, npix, g->n, image);
+            break;
+        case PG_W_BF16:
+            gather_kernel<__nv_bfloat16><<<pg_blocks(npix, 128), 128, 0, s>>>(
+                first, bg, L, D, g->c2m, g->m2c, g->m2r, g->nbr, (const __nv_bfloat16 *)g->W, g->rscale, g->LV,
+                g->kp, spp, npix, g->n, image);
+            break;
+        case PG_W_F16:
+            gather_kernel<__half><<<pg_blocks(npix, 128), 128, 0, s>>>(first, bg, L, D, g->c2m, g->m2c, g->m2r,
+                                                                      g->nbr, (const __half *)g->W, g->rscale,
+                                                                      g->LV, g->kp, spp, npix, g->n, image);
+            break;
+    }
+    PG_LAUNCH_CHECK();
+    return PG_OK;
+}

@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bars (from the method's statement of the target): neighbour lists bit-exact;
+FP32 radiance within 1e-5 relative; 16-bit edge weights within 2e-3
+relative. The relative error of a field x against the oracle's x_o is
+max_i |x_i - x_o,i| / max(|x_o,i|, 1e-3 mean|x_o|).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import pgrec
+from pgrec import synthetic
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+W16_TOL = 2e-3
+
+
+def rel_err(got, ref):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    den = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).mean() + 1e-300)
+    return float((np.abs(got - ref) / den).max())
+
+
+@pytest.fixture(scope="module")
+def pg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2404_11894_gb300 as pg
+
+    return pg
+
+
+PARITY_SCENES = {
+    # the plain-method workload at full size
+    "cube": pgrec.CUBE_CONST,
+    # heterogeneous cloud (albedo 0.99, g 0.8, sun + sky) at a size the oracle runs in seconds
+    "cloud": pgrec.CLOUD128.with_(width=64, height=64, spp=4),
+    # dense forward-scattering medium with an area light + environment
+    "dense": pgrec.CLOUD256_DENSE.with_(grid_res=64, width=40, height=40, spp=2, iters=20),
+}
+
+
+class Run:
+    pass
+
+
+def _gpu_forward(pg, rec, sc, wdtype="f32", k=None, iters=None, keep_history=False):
+    k = k or sc.k
+    iters = sc.iters if iters is None else iters
+    r = Run()
+    V = pg.Vertices.from_records(rec)
+    r.graph = pg.pg_build_graph(V, k)
+    r.c, r.D = pg.pg_aggregate(r.graph, V, wdtype)
+    L0 = torch.from_numpy(rec["L0"]).cuda()
+    r.L, r.res, r.done = pg.pg_propagate(r.graph, L0, iters, keep_history=keep_history, want_residual=True)
+    first = torch.from_numpy(rec["first"]).cuda()
+    bg = torch.from_numpy(rec["bg"]).cuda()
+    r.img = pg.pg_gather(r.graph, r.L, r.D, first, bg, sc.spp, sc.width, sc.height)
+    torch.cuda.synchronize()
+    r.V = V
+    return r
+
+
+@pytest.fixture(scope="module", params=list(PARITY_SCENES))
+def case(request, pg):
+    sc = PARITY_SCENES[request.param]
+    rec = pgrec.trace(sc)
+    ref = oracle.forward(rec, rec["first"], rec["bg"], sc.spp, sc.width, sc.height, sc.k, sc.iters)
+    gpu = _gpu_forward(pg, rec, sc)
+    return sc, rec, ref, gpu
+
+
+def test_neighbors_bit_exact(case):
+    sc, rec, ref, gpu = case
+    nbr = gpu.graph.neighbors().cpu().numpy()
+    assert nbr.shape == ref["nbr"].shape
+    assert np.array_equal(nbr, ref["nbr"])
+
+
+def test_direct_terms(case):
+    sc, rec, ref, gpu = case
+    assert rel_err(gpu.c.cpu().numpy(), ref["c"]) <= FP32_TOL
+    assert rel_err(gpu.D.cpu().numpy(), ref["D"]) <= FP32_TOL
+
+
+def test_propagated_radiance(case):
+    sc, rec, ref, gpu = case
+    assert gpu.done == sc.iters
+    assert rel_err(gpu.L.cpu().numpy(), ref["L"]) <= FP32_TOL
+    np.testing.assert_allclose(gpu.res, ref["residuals"], rtol=1e-3, atol=1e-7)
+
+
+def test_image(case):
+    sc, rec, ref, gpu = case
+    img = gpu.img.cpu().numpy()
+    assert img.shape == (sc.height, sc.width)
+    assert rel_err(img, ref["image"]) <= FP32_TOL
+
+
+def test_graph_counts(case):
+    sc, rec, ref, gpu = case
+    info = gpu.graph.info()
+    succ = rec["succ"]
+    has_pred = np.zeros(rec["n"], bool)
+    has_pred[succ[succ >= 0]] = True
+    assert info["n_active"] == int(has_pred.sum())
+    nb = ref["nbr"]
+    real = (nb >= 0) & (succ[np.where(nb >= 0, nb, 0)] >= 0)
+    assert info["nnz_swept"] == int(real[has_pred].sum())
+
+
+@pytest.mark.parametrize("wdtype", ["bf16", "f16"])
+def test_16bit_weights(case, pg, wdtype):
+    sc, rec, ref, _ = case
+    gpu = _gpu_forward(pg, rec, sc, wdtype=wdtype)
+    err = rel_err(gpu.img.cpu().numpy(), ref["image"])
+    assert err <= W16_TOL, f"{wdtype} image error {err:.2e}"
+    assert rel_err(gpu.L.cpu().numpy(), ref["L"]) <= 10 * W16_TOL
+
+
+def test_k1_is_path_tracing(pg):
+    """No neighbour edges: the output is the path tracer's own image."""
+    sc = pgrec.CLOUD64_GRAD.with_(width=32, height=32, spp=2)
+    rec = pgrec.trace(sc)
+    gpu = _gpu_forward(pg, rec, sc, k=1, iters=4)
+    assert rel_err(gpu.img.cpu().numpy(), rec["pt_image"]) <= FP32_TOL
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 5, 8, 13, 16, 32])
+def test_neighbors_ties_radius(pg, k):
+    """Lattice points: many equal distances and duplicate positions."""
+    rng = np.random.default_rng(k)
+    n = 3000
+    pos = (rng.integers(0, 12, size=(n, 3)) / 12.0).astype(np.float32)
+    V = synthetic.random_records(n, seed=k)
+    V["px"], V["py"], V["pz"] = pos[:, 0].copy(), pos[:, 1].copy(), pos[:, 2].copy()
+    q = oracle.quantize(V["px"], V["py"], V["pz"], (0, 0, 0), (1, 1, 1))
+    for r2 in (-1, int((2 ** 21 / 12) ** 2 * 2)):
+        Vd = pg.Vertices.from_records(V)
+        graph = pg.pg_build_graph(Vd, k, r2_max=r2, grid_level=4)
+        got = graph.neighbors().cpu().numpy()
+        want = oracle.knn(q, k, None if r2 < 0 else r2)
+        assert np.array_equal(got, want), (k, r2)
+
+
+def test_random_records_all_paths(pg):
+    """Synthetic records: random directions, delta and continuous lights,
+    short paths, empty camera paths; non-multiple-of-tile sizes."""
+    V = synthetic.random_records(4999, seed=11, n_paths=3 * 40 * 30)
+    k, iters, spp, w, h = 16, 7, 3, 40, 30
+    ref = oracle.forward(V, V["first"], V["bg"], spp, w, h, k, iters)
+    Vd = pg.Vertices.from_records(V)
+    graph = pg.pg_build_graph(Vd, k)
+    c, D = pg.pg_aggregate(graph, Vd, "f32")
+    L = pg.pg_propagate(graph, torch.from_numpy(V["L0"]).cuda(), iters)
+    img = pg.pg_gather(graph, L, D, torch.from_numpy(V["first"]).cuda(), torch.from_numpy(V["bg"]).cuda(), spp, w, h)
+    assert np.array_equal(graph.neighbors().cpu().numpy(), ref["nbr"])
+    assert rel_err(c.cpu().numpy(), ref["c"]) <= FP32_TOL
+    assert rel_err(D.cpu().numpy(), ref["D"]) <= FP32_TOL
+    assert rel_err(L.cpu().numpy(), ref["L"]) <= FP32_TOL
+    assert rel_err(img.cpu().numpy(), ref["image"]) <= FP32_TOL
+
+
+def test_early_stop(pg):
+    sc = pgrec.CUBE_CONST.with_(width=32, height=32)
+    rec = pgrec.trace(sc)
+    V = pg.Vertices.from_records(rec)
+    graph = pg.pg_build_graph(V, sc.k)
+    pg.pg_aggregate(graph, V)
+    L0 = torch.from_numpy(rec["L0"]).cuda()
+    L, res, done = pg.pg_propagate(graph, L0, 200, tol=1e-4, want_residual=True)
+    assert 1 <= done < 200
+    assert res[done - 1] < 1e-4 and (done == 1 or res[done - 2] >= 1e-4)
+    assert np.all(res[done:] == 0)
+    ref = oracle.forward(rec, rec["first"], rec["bg"], sc.spp, sc.width, sc.height, sc.k, done)
+    assert rel_err(L.cpu().numpy(), ref["L"]) <= FP32_TOL
+
+
+def test_empty_and_tiny(pg):
+    # no vertices at all: every camera ray left the medium
+    empty = {f: np.zeros(0, np.float32) for f in pgrec.F32_FIELDS}
+    empty["e_delta"] = np.zeros(0, np.uint8)
+    empty["succ"] = np.zeros(0, np.int32)
+    V = pg.Vertices.from_records(empty)
+    graph = pg.pg_build_graph(V, 8)
+    c, D = pg.pg_aggregate(graph, V)
+    L = pg.pg_propagate(graph, torch.zeros(0, device="cuda"), 5)
+    bg = torch.rand(2 * 3 * 4, device="cuda")
+    img = pg.pg_gather(graph, L, D, torch.full((24,), -1, dtype=torch.int32, device="cuda"), bg, 4, 3, 2)
+    np.testing.assert_allclose(img.cpu().numpy(), bg.view(2, 3, 4).mean(2).cpu().numpy(), rtol=1e-6)
+    # fewer vertices than k, one path
+    V3 = synthetic.random_records(3, seed=1, n_paths=1, max_len=3)
+    ref = oracle.forward(V3, V3["first"], V3["bg"], 1, 1, 1, 8, 3)
+    Vd = pg.Vertices.from_records(V3)
+    graph = pg.pg_build_graph(Vd, 8)
+    c, D = pg.pg_aggregate(graph, Vd)
+    L = pg.pg_propagate(graph, torch.from_numpy(V3["L0"]).cuda(), 3)
+    img = pg.pg_gather(graph, L, D, torch.from_numpy(V3["first"]).cuda(), torch.from_numpy(V3["bg"]).cuda(), 1, 1, 1)
+    assert np.array_equal(graph.neighbors().cpu().numpy(), ref["nbr"])
+    assert rel_err(img.cpu().numpy(), ref["image"]) <= FP32_TOL
+
+
+def test_bad_inputs_rejected(pg):
+    V = synthetic.random_records(100, seed=3)
+    bad = dict(V)
+    bad["px"] = V["px"].copy()
+    bad["px"][7] = np.nan
+    with pytest.raises(pg.PgError) as e:
+        pg.pg_build_graph(pg.Vertices.from_records(bad), 8)
+    assert e.value.status == 4
+    two = dict(V)
+    two["succ"] = V["succ"].copy()
+    two["succ"][0] = 5
+    two["succ"][1] = 5  # two predecessors
+    Vd = pg.Vertices.from_records(two)
+    graph = pg.pg_build_graph(Vd, 8)
+    with pytest.raises(pg.PgError) as e:
+        pg.pg_aggregate(graph, Vd)
+    assert e.value.status == 1
+    with pytest.raises(pg.PgError) as e:
+        pg.pg_propagate(pg.pg_build_graph(Vd, 8), torch.zeros(100, device="cuda"), 3)
+    assert e.value.status == 7
