@@ -280,11 +280,16 @@ def propagate(V, nbr, A, c, L0, iters, keep_history=False):
     """iters Jacobi sweeps from L0 (the path tracer's estimate, Section 4).
 
     Returns (L, history, residuals): history[t] = L after t sweeps
-    (history[0] = L0); residuals[t-1] = ||L_t - L_{t-1}||_2 / ||L_t||_2.
+    (history[0] = L0 with path ends set to zero);
+    residuals[t-1] = ||L_t - L_{t-1}||_2 / ||L_t||_2.
     Parity: pinned by the dense solve (I - P A+)^-1 P A°L° on tiny graphs,
     the isotropic geometric series, and the K=1 path-tracing fixed point.
     """
-    L = np.asarray(L0, np.float64).copy()
+    # L+ is indexed by continuation edges (Section 3.5, the vector of incoming
+    # indirect radiance "from all the incoming continuation edges"): a vertex
+    # whose path ends has no such edge, so its entry is zero from the start.
+    succ = np.asarray(V["succ"], np.int64)
+    L = np.where(succ >= 0, np.asarray(L0, np.float64), 0.0)
     hist = [L.copy()] if keep_history else None
     res = []
     for _ in range(iters):
