@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark of the volumetric path-graph hot path on GB300.
+
+One step = one pass of the whole hot path over the heterogeneous-cloud
+workload (128^3 fBm medium, albedo 0.99, HG g = 0.8, sun + sky, 256x256
+pixels, 16 spp, depth 64, about 8.7M scattering vertices; k = 16, 30 sweeps,
+FP32 weights): graph build, aggregation, propagation with history, output,
+and the adjoint sweep for an image loss.
+
+Prints one JSON line (rank 0). `value` is propagation edge-updates per
+second of the whole step (forward + reverse sweeps over the step's wall time
+on the device); per-stage times, the propagation-only rate, the 16-bit
+weight variants, the roofline of the sweep kernel and the FP64 oracle's rate
+on the host cores are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "propagation edge-updates/s & % HBM peak; 16-bit vs FP32 weights at <=2e-3 rel err"
+UNIT = "edge-updates/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+
+    import paper_2404_11894_gb300 as pg
+    import pgrec
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    sc = pgrec.CLOUD128
+    if world > 1:  # independent renders (replicas), one per rank
+        sc = sc.with_(seed=sc.seed + rank)
+    rec = pgrec.trace(sc)
+    n, P = rec["n"], rec["n_paths"]
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    # host copies in pinned memory (for the end-to-end leg)
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a))
+        return t.pin_memory()
+
+    host = {k: pinned(rec[k]) for k in pg.VERTEX_F32 + ("e_delta", "succ", "L0", "first", "bg")}
+    rng = np.random.default_rng(0)
+    target = rec["pt_image"].astype(np.float32) * rng.uniform(0.9, 1.1, rec["pt_image"].shape).astype(np.float32)
+    host_target = pinned(target)
+    dev_in = {k: v.to(dev) for k, v in host.items()}
+    dev_target = host_target.to(dev)
+    V = pg.Vertices({k: dev_in[k] for k in pg.VERTEX_F32 + ("e_delta", "succ")})
+    solver = pg.Solver(k=sc.k, iters=sc.iters, wdtype="f32", adjoint=not args.no_adjoint)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(V, L0, first, bg, tgt, marks=None):
+        return solver.step(V, L0, first, bg, sc.spp, sc.width, sc.height, tgt, marks=marks)
+
+    for _ in range(args.warmup):
+        step(V, dev_in["L0"], dev_in["first"], dev_in["bg"], dev_target)
+    torch.cuda.synchronize()
+    info = solver.graph.info()
+    nnz = info["nnz_swept"]
+    sweeps_per_step = sc.iters * (2 if not args.no_adjoint else 1)
+    edge_updates_step = nnz * sweeps_per_step
+
+    # ---- device-timed region (inputs resident in HBM)
+    stage_names = ["build", "aggregate", "propagate", "gather", "adjoint"]
+    marks_all = []
+    launches0 = pg.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    for _ in range(args.steps):
+        marks = {nm: (ev(), ev()) for nm in stage_names}
+        step(V, dev_in["L0"], dev_in["first"], dev_in["bg"], dev_target, marks=marks)
+        marks_all.append(marks)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = pg.launch_count() - launches0
+    t_dev = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_dev], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_dev = float(tt.item())
+        eu = torch.tensor([float(edge_updates_step)], device=dev)
+        torch.distributed.all_reduce(eu)
+        total_updates = float(eu.item()) * args.steps
+    else:
+        total_updates = float(edge_updates_step) * args.steps
+    stage_ms = {nm: float(np.mean([m[nm][0].elapsed_time(m[nm][1]) for m in marks_all if m[nm][0].query()]))
+                for nm in stage_names if not (args.no_adjoint and nm == "adjoint")}
+
+    # ---- sweep kernel roofline: propagation time minus its permutation prologue/epilogue
+    t0 = time.time()
+    prop_base = solver.time_propagate(0, reps=5)
+    prop_full = solver.time_propagate(sc.iters, reps=3)
+    sweep_ms = (prop_full - prop_base) / sc.iters
+    wb = 4
+    bytes_sweep = nnz * (4 + wb) + info["n_active"] * 12
+    achieved = bytes_sweep / (sweep_ms / 1e3) / 1e9
+    peak, peak_kind = _peaks()
+    traffic = _profile_traffic("sweep_f32", n)
+
+    # ---- 16-bit weights: propagation rate and error against FP32 (same inputs)
+    prec = {}
+    if not args.quick:
+        img32 = solver.last_image.clone()
+        for wd in ("bf16", "f16"):
+            s16 = pg.Solver(k=sc.k, iters=sc.iters, wdtype=wd, adjoint=False)
+            s16.step(V, dev_in["L0"], dev_in["first"], dev_in["bg"], sc.spp, sc.width, sc.height, None)
+            torch.cuda.synchronize()
+            pb = s16.time_propagate(0, reps=5)
+            pf = s16.time_propagate(sc.iters, reps=3)
+            sw = (pf - pb) / sc.iters
+            a = img32.double()
+            b = s16.last_image.double()
+            den = torch.clamp(a.abs(), min=1e-3 * float(a.abs().mean()))
+            prec[wd] = {"sweep_ms": round(sw, 4), "edge_updates_per_s": nnz / (sw / 1e3),
+                        "algorithmic_GBps": (nnz * (4 + 2) + info["n_active"] * 16) / (sw / 1e3) / 1e9,
+                        "speedup_vs_f32": round(sweep_ms / sw, 3),
+                        "max_rel_err_vs_f32": float(((a - b).abs() / den).max()),
+                        "mean_rel_err_vs_f32": float(((a - b).abs() / den).mean())}
+            s16.close()
+
+    # ---- end to end through the public API: host records -> image on the host
+    e2e_t = []
+    h2d = sum(int(v.numel() * v.element_size()) for v in host.values()) + host_target.numel() * 4
+    d2h = sc.width * sc.height * 4
+    for i in range(args.steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        img = solver.solve_host(host, host_target, sc.spp, sc.width, sc.height)
+        t1 = time.perf_counter()
+        if i > 0:
+            e2e_t.append(t1 - t0)
+    e2e_value = edge_updates_step / float(np.mean(e2e_t))
+
+    value = total_updates / t_dev
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": sc.name, "vertices": n, "paths": P, "k": sc.k, "iters": sc.iters,
+                   "weights": "f32", "nnz_per_sweep": nnz, "n_active": info["n_active"],
+                   "sweeps_per_step": sweeps_per_step, "edge_updates_per_step": edge_updates_step,
+                   "step": "build+aggregate+propagate(history)+gather" + ("" if args.no_adjoint else "+adjoint"),
+                   "l2": "inputs larger than L2 (vertex records %.0f MB > 129 MB)" % (
+                       sum(int(v.numel() * v.element_size()) for v in dev_in.values()) / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "stages_ms": stage_ms,
+        "propagate_edge_updates_per_s": nnz / (sweep_ms / 1e3),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "sweep_kernel<16,float>",
+                     "sweep_ms": sweep_ms, "algorithmic_bytes_per_launch": bytes_sweep, "peak_kind": peak_kind},
+        "precision": prec,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    solver.close()
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(rec, sc, args)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _profile_traffic(kind, n):
+    """DRAM bytes per sweep launch from the committed ncu summary, if any."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kind)
+    if not e:
+        return None
+    return e["dram_bytes_per_launch"] * (n / e["vertices"]) if e.get("scale_with_n") else e["dram_bytes_per_launch"]
+
+
+# ----------------------------------------------------------------------------- oracle arm
+def oracle_sample(rec, sc, stride):
+    """Every `stride`-th pixel in x and y, all of its paths."""
+    import pgrec
+
+    sub = pgrec.sample_pixels(rec, sc.width, sc.height, sc.spp, stride)
+    return sub, sub["n_paths"]
+
+
+def oracle_step(sub, sc, npix, adjoint=True):
+    import oracle
+
+    t0 = time.perf_counter()
+    q = oracle.quantize(sub["px"], sub["py"], sub["pz"], (0, 0, 0), (1, 1, 1))
+    nbr = oracle.knn(q, sc.k)
+    agg = oracle.aggregate(sub, nbr)
+    L, hist, res = oracle.propagate(sub, nbr, agg["A"], agg["c"], sub["L0"], sc.iters, keep_history=adjoint)
+    vals = oracle.path_values(sub, nbr, agg["A"], L, agg["D"], sub["first"], sub["bg"])
+    img = vals.reshape(-1, sc.spp).mean(axis=1)
+    if adjoint:
+        dI = img - 0.5 * img  # any image-loss gradient of the right shape
+        w = npix
+        oracle.adjoint(sub, nbr, sc.iters, sub["L0"], dI.reshape(1, w), sub["first"], sub["bg"], sc.spp, w, 1)
+    t = time.perf_counter() - t0
+    succ = np.asarray(sub["succ"])
+    has_pred = np.zeros(sub["n"], bool)
+    has_pred[succ[succ >= 0]] = True
+    real = (nbr >= 0) & (succ[np.where(nbr >= 0, nbr, 0)] >= 0)
+    nnz = int(real[has_pred].sum())
+    return t, nnz * sc.iters * (2 if adjoint else 1)
+
+
+def cpu_baseline(rec, sc, args):
+    sub, hi = oracle_sample(rec, sc, args.oracle_stride)
+    t, updates = oracle_step(sub, sc, hi // sc.spp, adjoint=not args.no_adjoint)
+    return {"value": updates / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"every {args.oracle_stride}th pixel in x and y: {hi} of {rec['n_paths']} paths "
+                      f"({sub['n']} vertices) of the same workload; whole oracle step (kNN, aggregation, "
+                      f"{sc.iters} sweeps, output{', adjoint' if not args.no_adjoint else ''}) in {t:.1f} s "
+                      f"on one host core"}
+
+
+def run_reference(args):
+    import pgrec
+
+    rank, world, local = _dist()
+    if rank != 0:
+        return
+    sc = pgrec.CLOUD128
+    rec = pgrec.trace(sc)
+    sub, hi = oracle_sample(rec, sc, args.oracle_stride)
+    for _ in range(args.warmup):
+        oracle_step(sub, sc, hi // sc.spp, adjoint=not args.no_adjoint)
+    ts, ups = [], 0
+    for _ in range(args.steps):
+        t, u = oracle_step(sub, sc, hi // sc.spp, adjoint=not args.no_adjoint)
+        ts.append(t)
+        ups += u
+    value = ups / sum(ts)
+    sample = (f"every {args.oracle_stride}th pixel in x and y: {hi} of {rec['n_paths']} paths "
+              f"({sub['n']} vertices) of {sc.name}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ts)) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": sc.name, "k": sc.k, "iters": sc.iters, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the 16-bit weight runs")
+    ap.add_argument("--oracle-stride", type=int, default=10)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        args.warmup = min(args.warmup, 3)
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

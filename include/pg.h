@@ -216,6 +216,10 @@ pg_status pg_graph_release_weights(pg_graph *g);
 void pg_graph_destroy(pg_graph *g);
 const char *pg_status_string(pg_status s);
 
+/* Diagnostic (no counterpart in the paper): number of CUDA kernels this
+ * library has launched in the process so far. Thread-safe; never fails. */
+int64_t pg_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

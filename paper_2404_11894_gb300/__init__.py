@@ -151,5 +151,12 @@ def pg_propagate_adjoint(graph: Graph, dI: torch.Tensor, first: torch.Tensor, sp
     return {"grad_sigma_s": gs, "grad_g": gg, "grad_albedo": ga}
 
 
-__all__ = ["Vertices", "Graph", "PgError", "pg_build_graph", "pg_aggregate", "pg_propagate", "pg_gather",
+def launch_count() -> int:
+    """Kernels launched by libpg in this process (diagnostic)."""
+    return int(_LIB.pg_launch_count())
+
+
+from .solver import Solver  # noqa: E402
+
+__all__ = ["Solver", "launch_count", "Vertices", "Graph", "PgError", "pg_build_graph", "pg_aggregate", "pg_propagate", "pg_gather",
            "pg_propagate_adjoint"]

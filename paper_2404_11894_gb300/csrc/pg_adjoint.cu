@@ -1,16 +1,636 @@
-// Adjoint of aggregation -> propagation -> output (placeholder until the
-// reverse sweep lands).
+// Adjoint of aggregation -> propagation -> output for a fixed graph.
+//
+// The forward pass in sweep rows r (see pg_aggregate.cu) is
+//   y_t[r] = sum_i W~[r][i] y_{t-1}[col[r][i]] + b[r],  t = 1..T, r active,
+//   val_p  = bg_p + sum_i W~[f][i] y_T[col[f][i]] + (tau/p_t)_f D_f
+// with W~ = (tau/p_t)_s A+ (times the row scale for 16-bit weights) and
+// b = (tau/p_t)_s c_s. For dLoss/dImage = dI, each path's first vertex f gets
+// nu_f = dI[pixel]/spp, and the reverse sweeps are
+//   mu_T = W~^T nu,   mu_{t-1} = W~^T mu_t   (t = T..2).
+// Every weight of row s is sigma_s(s) times a factor, so
+//   dLoss/dsigma_s(s) = ( sum_t mu_t[s] y_t[s] + nu_s (val_s - bg) ) / sigma_s(s).
+// For g the per-edge adjoints Gamma[s][i] = sum_t mu_t[s] y_{t-1}[col] (+ the
+// output term) and beta_s = sum_t mu_t[s] are pushed through the derivatives
+// of the MIS weights (numerators and marginal densities).
+//
+// W~^T is applied either from a transposed copy of the stored weights
+// (columns sorted by row: deterministic), or, with recompute_weights, by
+// re-evaluating each row's weights from the vertex records and scattering
+// with atomic adds (no weight memory).
 #include "pg_internal.cuh"
+
+template <typename WT>
+__device__ __forceinline__ float wload(const WT *W, int64_t i);
+template <>
+__device__ __forceinline__ float wload<float>(const float *W, int64_t i) { return W[i]; }
+template <>
+__device__ __forceinline__ float wload<__nv_bfloat16>(const __nv_bfloat16 *W, int64_t i) { return __bfloat162float(W[i]); }
+template <>
+__device__ __forceinline__ float wload<__half>(const __half *W, int64_t i) { return __half2float(W[i]); }
+
+// ------------------------------------------------------------------ transpose build
+__global__ void tcount_kernel(const int32_t *__restrict__ col, int64_t n, int kp, int32_t *__restrict__ cnt) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * kp) return;
+    int32_t c = col[e];
+    if (c < n) atomicAdd(&cnt[c], 1);
+}
+
+template <typename WT>
+__global__ void tfill_kernel(const int32_t *__restrict__ col, const WT *__restrict__ W, int64_t n, int kp,
+                             const int32_t *__restrict__ tptr, int32_t *__restrict__ fill, int32_t *__restrict__ trow,
+                             WT *__restrict__ tW) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * kp) return;
+    int32_t c = col[e];
+    if (c >= n) return;
+    int32_t pos = tptr[c] + atomicAdd(&fill[c], 1);
+    trow[pos] = (int32_t)(e / kp);
+    tW[pos] = W[e];
+}
+
+// order each column's entries by source row (a row appears once per column)
+template <typename WT>
+__global__ void tsort_kernel(const int32_t *__restrict__ tptr, int64_t ncols, int32_t *__restrict__ trow,
+                             WT *__restrict__ tW) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    int32_t a = tptr[c], b = tptr[c + 1];
+    for (int32_t i = a + 1; i < b; i++) {
+        int32_t kr = trow[i];
+        WT kw = tW[i];
+        int32_t j = i - 1;
+        while (j >= a && trow[j] > kr) {
+            trow[j + 1] = trow[j];
+            tW[j + 1] = tW[j];
+            j--;
+        }
+        trow[j + 1] = kr;
+        tW[j + 1] = kw;
+    }
+}
+
+// ------------------------------------------------------------------ seeds
+// nu on first-vertex rows; us = nu * row scale (what W^T multiplies)
+__global__ void seed_kernel(const int32_t *__restrict__ first, const float *__restrict__ dI, int64_t n_paths,
+                            int spp, int64_t n, const int32_t *__restrict__ c2m, const int32_t *__restrict__ m2r,
+                            const float *__restrict__ rscale, float *__restrict__ nu, float *__restrict__ us) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_paths) return;
+    int32_t f = first[p];
+    if (f < 0 || f >= n) return;
+    int32_t r = m2r[c2m[f]];
+    float v = dI[p / spp] / (float)spp;
+    nu[r] = v; // a vertex starts at most one path
+    us[r] = rscale ? v * rscale[r] : v;
+}
+
+// ------------------------------------------------------------------ reverse sweep (stored transpose)
+// One group of 8 lanes per column c: mu_out[c] = sum_e tW[e] us_in[trow[e]].
+// Also accumulates G[c] += mu_in[c] * y_t[c] and B[c] += mu_in[c] when y_t.
+template <typename WT>
+__global__ void __launch_bounds__(256) tsweep_kernel(const int32_t *__restrict__ tptr,
+                                                     const int32_t *__restrict__ trow, const WT *__restrict__ tW,
+                                                     const float *__restrict__ us_in, const float *__restrict__ mu_in,
+                                                     const float *__restrict__ y_t, const float *__restrict__ rscale,
+                                                     int64_t ncols, int write_out, float *__restrict__ mu_out,
+                                                     float *__restrict__ us_out, float *__restrict__ G,
+                                                     float *__restrict__ B) {
+    constexpr int LPC = 8;
+    const int lane = threadIdx.x & 31;
+    const int q = lane & (LPC - 1);
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPC;
+    const bool ok = c < ncols;
+    float acc = 0.0f;
+    if (ok && write_out) {
+        int32_t a = tptr[c], b = tptr[c + 1];
+        for (int32_t e = a + q; e < b; e += LPC) acc = fmaf(wload<WT>(tW, e), __ldg(us_in + trow[e]), acc);
+    }
+#pragma unroll
+    for (int o = LPC / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (ok && q == 0) {
+        if (write_out) {
+            mu_out[c] = acc;
+            us_out[c] = rscale ? acc * rscale[c] : acc;
+        }
+        if (y_t) {
+            float m = mu_in[c];
+            G[c] = fmaf(m, y_t[c], G[c]);
+            B[c] += m;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ per-edge adjoints (for g)
+// Gamma[r][i] += mu[r] * y_prev[col[r][i]] over the rows [r0, r1)
+__global__ void gamma_kernel(const int32_t *__restrict__ col, const float *__restrict__ mu,
+                             const float *__restrict__ y_prev, int64_t r0, int64_t r1, int kp,
+                             float *__restrict__ Gam) {
+    int64_t e = r0 * kp + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= r1 * kp) return;
+    float m = mu[e / kp];
+    if (m != 0.0f) Gam[e] = fmaf(m, y_prev[col[e]], Gam[e]);
+}
+
+// output term of first-vertex rows: G[f] = nu_f (val_f - bg) with
+// val_f - bg = sum_i W~[f][i] y_T[col] + (tau/p_t)_f D_f
+template <typename WT>
+__global__ void first_rows_kernel(const int32_t *__restrict__ first, int64_t n_paths, int64_t n,
+                                  const int32_t *__restrict__ c2m, const int32_t *__restrict__ m2r,
+                                  const int32_t *__restrict__ col, const WT *__restrict__ W,
+                                  const float *__restrict__ rscale, const float *__restrict__ yT,
+                                  const float4 *__restrict__ LV, const float *__restrict__ D_m,
+                                  const float *__restrict__ nu, int kp, float *__restrict__ G) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_paths) return;
+    int32_t f = first[p];
+    if (f < 0 || f >= n) return;
+    int32_t m = c2m[f];
+    int64_t r = m2r[m];
+    float sum = 0.0f;
+    for (int i = 0; i < kp; i++) sum = fmaf(wload<WT>(W, r * kp + i), yT[col[r * kp + i]], sum);
+    if (rscale) sum *= rscale[r];
+    G[r] += nu[r] * (sum + LV[m].w * D_m[m]);
+}
+
+// ------------------------------------------------------------------ recompute mode
+// Row s (Morton m) re-evaluates its weights W~[s][j] = w_s sigma_s rho_s(o_s,d_j)
+// / sum_l rho_l(o_l,d_j) and scatters u[r] W~ into out[col] with atomics.
+// Also accumulates G/B (y_t given) and Gamma (Gam given) for rows with u != 0.
+template <int KP>
+__global__ void __launch_bounds__(256) recompute_scatter_kernel(
+    const int32_t *__restrict__ nbr, const float4 *__restrict__ OG, const float4 *__restrict__ DP,
+    const float4 *__restrict__ LV, const int32_t *__restrict__ succ_m, const int32_t *__restrict__ m2r,
+    const int32_t *__restrict__ r2m, int64_t r0, int64_t r1, int64_t n, const float *__restrict__ u,
+    const float *__restrict__ y_t, const float *__restrict__ y_prev, int write_out, float *__restrict__ out,
+    float *__restrict__ G, float *__restrict__ B, float *__restrict__ Gam) {
+    __shared__ float4 s_o[256];
+    __shared__ float2 s_ab[256];
+    const int lane = threadIdx.x & 31;
+    const int j = lane & (KP - 1);
+    const int gbase = threadIdx.x - j;
+    const int64_t r = r0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / KP;
+    const bool row_ok = r < r1;
+    const int32_t m = row_ok ? r2m[r] : 0;
+    const float ur = row_ok ? u[r] : 0.0f;
+    const bool live_row = row_ok && ur != 0.0f;
+    int32_t nj = row_ok ? nbr[(int64_t)m * KP + j] : -1;
+    const bool valid = nj >= 0;
+    float4 og = make_float4(0.f, 0.f, 1.f, 0.f), dp = make_float4(0.f, 0.f, 1.f, 0.f);
+    int32_t sj = -1;
+    if (valid) {
+        og = OG[nj];
+        dp = DP[nj];
+        sj = succ_m[nj];
+    }
+    HGc hc = hg_consts(og.w);
+    s_o[threadIdx.x] = make_float4(og.x, og.y, og.z, valid ? hc.C : 0.0f);
+    s_ab[threadIdx.x] = make_float2(valid ? hc.a : 1.0f, valid ? hc.b2 : 0.0f);
+    __syncwarp();
+    if (__any_sync(0xffffffffu, live_row)) {
+        float pm_d = 0.0f;
+#pragma unroll 4
+        for (int l = 0; l < KP; l++) {
+            float4 so = s_o[gbase + l];
+            float2 ab = s_ab[gbase + l];
+            HGc h;
+            h.C = so.w;
+            h.a = ab.x;
+            h.b2 = ab.y;
+            pm_d += hg_eval(h, one_plus_dot(so.x, so.y, so.z, dp.x, dp.y, dp.z));
+        }
+        const float4 so = s_o[gbase];
+        const float2 sab = s_ab[gbase];
+        HGc hs;
+        hs.C = so.w;
+        hs.a = sab.x;
+        hs.b2 = sab.y;
+        const float4 lvs = LV[m];
+        float rho_sd = hg_eval(hs, one_plus_dot(so.x, so.y, so.z, dp.x, dp.y, dp.z));
+        if (live_row && valid && sj >= 0) {
+            int32_t cl = m2r[sj];
+            float Wt = lvs.w * (lvs.z * rho_sd / pm_d);
+            if (write_out) atomicAdd(out + cl, ur * Wt);
+            if (Gam) Gam[r * KP + j] = fmaf(ur, y_prev[cl], Gam[r * KP + j]);
+        }
+    }
+    if (row_ok && j == 0 && y_t) {
+        G[r] = fmaf(ur, y_t[r], G[r]);
+        B[r] += ur;
+    }
+}
+
+// first-vertex rows in recompute mode: G[f] = nu_f (val_f - bg)
+template <int KP>
+__global__ void __launch_bounds__(256) recompute_first_kernel(
+    const int32_t *__restrict__ nbr, const float4 *__restrict__ OG, const float4 *__restrict__ DP,
+    const float4 *__restrict__ LV, const int32_t *__restrict__ succ_m, const int32_t *__restrict__ m2r,
+    const int32_t *__restrict__ r2m, int64_t r0, int64_t r1, const float *__restrict__ nu,
+    const float *__restrict__ yT, const float *__restrict__ D_m, float *__restrict__ G) {
+    __shared__ float4 s_o[256];
+    __shared__ float2 s_ab[256];
+    const int lane = threadIdx.x & 31;
+    const int j = lane & (KP - 1);
+    const int gbase = threadIdx.x - j;
+    const int src = lane & ~(KP - 1);
+    const int64_t r = r0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / KP;
+    const bool row_ok = r < r1;
+    const int32_t m = row_ok ? r2m[r] : 0;
+    int32_t nj = row_ok ? nbr[(int64_t)m * KP + j] : -1;
+    const bool valid = nj >= 0;
+    float4 og = make_float4(0.f, 0.f, 1.f, 0.f), dp = make_float4(0.f, 0.f, 1.f, 0.f);
+    int32_t sj = -1;
+    if (valid) {
+        og = OG[nj];
+        dp = DP[nj];
+        sj = succ_m[nj];
+    }
+    HGc hc = hg_consts(og.w);
+    s_o[threadIdx.x] = make_float4(og.x, og.y, og.z, valid ? hc.C : 0.0f);
+    s_ab[threadIdx.x] = make_float2(valid ? hc.a : 1.0f, valid ? hc.b2 : 0.0f);
+    __syncwarp();
+    float pm_d = 0.0f;
+#pragma unroll 4
+    for (int l = 0; l < KP; l++) {
+        float4 so = s_o[gbase + l];
+        float2 ab = s_ab[gbase + l];
+        HGc h;
+        h.C = so.w;
+        h.a = ab.x;
+        h.b2 = ab.y;
+        pm_d += hg_eval(h, one_plus_dot(so.x, so.y, so.z, dp.x, dp.y, dp.z));
+    }
+    const float4 so = s_o[gbase];
+    const float2 sab = s_ab[gbase];
+    HGc hs;
+    hs.C = so.w;
+    hs.a = sab.x;
+    hs.b2 = sab.y;
+    const float4 lvs = row_ok ? LV[m] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float rho_sd = hg_eval(hs, one_plus_dot(so.x, so.y, so.z, dp.x, dp.y, dp.z));
+    float term = 0.0f;
+    if (row_ok && valid && sj >= 0) term = lvs.w * (lvs.z * rho_sd / pm_d) * yT[m2r[sj]];
+#pragma unroll
+    for (int o = KP / 2; o > 0; o >>= 1) term += __shfl_xor_sync(0xffffffffu, term, o);
+    (void)src;
+    if (row_ok && j == 0) G[r] += nu[r] * (term + lvs.w * D_m[m]);
+}
+
+// ------------------------------------------------------------------ outputs
+__global__ void grad_sigma_kernel(const float *__restrict__ G, const int32_t *__restrict__ c2m,
+                                  const int32_t *__restrict__ m2r, const float4 *__restrict__ LV, int64_t n,
+                                  float *__restrict__ gs_out, const int32_t *__restrict__ voxel,
+                                  const float *__restrict__ sigma_t, float *__restrict__ ga, int64_t n_vox) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int32_t m = c2m[v];
+    float ss = LV[m].z;
+    float gsv = ss > 0.0f ? G[m2r[m]] / ss : 0.0f;
+    if (gs_out) gs_out[v] = gsv;
+    if (ga) {
+        int32_t x = voxel[v];
+        if (x >= 0 && x < n_vox) atomicAdd(ga + x, sigma_t[v] * gsv);
+    }
+}
+
+// d/dg of every weight of row s (Morton m) given the edge adjoints
+// Gamma (dLoss/dW~), beta (dLoss/db) and nu (dLoss/d(w D)); contributions to
+// g_l of every l in N(s) are added atomically into gg (Morton order).
+template <int KP>
+__global__ void __launch_bounds__(256) grad_g_kernel(
+    const int32_t *__restrict__ nbr, const float4 *__restrict__ OG, const float4 *__restrict__ DP,
+    const float4 *__restrict__ EP, const float4 *__restrict__ LV, const int32_t *__restrict__ m2r, int64_t n,
+    const float *__restrict__ Gam, const float *__restrict__ B, const float *__restrict__ nu,
+    const float *__restrict__ rscale, float *__restrict__ gg) {
+    __shared__ float4 s_o[256];   // (o_l, g_l)
+    __shared__ float4 s_d[256];   // (d_j, coefficient for rho'_l(o_l, d_j))
+    __shared__ float4 s_e[256];   // (e_j, coefficient for rho'_l(o_l, e_j))
+    const int lane = threadIdx.x & 31;
+    const int j = lane & (KP - 1);
+    const int gbase = threadIdx.x - j;
+    const int src = lane & ~(KP - 1);
+    const int64_t m = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / KP;
+    const bool row_ok = m < n;
+    int32_t nj = row_ok ? nbr[m * KP + j] : -1;
+    const bool valid = nj >= 0;
+    float4 og = make_float4(0.f, 0.f, 1.f, 0.f), dp = make_float4(0.f, 0.f, 1.f, 0.f),
+           ep = make_float4(0.f, 0.f, 1.f, 0.f), lv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+        og = OG[nj];
+        dp = DP[nj];
+        ep = EP[nj];
+        lv = LV[nj];
+    }
+    s_o[threadIdx.x] = og;
+    __syncwarp();
+    const float K = (float)__popc(__ballot_sync(0xffffffffu, valid) &
+                                  ((KP == 32) ? 0xffffffffu : (((1u << KP) - 1u) << src)));
+    // marginals of this lane's samples
+    float pm_d = 0.0f, pm_e = 0.0f;
+#pragma unroll 4
+    for (int l = 0; l < KP; l++) {
+        float4 so = s_o[gbase + l];
+        bool lv_ok = __shfl_sync(0xffffffffu, valid, src + l);
+        if (lv_ok) {
+            HGc h = hg_consts(so.w);
+            pm_d += hg_eval(h, one_plus_dot(so.x, so.y, so.z, dp.x, dp.y, dp.z));
+            pm_e += hg_eval(h, one_plus_dot(so.x, so.y, so.z, ep.x, ep.y, ep.z));
+        }
+    }
+    const float4 os = s_o[gbase];
+    const float sig = __shfl_sync(0xffffffffu, lv.z, src);
+    const float w_s = __shfl_sync(0xffffffffu, lv.w, src);
+    const int64_t r = row_ok ? m2r[m] : 0;
+    (void)rscale; // Gamma is already the adjoint of the full weight value
+    // adjoints w.r.t. A+ (per entry), c and D of this row
+    const float gA = row_ok && valid ? w_s * Gam[r * KP + j] : 0.0f;
+    const float gc = row_ok ? w_s * B[r] : 0.0f;
+    const float gD = row_ok ? w_s * nu[r] : 0.0f;
+    float drho_sd, drho_se, rho_sd, rho_se;
+    drho_sd = hg_eval_dg(os.w, one_plus_dot(os.x, os.y, os.z, dp.x, dp.y, dp.z), &rho_sd);
+    drho_se = hg_eval_dg(os.w, one_plus_dot(os.x, os.y, os.z, ep.x, ep.y, ep.z), &rho_se);
+    const bool delta = ep.w < 0.0f;
+    const float me = pm_e + K * ep.w;
+    const float mph = pm_d + K * dp.w;
+    float cd = 0.0f, ce = 0.0f, num = 0.0f;
+    if (valid && row_ok) {
+        // marginal terms: coefficient of rho'_l(o_l, d_j) and rho'_l(o_l, e_j)
+        cd = -sig * rho_sd * (gA / (pm_d * pm_d) + gc * lv.y / (mph * mph));
+        ce = delta ? 0.0f : -sig * rho_se * gc * lv.x / (me * me);
+        // numerator terms: derivatives w.r.t. g_s of rho_s(o_s, .)
+        num = sig * drho_sd * (gA / pm_d + gc * lv.y / mph) +
+              sig * drho_se * gc * lv.x / (delta ? K : me);
+    }
+    s_d[threadIdx.x] = make_float4(dp.x, dp.y, dp.z, cd);
+    s_e[threadIdx.x] = make_float4(ep.x, ep.y, ep.z, ce);
+    __syncwarp();
+    // lane l: contribution to g_l = sum_j cd_j rho'_l(o_l,d_j) + ce_j rho'_l(o_l,e_j)
+    float acc = 0.0f;
+    if (valid && row_ok) {
+#pragma unroll 4
+        for (int jj = 0; jj < KP; jj++) {
+            float4 sd = s_d[gbase + jj], se = s_e[gbase + jj];
+            float dummy;
+            if (sd.w != 0.0f) acc += sd.w * hg_eval_dg(og.w, one_plus_dot(og.x, og.y, og.z, sd.x, sd.y, sd.z), &dummy);
+            if (se.w != 0.0f) acc += se.w * hg_eval_dg(og.w, one_plus_dot(og.x, og.y, og.z, se.x, se.y, se.z), &dummy);
+        }
+    }
+    // the row's own g_s: numerators and the non-aggregated direct term
+    float nsum = num;
+#pragma unroll
+    for (int o = KP / 2; o > 0; o >>= 1) nsum += __shfl_xor_sync(0xffffffffu, nsum, o);
+    if (valid && row_ok) {
+        if (j == 0) {
+            // D_s = sigma_s (De + Dp) with K = 1, own samples (slot 0 = s)
+            float dDe = delta ? drho_se * lv.x : drho_se * lv.x * ep.w / ((rho_se + ep.w) * (rho_se + ep.w));
+            float dDp = drho_sd * lv.y * dp.w / ((rho_sd + dp.w) * (rho_sd + dp.w));
+            acc += nsum + gD * sig * (dDe + dDp);
+        }
+        if (acc != 0.0f) atomicAdd(gg + nj, acc);
+    }
+}
+
+__global__ void permute_m2c_kernel(const float *__restrict__ in_m, const int32_t *__restrict__ c2m, int64_t n,
+                                   float *__restrict__ out_c) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    out_c[v] = in_m[c2m[v]];
+}
+
+// ------------------------------------------------------------------ host
+template <typename WT>
+static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
+    const int64_t n = g->n;
+    const int kp = g->kp;
+    int32_t *cnt = nullptr, *fill = nullptr, *d_total = nullptr;
+    pg_status st = pg_alloc(g, (void **)&g->t_ptr, 4 * (size_t)(n + 1), s);
+    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&fill, 4 * (size_t)(n + 1), s);
+    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&d_total, 16, s);
+    if (st != PG_OK) return st;
+    cnt = g->t_ptr;
+    PG_CUDA(cudaMemsetAsync(cnt, 0, 4 * (size_t)(n + 1), s));
+    PG_CUDA(cudaMemsetAsync(fill, 0, 4 * (size_t)(n + 1), s));
+    tcount_kernel<<<pg_blocks(n * kp, 256), 256, 0, s>>>(g->col, n, kp, cnt);
+    PG_LAUNCH_CHECK();
+    PG_TRY(pg_scan_exclusive(g, g->t_ptr, n + 1, d_total, s));
+    int32_t h_total = 0;
+    PG_CUDA(cudaMemcpyAsync(&h_total, d_total, 4, cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    g->nnz_t = h_total;
+    PG_TRY(pg_alloc(g, (void **)&g->t_row, 4 * (size_t)(h_total > 0 ? h_total : 1), s));
+    PG_TRY(pg_alloc(g, (void **)&g->t_W, sizeof(WT) * (size_t)(h_total > 0 ? h_total : 1), s));
+    tfill_kernel<WT><<<pg_blocks(n * kp, 256), 256, 0, s>>>(g->col, (const WT *)g->W, n, kp, g->t_ptr, fill,
+                                                            g->t_row, (WT *)g->t_W);
+    PG_LAUNCH_CHECK();
+    tsort_kernel<WT><<<pg_blocks(n, 128), 128, 0, s>>>(g->t_ptr, n, g->t_row, (WT *)g->t_W);
+    PG_LAUNCH_CHECK();
+    cudaFreeAsync(fill, s);
+    cudaFreeAsync(d_total, s);
+    return PG_OK;
+}
+
+template <typename WT>
+static pg_status adjoint_store(pg_graph *g, float *nu, float *us0, float *mu_a, float *mu_b, float *us_a,
+                               float *us_b, float *G, float *B, float *Gam, cudaStream_t s) {
+    const int64_t n = g->n, na = g->n_active;
+    const int T = g->hist_iters;
+    const int64_t stride = n + 1;
+    const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
+    if (!g->t_ptr) PG_TRY(build_transpose<WT>(g, s));
+    const int tb = pg_blocks(na * 8, 256);
+    // mu_T = W^T nu
+    float *mu_cur = mu_a, *us_cur = us_a, *mu_nxt = mu_b, *us_nxt = us_b;
+    tsweep_kernel<WT><<<tb, 256, 0, s>>>(g->t_ptr, g->t_row, (const WT *)g->t_W, us0, nullptr, nullptr, rs, na, 1,
+                                         mu_cur, us_cur, G, B);
+    PG_LAUNCH_CHECK();
+    if (Gam) {
+        // output term of the per-edge adjoint: Gamma[f][i] = nu_f y_T[col]
+        gamma_kernel<<<pg_blocks((n - na) * g->kp, 256), 256, 0, s>>>(g->col, nu, g->hist + (int64_t)T * stride, na,
+                                                                        n, g->kp, Gam);
+        PG_LAUNCH_CHECK();
+    }
+    for (int t = T; t >= 1; t--) {
+        const float *y_t = g->hist + (int64_t)t * stride;
+        if (Gam) {
+            gamma_kernel<<<pg_blocks(na * g->kp, 256), 256, 0, s>>>(g->col, mu_cur, g->hist + (int64_t)(t - 1) * stride,
+                                                                   0, na, g->kp, Gam);
+            PG_LAUNCH_CHECK();
+        }
+        tsweep_kernel<WT><<<tb, 256, 0, s>>>(g->t_ptr, g->t_row, (const WT *)g->t_W, us_cur, mu_cur, y_t, rs, na,
+                                             t > 1 ? 1 : 0, mu_nxt, us_nxt, G, B);
+        PG_LAUNCH_CHECK();
+        float *tm = mu_cur; mu_cur = mu_nxt; mu_nxt = tm;
+        float *tu = us_cur; us_cur = us_nxt; us_nxt = tu;
+    }
+    return PG_OK;
+}
+
+template <int KP>
+static pg_status adjoint_recompute(pg_graph *g, float *nu, float *mu_a, float *mu_b, float *G, float *B, float *Gam,
+                                   cudaStream_t s) {
+    const int64_t n = g->n, na = g->n_active;
+    const int T = g->hist_iters;
+    const int64_t stride = n + 1;
+    const int rows_all = pg_blocks(n * KP, 256);
+    (void)rows_all;
+    // mu_T = W^T nu from the first-vertex rows [na, n)
+    PG_CUDA(cudaMemsetAsync(mu_a, 0, 4 * (size_t)(n + 1), s));
+    const float *yT = g->hist + (int64_t)T * stride;
+    recompute_scatter_kernel<KP><<<pg_blocks((n - na) * KP, 256), 256, 0, s>>>(
+        g->nbr, g->OG, g->DP, g->LV, g->succ_m, g->m2r, g->r2m, na, n, n, nu, nullptr, yT, 1, mu_a, G, B, Gam);
+    PG_LAUNCH_CHECK();
+    float *mu_cur = mu_a, *mu_nxt = mu_b;
+    for (int t = T; t >= 1; t--) {
+        PG_CUDA(cudaMemsetAsync(mu_nxt, 0, 4 * (size_t)(n + 1), s));
+        const float *y_t = g->hist + (int64_t)t * stride;
+        const float *y_p = g->hist + (int64_t)(t - 1) * stride;
+        recompute_scatter_kernel<KP><<<pg_blocks(na * KP, 256), 256, 0, s>>>(
+            g->nbr, g->OG, g->DP, g->LV, g->succ_m, g->m2r, g->r2m, 0, na, n, mu_cur, y_t, y_p, t > 1 ? 1 : 0,
+            mu_nxt, G, B, Gam);
+        PG_LAUNCH_CHECK();
+        float *tm = mu_cur; mu_cur = mu_nxt; mu_nxt = tm;
+    }
+    // output term of first-vertex rows
+    recompute_first_kernel<KP><<<pg_blocks((n - na) * KP, 256), 256, 0, s>>>(
+        g->nbr, g->OG, g->DP, g->LV, g->succ_m, g->m2r, g->r2m, na, n, nu, yT, g->D_m, G);
+    PG_LAUNCH_CHECK();
+    return PG_OK;
+}
+
+template <int KP>
+static pg_status launch_grad_g(pg_graph *g, const float *Gam, const float *B, const float *nu, float *gg_m,
+                               cudaStream_t s) {
+    const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
+    grad_g_kernel<KP><<<pg_blocks(g->n * KP, 256), 256, 0, s>>>(g->nbr, g->OG, g->DP, g->EP, g->LV, g->m2r, g->n,
+                                                               Gam, B, nu, rs, gg_m);
+    PG_LAUNCH_CHECK();
+    return PG_OK;
+}
 
 extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const int32_t *first, int64_t n_paths,
                                           int32_t spp, int32_t width, int32_t height, float *grad_sigma_s,
                                           float *grad_g, const int32_t *voxel, const float *sigma_t,
                                           float *grad_albedo_vox, int64_t n_vox, int32_t recompute_weights,
                                           pg_stream_t stream) {
-    (void)g; (void)dI; (void)first; (void)n_paths; (void)spp; (void)width; (void)height; (void)grad_sigma_s;
-    (void)grad_g; (void)voxel; (void)sigma_t; (void)grad_albedo_vox; (void)n_vox; (void)recompute_weights;
-    (void)stream;
-    return PG_ERR_UNSUPPORTED;
+    if (!g || spp <= 0 || width < 0 || height < 0) return PG_ERR_INVALID_ARG;
+    if (n_paths != (int64_t)width * height * spp) return PG_ERR_INVALID_ARG;
+    if (!g->aggregated || g->hist_iters < 0 || !g->hist) return PG_ERR_STATE;
+    if (!recompute_weights && !g->W && !g->t_W) return PG_ERR_STATE;
+    if (grad_albedo_vox && (!voxel || !sigma_t || n_vox < 0)) return PG_ERR_INVALID_ARG;
+    if (n_paths > 0 && (!dI || !first)) return PG_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->stream = s;
+    const int64_t n = g->n;
+    if (grad_albedo_vox && n_vox > 0) PG_CUDA(cudaMemsetAsync(grad_albedo_vox, 0, 4 * (size_t)n_vox, s));
+    if (n == 0) return PG_OK;
+    const bool want_g = grad_g != nullptr;
+    float *nu = nullptr, *us0 = nullptr, *mu_a = nullptr, *mu_b = nullptr, *us_a = nullptr, *us_b = nullptr;
+    float *G = nullptr, *B = nullptr, *Gam = nullptr, *gg_m = nullptr;
+    const size_t vb = 4 * (size_t)(n + 1);
+    pg_status st = PG_OK;
+#define T_ALLOC(p, bytes) \
+    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&(p), (bytes), s)
+    T_ALLOC(nu, vb);
+    T_ALLOC(us0, vb);
+    T_ALLOC(mu_a, vb);
+    T_ALLOC(mu_b, vb);
+    T_ALLOC(us_a, vb);
+    T_ALLOC(us_b, vb);
+    T_ALLOC(G, vb);
+    T_ALLOC(B, vb);
+    if (want_g) {
+        T_ALLOC(Gam, 4 * (size_t)n * g->kp);
+        T_ALLOC(gg_m, vb);
+    }
+#undef T_ALLOC
+    if (st == PG_OK) {
+        cudaMemsetAsync(nu, 0, vb, s);
+        cudaMemsetAsync(us0, 0, vb, s);
+        cudaMemsetAsync(G, 0, vb, s);
+        cudaMemsetAsync(B, 0, vb, s);
+        cudaMemsetAsync(mu_a, 0, vb, s);
+        cudaMemsetAsync(mu_b, 0, vb, s);
+        cudaMemsetAsync(us_a, 0, vb, s); // rows past n_active must read as zero
+        cudaMemsetAsync(us_b, 0, vb, s);
+        if (want_g) {
+            cudaMemsetAsync(Gam, 0, 4 * (size_t)n * g->kp, s);
+            cudaMemsetAsync(gg_m, 0, vb, s);
+        }
+        if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+    }
+    if (st == PG_OK && n_paths > 0) {
+        const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
+        seed_kernel<<<pg_blocks(n_paths, 256), 256, 0, s>>>(first, dI, n_paths, spp, n, g->c2m, g->m2r,
+                                                             recompute_weights ? nullptr : rs, nu, us0);
+        if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+        pg_count_launches(1);
+    }
+    if (st == PG_OK) {
+        if (recompute_weights) {
+            switch (g->kp) {
+                case 4: st = adjoint_recompute<4>(g, nu, mu_a, mu_b, G, B, Gam, s); break;
+                case 8: st = adjoint_recompute<8>(g, nu, mu_a, mu_b, G, B, Gam, s); break;
+                case 16: st = adjoint_recompute<16>(g, nu, mu_a, mu_b, G, B, Gam, s); break;
+                case 32: st = adjoint_recompute<32>(g, nu, mu_a, mu_b, G, B, Gam, s); break;
+                default: st = PG_ERR_UNSUPPORTED;
+            }
+        } else {
+            switch (g->wdtype) {
+                case PG_W_F32: st = adjoint_store<float>(g, nu, us0, mu_a, mu_b, us_a, us_b, G, B, Gam, s); break;
+                case PG_W_BF16:
+                    st = adjoint_store<__nv_bfloat16>(g, nu, us0, mu_a, mu_b, us_a, us_b, G, B, Gam, s);
+                    break;
+                case PG_W_F16: st = adjoint_store<__half>(g, nu, us0, mu_a, mu_b, us_a, us_b, G, B, Gam, s); break;
+            }
+            if (st == PG_OK && n_paths > 0) {
+                const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
+                const float *yT = g->hist + (int64_t)g->hist_iters * (n + 1);
+                switch (g->wdtype) {
+                    case PG_W_F32:
+                        first_rows_kernel<float><<<pg_blocks(n_paths, 256), 256, 0, s>>>(
+                            first, n_paths, n, g->c2m, g->m2r, g->col, (const float *)g->W, rs, yT, g->LV, g->D_m,
+                            nu, g->kp, G);
+                        break;
+                    case PG_W_BF16:
+                        first_rows_kernel<__nv_bfloat16><<<pg_blocks(n_paths, 256), 256, 0, s>>>(
+                            first, n_paths, n, g->c2m, g->m2r, g->col, (const __nv_bfloat16 *)g->W, rs, yT, g->LV,
+                            g->D_m, nu, g->kp, G);
+                        break;
+                    case PG_W_F16:
+                        first_rows_kernel<__half><<<pg_blocks(n_paths, 256), 256, 0, s>>>(
+                            first, n_paths, n, g->c2m, g->m2r, g->col, (const __half *)g->W, rs, yT, g->LV, g->D_m,
+                            nu, g->kp, G);
+                        break;
+                }
+                if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+                pg_count_launches(1);
+            }
+        }
+    }
+    if (st == PG_OK && (grad_sigma_s || grad_albedo_vox)) {
+        grad_sigma_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(G, g->c2m, g->m2r, g->LV, n, grad_sigma_s, voxel, sigma_t,
+                                                            grad_albedo_vox, n_vox);
+        if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+        pg_count_launches(1);
+    }
+    if (st == PG_OK && want_g) {
+        switch (g->kp) {
+            case 4: st = launch_grad_g<4>(g, Gam, B, nu, gg_m, s); break;
+            case 8: st = launch_grad_g<8>(g, Gam, B, nu, gg_m, s); break;
+            case 16: st = launch_grad_g<16>(g, Gam, B, nu, gg_m, s); break;
+            case 32: st = launch_grad_g<32>(g, Gam, B, nu, gg_m, s); break;
+            default: st = PG_ERR_UNSUPPORTED;
+        }
+        if (st == PG_OK) {
+            permute_m2c_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(gg_m, g->c2m, n, grad_g);
+            if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+            pg_count_launches(1);
+        }
+    }
+    float *bufs[] = {nu, us0, mu_a, mu_b, us_a, us_b, G, B, Gam, gg_m};
+    for (float *p : bufs)
+        if (p) cudaFreeAsync(p, s);
+    return st;
 }
 
 extern "C" pg_status pg_graph_release_weights(pg_graph *g) {
@@ -18,5 +638,8 @@ extern "C" pg_status pg_graph_release_weights(pg_graph *g) {
     size_t wb = pg_wbytes(g->wdtype);
     pg_free(g, (void **)&g->W, wb * (size_t)g->n * (size_t)g->kp);
     pg_free(g, (void **)&g->t_W, wb * (size_t)g->nnz_t);
+    pg_free(g, (void **)&g->t_row, 4 * (size_t)g->nnz_t);
+    pg_free(g, (void **)&g->t_ptr, 4 * (size_t)(g->n + 1));
+    g->nnz_t = 0;
     return PG_OK;
 }

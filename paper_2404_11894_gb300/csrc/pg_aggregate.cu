@@ -76,6 +76,14 @@ template <>
 __device__ __forceinline__ __nv_bfloat16 to_w<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
 template <>
 __device__ __forceinline__ __half to_w<__half>(float x) { return __float2half_rn(x); }
+template <typename WT>
+__device__ __forceinline__ float from_w(WT x);
+template <>
+__device__ __forceinline__ float from_w<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ float from_w<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <>
+__device__ __forceinline__ float from_w<__half>(__half x) { return __half2float(x); }
 
 // One group of KP lanes per row s (Morton order m); lane j owns neighbour
 // slot j of N(s). Strategy data (o_l, HG constants of g_l) of the row's
@@ -126,8 +134,8 @@ __global__ void __launch_bounds__(256) aggregate_kernel(
         h.C = so.w;
         h.a = ab.x;
         h.b2 = ab.y;
-        pm_d += hg_eval(h, dot3(so.x, so.y, so.z, dp.x, dp.y, dp.z));
-        pm_e += hg_eval(h, dot3(so.x, so.y, so.z, ep.x, ep.y, ep.z));
+        pm_d += hg_eval(h, one_plus_dot(so.x, so.y, so.z, dp.x, dp.y, dp.z));
+        pm_e += hg_eval(h, one_plus_dot(so.x, so.y, so.z, ep.x, ep.y, ep.z));
     }
     // receiver s = slot 0 of the group
     const float4 so = s_o[gbase];
@@ -139,8 +147,8 @@ __global__ void __launch_bounds__(256) aggregate_kernel(
     const int src = lane & ~(KP - 1);
     const float sig_s = __shfl_sync(0xffffffffu, lv.z, src);
     const float w_s = __shfl_sync(0xffffffffu, lv.w, src);
-    float rho_sd = hg_eval(hs, dot3(so.x, so.y, so.z, dp.x, dp.y, dp.z));
-    float rho_se = hg_eval(hs, dot3(so.x, so.y, so.z, ep.x, ep.y, ep.z));
+    float rho_sd = hg_eval(hs, one_plus_dot(so.x, so.y, so.z, dp.x, dp.y, dp.z));
+    float rho_se = hg_eval(hs, one_plus_dot(so.x, so.y, so.z, ep.x, ep.y, ep.z));
     float A = 0.0f, term = 0.0f;
     if (valid) {
         A = sig_s * rho_sd / pm_d;
@@ -171,8 +179,27 @@ __global__ void __launch_bounds__(256) aggregate_kernel(
         for (int o = KP / 2; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         scale = mx > 0.0f ? mx : 1.0f;
     }
+    // 16-bit payload: round along the row with error diffusion over the
+    // entries the sweep uses (slot order), so the row's total weight is kept
+    // to within half an ulp of one entry and the rounding errors cancel
+    // against the slowly varying radiance of neighbouring samples.
+    WT wq = to_w<WT>(Wt);
+    if (WTraits<WT>::id != PG_W_F32) {
+        const bool live = valid && sj >= 0;
+        const float x = Wt / scale;
+        float carry = 0.0f;
+#pragma unroll
+        for (int l = 0; l < KP; l++) {
+            if (j == l) {
+                float v = live ? x + carry : x;
+                wq = to_w<WT>(v);
+                if (live) carry = v - from_w<WT>(wq);
+            }
+            carry = __shfl_sync(0xffffffffu, carry, src + l);
+        }
+    }
     if (row_ok) {
-        W[(int64_t)r * KP + j] = to_w<WT>(WTraits<WT>::id == PG_W_F32 ? Wt : Wt / scale);
+        W[(int64_t)r * KP + j] = wq;
         col[(int64_t)r * KP + j] = cl;
         if (j == 0) {
             b[r] = w_s * c;

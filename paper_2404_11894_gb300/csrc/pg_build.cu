@@ -363,8 +363,7 @@ static pg_status graph_free_all(pg_graph *g) {
 
 extern "C" void pg_graph_destroy(pg_graph *g) {
     if (!g) return;
-    graph_free_all(g);
-    cudaStreamSynchronize(g->stream);
+    graph_free_all(g); // stream-ordered frees: no synchronisation needed
     (void)cudaGetLastError();
     delete g;
 }

@@ -92,7 +92,11 @@ struct pg_graph {
         }                                              \
     } while (0)
 
-#define PG_LAUNCH_CHECK() PG_CUDA(cudaGetLastError())
+#define PG_LAUNCH_CHECK()     \
+    do {                      \
+        pg_count_launches(1); \
+        PG_CUDA(cudaGetLastError()); \
+    } while (0)
 
 static inline int pg_blocks(int64_t work, int threads) {
     int64_t b = (work + threads - 1) / threads;
@@ -102,6 +106,7 @@ static inline int pg_blocks(int64_t work, int threads) {
 pg_status pg_alloc(pg_graph *g, void **p, size_t bytes, cudaStream_t s);
 void pg_free(pg_graph *g, void **p, size_t bytes);
 int pg_num_sms();
+void pg_count_launches(int k); // diagnostic count of kernel launches
 
 // Stable LSD radix sort of (key, value) pairs by key bits [0, nbits).
 pg_status pg_radix_sort(pg_graph *g, uint32_t *keys, int32_t *vals, int64_t n, int nbits, cudaStream_t s);
@@ -109,10 +114,42 @@ pg_status pg_radix_sort(pg_graph *g, uint32_t *keys, int32_t *vals, int64_t n, i
 pg_status pg_scan_exclusive(pg_graph *g, int32_t *data, int64_t n, int32_t *d_total, cudaStream_t s);
 
 // ------------------------------------------------------------------ device math
+// 1 + a.b for unit vectors, with the rounding errors of the three products
+// and two sums carried along (error-free transformations: TwoProduct by FMA,
+// TwoSum by Knuth's six-operation form). Near the forward peak of a
+// phase function 1 + a.b is tiny and a plain float32 dot product would lose
+// most of its digits. Explicit _rn intrinsics keep the compiler from fusing
+// the sums into FMAs, which would break the error-free transformations.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+__device__ __forceinline__ float one_plus_dot(float ax, float ay, float az, float bx, float by, float bz) {
+    float p = __fmul_rn(ax, bx);
+    float err = __fmaf_rn(ax, bx, -p);
+    float h = __fmul_rn(ay, by);
+    float f = __fmaf_rn(ay, by, -h);
+    float s, q;
+    two_sum(p, h, s, q);
+    err = __fadd_rn(err, __fadd_rn(f, q));
+    h = __fmul_rn(az, bz);
+    f = __fmaf_rn(az, bz, -h);
+    two_sum(s, h, p, q);
+    err = __fadd_rn(err, __fadd_rn(f, q));
+    two_sum(1.0f, p, s, q);
+    return __fadd_rn(s, __fadd_rn(q, err));
+}
+// rsqrt refined by one Newton step (the hardware estimate alone is ~2 ulp)
+__device__ __forceinline__ float rsqrt_nr(float x) {
+    float r = rsqrtf(x);
+    return r * fmaf(-0.5f * x, r * r, 1.5f);
+}
+
 // Henyey-Greenstein rho(o, d) with mu = -o.d, written as
 //   (1-g^2)/(4 pi) * den^(-3/2),  den = (1-g)^2 + 2 g (1 + o.d)
-// (equal to 1 + g^2 - 2 g mu); this form keeps the forward peak accurate in
-// float32. hgc holds (C = (1-g^2)/(4 pi), (1-g)^2, 2g) for the strategy.
+// (equal to 1 + g^2 - 2 g mu). hgc holds (C = (1-g^2)/(4 pi), (1-g)^2, 2g)
+// for the strategy; opd is 1 + o.d from one_plus_dot.
 struct HGc {
     float C, a, b2;
 };
@@ -125,25 +162,21 @@ __device__ __forceinline__ HGc hg_consts(float g) {
     h.b2 = 2.0f * g;
     return h;
 }
-__device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, float by, float bz) {
-    return fmaf(az, bz, fmaf(ay, by, ax * bx));
+__device__ __forceinline__ float hg_eval(const HGc &h, float opd) {
+    float den = fmaf(h.b2, opd, h.a);
+    float r = rsqrt_nr(den);
+    return h.C * (r * r * r);
 }
-__device__ __forceinline__ float hg_eval(const HGc &h, float od) {
-    float den = fmaf(h.b2, 1.0f + od, h.a);
-    float r = rsqrtf(den);
-    return h.C * r * r * r;
-}
-// d rho / d g = rho * ( -2g/(1-g^2) - 3 (g - mu) / den ),  mu = -o.d
-__device__ __forceinline__ float hg_eval_dg(float g, float od, float *rho_out) {
+// d rho / d g = -2g/(4 pi) den^-3/2 - 3 (1-g^2)/(4 pi) (g + o.d) den^-5/2
+__device__ __forceinline__ float hg_eval_dg(float g, float opd, float *rho_out) {
     const float inv4pi = 0.0795774715459476679f;
     float omg = 1.0f - g;
-    float den = fmaf(2.0f * g, 1.0f + od, omg * omg);
-    float r = rsqrtf(den);
-    float rho = (1.0f - g * g) * inv4pi * r * r * r;
-    *rho_out = rho;
-    // -2g/(4pi) den^-3/2 - 1.5 (1-g^2)/(4pi) (2g + 2 od) den^-5/2
+    float den = fmaf(2.0f * g, opd, omg * omg);
+    float r = rsqrt_nr(den);
     float r3 = r * r * r;
-    return -2.0f * g * inv4pi * r3 - 3.0f * (1.0f - g * g) * inv4pi * (g + od) * r3 * r * r;
+    float C = (1.0f - g * g) * inv4pi;
+    *rho_out = C * r3;
+    return -2.0f * g * inv4pi * r3 - 3.0f * C * ((g - 1.0f) + opd) * (r3 * r * r);
 }
 
 __device__ __forceinline__ uint32_t part1by2(uint32_t x) {

@@ -80,24 +80,42 @@ __global__ void __launch_bounds__(SWEEP_THREADS) sweep_kernel(
     constexpr int LPR = KP / 4;
     const int lane = threadIdx.x & 31;
     const int q = lane & (LPR - 1);
-    const int64_t total = n_active * LPR;
-    const int64_t total_w = (total + 31) & ~(int64_t)31; // whole warps iterate together
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // Each block owns one contiguous chunk of rows and walks it in order:
+    // rows are in Morton order, so consecutive rows share most neighbour
+    // columns and their y gathers hit in this SM's L1.
+    constexpr int RPB = SWEEP_THREADS / LPR; // rows per block iteration
+    const int64_t chunk = ((n_active + gridDim.x - 1) / gridDim.x + RPB - 1) / RPB * RPB;
+    const int64_t r0 = (int64_t)blockIdx.x * chunk;
+    const int64_t r1 = min(n_active, r0 + chunk);
     float rd = 0.0f, rn = 0.0f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total_w; i += stride) {
-        const int64_t row = i / LPR;
-        const bool ok = i < total;
-        float acc = 0.0f;
+    for (int64_t base = r0; base < r1; base += RPB) { // uniform across the block
+        const int64_t row = base + threadIdx.x / LPR;
+        const bool ok = row < r1;
+        // compensated sum of the row's products (the kernel is memory-bound,
+        // so the extra additions are free; they keep 30+ sweeps at albedo
+        // ~1 within float32 rounding of the exact iterate)
+        float acc = 0.0f, cmp = 0.0f;
         if (ok) {
             const int4 c4 = __ldcs(reinterpret_cast<const int4 *>(col + row * KP) + q);
             const float4 w4 = W4<WT>::load(W + row * KP + q * 4);
-            acc = w4.x * __ldg(yin + c4.x);
-            acc = fmaf(w4.y, __ldg(yin + c4.y), acc);
-            acc = fmaf(w4.z, __ldg(yin + c4.z), acc);
-            acc = fmaf(w4.w, __ldg(yin + c4.w), acc);
+            const float p0 = __fmul_rn(w4.x, __ldg(yin + c4.x));
+            const float p1 = __fmul_rn(w4.y, __ldg(yin + c4.y));
+            const float p2 = __fmul_rn(w4.z, __ldg(yin + c4.z));
+            const float p3 = __fmul_rn(w4.w, __ldg(yin + c4.w));
+            float e;
+            two_sum(p0, p1, acc, cmp);
+            two_sum(acc, p2, acc, e);
+            cmp = __fadd_rn(cmp, e);
+            two_sum(acc, p3, acc, e);
+            cmp = __fadd_rn(cmp, e);
         }
 #pragma unroll
-        for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        for (int o = LPR / 2; o > 0; o >>= 1) {
+            float oa = __shfl_xor_sync(0xffffffffu, acc, o), oc = __shfl_xor_sync(0xffffffffu, cmp, o), e;
+            two_sum(acc, oa, acc, e);
+            cmp = __fadd_rn(cmp, __fadd_rn(oc, e));
+        }
+        acc = __fadd_rn(acc, cmp);
         if (ok && q == 0) {
             const float s = WTraits<WT>::id == PG_W_F32 ? 1.0f : rscale[row];
             const float yn = fmaf(acc, s, b[row]);
@@ -275,7 +293,8 @@ extern "C" pg_status pg_propagate(pg_graph *g, const float *c, const float *L0, 
     if (buser) cudaFreeAsync(buser, s);
     if (st != PG_OK) return st;
     if (keep_history) g->hist_iters = iters;
-    if (residual || iters_done) {
+    // with early stopping the stored history ends at the last sweep that ran
+    if (residual || iters_done || (keep_history && tol > 0.0)) {
         int32_t ctrl[4] = {0, 0, 0, 0};
         PG_CUDA(cudaMemcpyAsync(ctrl, g->d_ctrl, 16, cudaMemcpyDeviceToHost, s));
         if (residual && iters > 0)

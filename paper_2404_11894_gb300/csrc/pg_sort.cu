@@ -1,8 +1,31 @@
 // Device primitives: stream-ordered allocation, exclusive scan, and a stable
 // LSD radix sort of (uint32 key, int32 value) pairs.
+#include <atomic>
+
 #include "pg_internal.cuh"
 
+static std::atomic<long long> g_launches{0};
+void pg_count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+extern "C" int64_t pg_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+// Keep freed blocks in the device's default stream-ordered pool instead of
+// returning them to the driver at every synchronisation, so a graph rebuilt
+// every frame reuses its memory.
+static void pool_keep_memory() {
+    static bool done = false;
+    if (done) return;
+    done = true;
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    (void)cudaGetLastError();
+}
+
 pg_status pg_alloc(pg_graph *g, void **p, size_t bytes, cudaStream_t s) {
+    pool_keep_memory();
     *p = nullptr;
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMallocAsync(p, bytes, s);

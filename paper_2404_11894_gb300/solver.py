@@ -1,0 +1,82 @@
+"""The whole hot path as one call: graph, aggregation, propagation, output
+and (optionally) the adjoint of an L2 image loss."""
+from __future__ import annotations
+
+import torch
+
+from . import pg_aggregate, pg_build_graph, pg_gather, pg_propagate, pg_propagate_adjoint, Vertices
+
+
+class Solver:
+    """Runs the path-graph hot path on device-resident records.
+
+    k: neighbours per vertex (self included); iters: propagation sweeps;
+    wdtype: 'f32' | 'bf16' | 'f16' edge weights; adjoint: also run
+    pg_propagate_adjoint for the loss 1/2 |image - target|^2.
+    """
+
+    def __init__(self, k: int, iters: int, wdtype: str = "f32", adjoint: bool = True,
+                 bbox_lo=(0.0, 0.0, 0.0), bbox_hi=(1.0, 1.0, 1.0), recompute_weights: bool = False):
+        self.k, self.iters, self.wdtype, self.adjoint = k, iters, wdtype, adjoint
+        self.bbox_lo, self.bbox_hi = bbox_lo, bbox_hi
+        self.recompute_weights = recompute_weights
+        self.graph = None
+        self.last_image = None
+        self.grads = None
+
+    def step(self, V: Vertices, L0, first, bg, spp, width, height, target=None, marks=None):
+        """One pass; ``marks`` maps stage names to (start, end) CUDA events."""
+        def mark(name, i):
+            if marks is not None and name in marks:
+                marks[name][i].record(torch.cuda.current_stream())
+
+        if self.graph is not None:
+            self.graph.close()
+        mark("build", 0)
+        self.graph = pg_build_graph(V, self.k, self.bbox_lo, self.bbox_hi)
+        mark("build", 1)
+        mark("aggregate", 0)
+        self._c, self.D = pg_aggregate(self.graph, V, self.wdtype)
+        mark("aggregate", 1)
+        self._L0 = L0
+        mark("propagate", 0)
+        use_adj = self.adjoint and target is not None
+        self.L = pg_propagate(self.graph, L0, self.iters, keep_history=use_adj)
+        mark("propagate", 1)
+        mark("gather", 0)
+        img = pg_gather(self.graph, self.L, self.D, first, bg, spp, width, height)
+        mark("gather", 1)
+        self.last_image = img
+        if use_adj:
+            mark("adjoint", 0)
+            dI = img - target
+            self.grads = pg_propagate_adjoint(self.graph, dI, first, spp, width, height,
+                                              recompute_weights=self.recompute_weights)
+            mark("adjoint", 1)
+        return img
+
+    def time_propagate(self, iters: int, reps: int = 3) -> float:
+        """Mean device time (ms) of pg_propagate on the current graph."""
+        s = torch.cuda.current_stream()
+        L = torch.empty_like(self._L0)
+        pg_propagate(self.graph, self._L0, iters, out=L)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            pg_propagate(self.graph, self._L0, iters, out=L)
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def solve_host(self, host: dict, host_target, spp, width, height):
+        """End to end from pinned host records to the image on the host."""
+        dev = {k: v.to("cuda", non_blocking=True) for k, v in host.items()}
+        tgt = host_target.to("cuda", non_blocking=True) if host_target is not None else None
+        V = Vertices({k: dev[k] for k in dev if k not in ("L0", "first", "bg")})
+        img = self.step(V, dev["L0"], dev["first"], dev["bg"], spp, width, height, tgt)
+        return img.to("cpu")
+
+    def close(self):
+        if self.graph is not None:
+            self.graph.close()
+            self.graph = None

@@ -240,3 +240,49 @@ def subset_paths(rec: dict, path_lo: int, path_hi: int) -> dict:
     out["n"] = v1 - v0
     out["n_paths"] = path_hi - path_lo
     return out
+
+
+def sample_pixels(rec: dict, width: int, height: int, spp: int, stride: int) -> dict:
+    """Records of the paths of every `stride`-th pixel in x and y (all spp),
+    re-indexed from zero; the result is a (height/stride x width/stride)
+    image's worth of paths with every path's vertices still contiguous."""
+    ys = np.arange(0, height, stride)
+    xs = np.arange(0, width, stride)
+    pix = (ys[:, None] * width + xs[None, :]).reshape(-1)
+    paths = (pix[:, None] * spp + np.arange(spp)[None, :]).reshape(-1)
+    first = rec["first"][paths]
+    # vertex ranges of the chosen paths (a path runs from first along succ)
+    starts, lens = [], []
+    succ = rec["succ"]
+    for f in first:
+        if f < 0:
+            lens.append(0)
+            starts.append(0)
+            continue
+        v, ln = int(f), 1
+        while succ[v] >= 0:
+            v = int(succ[v])
+            ln += 1
+        starts.append(int(f))
+        lens.append(ln)
+    lens = np.array(lens, np.int64)
+    starts = np.array(starts, np.int64)
+    idx = np.concatenate([np.arange(s, s + ln) for s, ln in zip(starts, lens) if ln > 0]) if lens.sum() else \
+        np.zeros(0, np.int64)
+    new_first = np.where(lens > 0, np.concatenate([[0], np.cumsum(lens)[:-1]]), -1).astype(np.int32)
+    out = {f: np.ascontiguousarray(rec[f][idx]) for f in F32_FIELDS + ("L0_f64", "e_delta", "voxel")}
+    old2new = np.full(rec["n"], -1, np.int64)
+    old2new[idx] = np.arange(len(idx))
+    s = succ[idx].astype(np.int64)
+    out["succ"] = np.where(s >= 0, old2new[np.where(s >= 0, s, 0)], -1).astype(np.int32)
+    out["first"] = new_first
+    out["bg"] = np.ascontiguousarray(rec["bg"][paths])
+    out["pt_value"] = np.ascontiguousarray(rec["pt_value"][paths])
+    for k in ("density", "albedo_grid", "majorant"):
+        out[k] = rec[k]
+    out["spp"] = spp
+    out["width"] = len(xs)
+    out["height"] = len(ys)
+    out["n"] = int(len(idx))
+    out["n_paths"] = int(len(paths))
+    return out

@@ -25,9 +25,9 @@ def _declared():
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2404_11894_gb300 import build
+    import __graft_entry__
 
-    build.build()
+    __graft_entry__._build_module().build()
     from paper_2404_11894_gb300 import _lib
 
     return _lib.load()

@@ -1,0 +1,150 @@
+"""GPU adjoint (pg_propagate_adjoint) against the FP64 oracle's adjoint and
+central finite differences of the oracle's forward map.
+
+Bar: |g - g_ref| <= 1e-3 max(|g_ref|, 1e-3 max|g_ref|) per element.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import pgrec
+
+pytestmark = pytest.mark.gpu
+
+ADJ_TOL = 1e-3
+
+
+def adj_err(got, ref):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    den = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max() + 1e-300)
+    return float((np.abs(got - ref) / den).max())
+
+
+@pytest.fixture(scope="module")
+def pg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2404_11894_gb300 as pg
+
+    return pg
+
+
+def _setup(sc, T, seed=5):
+    rec = pgrec.trace(sc)
+    q = oracle.quantize(rec["px"], rec["py"], rec["pz"], (0, 0, 0), (1, 1, 1))
+    nbr = oracle.knn(q, sc.k)
+    rng = np.random.default_rng(seed)
+    # target: the same pipeline with a perturbed per-voxel albedo
+    G = sc.grid_res
+    pert = rng.uniform(-0.03, 0.03, G ** 3)
+    sig_t = rec["sigma_t"].astype(np.float64)
+    sig_tgt = (sc.albedo + pert[rec["voxel"]]) * sig_t
+    target = oracle.forward(rec, rec["first"], rec["bg"], sc.spp, sc.width, sc.height, sc.k, T, nbr=nbr,
+                            sigma_s=sig_tgt)["image"]
+    base = oracle.forward(rec, rec["first"], rec["bg"], sc.spp, sc.width, sc.height, sc.k, T, nbr=nbr)
+    _, dI = oracle.image_loss(base["image"], target)
+    return rec, nbr, target, dI
+
+
+def _gpu_adjoint(pg, rec, sc, T, dI, wdtype="f32", recompute=False, want_g=True):
+    V = pg.Vertices.from_records(rec)
+    graph = pg.pg_build_graph(V, sc.k)
+    _, D = pg.pg_aggregate(graph, V, wdtype)
+    L = pg.pg_propagate(graph, torch.from_numpy(rec["L0"]).cuda(), T, keep_history=True)
+    first = torch.from_numpy(rec["first"]).cuda()
+    pg.pg_gather(graph, L, D, first, torch.from_numpy(rec["bg"]).cuda(), sc.spp, sc.width, sc.height)
+    if recompute:
+        graph.release_weights()
+    out = pg.pg_propagate_adjoint(graph, torch.from_numpy(np.asarray(dI, np.float32)).cuda(), first, sc.spp,
+                                  sc.width, sc.height, want_g=want_g,
+                                  voxel=torch.from_numpy(rec["voxel"]).cuda(),
+                                  sigma_t=torch.from_numpy(rec["sigma_t"]).cuda(), n_vox=sc.grid_res ** 3,
+                                  recompute_weights=recompute)
+    torch.cuda.synchronize()
+    return {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+
+
+SMALL = pgrec.CLOUD64_GRAD.with_(width=32, height=32, spp=4, k=16)
+
+
+@pytest.fixture(scope="module")
+def small(pg):
+    T = 10
+    rec, nbr, target, dI = _setup(SMALL, T)
+    ref = oracle.adjoint(rec, nbr, T, rec["L0"], dI, rec["first"], rec["bg"], SMALL.spp, SMALL.width, SMALL.height,
+                         voxel=rec["voxel"], n_vox=SMALL.grid_res ** 3)
+    return rec, T, dI, ref
+
+
+@pytest.mark.parametrize("recompute", [False, True], ids=["stored", "recompute"])
+def test_adjoint_matches_oracle(pg, small, recompute):
+    rec, T, dI, ref = small
+    got = _gpu_adjoint(pg, rec, SMALL, T, dI, recompute=recompute)
+    assert adj_err(got["grad_sigma_s"], ref["grad_sigma_s"]) <= ADJ_TOL
+    assert adj_err(got["grad_g"], ref["grad_g"]) <= ADJ_TOL
+    assert adj_err(got["grad_albedo"], ref["grad_albedo"]) <= ADJ_TOL
+
+
+@pytest.mark.parametrize("wdtype", ["bf16", "f16"])
+def test_adjoint_16bit(pg, small, wdtype):
+    rec, T, dI, ref = small
+    got = _gpu_adjoint(pg, rec, SMALL, T, dI, wdtype=wdtype, want_g=False)
+    # the map differs from the FP64 one by the 16-bit weight rounding
+    assert adj_err(got["grad_albedo"], ref["grad_albedo"]) <= 2e-2
+
+
+def test_adjoint_voxels_finite_differences(pg):
+    """Per-voxel albedo gradient on 64 random occupied voxels against the
+    oracle's adjoint, and the directional derivative along those 64 voxels
+    against a central difference (h = 1e-3) of the oracle's forward map."""
+    sc = pgrec.CLOUD64_GRAD.with_(width=48, height=48, spp=4)
+    T = sc.iters
+    rec, nbr, target, dI = _setup(sc, T, seed=7)
+    got = _gpu_adjoint(pg, rec, sc, T, dI, want_g=False)
+    ref = oracle.adjoint(rec, nbr, T, rec["L0"], dI, rec["first"], rec["bg"], sc.spp, sc.width, sc.height,
+                         voxel=rec["voxel"], n_vox=sc.grid_res ** 3)
+    rng = np.random.default_rng(1)
+    vox = rng.choice(np.unique(rec["voxel"]), 64, replace=False)
+    ga, gr = got["grad_albedo"][vox], ref["grad_albedo"][vox]
+    assert adj_err(ga, gr) <= ADJ_TOL
+    # directional central difference along a random combination of the voxels
+    dirn = rng.normal(size=64)
+    delta = np.zeros(sc.grid_res ** 3)
+    delta[vox] = dirn
+    h = 1e-3
+    sig0 = rec["sigma_s"].astype(np.float64)
+    st = rec["sigma_t"].astype(np.float64)
+
+    def loss(sig):
+        img = oracle.forward(rec, rec["first"], rec["bg"], sc.spp, sc.width, sc.height, sc.k, T, nbr=nbr,
+                             sigma_s=sig)["image"]
+        return oracle.image_loss(img, target)[0]
+
+    fd = (loss(sig0 + h * delta[rec["voxel"]] * st) - loss(sig0 - h * delta[rec["voxel"]] * st)) / (2 * h)
+    assert float(ga @ dirn) == pytest.approx(fd, rel=ADJ_TOL)
+
+
+def test_autograd_function(pg):
+    from paper_2404_11894_gb300.autograd import render
+
+    sc = pgrec.CLOUD64_GRAD.with_(width=24, height=24, spp=2, k=8)
+    rec = pgrec.trace(sc)
+    t = {k: torch.from_numpy(np.ascontiguousarray(rec[k])).cuda() for k in pg.VERTEX_F32 + ("e_delta", "succ")}
+    sig = t["sigma_s"].clone().requires_grad_(True)
+    g = t["g"].clone().requires_grad_(True)
+    L0 = torch.from_numpy(rec["L0"]).cuda()
+    first = torch.from_numpy(rec["first"]).cuda()
+    bg = torch.from_numpy(rec["bg"]).cuda()
+    target = torch.from_numpy(rec["pt_image"].astype(np.float32)).cuda() * 0.9
+    img = render(sig, g, t, L0, first, bg, sc.spp, sc.width, sc.height, k=sc.k, iters=6)
+    loss = 0.5 * ((img - target) ** 2).sum()
+    loss.backward()
+    q = oracle.quantize(rec["px"], rec["py"], rec["pz"], (0, 0, 0), (1, 1, 1))
+    nbr = oracle.knn(q, sc.k)
+    base = oracle.forward(rec, rec["first"], rec["bg"], sc.spp, sc.width, sc.height, sc.k, 6, nbr=nbr)
+    _, dI = oracle.image_loss(base["image"], target.cpu().numpy())
+    ref = oracle.adjoint(rec, nbr, 6, rec["L0"], dI, rec["first"], rec["bg"], sc.spp, sc.width, sc.height)
+    assert adj_err(sig.grad.cpu().numpy(), ref["grad_sigma_s"]) <= ADJ_TOL
+    assert adj_err(g.grad.cpu().numpy(), ref["grad_g"]) <= ADJ_TOL
