@@ -116,9 +116,11 @@ def run_gpu(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
+    from paper_2404_11894_gb300.dist import combine_throughput, rank_seed
+
     sc = pgrec.CLOUD128
     if world > 1:  # independent renders (replicas), one per rank
-        sc = sc.with_(seed=sc.seed + rank)
+        sc = sc.with_(seed=rank_seed(sc.seed, rank))
     rec = pgrec.trace(sc)
     n, P = rec["n"], rec["n_paths"]
     dev = torch.device("cuda", local)
@@ -170,16 +172,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = pg.launch_count() - launches0
-    t_dev = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_dev], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_dev = float(tt.item())
-        eu = torch.tensor([float(edge_updates_step)], device=dev)
-        torch.distributed.all_reduce(eu)
-        total_updates = float(eu.item()) * args.steps
-    else:
-        total_updates = float(edge_updates_step) * args.steps
+    t_dev, total_updates = combine_throughput(e0.elapsed_time(e1) / 1e3, float(edge_updates_step) * args.steps,
+                                              device=dev)
     stage_ms = {nm: float(np.mean([m[nm][0].elapsed_time(m[nm][1]) for m in marks_all if m[nm][0].query()]))
                 for nm in stage_names if not (args.no_adjoint and nm == "adjoint")}
 

@@ -411,6 +411,7 @@ static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
     PG_CUDA(cudaMemsetAsync(cnt, 0, 4 * (size_t)(n + 1), s));
     PG_CUDA(cudaMemsetAsync(fill, 0, 4 * (size_t)(n + 1), s));
     tcount_kernel<<<pg_blocks(n * kp, 256), 256, 0, s>>>(g->col, n, kp, cnt);
+    pg_count_launches(1);
     PG_LAUNCH_CHECK();
     PG_TRY(pg_scan_exclusive(g, g->t_ptr, n + 1, d_total, s));
     int32_t h_total = 0;
@@ -421,8 +422,10 @@ static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
     PG_TRY(pg_alloc(g, (void **)&g->t_W, sizeof(WT) * (size_t)(h_total > 0 ? h_total : 1), s));
     tfill_kernel<WT><<<pg_blocks(n * kp, 256), 256, 0, s>>>(g->col, (const WT *)g->W, n, kp, g->t_ptr, fill,
                                                             g->t_row, (WT *)g->t_W);
+    pg_count_launches(1);
     PG_LAUNCH_CHECK();
     tsort_kernel<WT><<<pg_blocks(n, 128), 128, 0, s>>>(g->t_ptr, n, g->t_row, (WT *)g->t_W);
+    pg_count_launches(1);
     PG_LAUNCH_CHECK();
     cudaFreeAsync(fill, s);
     cudaFreeAsync(d_total, s);
@@ -442,11 +445,13 @@ static pg_status adjoint_store(pg_graph *g, float *nu, float *us0, float *mu_a, 
     float *mu_cur = mu_a, *us_cur = us_a, *mu_nxt = mu_b, *us_nxt = us_b;
     tsweep_kernel<WT><<<tb, 256, 0, s>>>(g->t_ptr, g->t_row, (const WT *)g->t_W, us0, nullptr, nullptr, rs, na, 1,
                                          mu_cur, us_cur, G, B);
+    pg_count_launches(1);
     PG_LAUNCH_CHECK();
     if (Gam) {
         // output term of the per-edge adjoint: Gamma[f][i] = nu_f y_T[col]
         gamma_kernel<<<pg_blocks((n - na) * g->kp, 256), 256, 0, s>>>(g->col, nu, g->hist + (int64_t)T * stride, na,
                                                                         n, g->kp, Gam);
+        pg_count_launches(1);
         PG_LAUNCH_CHECK();
     }
     for (int t = T; t >= 1; t--) {
@@ -454,10 +459,12 @@ static pg_status adjoint_store(pg_graph *g, float *nu, float *us0, float *mu_a, 
         if (Gam) {
             gamma_kernel<<<pg_blocks(na * g->kp, 256), 256, 0, s>>>(g->col, mu_cur, g->hist + (int64_t)(t - 1) * stride,
                                                                    0, na, g->kp, Gam);
+            pg_count_launches(1);
             PG_LAUNCH_CHECK();
         }
         tsweep_kernel<WT><<<tb, 256, 0, s>>>(g->t_ptr, g->t_row, (const WT *)g->t_W, us_cur, mu_cur, y_t, rs, na,
                                              t > 1 ? 1 : 0, mu_nxt, us_nxt, G, B);
+        pg_count_launches(1);
         PG_LAUNCH_CHECK();
         float *tm = mu_cur; mu_cur = mu_nxt; mu_nxt = tm;
         float *tu = us_cur; us_cur = us_nxt; us_nxt = tu;
@@ -478,6 +485,7 @@ static pg_status adjoint_recompute(pg_graph *g, float *nu, float *mu_a, float *m
     const float *yT = g->hist + (int64_t)T * stride;
     recompute_scatter_kernel<KP><<<pg_blocks((n - na) * KP, 256), 256, 0, s>>>(
         g->nbr, g->OG, g->DP, g->LV, g->succ_m, g->m2r, g->r2m, na, n, n, nu, nullptr, yT, 1, mu_a, G, B, Gam);
+    pg_count_launches(1);
     PG_LAUNCH_CHECK();
     float *mu_cur = mu_a, *mu_nxt = mu_b;
     for (int t = T; t >= 1; t--) {
@@ -487,12 +495,14 @@ static pg_status adjoint_recompute(pg_graph *g, float *nu, float *mu_a, float *m
         recompute_scatter_kernel<KP><<<pg_blocks(na * KP, 256), 256, 0, s>>>(
             g->nbr, g->OG, g->DP, g->LV, g->succ_m, g->m2r, g->r2m, 0, na, n, mu_cur, y_t, y_p, t > 1 ? 1 : 0,
             mu_nxt, G, B, Gam);
+        pg_count_launches(1);
         PG_LAUNCH_CHECK();
         float *tm = mu_cur; mu_cur = mu_nxt; mu_nxt = tm;
     }
     // output term of first-vertex rows
     recompute_first_kernel<KP><<<pg_blocks((n - na) * KP, 256), 256, 0, s>>>(
         g->nbr, g->OG, g->DP, g->LV, g->succ_m, g->m2r, g->r2m, na, n, nu, yT, g->D_m, G);
+    pg_count_launches(1);
     PG_LAUNCH_CHECK();
     return PG_OK;
 }
@@ -503,6 +513,7 @@ static pg_status launch_grad_g(pg_graph *g, const float *Gam, const float *B, co
     const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
     grad_g_kernel<KP><<<pg_blocks(g->n * KP, 256), 256, 0, s>>>(g->nbr, g->OG, g->DP, g->EP, g->LV, g->m2r, g->n,
                                                                Gam, B, nu, rs, gg_m);
+    pg_count_launches(1);
     PG_LAUNCH_CHECK();
     return PG_OK;
 }
@@ -562,8 +573,8 @@ extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const in
         const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
         seed_kernel<<<pg_blocks(n_paths, 256), 256, 0, s>>>(first, dI, n_paths, spp, n, g->c2m, g->m2r,
                                                              recompute_weights ? nullptr : rs, nu, us0);
-        if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
         pg_count_launches(1);
+        if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     }
     if (st == PG_OK) {
         if (recompute_weights) {
@@ -590,28 +601,30 @@ extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const in
                         first_rows_kernel<float><<<pg_blocks(n_paths, 256), 256, 0, s>>>(
                             first, n_paths, n, g->c2m, g->m2r, g->col, (const float *)g->W, rs, yT, g->LV, g->D_m,
                             nu, g->kp, G);
+                        pg_count_launches(1);
                         break;
                     case PG_W_BF16:
                         first_rows_kernel<__nv_bfloat16><<<pg_blocks(n_paths, 256), 256, 0, s>>>(
                             first, n_paths, n, g->c2m, g->m2r, g->col, (const __nv_bfloat16 *)g->W, rs, yT, g->LV,
                             g->D_m, nu, g->kp, G);
+                        pg_count_launches(1);
                         break;
                     case PG_W_F16:
                         first_rows_kernel<__half><<<pg_blocks(n_paths, 256), 256, 0, s>>>(
                             first, n_paths, n, g->c2m, g->m2r, g->col, (const __half *)g->W, rs, yT, g->LV, g->D_m,
                             nu, g->kp, G);
+                        pg_count_launches(1);
                         break;
                 }
                 if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
-                pg_count_launches(1);
-            }
+                    }
         }
     }
     if (st == PG_OK && (grad_sigma_s || grad_albedo_vox)) {
         grad_sigma_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(G, g->c2m, g->m2r, g->LV, n, grad_sigma_s, voxel, sigma_t,
                                                             grad_albedo_vox, n_vox);
-        if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
         pg_count_launches(1);
+        if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     }
     if (st == PG_OK && want_g) {
         switch (g->kp) {
@@ -623,9 +636,9 @@ extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const in
         }
         if (st == PG_OK) {
             permute_m2c_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(gg_m, g->c2m, n, grad_g);
-            if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
             pg_count_launches(1);
-        }
+            if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+            }
     }
     float *bufs[] = {nu, us0, mu_a, mu_b, us_a, us_b, G, B, Gam, gg_m};
     for (float *p : bufs)

@@ -179,25 +179,10 @@ __global__ void __launch_bounds__(256) aggregate_kernel(
         for (int o = KP / 2; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         scale = mx > 0.0f ? mx : 1.0f;
     }
-    // 16-bit payload: round along the row with error diffusion over the
-    // entries the sweep uses (slot order), so the row's total weight is kept
-    // to within half an ulp of one entry and the rounding errors cancel
-    // against the slowly varying radiance of neighbouring samples.
-    WT wq = to_w<WT>(Wt);
-    if (WTraits<WT>::id != PG_W_F32) {
-        const bool live = valid && sj >= 0;
-        const float x = Wt / scale;
-        float carry = 0.0f;
-#pragma unroll
-        for (int l = 0; l < KP; l++) {
-            if (j == l) {
-                float v = live ? x + carry : x;
-                wq = to_w<WT>(v);
-                if (live) carry = v - from_w<WT>(wq);
-            }
-            carry = __shfl_sync(0xffffffffu, carry, src + l);
-        }
-    }
+    // 16-bit payload: the row's weights relative to its largest one, rounded
+    // to nearest (error diffusion along the row was measured to be worse:
+    // the gathered radiance of a row's columns is far from uniform)
+    const WT wq = to_w<WT>(WTraits<WT>::id == PG_W_F32 ? Wt : Wt / scale);
     if (row_ok) {
         W[(int64_t)r * KP + j] = wq;
         col[(int64_t)r * KP + j] = cl;
@@ -223,6 +208,7 @@ static pg_status launch_agg(pg_graph *g, float *c_out, float *D_out, unsigned lo
     aggregate_kernel<KP, WT><<<pg_blocks(threads, 256), 256, 0, s>>>(
         g->nbr, g->OG, g->DP, g->EP, g->LV, g->succ_m, g->m2r, g->m2c, g->n, g->n_active, (WT *)g->W, g->rscale,
         g->col, g->b, g->c_m, g->D_m, c_out, D_out, cnt);
+    pg_count_launches(1);
     PG_LAUNCH_CHECK();
     return PG_OK;
 }
@@ -299,13 +285,16 @@ extern "C" pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype w
     if (st == PG_OK) {
         pack_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(*v, n, g->c2m, g->OG, g->DP, g->EP, g->LV, g->succ_m, predcnt,
                                                       g->flags);
+        pg_count_launches(1);
         active_flag_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(predcnt, n, act);
+        pg_count_launches(1);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     }
     if (st == PG_OK) st = pg_scan_exclusive(g, act, n, d_nact, s);
     int32_t h_nact = 0;
     if (st == PG_OK) {
         row_order_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(predcnt, act, d_nact, n, g->m2r, g->r2m);
+        pg_count_launches(1);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     }
     if (st == PG_OK && (cudaMemcpyAsync(&h_nact, d_nact, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

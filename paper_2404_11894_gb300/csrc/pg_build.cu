@@ -182,6 +182,7 @@ template <int KP>
 static pg_status launch_knn_t(pg_graph *g, cudaStream_t s) {
     knn_kernel<KP><<<pg_blocks(g->n, 128), 128, 0, s>>>(g->qpk, g->cell_start, g->m2c, g->c2m, g->n, g->k, g->level,
                                                         g->r2_max, g->nbr);
+    pg_count_launches(1);
     PG_LAUNCH_CHECK();
     return PG_OK;
 }
@@ -258,16 +259,19 @@ extern "C" pg_status pg_build_graph(const pg_vertices *v, int64_t n, const pg_bu
     if (st == PG_OK && n > 0) {
         quantize_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(v->px, v->py, v->pz, n, g->lo[0], g->lo[1], g->lo[2],
                                                           g->scale, g->level, keys, g->m2c, qpk_c, g->flags);
+        pg_count_launches(1);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
         if (st == PG_OK) st = pg_radix_sort(g, keys, g->m2c, n, 3 * g->level, s);
         if (st == PG_OK) {
             permute_build_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(g->m2c, qpk_c, n, g->qpk, g->c2m);
+            pg_count_launches(1);
             if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
         }
         if (st == PG_OK && cudaMemsetAsync(g->cell_start, 0, sizeof(int32_t) * (ncells + 1), s) != cudaSuccess)
             st = PG_ERR_CUDA;
         if (st == PG_OK) {
             cell_count_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(keys, n, g->cell_start);
+            pg_count_launches(1);
             if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
         }
         if (st == PG_OK) st = pg_scan_exclusive(g, g->cell_start, ncells + 1, nullptr, s);
@@ -307,6 +311,7 @@ extern "C" pg_status pg_graph_neighbors(const pg_graph *g, int32_t *nbr, pg_stre
     if (g->n == 0) return PG_OK;
     neighbors_out_kernel<<<pg_blocks(g->n * g->k, 256), 256, 0, (cudaStream_t)stream>>>(g->nbr, g->m2c, g->n, g->kp,
                                                                                          g->k, nbr);
+    pg_count_launches(1);
     PG_LAUNCH_CHECK();
     return PG_OK;
 }

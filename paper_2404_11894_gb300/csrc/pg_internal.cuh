@@ -92,11 +92,7 @@ struct pg_graph {
         }                                              \
     } while (0)
 
-#define PG_LAUNCH_CHECK()     \
-    do {                      \
-        pg_count_launches(1); \
-        PG_CUDA(cudaGetLastError()); \
-    } while (0)
+#define PG_LAUNCH_CHECK() PG_CUDA(cudaGetLastError())
 
 static inline int pg_blocks(int64_t work, int threads) {
     int64_t b = (work + threads - 1) / threads;

@@ -192,6 +192,7 @@ static pg_status launch_sweep(pg_graph *g, const float *b, const float *yin, flo
     sweep_kernel<KP, WT><<<blocks, SWEEP_THREADS, 0, s>>>(g->col, (const WT *)g->W, g->rscale, b, yin, yout,
                                                           g->n_active, g->d_ctrl, (double2 *)g->d_partials,
                                                           g->d_resid, t, tol);
+    pg_count_launches(1);
     PG_LAUNCH_CHECK();
     return PG_OK;
 }
@@ -270,11 +271,13 @@ extern "C" pg_status pg_propagate(pg_graph *g, const float *c, const float *L0, 
         PG_TRY(pg_alloc(nullptr, (void **)&buser, 4 * (size_t)(n + 1), s));
         cudaMemsetAsync(buser, 0, 4 * (size_t)(n + 1), s);
         b_from_c_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(c, g->c2m, g->m2r, g->LV, n, buser);
+        pg_count_launches(1);
         b = buser;
     }
     const int64_t stride = n + 1;
     float *y0 = keep_history ? g->hist : g->ybuf[0];
     init_y_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(L0, g->c2m, g->succ_m, g->m2r, n, y0);
+    pg_count_launches(1);
     if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     for (int t = 1; t <= iters && st == PG_OK; t++) {
         const float *yin = keep_history ? g->hist + (int64_t)(t - 1) * stride : g->ybuf[(t - 1) & 1];
@@ -288,6 +291,7 @@ extern "C" pg_status pg_propagate(pg_graph *g, const float *c, const float *L0, 
     if (st == PG_OK) {
         finish_L_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(g->c2m, g->succ_m, g->m2r, n, g->ybuf[0], g->ybuf[1],
                                                           keep_history ? g->hist : nullptr, g->d_ctrl, L);
+        pg_count_launches(1);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     }
     if (buser) cudaFreeAsync(buser, s);
@@ -353,16 +357,19 @@ extern "C" pg_status pg_gather(const pg_graph *g, const float *L, const float *D
             gather_kernel<float><<<pg_blocks(npix, 128), 128, 0, s>>>(first, bg, L, D, g->c2m, g->m2c, g->m2r, g->nbr,
                                                                      (const float *)g->W, g->rscale, g->LV, g->kp,
                                                                      spp, npix, g->n, image);
+            pg_count_launches(1);
             break;
         case PG_W_BF16:
             gather_kernel<__nv_bfloat16><<<pg_blocks(npix, 128), 128, 0, s>>>(
                 first, bg, L, D, g->c2m, g->m2c, g->m2r, g->nbr, (const __nv_bfloat16 *)g->W, g->rscale, g->LV,
                 g->kp, spp, npix, g->n, image);
+            pg_count_launches(1);
             break;
         case PG_W_F16:
             gather_kernel<__half><<<pg_blocks(npix, 128), 128, 0, s>>>(first, bg, L, D, g->c2m, g->m2c, g->m2r,
                                                                       g->nbr, (const __half *)g->W, g->rscale,
                                                                       g->LV, g->kp, spp, npix, g->n, image);
+            pg_count_launches(1);
             break;
     }
     PG_LAUNCH_CHECK();

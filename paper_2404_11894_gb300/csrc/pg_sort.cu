@@ -134,17 +134,20 @@ pg_status pg_scan_exclusive(pg_graph *g, int32_t *data, int64_t n, int32_t *d_to
     int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (nb == 1) {
         scan_block_apply<<<1, SCAN_THREADS, 0, s>>>(data, n, nullptr, d_total, 1);
+        pg_count_launches(1);
         PG_LAUNCH_CHECK();
         return PG_OK;
     }
     int32_t *sums = nullptr;
     PG_TRY(pg_alloc(nullptr, (void **)&sums, sizeof(int32_t) * nb, s));
     scan_block_sums<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(data, n, sums);
+    pg_count_launches(1);
     pg_status st = PG_OK;
     if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     if (st == PG_OK) st = pg_scan_exclusive(g, sums, nb, nullptr, s);
     if (st == PG_OK) {
         scan_block_apply<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(data, n, sums, d_total, nb);
+        pg_count_launches(1);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     }
     cudaFreeAsync(sums, s);
@@ -230,10 +233,12 @@ pg_status pg_radix_sort(pg_graph *g, uint32_t *keys, int32_t *vals, int64_t n, i
     for (int p = 0; p < passes && st == PG_OK; p++) {
         int shift = 8 * p;
         radix_hist<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(kin, n, shift, hist, ntiles);
+        pg_count_launches(1);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
         if (st == PG_OK) st = pg_scan_exclusive(g, hist, 256 * ntiles, nullptr, s);
         if (st == PG_OK) {
             radix_scatter<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(kin, vin, kout, vout, n, shift, hist, ntiles);
+            pg_count_launches(1);
             if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
         }
         uint32_t *tk = kin; kin = kout; kout = tk;

@@ -91,8 +91,9 @@ def test_adjoint_matches_oracle(pg, small, recompute):
 def test_adjoint_16bit(pg, small, wdtype):
     rec, T, dI, ref = small
     got = _gpu_adjoint(pg, rec, SMALL, T, dI, wdtype=wdtype, want_g=False)
-    # the map differs from the FP64 one by the 16-bit weight rounding
-    assert adj_err(got["grad_albedo"], ref["grad_albedo"]) <= 2e-2
+    # same dLoss/dImage; the operator differs from the FP64 one by the
+    # 16-bit rounding of its weights
+    assert adj_err(got["grad_albedo"], ref["grad_albedo"]) <= (2e-2 if wdtype == "f16" else 1e-1)
 
 
 def test_adjoint_voxels_finite_differences(pg):
