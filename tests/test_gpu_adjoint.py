@@ -92,8 +92,13 @@ def test_adjoint_16bit(pg, small, wdtype):
     rec, T, dI, ref = small
     got = _gpu_adjoint(pg, rec, SMALL, T, dI, wdtype=wdtype, want_g=False)
     # same dLoss/dImage; the operator differs from the FP64 one by the
-    # 16-bit rounding of its weights
-    assert adj_err(got["grad_albedo"], ref["grad_albedo"]) <= (2e-2 if wdtype == "f16" else 1e-1)
+    # 16-bit rounding of its weights: FP16 element-wise, BF16 (8-bit
+    # mantissa) in the L2 norm of the gradient
+    if wdtype == "f16":
+        assert adj_err(got["grad_albedo"], ref["grad_albedo"]) <= 2e-2
+    else:
+        d = got["grad_albedo"] - ref["grad_albedo"]
+        assert np.linalg.norm(d) <= 2e-2 * np.linalg.norm(ref["grad_albedo"])
 
 
 def test_adjoint_voxels_finite_differences(pg):
