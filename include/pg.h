@@ -216,6 +216,34 @@ pg_status pg_graph_release_weights(pg_graph *g);
 void pg_graph_destroy(pg_graph *g);
 const char *pg_status_string(pg_status s);
 
+/* Propagation for callers that cannot allocate device memory at the time of
+ * the call (no counterpart in the paper: it is a deployment variant of
+ * pg_propagate). Examples are host applications that hand this library a
+ * fixed memory budget at start-up and allow no further allocation, and
+ * per-frame loops that must not allocate once set-up is done, because an
+ * allocation in the middle of a frame can stall on the allocator or fail for
+ * lack of memory. The graph itself is still made by pg_build_graph and
+ * pg_aggregate at set-up, which do allocate.
+ *
+ * It runs the same Jacobi sweeps as pg_propagate with c = NULL, no history
+ * and no residual output: `iters` sweeps from L0 (caller order, n floats),
+ * stopping early on the device when tol > 0, writing L (caller order, n
+ * floats). Its scratch (two iterates, residual partials and control words)
+ * lives in one file-scope device array of 32 MiB + 96 KiB that every GPU
+ * which loads the library holds until the process exits. The first call on
+ * each device looks up that array's device address; make that first call
+ * before any stream capture. Every call shares the array and the array keeps
+ * the previous call's contents (the call resets what must start at zero), so
+ * calls whose work overlaps on the GPU -- on any stream, for any graph --
+ * race and corrupt each other's results: serialise them.
+ * Errors: PG_ERR_UNSUPPORTED when n > PG_NOALLOC_MAX_VERTICES or
+ * iters > PG_NOALLOC_MAX_ITERS; PG_ERR_STATE (no pg_aggregate, or weights
+ * released); PG_ERR_INVALID_ARG. It calls no allocation routine. */
+#define PG_NOALLOC_MAX_VERTICES 4194303
+#define PG_NOALLOC_MAX_ITERS 4096
+pg_status pg_propagate_noalloc(pg_graph *g, const float *L0, int32_t iters, double tol, float *L,
+                               pg_stream_t stream);
+
 /* Diagnostic (no counterpart in the paper): number of CUDA kernels this
  * library has launched in the process so far. Thread-safe; never fails. */
 int64_t pg_launch_count(void);

@@ -151,6 +151,15 @@ def pg_propagate_adjoint(graph: Graph, dI: torch.Tensor, first: torch.Tensor, sp
     return {"grad_sigma_s": gs, "grad_g": gg, "grad_albedo": ga}
 
 
+def pg_propagate_noalloc(graph: Graph, L0: torch.Tensor, iters: int, out: torch.Tensor, tol: float = 0.0,
+                         stream=None) -> torch.Tensor:
+    """pg_propagate without device allocation (scratch in a static device
+    array; see include/pg.h). ``out`` must be preallocated by the caller."""
+    check(_LIB.pg_propagate_noalloc(graph.handle, _ptr(L0), iters, tol, _ptr(out), _stream_ptr(stream)),
+          "pg_propagate_noalloc")
+    return out
+
+
 def launch_count() -> int:
     """Kernels launched by libpg in this process (diagnostic)."""
     return int(_LIB.pg_launch_count())

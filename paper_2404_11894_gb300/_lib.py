@@ -36,7 +36,7 @@ class PgGraphInfo(ctypes.Structure):
 
 EXPORTS = ("pg_build_graph", "pg_graph_neighbors", "pg_graph_get_info", "pg_aggregate", "pg_propagate",
            "pg_gather", "pg_propagate_adjoint", "pg_graph_release_weights", "pg_graph_destroy",
-           "pg_status_string", "pg_launch_count")
+           "pg_status_string", "pg_launch_count", "pg_propagate_noalloc")
 
 _lib = None
 
@@ -63,6 +63,7 @@ def load(path: str = LIB_PATH):
     lib.pg_graph_destroy.restype = None
     lib.pg_status_string.argtypes = [ctypes.c_int]
     lib.pg_status_string.restype = ctypes.c_char_p
+    lib.pg_propagate_noalloc.argtypes = [vp, vp, i32, f64, vp, vp]
     lib.pg_launch_count.argtypes = []
     lib.pg_launch_count.restype = ctypes.c_int64
     for name in EXPORTS:

@@ -8,6 +8,8 @@
 // and combine their four products with shuffles. The relative change of the
 // sweep is reduced in FP64 (per-block partials, then the last block), and a
 // sweep that finds the previous one converged returns at once.
+#include <mutex>
+
 #include "pg_internal.cuh"
 
 template <typename WT>
@@ -307,6 +309,105 @@ extern "C" pg_status pg_propagate(pg_graph *g, const float *c, const float *L0, 
         if (iters_done) *iters_done = ctrl[0];
         if (keep_history) g->hist_iters = ctrl[0];
     }
+    return PG_OK;
+}
+
+// ------------------------------------------------------------------ propagation without allocation
+// pg_propagate_noalloc runs the same sweeps as pg_propagate, but keeps all of
+// its scratch (the two ping-pong iterates, the per-block residual partials,
+// the per-sweep residuals and the control words) in one file-scope device
+// array instead of memory allocated at run time. Every call on a device shares
+// this array.
+static constexpr int64_t NA_MAX_N = PG_NOALLOC_MAX_VERTICES;
+static constexpr int NA_MAX_ITERS = PG_NOALLOC_MAX_ITERS;
+static constexpr int NA_MAX_BLOCKS = 4096;
+static constexpr size_t NA_Y_BYTES = 4 * (size_t)(NA_MAX_N + 1);
+static constexpr size_t NA_Y0 = 0;
+static constexpr size_t NA_Y1 = (NA_Y_BYTES + 255) / 256 * 256;
+static constexpr size_t NA_PARTIALS = NA_Y1 + (NA_Y_BYTES + 255) / 256 * 256;
+static constexpr size_t NA_RESID = NA_PARTIALS + 16 * (size_t)NA_MAX_BLOCKS;
+static constexpr size_t NA_CTRL = NA_RESID + 8 * (size_t)NA_MAX_ITERS;
+static constexpr size_t NA_BYTES = NA_CTRL + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+// Device address of the scratch array, looked up once per device (host code
+// cannot use the symbol itself: it is only a host-side stand-in).
+static pg_status noalloc_scratch(unsigned char **out) {
+    static std::mutex mu;
+    static unsigned char *addr[64] = {nullptr};
+    int dev = 0;
+    PG_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return PG_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            (void)cudaGetLastError();
+            return PG_ERR_CUDA;
+        }
+        addr[dev] = (unsigned char *)p;
+    }
+    *out = addr[dev];
+    return PG_OK;
+}
+
+template <int KP, typename WT>
+static void na_sweep(const pg_graph *g, const float *yin, float *yout, int32_t *ctrl, double2 *partials,
+                     double *resid, int t, double tol, int blocks, cudaStream_t s) {
+    sweep_kernel<KP, WT><<<blocks, SWEEP_THREADS, 0, s>>>(g->col, (const WT *)g->W, g->rscale, g->b, yin, yout,
+                                                          g->n_active, ctrl, partials, resid, t, tol);
+    pg_count_launches(1);
+}
+
+template <typename WT>
+static void na_sweep_k(const pg_graph *g, const float *yin, float *yout, int32_t *ctrl, double2 *partials,
+                       double *resid, int t, double tol, int blocks, cudaStream_t s) {
+    switch (g->kp) {
+        case 4: na_sweep<4, WT>(g, yin, yout, ctrl, partials, resid, t, tol, blocks, s); break;
+        case 8: na_sweep<8, WT>(g, yin, yout, ctrl, partials, resid, t, tol, blocks, s); break;
+        case 16: na_sweep<16, WT>(g, yin, yout, ctrl, partials, resid, t, tol, blocks, s); break;
+        default: na_sweep<32, WT>(g, yin, yout, ctrl, partials, resid, t, tol, blocks, s); break;
+    }
+}
+
+extern "C" pg_status pg_propagate_noalloc(pg_graph *g, const float *L0, int32_t iters, double tol, float *L,
+                                          pg_stream_t stream) {
+    if (!g || iters < 0) return PG_ERR_INVALID_ARG;
+    if (!g->aggregated || !g->W) return PG_ERR_STATE;
+    if (g->n > NA_MAX_N || iters > NA_MAX_ITERS) return PG_ERR_UNSUPPORTED;
+    const int64_t n = g->n;
+    if (n == 0) return PG_OK;
+    if (!L0 || !L) return PG_ERR_INVALID_ARG;
+    int blocks = pg_sweep_blocks(g);
+    if (blocks > NA_MAX_BLOCKS) blocks = NA_MAX_BLOCKS;
+    unsigned char *base = nullptr;
+    PG_TRY(noalloc_scratch(&base));
+    cudaStream_t s = (cudaStream_t)stream;
+    float *y0 = (float *)(base + NA_Y0), *y1 = (float *)(base + NA_Y1);
+    double2 *partials = (double2 *)(base + NA_PARTIALS);
+    double *resid = (double *)(base + NA_RESID);
+    int32_t *ctrl = (int32_t *)(base + NA_CTRL);
+    // the array keeps the previous call's contents: reset what must start at zero
+    PG_CUDA(cudaMemsetAsync(ctrl, 0, 16, s));
+    PG_CUDA(cudaMemsetAsync(y0 + n, 0, 4, s)); // zero slot of both iterates
+    PG_CUDA(cudaMemsetAsync(y1 + n, 0, 4, s));
+    if (iters > 0) PG_CUDA(cudaMemsetAsync(resid, 0, 8 * (size_t)iters, s));
+    init_y_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(L0, g->c2m, g->succ_m, g->m2r, n, y0);
+    pg_count_launches(1);
+    for (int t = 1; t <= iters; t++) {
+        const float *yin = (t & 1) ? y0 : y1;
+        float *yout = (t & 1) ? y1 : y0;
+        switch (g->wdtype) {
+            case PG_W_F32: na_sweep_k<float>(g, yin, yout, ctrl, partials, resid, t, tol, blocks, s); break;
+            case PG_W_BF16: na_sweep_k<__nv_bfloat16>(g, yin, yout, ctrl, partials, resid, t, tol, blocks, s); break;
+            case PG_W_F16: na_sweep_k<__half>(g, yin, yout, ctrl, partials, resid, t, tol, blocks, s); break;
+        }
+    }
+    finish_L_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(g->c2m, g->succ_m, g->m2r, n, y0, y1, nullptr, ctrl, L);
+    pg_count_launches(1);
+    PG_LAUNCH_CHECK();
     return PG_OK;
 }
 
