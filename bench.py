@@ -119,6 +119,8 @@ def run_gpu(args):
     from paper_2404_11894_gb300.dist import combine_throughput, rank_seed
 
     sc = pgrec.CLOUD128
+    if args.scale != 1.0:  # smaller image of the same scene (profiling captures)
+        sc = sc.with_(width=int(sc.width * args.scale), height=int(sc.height * args.scale))
     if world > 1:  # independent renders (replicas), one per rank
         sc = sc.with_(seed=rank_seed(sc.seed, rank))
     rec = pgrec.trace(sc)
@@ -138,7 +140,8 @@ def run_gpu(args):
     dev_in = {k: v.to(dev) for k, v in host.items()}
     dev_target = host_target.to(dev)
     V = pg.Vertices({k: dev_in[k] for k in pg.VERTEX_F32 + ("e_delta", "succ")})
-    solver = pg.Solver(k=sc.k, iters=sc.iters, wdtype="f32", adjoint=not args.no_adjoint)
+    solver = pg.Solver(k=sc.k, iters=sc.iters, wdtype="f32", adjoint=not args.no_adjoint,
+                       recompute_weights=args.adjoint_mode)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
@@ -347,6 +350,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the 16-bit weight runs")
     ap.add_argument("--oracle-stride", type=int, default=10)
+    ap.add_argument("--scale", type=float, default=1.0, help="image resolution factor (profiling only)")
+    ap.add_argument("--adjoint-mode", type=int, default=2, choices=[0, 1, 2],
+                    help="reverse sweep: 0 transposed copy, 1 recomputed weights, 2 atomic scatter")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

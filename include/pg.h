@@ -196,11 +196,18 @@ pg_status pg_gather(const pg_graph *g, const float *L, const float *D, const int
  *             gradient, sigma_s = albedo[voxel(v)] * sigma_t(v):
  *             grad_albedo_vox[x] = sum_{v: voxel(v)=x} sigma_t(v) dLoss/dsigma_s(v)
  *             (overwritten, n_vox floats); pass NULL to skip
- *   recompute_weights  0: use the stored weights and a transposed copy kept
- *             in the graph (fast, nnz*(4+weight bytes) extra memory);
- *             1: re-evaluate every edge weight from the vertex records in
- *             each reverse sweep (no weight memory; summation order of the
- *             reverse sweep is not deterministic).
+ *   recompute_weights  how W^T is applied in the reverse sweeps:
+ *             0: from a transposed copy of the stored weights, built on the
+ *                first call and kept in the graph (nnz * (4 + weight bytes)
+ *                extra memory); deterministic summation order;
+ *             1: every edge weight re-evaluated from the vertex records in
+ *                each reverse sweep (no weight memory needed at all: works
+ *                after pg_graph_release_weights);
+ *             2: from the stored weights in their forward row layout, with
+ *                atomic adds into the reverse iterate (no transposed copy).
+ *             Modes 1 and 2 sum in a non-deterministic order (float atomics).
+ * With grad_g, the reverse iterates of every sweep are kept for the call
+ * ((iters + 1) * (n + 1) floats of temporary memory).
  * Gradients of vertices with sigma_s = 0 are reported as 0.
  * Errors: PG_ERR_STATE (no history), PG_ERR_INVALID_ARG. */
 pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const int32_t *first, int64_t n_paths, int32_t spp,

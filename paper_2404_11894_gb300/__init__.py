@@ -140,8 +140,10 @@ def pg_gather(graph: Graph, L: torch.Tensor, D: torch.Tensor, first: torch.Tenso
 
 def pg_propagate_adjoint(graph: Graph, dI: torch.Tensor, first: torch.Tensor, spp: int, width: int, height: int,
                          want_sigma_s: bool = True, want_g: bool = True, voxel: torch.Tensor | None = None,
-                         sigma_t: torch.Tensor | None = None, n_vox: int = 0, recompute_weights: bool = False,
+                         sigma_t: torch.Tensor | None = None, n_vox: int = 0, recompute_weights: int = 0,
                          stream=None) -> dict:
+    """recompute_weights: 0 transposed copy (deterministic), 1 re-evaluate
+    weights, 2 stored rows with atomic scatter (see include/pg.h)."""
     gs = torch.empty(graph.n, dtype=torch.float32, device="cuda") if want_sigma_s else None
     gg = torch.empty(graph.n, dtype=torch.float32, device="cuda") if want_g else None
     ga = torch.empty(n_vox, dtype=torch.float32, device="cuda") if voxel is not None else None

@@ -32,7 +32,7 @@ class PathGraphFunction(torch.autograd.Function):
     def backward(ctx, dI):
         grads = pg_propagate_adjoint(ctx.graph, dI.contiguous(), ctx.first, ctx.spp, ctx.width, ctx.height,
                                      want_sigma_s=ctx.needs_input_grad[0], want_g=ctx.needs_input_grad[1],
-                                     recompute_weights=ctx.recompute)
+                                     recompute_weights=int(ctx.recompute))
         ctx.graph.close()
         return (grads["grad_sigma_s"], grads["grad_g"]) + (None,) * 11
 

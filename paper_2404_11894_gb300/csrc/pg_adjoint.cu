@@ -10,8 +10,9 @@
 // Every weight of row s is sigma_s(s) times a factor, so
 //   dLoss/dsigma_s(s) = ( sum_t mu_t[s] y_t[s] + nu_s (val_s - bg) ) / sigma_s(s).
 // For g the per-edge adjoints Gamma[s][i] = sum_t mu_t[s] y_{t-1}[col] (+ the
-// output term) and beta_s = sum_t mu_t[s] are pushed through the derivatives
-// of the MIS weights (numerators and marginal densities).
+// output term nu_s y_T[col]) are formed from the kept iterates y_t and the
+// reverse iterates mu_t, and with beta_s = sum_t mu_t[s] pushed through the
+// derivatives of the MIS weights (numerators and marginal densities).
 //
 // W~^T is applied either from a transposed copy of the stored weights
 // (columns sorted by row: deterministic), or, with recompute_weights, by
@@ -27,6 +28,37 @@ template <>
 __device__ __forceinline__ float wload<__nv_bfloat16>(const __nv_bfloat16 *W, int64_t i) { return __bfloat162float(W[i]); }
 template <>
 __device__ __forceinline__ float wload<__half>(const __half *W, int64_t i) { return __half2float(W[i]); }
+
+template <typename WT>
+struct W4L;
+template <>
+struct W4L<float> {
+    static __device__ __forceinline__ float4 load(const float *p) { return __ldcs(reinterpret_cast<const float4 *>(p)); }
+};
+template <>
+struct W4L<__nv_bfloat16> {
+    static __device__ __forceinline__ float4 load(const __nv_bfloat16 *p) {
+        uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
+        __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162 *>(&u.x), b = *reinterpret_cast<__nv_bfloat162 *>(&u.y);
+        float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+};
+template <>
+struct W4L<__half> {
+    static __device__ __forceinline__ float4 load(const __half *p) {
+        uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
+        __half2 a = *reinterpret_cast<__half2 *>(&u.x), b = *reinterpret_cast<__half2 *>(&u.y);
+        float2 fa = __half22float2(a), fb = __half22float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+};
+
+__global__ void scale_rows_kernel(const float *__restrict__ mu, const float *__restrict__ rs, int64_t na,
+                                  float *__restrict__ us) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < na) us[r] = mu[r] * rs[r];
+}
 
 // ------------------------------------------------------------------ transpose build
 __global__ void tcount_kernel(const int32_t *__restrict__ col, int64_t n, int kp, int32_t *__restrict__ cnt) {
@@ -121,17 +153,6 @@ __global__ void __launch_bounds__(256) tsweep_kernel(const int32_t *__restrict__
     }
 }
 
-// ------------------------------------------------------------------ per-edge adjoints (for g)
-// Gamma[r][i] += mu[r] * y_prev[col[r][i]] over the rows [r0, r1)
-__global__ void gamma_kernel(const int32_t *__restrict__ col, const float *__restrict__ mu,
-                             const float *__restrict__ y_prev, int64_t r0, int64_t r1, int kp,
-                             float *__restrict__ Gam) {
-    int64_t e = r0 * kp + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= r1 * kp) return;
-    float m = mu[e / kp];
-    if (m != 0.0f) Gam[e] = fmaf(m, y_prev[col[e]], Gam[e]);
-}
-
 // output term of first-vertex rows: G[f] = nu_f (val_f - bg) with
 // val_f - bg = sum_i W~[f][i] y_T[col] + (tau/p_t)_f D_f
 template <typename WT>
@@ -153,17 +174,50 @@ __global__ void first_rows_kernel(const int32_t *__restrict__ first, int64_t n_p
     G[r] += nu[r] * (sum + LV[m].w * D_m[m]);
 }
 
+// ------------------------------------------------------------------ reverse sweep (stored rows, scatter)
+// Rows [r0, r1) in the forward layout: out[col[r][i]] += W[r][i] * us_in[r]
+// with float atomics (no transposed copy), KP/4 lanes per row and 16-byte
+// loads like the forward sweep. Accumulates G[r] += mu_in[r] y_t[r] and
+// B[r] += mu_in[r] when y_t is given.
+template <int KP, typename WT>
+__global__ void __launch_bounds__(256) scatter_sweep_kernel(
+    const int32_t *__restrict__ col, const WT *__restrict__ W, int64_t r0, int64_t r1, int64_t n,
+    const float *__restrict__ us_in, const float *__restrict__ mu_in, const float *__restrict__ y_t, int write_out,
+    float *__restrict__ out, float *__restrict__ G, float *__restrict__ B) {
+    constexpr int LPR = KP / 4;
+    const int lane = threadIdx.x & 31;
+    const int q = lane & (LPR - 1);
+    const int64_t row = r0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPR;
+    if (row >= r1) return;
+    const float u = us_in[row];
+    if (write_out && u != 0.0f) {
+        const int4 c4 = __ldcs(reinterpret_cast<const int4 *>(col + row * KP) + q);
+        const float4 w4 = W4L<WT>::load(W + row * KP + q * 4);
+        if (c4.x < n) atomicAdd(out + c4.x, w4.x * u);
+        if (c4.y < n) atomicAdd(out + c4.y, w4.y * u);
+        if (c4.z < n) atomicAdd(out + c4.z, w4.z * u);
+        if (c4.w < n) atomicAdd(out + c4.w, w4.w * u);
+    }
+    if (y_t && q == 0) {
+        const float m = mu_in[row];
+        G[row] = fmaf(m, y_t[row], G[row]);
+        B[row] += m;
+    }
+}
+
 // ------------------------------------------------------------------ recompute mode
 // Row s (Morton m) re-evaluates its weights W~[s][j] = w_s sigma_s rho_s(o_s,d_j)
 // / sum_l rho_l(o_l,d_j) and scatters u[r] W~ into out[col] with atomics.
-// Also accumulates G/B (y_t given) and Gamma (Gam given) for rows with u != 0.
+// Also accumulates G/B (y_t given) for rows with u != 0.
 template <int KP>
 __global__ void __launch_bounds__(256) recompute_scatter_kernel(
     const int32_t *__restrict__ nbr, const float4 *__restrict__ OG, const float4 *__restrict__ DP,
     const float4 *__restrict__ LV, const int32_t *__restrict__ succ_m, const int32_t *__restrict__ m2r,
     const int32_t *__restrict__ r2m, int64_t r0, int64_t r1, int64_t n, const float *__restrict__ u,
     const float *__restrict__ y_t, const float *__restrict__ y_prev, int write_out, float *__restrict__ out,
-    float *__restrict__ G, float *__restrict__ B, float *__restrict__ Gam) {
+    float *__restrict__ G, float *__restrict__ B, float *__restrict__ unused) {
+    (void)y_prev;
+    (void)unused;
     __shared__ float4 s_o[256];
     __shared__ float2 s_ab[256];
     const int lane = threadIdx.x & 31;
@@ -211,7 +265,6 @@ __global__ void __launch_bounds__(256) recompute_scatter_kernel(
             int32_t cl = m2r[sj];
             float Wt = lvs.w * (lvs.z * rho_sd / pm_d);
             if (write_out) atomicAdd(out + cl, ur * Wt);
-            if (Gam) Gam[r * KP + j] = fmaf(ur, y_prev[cl], Gam[r * KP + j]);
         }
     }
     if (row_ok && j == 0 && y_t) {
@@ -300,8 +353,9 @@ template <int KP>
 __global__ void __launch_bounds__(256) grad_g_kernel(
     const int32_t *__restrict__ nbr, const float4 *__restrict__ OG, const float4 *__restrict__ DP,
     const float4 *__restrict__ EP, const float4 *__restrict__ LV, const int32_t *__restrict__ m2r, int64_t n,
-    const float *__restrict__ Gam, const float *__restrict__ B, const float *__restrict__ nu,
-    const float *__restrict__ rscale, float *__restrict__ gg) {
+    int64_t n_active, const int32_t *__restrict__ col, const float *__restrict__ yhist,
+    const float *__restrict__ muhist, int T, const float *__restrict__ B, const float *__restrict__ nu,
+    float *__restrict__ gg) {
     __shared__ float4 s_o[256];   // (o_l, g_l)
     __shared__ float4 s_d[256];   // (d_j, coefficient for rho'_l(o_l, d_j))
     __shared__ float4 s_e[256];   // (e_j, coefficient for rho'_l(o_l, e_j))
@@ -341,9 +395,21 @@ __global__ void __launch_bounds__(256) grad_g_kernel(
     const float sig = __shfl_sync(0xffffffffu, lv.z, src);
     const float w_s = __shfl_sync(0xffffffffu, lv.w, src);
     const int64_t r = row_ok ? m2r[m] : 0;
-    (void)rscale; // Gamma is already the adjoint of the full weight value
+    // edge adjoint Gamma = dLoss/dW~ of this entry: sum over the sweeps that
+    // used it (mu_t of the row times the iterate it multiplied), or the output
+    // term nu y_T for a path's first vertex
+    float Gam = 0.0f;
+    if (row_ok && valid) {
+        const int32_t cl = col[r * KP + j];
+        const int64_t stride = n + 1;
+        if (r < n_active) {
+            for (int t = 1; t <= T; t++) Gam = fmaf(muhist[t * stride + r], yhist[(t - 1) * stride + cl], Gam);
+        } else {
+            Gam = nu[r] * yhist[(int64_t)T * stride + cl];
+        }
+    }
     // adjoints w.r.t. A+ (per entry), c and D of this row
-    const float gA = row_ok && valid ? w_s * Gam[r * KP + j] : 0.0f;
+    const float gA = w_s * Gam;
     const float gc = row_ok ? w_s * B[r] : 0.0f;
     const float gD = row_ok ? w_s * nu[r] : 0.0f;
     float drho_sd, drho_se, rho_sd, rho_se;
@@ -433,71 +499,104 @@ static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
 }
 
 template <typename WT>
-static pg_status adjoint_store(pg_graph *g, float *nu, float *us0, float *mu_a, float *mu_b, float *us_a,
-                               float *us_b, float *G, float *B, float *Gam, cudaStream_t s) {
+static pg_status adjoint_store(pg_graph *g, float *us0, float *mu_a, float *mu_b, float *us_a, float *us_b,
+                               float *G, float *B, float *muhist, cudaStream_t s) {
     const int64_t n = g->n, na = g->n_active;
     const int T = g->hist_iters;
     const int64_t stride = n + 1;
     const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
     if (!g->t_ptr) PG_TRY(build_transpose<WT>(g, s));
     const int tb = pg_blocks(na * 8, 256);
+    // mu_t lives in slice t of the history when one is kept, else ping-pong
+    auto mu_slot = [&](int t) { return muhist ? muhist + (int64_t)t * stride : ((t & 1) ? mu_b : mu_a); };
+    float *us_cur = us_a, *us_nxt = us_b;
     // mu_T = W^T nu
-    float *mu_cur = mu_a, *us_cur = us_a, *mu_nxt = mu_b, *us_nxt = us_b;
     tsweep_kernel<WT><<<tb, 256, 0, s>>>(g->t_ptr, g->t_row, (const WT *)g->t_W, us0, nullptr, nullptr, rs, na, 1,
-                                         mu_cur, us_cur, G, B);
+                                         mu_slot(T), us_cur, G, B);
     pg_count_launches(1);
     PG_LAUNCH_CHECK();
-    if (Gam) {
-        // output term of the per-edge adjoint: Gamma[f][i] = nu_f y_T[col]
-        gamma_kernel<<<pg_blocks((n - na) * g->kp, 256), 256, 0, s>>>(g->col, nu, g->hist + (int64_t)T * stride, na,
-                                                                        n, g->kp, Gam);
-        pg_count_launches(1);
-        PG_LAUNCH_CHECK();
-    }
     for (int t = T; t >= 1; t--) {
         const float *y_t = g->hist + (int64_t)t * stride;
-        if (Gam) {
-            gamma_kernel<<<pg_blocks(na * g->kp, 256), 256, 0, s>>>(g->col, mu_cur, g->hist + (int64_t)(t - 1) * stride,
-                                                                   0, na, g->kp, Gam);
-            pg_count_launches(1);
-            PG_LAUNCH_CHECK();
-        }
-        tsweep_kernel<WT><<<tb, 256, 0, s>>>(g->t_ptr, g->t_row, (const WT *)g->t_W, us_cur, mu_cur, y_t, rs, na,
-                                             t > 1 ? 1 : 0, mu_nxt, us_nxt, G, B);
+        tsweep_kernel<WT><<<tb, 256, 0, s>>>(g->t_ptr, g->t_row, (const WT *)g->t_W, us_cur, mu_slot(t), y_t, rs,
+                                             na, t > 1 ? 1 : 0, mu_slot(t - 1), us_nxt, G, B);
         pg_count_launches(1);
         PG_LAUNCH_CHECK();
-        float *tm = mu_cur; mu_cur = mu_nxt; mu_nxt = tm;
         float *tu = us_cur; us_cur = us_nxt; us_nxt = tu;
     }
     return PG_OK;
 }
 
-template <int KP>
-static pg_status adjoint_recompute(pg_graph *g, float *nu, float *mu_a, float *mu_b, float *G, float *B, float *Gam,
-                                   cudaStream_t s) {
+template <int KP, typename WT>
+static pg_status adjoint_scatter(pg_graph *g, float *us0, float *mu_a, float *mu_b, float *us_a, float *us_b,
+                                 float *G, float *B, float *muhist, cudaStream_t s) {
     const int64_t n = g->n, na = g->n_active;
     const int T = g->hist_iters;
     const int64_t stride = n + 1;
-    const int rows_all = pg_blocks(n * KP, 256);
-    (void)rows_all;
-    // mu_T = W^T nu from the first-vertex rows [na, n)
-    PG_CUDA(cudaMemsetAsync(mu_a, 0, 4 * (size_t)(n + 1), s));
-    const float *yT = g->hist + (int64_t)T * stride;
-    recompute_scatter_kernel<KP><<<pg_blocks((n - na) * KP, 256), 256, 0, s>>>(
-        g->nbr, g->OG, g->DP, g->LV, g->succ_m, g->m2r, g->r2m, na, n, n, nu, nullptr, yT, 1, mu_a, G, B, Gam);
+    const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
+    auto mu_slot = [&](int t) { return muhist ? muhist + (int64_t)t * stride : ((t & 1) ? mu_b : mu_a); };
+    // mu_T = W^T nu: scatter from the first-vertex rows [na, n)
+    PG_CUDA(cudaMemsetAsync(mu_slot(T), 0, 4 * (size_t)stride, s));
+    scatter_sweep_kernel<KP, WT><<<pg_blocks((n - na) * (KP / 4), 256), 256, 0, s>>>(
+        g->col, (const WT *)g->W, na, n, n, us0, nullptr, nullptr, 1, mu_slot(T), G, B);
     pg_count_launches(1);
     PG_LAUNCH_CHECK();
-    float *mu_cur = mu_a, *mu_nxt = mu_b;
+    float *us_cur = us_a;
     for (int t = T; t >= 1; t--) {
-        PG_CUDA(cudaMemsetAsync(mu_nxt, 0, 4 * (size_t)(n + 1), s));
+        // us = mu_t * row scale (the 16-bit payload multiplies it)
+        const float *mu_t = mu_slot(t);
+        const float *us_in = mu_t;
+        if (rs) {
+            scale_rows_kernel<<<pg_blocks(na, 256), 256, 0, s>>>(mu_t, rs, na, us_cur);
+            pg_count_launches(1);
+            us_in = us_cur;
+        }
+        if (t > 1) PG_CUDA(cudaMemsetAsync(mu_slot(t - 1), 0, 4 * (size_t)stride, s));
+        scatter_sweep_kernel<KP, WT><<<pg_blocks(na * (KP / 4), 256), 256, 0, s>>>(
+            g->col, (const WT *)g->W, 0, na, n, us_in, mu_t, g->hist + (int64_t)t * stride, t > 1 ? 1 : 0,
+            mu_slot(t - 1), G, B);
+        pg_count_launches(1);
+        PG_LAUNCH_CHECK();
+    }
+    (void)us_b;
+    return PG_OK;
+}
+
+template <typename WT>
+static pg_status adjoint_scatter_k(pg_graph *g, float *us0, float *mu_a, float *mu_b, float *us_a, float *us_b,
+                                   float *G, float *B, float *muhist, cudaStream_t s) {
+    switch (g->kp) {
+        case 4: return adjoint_scatter<4, WT>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s);
+        case 8: return adjoint_scatter<8, WT>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s);
+        case 16: return adjoint_scatter<16, WT>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s);
+        case 32: return adjoint_scatter<32, WT>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s);
+        default: return PG_ERR_UNSUPPORTED;
+    }
+}
+
+template <int KP>
+static pg_status adjoint_recompute(pg_graph *g, float *nu, float *mu_a, float *mu_b, float *G, float *B,
+                                   float *muhist, cudaStream_t s) {
+    const int64_t n = g->n, na = g->n_active;
+    const int T = g->hist_iters;
+    const int64_t stride = n + 1;
+    auto mu_slot = [&](int t) { return muhist ? muhist + (int64_t)t * stride : ((t & 1) ? mu_b : mu_a); };
+    // mu_T = W^T nu from the first-vertex rows [na, n)
+    PG_CUDA(cudaMemsetAsync(mu_slot(T), 0, 4 * (size_t)(n + 1), s));
+    const float *yT = g->hist + (int64_t)T * stride;
+    recompute_scatter_kernel<KP><<<pg_blocks((n - na) * KP, 256), 256, 0, s>>>(
+        g->nbr, g->OG, g->DP, g->LV, g->succ_m, g->m2r, g->r2m, na, n, n, nu, nullptr, yT, 1, mu_slot(T), G, B,
+        nullptr);
+    pg_count_launches(1);
+    PG_LAUNCH_CHECK();
+    for (int t = T; t >= 1; t--) {
+        if (t > 1) PG_CUDA(cudaMemsetAsync(mu_slot(t - 1), 0, 4 * (size_t)(n + 1), s));
         const float *y_t = g->hist + (int64_t)t * stride;
         const float *y_p = g->hist + (int64_t)(t - 1) * stride;
         recompute_scatter_kernel<KP><<<pg_blocks(na * KP, 256), 256, 0, s>>>(
-            g->nbr, g->OG, g->DP, g->LV, g->succ_m, g->m2r, g->r2m, 0, na, n, mu_cur, y_t, y_p, t > 1 ? 1 : 0,
-            mu_nxt, G, B, Gam);
+            g->nbr, g->OG, g->DP, g->LV, g->succ_m, g->m2r, g->r2m, 0, na, n, mu_slot(t), y_t, y_p, t > 1 ? 1 : 0,
+            mu_slot(t - 1), G, B, nullptr);
         pg_count_launches(1);
         PG_LAUNCH_CHECK();
-        float *tm = mu_cur; mu_cur = mu_nxt; mu_nxt = tm;
     }
     // output term of first-vertex rows
     recompute_first_kernel<KP><<<pg_blocks((n - na) * KP, 256), 256, 0, s>>>(
@@ -508,11 +607,11 @@ static pg_status adjoint_recompute(pg_graph *g, float *nu, float *mu_a, float *m
 }
 
 template <int KP>
-static pg_status launch_grad_g(pg_graph *g, const float *Gam, const float *B, const float *nu, float *gg_m,
+static pg_status launch_grad_g(pg_graph *g, const float *muhist, const float *B, const float *nu, float *gg_m,
                                cudaStream_t s) {
-    const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
     grad_g_kernel<KP><<<pg_blocks(g->n * KP, 256), 256, 0, s>>>(g->nbr, g->OG, g->DP, g->EP, g->LV, g->m2r, g->n,
-                                                               Gam, B, nu, rs, gg_m);
+                                                               g->n_active, g->col, g->hist, muhist,
+                                                               g->hist_iters, B, nu, gg_m);
     pg_count_launches(1);
     PG_LAUNCH_CHECK();
     return PG_OK;
@@ -526,7 +625,8 @@ extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const in
     if (!g || spp <= 0 || width < 0 || height < 0) return PG_ERR_INVALID_ARG;
     if (n_paths != (int64_t)width * height * spp) return PG_ERR_INVALID_ARG;
     if (!g->aggregated || g->hist_iters < 0 || !g->hist) return PG_ERR_STATE;
-    if (!recompute_weights && !g->W && !g->t_W) return PG_ERR_STATE;
+    if (recompute_weights < 0 || recompute_weights > 2) return PG_ERR_INVALID_ARG;
+    if (recompute_weights != 1 && !g->W) return PG_ERR_STATE;
     if (grad_albedo_vox && (!voxel || !sigma_t || n_vox < 0)) return PG_ERR_INVALID_ARG;
     if (n_paths > 0 && (!dI || !first)) return PG_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -536,7 +636,7 @@ extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const in
     if (n == 0) return PG_OK;
     const bool want_g = grad_g != nullptr;
     float *nu = nullptr, *us0 = nullptr, *mu_a = nullptr, *mu_b = nullptr, *us_a = nullptr, *us_b = nullptr;
-    float *G = nullptr, *B = nullptr, *Gam = nullptr, *gg_m = nullptr;
+    float *G = nullptr, *B = nullptr, *muhist = nullptr, *gg_m = nullptr;
     const size_t vb = 4 * (size_t)(n + 1);
     pg_status st = PG_OK;
 #define T_ALLOC(p, bytes) \
@@ -550,7 +650,7 @@ extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const in
     T_ALLOC(G, vb);
     T_ALLOC(B, vb);
     if (want_g) {
-        T_ALLOC(Gam, 4 * (size_t)n * g->kp);
+        T_ALLOC(muhist, vb * (size_t)(g->hist_iters + 1)); // mu_t per reverse sweep
         T_ALLOC(gg_m, vb);
     }
 #undef T_ALLOC
@@ -564,7 +664,7 @@ extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const in
         cudaMemsetAsync(us_a, 0, vb, s); // rows past n_active must read as zero
         cudaMemsetAsync(us_b, 0, vb, s);
         if (want_g) {
-            cudaMemsetAsync(Gam, 0, 4 * (size_t)n * g->kp, s);
+            cudaMemsetAsync(muhist, 0, vb * (size_t)(g->hist_iters + 1), s);
             cudaMemsetAsync(gg_m, 0, vb, s);
         }
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
@@ -572,52 +672,61 @@ extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const in
     if (st == PG_OK && n_paths > 0) {
         const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
         seed_kernel<<<pg_blocks(n_paths, 256), 256, 0, s>>>(first, dI, n_paths, spp, n, g->c2m, g->m2r,
-                                                             recompute_weights ? nullptr : rs, nu, us0);
+                                                             recompute_weights == 1 ? nullptr : rs, nu, us0);
         pg_count_launches(1);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     }
     if (st == PG_OK) {
-        if (recompute_weights) {
+        if (recompute_weights == 2) {
+            switch (g->wdtype) {
+                case PG_W_F32: st = adjoint_scatter_k<float>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s); break;
+                case PG_W_BF16:
+                    st = adjoint_scatter_k<__nv_bfloat16>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s);
+                    break;
+                case PG_W_F16: st = adjoint_scatter_k<__half>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s); break;
+            }
+        } else if (recompute_weights) {
             switch (g->kp) {
-                case 4: st = adjoint_recompute<4>(g, nu, mu_a, mu_b, G, B, Gam, s); break;
-                case 8: st = adjoint_recompute<8>(g, nu, mu_a, mu_b, G, B, Gam, s); break;
-                case 16: st = adjoint_recompute<16>(g, nu, mu_a, mu_b, G, B, Gam, s); break;
-                case 32: st = adjoint_recompute<32>(g, nu, mu_a, mu_b, G, B, Gam, s); break;
+                case 4: st = adjoint_recompute<4>(g, nu, mu_a, mu_b, G, B, muhist, s); break;
+                case 8: st = adjoint_recompute<8>(g, nu, mu_a, mu_b, G, B, muhist, s); break;
+                case 16: st = adjoint_recompute<16>(g, nu, mu_a, mu_b, G, B, muhist, s); break;
+                case 32: st = adjoint_recompute<32>(g, nu, mu_a, mu_b, G, B, muhist, s); break;
                 default: st = PG_ERR_UNSUPPORTED;
             }
         } else {
             switch (g->wdtype) {
-                case PG_W_F32: st = adjoint_store<float>(g, nu, us0, mu_a, mu_b, us_a, us_b, G, B, Gam, s); break;
+                case PG_W_F32: st = adjoint_store<float>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s); break;
                 case PG_W_BF16:
-                    st = adjoint_store<__nv_bfloat16>(g, nu, us0, mu_a, mu_b, us_a, us_b, G, B, Gam, s);
+                    st = adjoint_store<__nv_bfloat16>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s);
                     break;
-                case PG_W_F16: st = adjoint_store<__half>(g, nu, us0, mu_a, mu_b, us_a, us_b, G, B, Gam, s); break;
+                case PG_W_F16: st = adjoint_store<__half>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s); break;
             }
-            if (st == PG_OK && n_paths > 0) {
-                const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
-                const float *yT = g->hist + (int64_t)g->hist_iters * (n + 1);
-                switch (g->wdtype) {
-                    case PG_W_F32:
-                        first_rows_kernel<float><<<pg_blocks(n_paths, 256), 256, 0, s>>>(
-                            first, n_paths, n, g->c2m, g->m2r, g->col, (const float *)g->W, rs, yT, g->LV, g->D_m,
-                            nu, g->kp, G);
-                        pg_count_launches(1);
-                        break;
-                    case PG_W_BF16:
-                        first_rows_kernel<__nv_bfloat16><<<pg_blocks(n_paths, 256), 256, 0, s>>>(
-                            first, n_paths, n, g->c2m, g->m2r, g->col, (const __nv_bfloat16 *)g->W, rs, yT, g->LV,
-                            g->D_m, nu, g->kp, G);
-                        pg_count_launches(1);
-                        break;
-                    case PG_W_F16:
-                        first_rows_kernel<__half><<<pg_blocks(n_paths, 256), 256, 0, s>>>(
-                            first, n_paths, n, g->c2m, g->m2r, g->col, (const __half *)g->W, rs, yT, g->LV, g->D_m,
-                            nu, g->kp, G);
-                        pg_count_launches(1);
-                        break;
-                }
-                if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
-                    }
+        }
+        // output term of the first-vertex rows from the stored weights
+        if (st == PG_OK && recompute_weights != 1 && n_paths > 0) {
+            const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
+            const float *yT = g->hist + (int64_t)g->hist_iters * (n + 1);
+            switch (g->wdtype) {
+                case PG_W_F32:
+                    first_rows_kernel<float><<<pg_blocks(n_paths, 256), 256, 0, s>>>(
+                        first, n_paths, n, g->c2m, g->m2r, g->col, (const float *)g->W, rs, yT, g->LV, g->D_m, nu,
+                        g->kp, G);
+                    pg_count_launches(1);
+                    break;
+                case PG_W_BF16:
+                    first_rows_kernel<__nv_bfloat16><<<pg_blocks(n_paths, 256), 256, 0, s>>>(
+                        first, n_paths, n, g->c2m, g->m2r, g->col, (const __nv_bfloat16 *)g->W, rs, yT, g->LV,
+                        g->D_m, nu, g->kp, G);
+                    pg_count_launches(1);
+                    break;
+                case PG_W_F16:
+                    first_rows_kernel<__half><<<pg_blocks(n_paths, 256), 256, 0, s>>>(
+                        first, n_paths, n, g->c2m, g->m2r, g->col, (const __half *)g->W, rs, yT, g->LV, g->D_m, nu,
+                        g->kp, G);
+                    pg_count_launches(1);
+                    break;
+            }
+            if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
         }
     }
     if (st == PG_OK && (grad_sigma_s || grad_albedo_vox)) {
@@ -628,10 +737,10 @@ extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const in
     }
     if (st == PG_OK && want_g) {
         switch (g->kp) {
-            case 4: st = launch_grad_g<4>(g, Gam, B, nu, gg_m, s); break;
-            case 8: st = launch_grad_g<8>(g, Gam, B, nu, gg_m, s); break;
-            case 16: st = launch_grad_g<16>(g, Gam, B, nu, gg_m, s); break;
-            case 32: st = launch_grad_g<32>(g, Gam, B, nu, gg_m, s); break;
+            case 4: st = launch_grad_g<4>(g, muhist, B, nu, gg_m, s); break;
+            case 8: st = launch_grad_g<8>(g, muhist, B, nu, gg_m, s); break;
+            case 16: st = launch_grad_g<16>(g, muhist, B, nu, gg_m, s); break;
+            case 32: st = launch_grad_g<32>(g, muhist, B, nu, gg_m, s); break;
             default: st = PG_ERR_UNSUPPORTED;
         }
         if (st == PG_OK) {
@@ -640,7 +749,7 @@ extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const in
             if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
             }
     }
-    float *bufs[] = {nu, us0, mu_a, mu_b, us_a, us_b, G, B, Gam, gg_m};
+    float *bufs[] = {nu, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, gg_m};
     for (float *p : bufs)
         if (p) cudaFreeAsync(p, s);
     return st;

@@ -56,6 +56,19 @@ __global__ void cell_count_kernel(const uint32_t *__restrict__ sorted_keys, int6
     atomicAdd(&counts[sorted_keys[m]], 1);
 }
 
+// The 26 neighbours of a cell, packed (dx+1) | (dy+1) << 2 | (dz+1) << 4 and
+// ordered by the number of non-zero offsets: faces, then edges, then corners.
+__constant__ int c_ring1[26];
+
+static void ring1_table(int out[26]) {
+    int n = 0;
+    for (int cls = 1; cls <= 3; cls++)
+        for (int dz = -1; dz <= 1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++)
+                    if ((dx != 0) + (dy != 0) + (dz != 0) == cls) out[n++] = (dx + 1) | ((dy + 1) << 2) | ((dz + 1) << 4);
+}
+
 // (d2, id) lexicographic order
 __device__ __forceinline__ bool knn_less(int64_t da, int32_t ia, int64_t db, int32_t ib) {
     return da < db || (da == db && ia < ib);
@@ -95,52 +108,61 @@ __global__ void __launch_bounds__(128) knn_kernel(const uint64_t *__restrict__ q
 
     if (km1 > 0) {
         for (int r = 0;; r++) {
-            for (int dz = -r; dz <= r; dz++) {
-                int z = cz + dz;
-                if (z < 0 || z >= G) continue;
-                for (int dy = -r; dy <= r; dy++) {
-                    int y = cy + dy;
-                    if (y < 0 || y >= G) continue;
-                    bool edge = (dz == -r || dz == r || dy == -r || dy == r);
-                    int step = edge ? 1 : (2 * r > 0 ? 2 * r : 1);
-                    for (int dx = -r; dx <= r; dx += step) {
-                        int x = cx + dx;
-                        if (x < 0 || x >= G) continue;
-                        uint32_t cell = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
-                        int32_t p0 = cell_start[cell], p1 = cell_start[cell + 1];
-                        for (int32_t p = p0; p < p1; p++) {
-                            if (p == m) continue;
-                            uint64_t cq = qpk[p];
-                            int32_t ex = (int32_t)(cq & PG_QMASK) - qx;
-                            int32_t ey = (int32_t)((cq >> 21) & PG_QMASK) - qy;
-                            int32_t ez = (int32_t)((cq >> 42) & PG_QMASK) - qz;
-                            int64_t d2 = (int64_t)ex * ex + (int64_t)ey * ey + (int64_t)ez * ez;
-                            if (d2 > worst_d) continue;
-                            if (r2_max >= 0 && d2 > r2_max) continue;
-                            int32_t id = m2c[p];
-                            if (!knn_less(d2, id, worst_d, worst_i)) continue;
-                            // insert into the sorted list, shifting larger entries up
+            // cells of ring r: r = 0 the own cell; r = 1 the 26 neighbours,
+            // nearest first (faces, edges, corners) so the list fills with
+            // good candidates early; r >= 2 the shell of the (2r+1)^3 block
+            const int span = 2 * r + 1;
+            const int ncell = r == 0 ? 1 : (r == 1 ? 26 : span * span * span);
+            for (int t = 0; t < ncell; t++) {
+                int dx, dy, dz;
+                if (r == 0) {
+                    dx = dy = dz = 0;
+                } else if (r == 1) {
+                    int o = c_ring1[t];
+                    dx = (o & 3) - 1;
+                    dy = ((o >> 2) & 3) - 1;
+                    dz = ((o >> 4) & 3) - 1;
+                } else {
+                    dx = t % span - r;
+                    dy = (t / span) % span - r;
+                    dz = t / (span * span) - r;
+                    if (abs(dx) != r && abs(dy) != r && abs(dz) != r) continue;
+                }
+                const int x = cx + dx, y = cy + dy, z = cz + dz;
+                if (x < 0 || x >= G || y < 0 || y >= G || z < 0 || z >= G) continue;
+                const uint32_t cell = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
+                const int32_t p0 = cell_start[cell], p1 = cell_start[cell + 1];
+                for (int32_t p = p0; p < p1; p++) {
+                    if (p == m) continue;
+                    uint64_t cq = qpk[p];
+                    int32_t ex = (int32_t)(cq & PG_QMASK) - qx;
+                    int32_t ey = (int32_t)((cq >> 21) & PG_QMASK) - qy;
+                    int32_t ez = (int32_t)((cq >> 42) & PG_QMASK) - qz;
+                    int64_t d2 = (int64_t)ex * ex + (int64_t)ey * ey + (int64_t)ez * ez;
+                    if (d2 > worst_d) continue;
+                    if (r2_max >= 0 && d2 > r2_max) continue;
+                    int32_t id = m2c[p];
+                    if (!knn_less(d2, id, worst_d, worst_i)) continue;
+                    // insert into the sorted list, shifting larger entries up
 #pragma unroll
-                            for (int i = M - 1; i > 0; --i) {
-                                if (knn_less(d2, id, bd[i], bi[i])) {
-                                    if (knn_less(d2, id, bd[i - 1], bi[i - 1])) {
-                                        bd[i] = bd[i - 1];
-                                        bi[i] = bi[i - 1];
-                                    } else {
-                                        bd[i] = d2;
-                                        bi[i] = id;
-                                    }
-                                }
+                    for (int i = M - 1; i > 0; --i) {
+                        if (knn_less(d2, id, bd[i], bi[i])) {
+                            if (knn_less(d2, id, bd[i - 1], bi[i - 1])) {
+                                bd[i] = bd[i - 1];
+                                bi[i] = bi[i - 1];
+                            } else {
+                                bd[i] = d2;
+                                bi[i] = id;
                             }
-                            if (knn_less(d2, id, bd[0], bi[0])) {
-                                bd[0] = d2;
-                                bi[0] = id;
-                            }
-                            found++;
-                            worst_d = bd[M - 1];
-                            worst_i = bi[M - 1];
                         }
                     }
+                    if (knn_less(d2, id, bd[0], bi[0])) {
+                        bd[0] = d2;
+                        bi[0] = id;
+                    }
+                    found++;
+                    worst_d = bd[M - 1];
+                    worst_i = bi[M - 1];
                 }
             }
             // lower bound on the distance to any vertex outside the scanned
@@ -188,6 +210,14 @@ static pg_status launch_knn_t(pg_graph *g, cudaStream_t s) {
 }
 
 pg_status pg_launch_knn(pg_graph *g, cudaStream_t s) {
+    static bool table_ready = false; // per process; set on the first build (any device)
+    static int ring[26];
+    if (!table_ready) {
+        ring1_table(ring);
+        table_ready = true;
+    }
+    // the constant lives per device: copy it before every launch (26 ints)
+    PG_CUDA(cudaMemcpyToSymbolAsync(c_ring1, ring, sizeof(ring), 0, cudaMemcpyHostToDevice, s));
     switch (g->kp) {
         case 4: return launch_knn_t<4>(g, s);
         case 8: return launch_knn_t<8>(g, s);

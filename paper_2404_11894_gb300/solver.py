@@ -16,10 +16,12 @@ class Solver:
     """
 
     def __init__(self, k: int, iters: int, wdtype: str = "f32", adjoint: bool = True,
-                 bbox_lo=(0.0, 0.0, 0.0), bbox_hi=(1.0, 1.0, 1.0), recompute_weights: bool = False):
+                 bbox_lo=(0.0, 0.0, 0.0), bbox_hi=(1.0, 1.0, 1.0), recompute_weights: int = 0,
+                 want_g: bool = True):
         self.k, self.iters, self.wdtype, self.adjoint = k, iters, wdtype, adjoint
         self.bbox_lo, self.bbox_hi = bbox_lo, bbox_hi
-        self.recompute_weights = recompute_weights
+        self.recompute_weights = int(recompute_weights)
+        self.want_g = want_g
         self.graph = None
         self.last_image = None
         self.grads = None
@@ -50,7 +52,7 @@ class Solver:
         if use_adj:
             mark("adjoint", 0)
             dI = img - target
-            self.grads = pg_propagate_adjoint(self.graph, dI, first, spp, width, height,
+            self.grads = pg_propagate_adjoint(self.graph, dI, first, spp, width, height, want_g=self.want_g,
                                               recompute_weights=self.recompute_weights)
             mark("adjoint", 1)
         return img

@@ -48,14 +48,14 @@ def _setup(sc, T, seed=5):
     return rec, nbr, target, dI
 
 
-def _gpu_adjoint(pg, rec, sc, T, dI, wdtype="f32", recompute=False, want_g=True):
+def _gpu_adjoint(pg, rec, sc, T, dI, wdtype="f32", recompute=0, want_g=True):
     V = pg.Vertices.from_records(rec)
     graph = pg.pg_build_graph(V, sc.k)
     _, D = pg.pg_aggregate(graph, V, wdtype)
     L = pg.pg_propagate(graph, torch.from_numpy(rec["L0"]).cuda(), T, keep_history=True)
     first = torch.from_numpy(rec["first"]).cuda()
     pg.pg_gather(graph, L, D, first, torch.from_numpy(rec["bg"]).cuda(), sc.spp, sc.width, sc.height)
-    if recompute:
+    if recompute == 1:
         graph.release_weights()
     out = pg.pg_propagate_adjoint(graph, torch.from_numpy(np.asarray(dI, np.float32)).cuda(), first, sc.spp,
                                   sc.width, sc.height, want_g=want_g,
@@ -78,7 +78,7 @@ def small(pg):
     return rec, T, dI, ref
 
 
-@pytest.mark.parametrize("recompute", [False, True], ids=["stored", "recompute"])
+@pytest.mark.parametrize("recompute", [0, 1, 2], ids=["transposed", "recompute", "scatter"])
 def test_adjoint_matches_oracle(pg, small, recompute):
     rec, T, dI, ref = small
     got = _gpu_adjoint(pg, rec, SMALL, T, dI, recompute=recompute)
@@ -87,10 +87,11 @@ def test_adjoint_matches_oracle(pg, small, recompute):
     assert adj_err(got["grad_albedo"], ref["grad_albedo"]) <= ADJ_TOL
 
 
+@pytest.mark.parametrize("mode", [0, 2], ids=["transposed", "scatter"])
 @pytest.mark.parametrize("wdtype", ["bf16", "f16"])
-def test_adjoint_16bit(pg, small, wdtype):
+def test_adjoint_16bit(pg, small, wdtype, mode):
     rec, T, dI, ref = small
-    got = _gpu_adjoint(pg, rec, SMALL, T, dI, wdtype=wdtype, want_g=False)
+    got = _gpu_adjoint(pg, rec, SMALL, T, dI, wdtype=wdtype, want_g=False, recompute=mode)
     # same dLoss/dImage; the operator differs from the FP64 one by the
     # 16-bit rounding of its weights: FP16 element-wise, BF16 (8-bit
     # mantissa) in the L2 norm of the gradient
