@@ -74,14 +74,151 @@ __device__ __forceinline__ bool knn_less(int64_t da, int32_t ia, int64_t db, int
     return da < db || (da == db && ia < ib);
 }
 
+// Fast path: one thread per query over its own cell and the 26 around it;
+// queries that need more rings go to the exact kernel. Each list entry is one
+// 64-bit key
+// (d2 << 31) | caller id, which orders like (d2, id) while d2 < 2^33 (always
+// true for near neighbours at the grid levels used here; a distance at or
+// above 2^33 saturates). A query whose final list holds a saturated
+// distance is queued for the exact kernel below, so the result is exact for
+// any input.
+static constexpr uint64_t KNN_SAT = (1ull << 33) - 1;
+
 template <int KP>
 __global__ void __launch_bounds__(128) knn_kernel(const uint64_t *__restrict__ qpk, const int32_t *__restrict__ cell_start,
                                                   const int32_t *__restrict__ m2c, const int32_t *__restrict__ c2m,
                                                   int64_t n, int k, int level, int64_t r2_max,
-                                                  int32_t *__restrict__ nbr) {
+                                                  int32_t *__restrict__ nbr, int32_t *__restrict__ redo,
+                                                  int32_t *__restrict__ redo_count) {
     constexpr int M = KP - 1;
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n) return;
+    const uint64_t qq = qpk[m];
+    const int32_t qx = (int32_t)(qq & PG_QMASK), qy = (int32_t)((qq >> 21) & PG_QMASK),
+                  qz = (int32_t)((qq >> 42) & PG_QMASK);
+    const int sh = PG_QBITS - level;
+    const int G = 1 << level;
+    const int64_t cs = (int64_t)1 << sh;
+    const int cx = qx >> sh, cy = qy >> sh, cz = qz >> sh;
+    const int km1 = k - 1;
+    // ascending list; the lowest M - (k-1) slots hold key 0, which no
+    // candidate displaces (comparisons are strict), so the (k-1)-th real
+    // entry is always slot M-1
+    const int pad = M - km1;
+    uint64_t bk[M > 0 ? M : 1];
+#pragma unroll
+    for (int i = 0; i < M; i++) bk[i] = i < pad ? 0ull : UINT64_MAX;
+    uint64_t worst = UINT64_MAX;
+    int found = 0;
+    if (km1 > 0) {
+        for (int r = 0;; r++) {
+            const int span = 2 * r + 1;
+            const int ncell = r == 0 ? 1 : (r == 1 ? 26 : span * span * span);
+            for (int t = 0; t < ncell; t++) {
+                int dx, dy, dz;
+                if (r == 0) {
+                    dx = dy = dz = 0;
+                } else if (r == 1) {
+                    int o = c_ring1[t];
+                    dx = (o & 3) - 1;
+                    dy = ((o >> 2) & 3) - 1;
+                    dz = ((o >> 4) & 3) - 1;
+                } else {
+                    dx = t % span - r;
+                    dy = (t / span) % span - r;
+                    dz = t / (span * span) - r;
+                    if (abs(dx) != r && abs(dy) != r && abs(dz) != r) continue;
+                }
+                const int x = cx + dx, y = cy + dy, z = cz + dz;
+                if (x < 0 || x >= G || y < 0 || y >= G || z < 0 || z >= G) continue;
+                const uint32_t cell = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
+                const int32_t p0 = cell_start[cell], p1 = cell_start[cell + 1];
+                for (int32_t p = p0; p < p1; p++) {
+                    if (p == m) continue;
+                    const uint64_t cq = qpk[p];
+                    const int32_t ex = (int32_t)(cq & PG_QMASK) - qx;
+                    const int32_t ey = (int32_t)((cq >> 21) & PG_QMASK) - qy;
+                    const int32_t ez = (int32_t)((cq >> 42) & PG_QMASK) - qz;
+                    const int64_t d2 = (int64_t)ex * ex + (int64_t)ey * ey + (int64_t)ez * ez;
+                    const uint64_t dk = d2 < (int64_t)KNN_SAT ? (uint64_t)d2 : KNN_SAT;
+                    if ((dk << 31) > worst) continue;
+                    if (r2_max >= 0 && d2 > r2_max) continue;
+                    const uint64_t key = (dk << 31) | (uint64_t)(uint32_t)m2c[p];
+                    if (key >= worst) continue;
+                    // insert, shifting larger keys up
+#pragma unroll
+                    for (int i = M - 1; i > 0; --i) {
+                        const uint64_t prev = bk[i - 1];
+                        if (key < bk[i]) bk[i] = key < prev ? prev : key;
+                    }
+                    if (key < bk[0]) bk[0] = key;
+                    found++;
+                    worst = bk[M - 1];
+                }
+            }
+            // lower bound on the distance to any vertex outside the scanned
+            // block of cells [c - r, c + r]^3
+            int64_t bnd = INT64_MAX;
+            {
+                int c[3] = {cx, cy, cz};
+                int32_t q[3] = {qx, qy, qz};
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    int lo_c = c[a] - r, hi_c = c[a] + r;
+                    if (lo_c > 0) {
+                        int64_t dlo = (int64_t)q[a] - (int64_t)lo_c * cs + 1;
+                        bnd = dlo < bnd ? dlo : bnd;
+                    }
+                    if (hi_c < G - 1) {
+                        int64_t dhi = (int64_t)(hi_c + 1) * cs - q[a];
+                        bnd = dhi < bnd ? dhi : bnd;
+                    }
+                }
+            }
+            if (bnd == INT64_MAX) break;                    // whole grid scanned
+            const int64_t bnd2 = bnd * bnd;
+            const int64_t worst_d = worst == UINT64_MAX ? INT64_MAX : (int64_t)(worst >> 31);
+            if (found >= km1 && worst_d < bnd2) break;       // nothing outside can enter
+            if (r2_max >= 0 && bnd2 > r2_max) break;         // nothing outside is in range
+            // a query that needs a second ring (sparse surroundings) would
+            // keep its whole warp busy for ~100 more cells: hand it over
+            if (r == 1) {
+                redo[atomicAdd(redo_count, 1)] = (int32_t)m;
+                return;
+            }
+        }
+    }
+    bool saturated = false;
+#pragma unroll
+    for (int i = 0; i < M; i++)
+        if (i >= pad && bk[i] != UINT64_MAX && (bk[i] >> 31) >= KNN_SAT) saturated = true;
+    if (saturated) {
+        redo[atomicAdd(redo_count, 1)] = (int32_t)m;
+        return;
+    }
+    int32_t *row = nbr + m * KP;
+    row[0] = (int32_t)m;
+#pragma unroll
+    for (int i = 0; i < M; i++) {
+        int pos = i - pad; // rank among the k-1 others
+        if (pos >= 0) row[1 + pos] = bk[i] != UINT64_MAX ? c2m[(int32_t)(bk[i] & 0x7fffffffu)] : -1;
+    }
+    for (int pos = km1; pos < M; pos++) row[1 + pos] = -1;
+}
+
+// Exact path for queued queries: entries (int64 d2, caller id) compared
+// lexicographically.
+template <int KP>
+__global__ void __launch_bounds__(128) knn_exact_kernel(const uint64_t *__restrict__ qpk,
+                                                        const int32_t *__restrict__ cell_start,
+                                                        const int32_t *__restrict__ m2c,
+                                                        const int32_t *__restrict__ c2m, const int32_t *__restrict__ list,
+                                                        const int32_t *__restrict__ d_count, int k, int level,
+                                                        int64_t r2_max, int32_t *__restrict__ nbr) {
+    constexpr int M = KP - 1;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= *d_count) return;
+    const int64_t m = list[t];
     const uint64_t qq = qpk[m];
     const int32_t qx = (int32_t)(qq & PG_QMASK), qy = (int32_t)((qq >> 21) & PG_QMASK),
                   qz = (int32_t)((qq >> 42) & PG_QMASK);
@@ -202,11 +339,30 @@ __global__ void __launch_bounds__(128) knn_kernel(const uint64_t *__restrict__ q
 
 template <int KP>
 static pg_status launch_knn_t(pg_graph *g, cudaStream_t s) {
-    knn_kernel<KP><<<pg_blocks(g->n, 128), 128, 0, s>>>(g->qpk, g->cell_start, g->m2c, g->c2m, g->n, g->k, g->level,
-                                                        g->r2_max, g->nbr);
-    pg_count_launches(1);
-    PG_LAUNCH_CHECK();
-    return PG_OK;
+    const int64_t n = g->n;
+    int32_t *redo = nullptr, *cnt = nullptr;
+    PG_TRY(pg_alloc(nullptr, (void **)&redo, 4 * (size_t)(n > 0 ? n : 1), s));
+    pg_status st = pg_alloc(nullptr, (void **)&cnt, 16, s);
+    if (st == PG_OK && cudaMemsetAsync(cnt, 0, 4, s) != cudaSuccess) st = PG_ERR_CUDA;
+    if (st == PG_OK) {
+        knn_kernel<KP><<<pg_blocks(n, 128), 128, 0, s>>>(g->qpk, g->cell_start, g->m2c, g->c2m, n, g->k, g->level,
+                                                        g->r2_max, g->nbr, redo, cnt);
+        pg_count_launches(1);
+        if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+    }
+    int32_t h_cnt = 0;
+    if (st == PG_OK && (cudaMemcpyAsync(&h_cnt, cnt, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess))
+        st = PG_ERR_CUDA;
+    if (st == PG_OK && h_cnt > 0) {
+        knn_exact_kernel<KP><<<pg_blocks(h_cnt, 128), 128, 0, s>>>(g->qpk, g->cell_start, g->m2c, g->c2m, redo, cnt,
+                                                                  g->k, g->level, g->r2_max, g->nbr);
+        pg_count_launches(1);
+        if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+    }
+    cudaFreeAsync(redo, s);
+    cudaFreeAsync(cnt, s);
+    return st;
 }
 
 pg_status pg_launch_knn(pg_graph *g, cudaStream_t s) {

@@ -74,7 +74,7 @@ __device__ __forceinline__ void block_sum2(double &a, double &b) {
 }
 
 template <int KP, typename WT>
-__global__ void __launch_bounds__(SWEEP_THREADS) sweep_kernel(
+__global__ void __launch_bounds__(SWEEP_THREADS, 8) sweep_kernel(
     const int32_t *__restrict__ col, const WT *__restrict__ W, const float *__restrict__ rscale,
     const float *__restrict__ b, const float *__restrict__ yin, float *__restrict__ yout, int64_t n_active,
     int32_t *__restrict__ ctrl, double2 *__restrict__ partials, double *__restrict__ resid, int t, double tol) {
@@ -84,47 +84,66 @@ __global__ void __launch_bounds__(SWEEP_THREADS) sweep_kernel(
     const int q = lane & (LPR - 1);
     // Each block owns one contiguous chunk of rows and walks it in order:
     // rows are in Morton order, so consecutive rows share most neighbour
-    // columns and their y gathers hit in this SM's L1.
-    constexpr int RPB = SWEEP_THREADS / LPR; // rows per block iteration
-    const int64_t chunk = ((n_active + gridDim.x - 1) / gridDim.x + RPB - 1) / RPB * RPB;
+    // columns and their y gathers hit in this SM's L1. Every iteration
+    // handles two row groups, so each thread has both groups' streamed loads
+    // and gathers in flight before it does any arithmetic.
+    constexpr int RPB = SWEEP_THREADS / LPR; // rows per block per group
+    constexpr int U = 2;                     // row groups per iteration
+    const int64_t chunk = ((n_active + gridDim.x - 1) / gridDim.x + U * RPB - 1) / (U * RPB) * (U * RPB);
     const int64_t r0 = (int64_t)blockIdx.x * chunk;
     const int64_t r1 = min(n_active, r0 + chunk);
     float rd = 0.0f, rn = 0.0f;
-    for (int64_t base = r0; base < r1; base += RPB) { // uniform across the block
-        const int64_t row = base + threadIdx.x / LPR;
-        const bool ok = row < r1;
-        // compensated sum of the row's products (the kernel is memory-bound,
-        // so the extra additions are free; they keep 30+ sweeps at albedo
-        // ~1 within float32 rounding of the exact iterate)
-        float acc = 0.0f, cmp = 0.0f;
-        if (ok) {
-            const int4 c4 = __ldcs(reinterpret_cast<const int4 *>(col + row * KP) + q);
-            const float4 w4 = W4<WT>::load(W + row * KP + q * 4);
-            const float p0 = __fmul_rn(w4.x, __ldg(yin + c4.x));
-            const float p1 = __fmul_rn(w4.y, __ldg(yin + c4.y));
-            const float p2 = __fmul_rn(w4.z, __ldg(yin + c4.z));
-            const float p3 = __fmul_rn(w4.w, __ldg(yin + c4.w));
-            float e;
-            two_sum(p0, p1, acc, cmp);
-            two_sum(acc, p2, acc, e);
-            cmp = __fadd_rn(cmp, e);
-            two_sum(acc, p3, acc, e);
-            cmp = __fadd_rn(cmp, e);
+    for (int64_t base = r0; base < r1; base += U * RPB) { // uniform across the block
+        int64_t row[U];
+        bool ok[U];
+        int4 c4[U];
+        float4 w4[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            row[u] = base + u * RPB + threadIdx.x / LPR;
+            ok[u] = row[u] < r1;
+            if (ok[u]) {
+                c4[u] = __ldcs(reinterpret_cast<const int4 *>(col + row[u] * KP) + q);
+                w4[u] = W4<WT>::load(W + row[u] * KP + q * 4);
+            } else {
+                c4[u] = make_int4(0, 0, 0, 0);
+                w4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        float g[U][4];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            g[u][0] = __ldg(yin + c4[u].x);
+            g[u][1] = __ldg(yin + c4[u].y);
+            g[u][2] = __ldg(yin + c4[u].z);
+            g[u][3] = __ldg(yin + c4[u].w);
         }
 #pragma unroll
-        for (int o = LPR / 2; o > 0; o >>= 1) {
-            float oa = __shfl_xor_sync(0xffffffffu, acc, o), oc = __shfl_xor_sync(0xffffffffu, cmp, o), e;
-            two_sum(acc, oa, acc, e);
-            cmp = __fadd_rn(cmp, __fadd_rn(oc, e));
-        }
-        acc = __fadd_rn(acc, cmp);
-        if (ok && q == 0) {
-            const float s = WTraits<WT>::id == PG_W_F32 ? 1.0f : rscale[row];
-            const float yn = fmaf(acc, s, b[row]);
-            const float d = yn - yin[row];
-            yout[row] = yn;
-            rd = fmaf(d, d, rd);
-            rn = fmaf(yn, yn, rn);
+        for (int u = 0; u < U; u++) {
+            // compensated sum of the row's products (the kernel is memory-bound,
+            // so the extra additions are free; they keep 30+ sweeps at albedo
+            // ~1 within float32 rounding of the exact iterate)
+            float acc, cmp, e;
+            two_sum(__fmul_rn(w4[u].x, g[u][0]), __fmul_rn(w4[u].y, g[u][1]), acc, cmp);
+            two_sum(acc, __fmul_rn(w4[u].z, g[u][2]), acc, e);
+            cmp = __fadd_rn(cmp, e);
+            two_sum(acc, __fmul_rn(w4[u].w, g[u][3]), acc, e);
+            cmp = __fadd_rn(cmp, e);
+#pragma unroll
+            for (int o = LPR / 2; o > 0; o >>= 1) {
+                float oa = __shfl_xor_sync(0xffffffffu, acc, o), oc = __shfl_xor_sync(0xffffffffu, cmp, o);
+                two_sum(acc, oa, acc, e);
+                cmp = __fadd_rn(cmp, __fadd_rn(oc, e));
+            }
+            acc = __fadd_rn(acc, cmp);
+            if (ok[u] && q == 0) {
+                const float sc = WTraits<WT>::id == PG_W_F32 ? 1.0f : rscale[row[u]];
+                const float yn = fmaf(acc, sc, b[row[u]]);
+                const float d = yn - yin[row[u]];
+                yout[row[u]] = yn;
+                rd = fmaf(d, d, rd);
+                rn = fmaf(yn, yn, rn);
+            }
         }
     }
     double a = rd, bb = rn;
