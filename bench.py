@@ -141,7 +141,7 @@ def run_gpu(args):
     dev_target = host_target.to(dev)
     V = pg.Vertices({k: dev_in[k] for k in pg.VERTEX_F32 + ("e_delta", "succ")})
     solver = pg.Solver(k=sc.k, iters=sc.iters, wdtype="f32", adjoint=not args.no_adjoint,
-                       recompute_weights=args.adjoint_mode)
+                       recompute_weights=args.adjoint_mode, want_g=False)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
@@ -191,6 +191,20 @@ def run_gpu(args):
     peak, peak_kind = _peaks()
     traffic = _profile_traffic("sweep_f32", n)
 
+    # ---- the adjoint with the HG g gradient as well (not part of the step)
+    adj_g_ms = None
+    if not args.no_adjoint and not args.quick:
+        e2, e3 = ev(), ev()
+        solver.want_g = True
+        solver.step(V, dev_in["L0"], dev_in["first"], dev_in["bg"], sc.spp, sc.width, sc.height, dev_target)
+        torch.cuda.synchronize()
+        marks = {"adjoint": (e2, e3)}
+        solver.step(V, dev_in["L0"], dev_in["first"], dev_in["bg"], sc.spp, sc.width, sc.height, dev_target,
+                    marks=marks)
+        torch.cuda.synchronize()
+        adj_g_ms = e2.elapsed_time(e3)
+        solver.want_g = False
+
     # ---- 16-bit weights: propagation rate and error against FP32 (same inputs)
     prec = {}
     if not args.quick:
@@ -233,11 +247,14 @@ def run_gpu(args):
         "config": {"workload": sc.name, "vertices": n, "paths": P, "k": sc.k, "iters": sc.iters,
                    "weights": "f32", "nnz_per_sweep": nnz, "n_active": info["n_active"],
                    "sweeps_per_step": sweeps_per_step, "edge_updates_per_step": edge_updates_step,
-                   "step": "build+aggregate+propagate(history)+gather" + ("" if args.no_adjoint else "+adjoint"),
+                   "step": "build+aggregate+propagate(history)+gather" + (
+                       "" if args.no_adjoint else "+adjoint(sigma_s, per-voxel albedo)"),
+                   "adjoint_mode": ["transposed", "recompute", "scatter"][args.adjoint_mode],
                    "l2": "inputs larger than L2 (vertex records %.0f MB > 129 MB)" % (
                        sum(int(v.numel() * v.element_size()) for v in dev_in.values()) / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "stages_ms": stage_ms,
+        "adjoint_with_g_gradient_ms": adj_g_ms,
         "propagate_edge_updates_per_s": nnz / (sweep_ms / 1e3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "sweep_kernel<16,float>",
@@ -351,7 +368,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the 16-bit weight runs")
     ap.add_argument("--oracle-stride", type=int, default=10)
     ap.add_argument("--scale", type=float, default=1.0, help="image resolution factor (profiling only)")
-    ap.add_argument("--adjoint-mode", type=int, default=2, choices=[0, 1, 2],
+    ap.add_argument("--adjoint-mode", type=int, default=0, choices=[0, 1, 2],
                     help="reverse sweep: 0 transposed copy, 1 recomputed weights, 2 atomic scatter")
     args = ap.parse_args()
     if args.warmup < 3:

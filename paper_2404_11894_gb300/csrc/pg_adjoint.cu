@@ -81,24 +81,61 @@ __global__ void tfill_kernel(const int32_t *__restrict__ col, const WT *__restri
     tW[pos] = W[e];
 }
 
-// order each column's entries by source row (a row appears once per column)
+// Order each column's entries by source row (a row appears once per column),
+// which makes the reverse sweep's summation order deterministic. Columns of
+// up to 32 entries (all of them for k <= 16 in practice) are sorted in
+// registers by a bitonic network; longer ones by insertion sort in memory.
 template <typename WT>
-__global__ void tsort_kernel(const int32_t *__restrict__ tptr, int64_t ncols, int32_t *__restrict__ trow,
-                             WT *__restrict__ tW) {
+__global__ void __launch_bounds__(128) tsort_kernel(const int32_t *__restrict__ tptr, int64_t ncols,
+                                                    int32_t *__restrict__ trow, WT *__restrict__ tW) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncols) return;
-    int32_t a = tptr[c], b = tptr[c + 1];
+    const int32_t a = tptr[c], b = tptr[c + 1], len = b - a;
+    if (len <= 1) return;
+    if (len <= 32) {
+        int32_t kr[32];
+        WT kw[32];
+#pragma unroll
+        for (int i = 0; i < 32; i++) {
+            kr[i] = i < len ? trow[a + i] : INT32_MAX;
+            kw[i] = i < len ? tW[a + i] : WT(0.0f);
+        }
+#pragma unroll
+        for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+#pragma unroll
+                for (int i = 0; i < 32; i++) {
+                    const int j = i ^ stride;
+                    if (j > i) {
+                        const bool up = (i & size) == 0;
+                        if ((kr[i] > kr[j]) == up) {
+                            int32_t tr = kr[i]; kr[i] = kr[j]; kr[j] = tr;
+                            WT tw = kw[i]; kw[i] = kw[j]; kw[j] = tw;
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 32; i++)
+            if (i < len) {
+                trow[a + i] = kr[i];
+                tW[a + i] = kw[i];
+            }
+        return;
+    }
     for (int32_t i = a + 1; i < b; i++) {
-        int32_t kr = trow[i];
-        WT kw = tW[i];
+        int32_t r = trow[i];
+        WT w = tW[i];
         int32_t j = i - 1;
-        while (j >= a && trow[j] > kr) {
+        while (j >= a && trow[j] > r) {
             trow[j + 1] = trow[j];
             tW[j + 1] = tW[j];
             j--;
         }
-        trow[j + 1] = kr;
-        tW[j + 1] = kw;
+        trow[j + 1] = r;
+        tW[j + 1] = w;
     }
 }
 
@@ -118,37 +155,61 @@ __global__ void seed_kernel(const int32_t *__restrict__ first, const float *__re
 }
 
 // ------------------------------------------------------------------ reverse sweep (stored transpose)
-// One group of 8 lanes per column c: mu_out[c] = sum_e tW[e] us_in[trow[e]].
-// Also accumulates G[c] += mu_in[c] * y_t[c] and B[c] += mu_in[c] when y_t.
+// Four lanes per column c: mu_out[c] = sum_e tW[e] us_in[trow[e]] over the
+// column's entries (rows ascending). Each lane loads all of its (up to 8)
+// entries before using them, so a column costs one round trip, and each
+// block walks one contiguous chunk of columns (neighbouring columns draw on
+// neighbouring rows). Also accumulates G[c] += mu_in[c] y_t[c] and
+// B[c] += mu_in[c] when y_t is given.
+static constexpr int TS_THREADS = 256;
+static constexpr int TS_LPC = 4;
+static constexpr int TS_PER_LANE = 8; // 4 lanes x 8 = 32 entries per column pass
+
 template <typename WT>
-__global__ void __launch_bounds__(256) tsweep_kernel(const int32_t *__restrict__ tptr,
-                                                     const int32_t *__restrict__ trow, const WT *__restrict__ tW,
-                                                     const float *__restrict__ us_in, const float *__restrict__ mu_in,
-                                                     const float *__restrict__ y_t, const float *__restrict__ rscale,
-                                                     int64_t ncols, int write_out, float *__restrict__ mu_out,
-                                                     float *__restrict__ us_out, float *__restrict__ G,
-                                                     float *__restrict__ B) {
-    constexpr int LPC = 8;
+__global__ void __launch_bounds__(TS_THREADS, 8) tsweep_kernel(
+    const int32_t *__restrict__ tptr, const int32_t *__restrict__ trow, const WT *__restrict__ tW,
+    const float *__restrict__ us_in, const float *__restrict__ mu_in, const float *__restrict__ y_t,
+    const float *__restrict__ rscale, int64_t ncols, int write_out, float *__restrict__ mu_out,
+    float *__restrict__ us_out, float *__restrict__ G, float *__restrict__ B) {
+    constexpr int CPB = TS_THREADS / TS_LPC; // columns per block per iteration
     const int lane = threadIdx.x & 31;
-    const int q = lane & (LPC - 1);
-    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPC;
-    const bool ok = c < ncols;
-    float acc = 0.0f;
-    if (ok && write_out) {
-        int32_t a = tptr[c], b = tptr[c + 1];
-        for (int32_t e = a + q; e < b; e += LPC) acc = fmaf(wload<WT>(tW, e), __ldg(us_in + trow[e]), acc);
-    }
+    const int q = lane & (TS_LPC - 1);
+    const int64_t chunk = ((ncols + gridDim.x - 1) / gridDim.x + CPB - 1) / CPB * CPB;
+    const int64_t c0 = (int64_t)blockIdx.x * chunk;
+    const int64_t c1 = min(ncols, c0 + chunk);
+    for (int64_t base = c0; base < c1; base += CPB) {
+        const int64_t c = base + threadIdx.x / TS_LPC;
+        const bool ok = c < c1;
+        float acc = 0.0f;
+        if (ok && write_out) {
+            int32_t a = tptr[c];
+            const int32_t b = tptr[c + 1];
+            for (; a < b; a += TS_LPC * TS_PER_LANE) {
+                int32_t rr[TS_PER_LANE];
+                float ww[TS_PER_LANE];
 #pragma unroll
-    for (int o = LPC / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (ok && q == 0) {
-        if (write_out) {
-            mu_out[c] = acc;
-            us_out[c] = rscale ? acc * rscale[c] : acc;
+                for (int u = 0; u < TS_PER_LANE; u++) {
+                    const int32_t e = a + q + TS_LPC * u;
+                    rr[u] = e < b ? trow[e] : -1;
+                    ww[u] = e < b ? wload<WT>(tW, e) : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < TS_PER_LANE; u++)
+                    if (rr[u] >= 0) acc = fmaf(ww[u], __ldg(us_in + rr[u]), acc);
+            }
         }
-        if (y_t) {
-            float m = mu_in[c];
-            G[c] = fmaf(m, y_t[c], G[c]);
-            B[c] += m;
+#pragma unroll
+        for (int o = TS_LPC / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (ok && q == 0) {
+            if (write_out) {
+                mu_out[c] = acc;
+                us_out[c] = rscale ? acc * rscale[c] : acc;
+            }
+            if (y_t) {
+                const float m = mu_in[c];
+                G[c] = fmaf(m, y_t[c], G[c]);
+                B[c] += m;
+            }
         }
     }
 }
@@ -490,7 +551,7 @@ static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
                                                             g->t_row, (WT *)g->t_W);
     pg_count_launches(1);
     PG_LAUNCH_CHECK();
-    tsort_kernel<WT><<<pg_blocks(n, 128), 128, 0, s>>>(g->t_ptr, n, g->t_row, (WT *)g->t_W);
+    tsort_kernel<WT><<<pg_blocks(g->n_active, 128), 128, 0, s>>>(g->t_ptr, g->n_active, g->t_row, (WT *)g->t_W);
     pg_count_launches(1);
     PG_LAUNCH_CHECK();
     cudaFreeAsync(fill, s);
@@ -506,18 +567,20 @@ static pg_status adjoint_store(pg_graph *g, float *us0, float *mu_a, float *mu_b
     const int64_t stride = n + 1;
     const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
     if (!g->t_ptr) PG_TRY(build_transpose<WT>(g, s));
-    const int tb = pg_blocks(na * 8, 256);
+    int64_t need = (na * TS_LPC + TS_THREADS - 1) / TS_THREADS;
+    int64_t cap = (int64_t)pg_num_sms() * 8;
+    const int tb = (int)(need < cap ? (need > 0 ? need : 1) : cap);
     // mu_t lives in slice t of the history when one is kept, else ping-pong
     auto mu_slot = [&](int t) { return muhist ? muhist + (int64_t)t * stride : ((t & 1) ? mu_b : mu_a); };
     float *us_cur = us_a, *us_nxt = us_b;
     // mu_T = W^T nu
-    tsweep_kernel<WT><<<tb, 256, 0, s>>>(g->t_ptr, g->t_row, (const WT *)g->t_W, us0, nullptr, nullptr, rs, na, 1,
+    tsweep_kernel<WT><<<tb, TS_THREADS, 0, s>>>(g->t_ptr, g->t_row, (const WT *)g->t_W, us0, nullptr, nullptr, rs, na, 1,
                                          mu_slot(T), us_cur, G, B);
     pg_count_launches(1);
     PG_LAUNCH_CHECK();
     for (int t = T; t >= 1; t--) {
         const float *y_t = g->hist + (int64_t)t * stride;
-        tsweep_kernel<WT><<<tb, 256, 0, s>>>(g->t_ptr, g->t_row, (const WT *)g->t_W, us_cur, mu_slot(t), y_t, rs,
+        tsweep_kernel<WT><<<tb, TS_THREADS, 0, s>>>(g->t_ptr, g->t_row, (const WT *)g->t_W, us_cur, mu_slot(t), y_t, rs,
                                              na, t > 1 ? 1 : 0, mu_slot(t - 1), us_nxt, G, B);
         pg_count_launches(1);
         PG_LAUNCH_CHECK();
