@@ -131,6 +131,9 @@ typedef struct {
     int64_t device_bytes;/* device memory held by the graph */
     int32_t weight_dtype;
     int32_t history_iters; /* sweeps stored by the last pg_propagate, -1 none */
+    int64_t knn_exact;   /* queries the graph build resolved with its exact
+                            (slow) neighbour search: sparse surroundings,
+                            large distances or dense ties */
 } pg_graph_info;
 
 pg_status pg_graph_get_info(const pg_graph *g, pg_graph_info *info);

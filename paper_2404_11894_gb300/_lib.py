@@ -31,7 +31,7 @@ class PgGraphInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("k", ctypes.c_int32), ("row_width", ctypes.c_int32),
                 ("grid_level", ctypes.c_int32), ("aggregated", ctypes.c_int32), ("n_active", ctypes.c_int64),
                 ("nnz_swept", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("weight_dtype", ctypes.c_int32),
-                ("history_iters", ctypes.c_int32)]
+                ("history_iters", ctypes.c_int32), ("knn_exact", ctypes.c_int64)]
 
 
 EXPORTS = ("pg_build_graph", "pg_graph_neighbors", "pg_graph_get_info", "pg_aggregate", "pg_propagate",

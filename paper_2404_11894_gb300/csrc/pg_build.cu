@@ -3,7 +3,8 @@
 // Vertices are quantised to 21-bit integer coordinates, bucketed into a
 // uniform grid of 2^L cells per axis whose cells are numbered in Morton
 // order, and stably sorted by cell (so a cell is a contiguous range of the
-// sorted "Morton order" m, and spatially close vertices are close in m).
+// sorted "Morton order" m, and spatially close vertices are close in m). A
+// table indexed by the cell's (x, y, z) gives each cell's (start, count).
 // Each query then scans rings of cells around its own and keeps its k-1
 // nearest others in registers, ordered by (squared integer distance, caller
 // index), until the k-1-th distance is provably below any unscanned cell.
@@ -15,7 +16,7 @@
 __global__ void quantize_kernel(const float *__restrict__ px, const float *__restrict__ py,
                                 const float *__restrict__ pz, int64_t n, float lo0, float lo1, float lo2,
                                 float scale, int level, uint32_t *__restrict__ cellkey, int32_t *__restrict__ idx,
-                                uint64_t *__restrict__ qpk_c, int32_t *__restrict__ flags) {
+                                int4 *__restrict__ qrec_c, int32_t *__restrict__ flags) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     float p[3] = {px[v], py[v], pz[v]};
@@ -38,16 +39,36 @@ __global__ void quantize_kernel(const float *__restrict__ px, const float *__res
     int sh = PG_QBITS - level;
     cellkey[v] = morton3(q[0] >> sh, q[1] >> sh, q[2] >> sh);
     idx[v] = (int32_t)v;
-    qpk_c[v] = (uint64_t)q[0] | ((uint64_t)q[1] << 21) | ((uint64_t)q[2] << 42);
+    qrec_c[v] = make_int4((int32_t)q[0], (int32_t)q[1], (int32_t)q[2], (int32_t)v);
 }
 
-__global__ void permute_build_kernel(const int32_t *__restrict__ m2c, const uint64_t *__restrict__ qpk_c,
-                                     int64_t n, uint64_t *__restrict__ qpk, int32_t *__restrict__ c2m) {
+__global__ void permute_build_kernel(const int32_t *__restrict__ m2c, const int4 *__restrict__ qrec_c, int64_t n,
+                                     int4 *__restrict__ qrec, int32_t *__restrict__ c2m) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n) return;
     int32_t c = m2c[m];
-    qpk[m] = qpk_c[c];
+    qrec[m] = qrec_c[c]; // .w is the caller index
     c2m[c] = (int32_t)m;
+}
+
+// (start, count) of every cell, indexed x + G (y + G z), from the Morton-
+// indexed exclusive prefix of the cell counts
+__device__ __forceinline__ uint32_t compact1by2(uint32_t x) {
+    x &= 0x09249249u;
+    x = (x ^ (x >> 2)) & 0x030C30C3u;
+    x = (x ^ (x >> 4)) & 0x0300F00Fu;
+    x = (x ^ (x >> 8)) & 0x030000FFu;
+    x = (x ^ (x >> 16)) & 0x000003FFu;
+    return x;
+}
+__global__ void cell_table_kernel(const int32_t *__restrict__ cell_start, int64_t ncells, int level,
+                                  int2 *__restrict__ cell_se) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    uint32_t x = compact1by2((uint32_t)c), y = compact1by2((uint32_t)c >> 1), z = compact1by2((uint32_t)c >> 2);
+    int64_t lin = (int64_t)x + ((int64_t)y << level) + ((int64_t)z << (2 * level));
+    int32_t a = cell_start[c];
+    cell_se[lin] = make_int2(a, cell_start[c + 1] - a);
 }
 
 __global__ void cell_count_kernel(const uint32_t *__restrict__ sorted_keys, int64_t n, int32_t *__restrict__ counts) {
@@ -76,26 +97,24 @@ __device__ __forceinline__ bool knn_less(int64_t da, int32_t ia, int64_t db, int
 
 // Fast path: one thread per query over its own cell and the 26 around it;
 // queries that need more rings go to the exact kernel. Each list entry is one
-// 64-bit key
-// (d2 << 31) | caller id, which orders like (d2, id) while d2 < 2^33 (always
-// true for near neighbours at the grid levels used here; a distance at or
-// above 2^33 saturates). A query whose final list holds a saturated
-// distance is queued for the exact kernel below, so the result is exact for
-// any input.
+// 64-bit key (d2 << 31) | caller id, which orders like (d2, id) while
+// d2 < 2^33. With cells of at most 2^14 quantisation units (grid level >= 7)
+// every candidate of the 3x3x3 block is closer than two cells per axis, so
+// d2 < 3 * 2^30 and the distance is computed in 32-bit arithmetic (D32);
+// otherwise in 64-bit, where a distance of 2^33 or more saturates and a final
+// list holding one is redone exactly.
 static constexpr uint64_t KNN_SAT = (1ull << 33) - 1;
 
-template <int KP>
-__global__ void __launch_bounds__(128) knn_kernel(const uint64_t *__restrict__ qpk, const int32_t *__restrict__ cell_start,
-                                                  const int32_t *__restrict__ m2c, const int32_t *__restrict__ c2m,
+template <int KP, bool D32>
+__global__ void __launch_bounds__(128, 4) knn_kernel(const int4 *__restrict__ qrec, const int2 *__restrict__ cell_se,
                                                   int64_t n, int k, int level, int64_t r2_max,
-                                                  int32_t *__restrict__ nbr, int32_t *__restrict__ redo,
-                                                  int32_t *__restrict__ redo_count) {
+                                                  const int32_t *__restrict__ c2m, int32_t *__restrict__ nbr,
+                                                  int32_t *__restrict__ redo, int32_t *__restrict__ redo_count) {
     constexpr int M = KP - 1;
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n) return;
-    const uint64_t qq = qpk[m];
-    const int32_t qx = (int32_t)(qq & PG_QMASK), qy = (int32_t)((qq >> 21) & PG_QMASK),
-                  qz = (int32_t)((qq >> 42) & PG_QMASK);
+    const int4 qr = qrec[m];
+    const int32_t qx = qr.x, qy = qr.y, qz = qr.z;
     const int sh = PG_QBITS - level;
     const int G = 1 << level;
     const int64_t cs = (int64_t)1 << sh;
@@ -109,98 +128,90 @@ __global__ void __launch_bounds__(128) knn_kernel(const uint64_t *__restrict__ q
 #pragma unroll
     for (int i = 0; i < M; i++) bk[i] = i < pad ? 0ull : UINT64_MAX;
     uint64_t worst = UINT64_MAX;
+    uint32_t worst32 = UINT32_MAX; // worst's distance part, clamped (D32)
     int found = 0;
     if (km1 > 0) {
-        for (int r = 0;; r++) {
-            const int span = 2 * r + 1;
-            const int ncell = r == 0 ? 1 : (r == 1 ? 26 : span * span * span);
-            for (int t = 0; t < ncell; t++) {
-                int dx, dy, dz;
-                if (r == 0) {
-                    dx = dy = dz = 0;
-                } else if (r == 1) {
-                    int o = c_ring1[t];
-                    dx = (o & 3) - 1;
-                    dy = ((o >> 2) & 3) - 1;
-                    dz = ((o >> 4) & 3) - 1;
+        for (int t = 0; t < 27; t++) {
+            int dx = 0, dy = 0, dz = 0;
+            if (t > 0) {
+                const int o = c_ring1[t - 1];
+                dx = (o & 3) - 1;
+                dy = ((o >> 2) & 3) - 1;
+                dz = ((o >> 4) & 3) - 1;
+            }
+            const int x = cx + dx, y = cy + dy, z = cz + dz;
+            if (x < 0 || x >= G || y < 0 || y >= G || z < 0 || z >= G) continue;
+            const int2 se = cell_se[(int64_t)x + ((int64_t)y << level) + ((int64_t)z << (2 * level))];
+            const int32_t p1 = se.x + se.y;
+            for (int32_t p = se.x; p < p1; p++) {
+                if (p == m) continue;
+                const int4 c = qrec[p];
+                uint64_t key;
+                if (D32) {
+                    const int32_t ex = c.x - qx, ey = c.y - qy, ez = c.z - qz;
+                    const uint32_t d2 = (uint32_t)(ex * ex) + (uint32_t)(ey * ey) + (uint32_t)(ez * ez);
+                    if (d2 > worst32) continue;
+                    if (r2_max >= 0 && (int64_t)d2 > r2_max) continue;
+                    key = ((uint64_t)d2 << 31) | (uint64_t)(uint32_t)c.w;
                 } else {
-                    dx = t % span - r;
-                    dy = (t / span) % span - r;
-                    dz = t / (span * span) - r;
-                    if (abs(dx) != r && abs(dy) != r && abs(dz) != r) continue;
-                }
-                const int x = cx + dx, y = cy + dy, z = cz + dz;
-                if (x < 0 || x >= G || y < 0 || y >= G || z < 0 || z >= G) continue;
-                const uint32_t cell = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
-                const int32_t p0 = cell_start[cell], p1 = cell_start[cell + 1];
-                for (int32_t p = p0; p < p1; p++) {
-                    if (p == m) continue;
-                    const uint64_t cq = qpk[p];
-                    const int32_t ex = (int32_t)(cq & PG_QMASK) - qx;
-                    const int32_t ey = (int32_t)((cq >> 21) & PG_QMASK) - qy;
-                    const int32_t ez = (int32_t)((cq >> 42) & PG_QMASK) - qz;
-                    const int64_t d2 = (int64_t)ex * ex + (int64_t)ey * ey + (int64_t)ez * ez;
+                    const int64_t ex = c.x - qx, ey = c.y - qy, ez = c.z - qz;
+                    const int64_t d2 = ex * ex + ey * ey + ez * ez;
                     const uint64_t dk = d2 < (int64_t)KNN_SAT ? (uint64_t)d2 : KNN_SAT;
                     if ((dk << 31) > worst) continue;
                     if (r2_max >= 0 && d2 > r2_max) continue;
-                    const uint64_t key = (dk << 31) | (uint64_t)(uint32_t)m2c[p];
-                    if (key >= worst) continue;
-                    // insert, shifting larger keys up
-#pragma unroll
-                    for (int i = M - 1; i > 0; --i) {
-                        const uint64_t prev = bk[i - 1];
-                        if (key < bk[i]) bk[i] = key < prev ? prev : key;
-                    }
-                    if (key < bk[0]) bk[0] = key;
-                    found++;
-                    worst = bk[M - 1];
+                    key = (dk << 31) | (uint64_t)(uint32_t)c.w;
                 }
-            }
-            // lower bound on the distance to any vertex outside the scanned
-            // block of cells [c - r, c + r]^3
-            int64_t bnd = INT64_MAX;
-            {
-                int c[3] = {cx, cy, cz};
-                int32_t q[3] = {qx, qy, qz};
+                if (key >= worst) continue;
+                // insert, shifting larger keys up
 #pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    int lo_c = c[a] - r, hi_c = c[a] + r;
-                    if (lo_c > 0) {
-                        int64_t dlo = (int64_t)q[a] - (int64_t)lo_c * cs + 1;
-                        bnd = dlo < bnd ? dlo : bnd;
-                    }
-                    if (hi_c < G - 1) {
-                        int64_t dhi = (int64_t)(hi_c + 1) * cs - q[a];
-                        bnd = dhi < bnd ? dhi : bnd;
-                    }
+                for (int i = M - 1; i > 0; --i) {
+                    const uint64_t prev = bk[i - 1];
+                    if (key < bk[i]) bk[i] = key < prev ? prev : key;
                 }
-            }
-            if (bnd == INT64_MAX) break;                    // whole grid scanned
-            const int64_t bnd2 = bnd * bnd;
-            const int64_t worst_d = worst == UINT64_MAX ? INT64_MAX : (int64_t)(worst >> 31);
-            if (found >= km1 && worst_d < bnd2) break;       // nothing outside can enter
-            if (r2_max >= 0 && bnd2 > r2_max) break;         // nothing outside is in range
-            // a query that needs a second ring (sparse surroundings) would
-            // keep its whole warp busy for ~100 more cells: hand it over
-            if (r == 1) {
-                redo[atomicAdd(redo_count, 1)] = (int32_t)m;
-                return;
+                if (key < bk[0]) bk[0] = key;
+                found++;
+                worst = bk[M - 1];
+                const uint64_t wd = worst >> 31;
+                worst32 = wd > 0xffffffffull ? 0xffffffffu : (uint32_t)wd;
             }
         }
-    }
-    bool saturated = false;
+        // done iff the (k-1)-th entry is closer than anything outside the block
+        int64_t bnd = INT64_MAX;
+        {
+            const int cc[3] = {cx, cy, cz};
+            const int32_t q[3] = {qx, qy, qz};
 #pragma unroll
-    for (int i = 0; i < M; i++)
-        if (i >= pad && bk[i] != UINT64_MAX && (bk[i] >> 31) >= KNN_SAT) saturated = true;
-    if (saturated) {
-        redo[atomicAdd(redo_count, 1)] = (int32_t)m;
-        return;
+            for (int a2 = 0; a2 < 3; a2++) {
+                if (cc[a2] - 1 > 0) {
+                    const int64_t dlo = (int64_t)q[a2] - (int64_t)(cc[a2] - 1) * cs + 1;
+                    bnd = dlo < bnd ? dlo : bnd;
+                }
+                if (cc[a2] + 1 < G - 1) {
+                    const int64_t dhi = (int64_t)(cc[a2] + 2) * cs - q[a2];
+                    bnd = dhi < bnd ? dhi : bnd;
+                }
+            }
+        }
+        bool done = bnd == INT64_MAX; // whole grid scanned
+        if (!done) {
+            const int64_t bnd2 = bnd * bnd;
+            const int64_t worst_d = worst == UINT64_MAX ? INT64_MAX : (int64_t)(worst >> 31);
+            done = (found >= km1 && worst_d < bnd2) || (r2_max >= 0 && bnd2 > r2_max);
+        }
+        bool saturated = false;
+#pragma unroll
+        for (int i = 0; i < M; i++)
+            if (i >= pad && bk[i] != UINT64_MAX && (bk[i] >> 31) >= KNN_SAT) saturated = true;
+        if (!done || saturated) {
+            redo[atomicAdd(redo_count, 1)] = (int32_t)m;
+            return;
+        }
     }
     int32_t *row = nbr + m * KP;
     row[0] = (int32_t)m;
 #pragma unroll
     for (int i = 0; i < M; i++) {
-        int pos = i - pad; // rank among the k-1 others
+        const int pos = i - pad; // rank among the k-1 others
         if (pos >= 0) row[1 + pos] = bk[i] != UINT64_MAX ? c2m[(int32_t)(bk[i] & 0x7fffffffu)] : -1;
     }
     for (int pos = km1; pos < M; pos++) row[1 + pos] = -1;
@@ -209,9 +220,8 @@ __global__ void __launch_bounds__(128) knn_kernel(const uint64_t *__restrict__ q
 // Exact path for queued queries: entries (int64 d2, caller id) compared
 // lexicographically.
 template <int KP>
-__global__ void __launch_bounds__(128) knn_exact_kernel(const uint64_t *__restrict__ qpk,
-                                                        const int32_t *__restrict__ cell_start,
-                                                        const int32_t *__restrict__ m2c,
+__global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__ qrec,
+                                                        const int2 *__restrict__ cell_se,
                                                         const int32_t *__restrict__ c2m, const int32_t *__restrict__ list,
                                                         const int32_t *__restrict__ d_count, int k, int level,
                                                         int64_t r2_max, int32_t *__restrict__ nbr) {
@@ -219,9 +229,8 @@ __global__ void __launch_bounds__(128) knn_exact_kernel(const uint64_t *__restri
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= *d_count) return;
     const int64_t m = list[t];
-    const uint64_t qq = qpk[m];
-    const int32_t qx = (int32_t)(qq & PG_QMASK), qy = (int32_t)((qq >> 21) & PG_QMASK),
-                  qz = (int32_t)((qq >> 42) & PG_QMASK);
+    const int4 qr = qrec[m];
+    const int32_t qx = qr.x, qy = qr.y, qz = qr.z;
     const int sh = PG_QBITS - level;
     const int G = 1 << level;
     const int64_t cs = (int64_t)1 << sh;
@@ -267,18 +276,16 @@ __global__ void __launch_bounds__(128) knn_exact_kernel(const uint64_t *__restri
                 }
                 const int x = cx + dx, y = cy + dy, z = cz + dz;
                 if (x < 0 || x >= G || y < 0 || y >= G || z < 0 || z >= G) continue;
-                const uint32_t cell = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
-                const int32_t p0 = cell_start[cell], p1 = cell_start[cell + 1];
+                const int2 se = cell_se[(int64_t)x + ((int64_t)y << level) + ((int64_t)z << (2 * level))];
+                const int32_t p0 = se.x, p1 = se.x + se.y;
                 for (int32_t p = p0; p < p1; p++) {
                     if (p == m) continue;
-                    uint64_t cq = qpk[p];
-                    int32_t ex = (int32_t)(cq & PG_QMASK) - qx;
-                    int32_t ey = (int32_t)((cq >> 21) & PG_QMASK) - qy;
-                    int32_t ez = (int32_t)((cq >> 42) & PG_QMASK) - qz;
-                    int64_t d2 = (int64_t)ex * ex + (int64_t)ey * ey + (int64_t)ez * ez;
+                    const int4 cq = qrec[p];
+                    const int64_t ex = cq.x - qx, ey = cq.y - qy, ez = cq.z - qz;
+                    const int64_t d2 = ex * ex + ey * ey + ez * ez;
                     if (d2 > worst_d) continue;
                     if (r2_max >= 0 && d2 > r2_max) continue;
-                    int32_t id = m2c[p];
+                    const int32_t id = cq.w;
                     if (!knn_less(d2, id, worst_d, worst_i)) continue;
                     // insert into the sorted list, shifting larger entries up
 #pragma unroll
@@ -345,18 +352,25 @@ static pg_status launch_knn_t(pg_graph *g, cudaStream_t s) {
     pg_status st = pg_alloc(nullptr, (void **)&cnt, 16, s);
     if (st == PG_OK && cudaMemsetAsync(cnt, 0, 4, s) != cudaSuccess) st = PG_ERR_CUDA;
     if (st == PG_OK) {
-        knn_kernel<KP><<<pg_blocks(n, 128), 128, 0, s>>>(g->qpk, g->cell_start, g->m2c, g->c2m, n, g->k, g->level,
-                                                        g->r2_max, g->nbr, redo, cnt);
-        pg_count_launches(1);
+        if (g->level >= 7) {
+            knn_kernel<KP, true><<<pg_blocks(n, 128), 128, 0, s>>>(g->qrec, g->cell_se, n, g->k, g->level, g->r2_max,
+                                                                  g->c2m, g->nbr, redo, cnt);
+            pg_count_launches(1);
+        } else {
+            knn_kernel<KP, false><<<pg_blocks(n, 128), 128, 0, s>>>(g->qrec, g->cell_se, n, g->k, g->level,
+                                                                   g->r2_max, g->c2m, g->nbr, redo, cnt);
+            pg_count_launches(1);
+        }
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     }
     int32_t h_cnt = 0;
     if (st == PG_OK && (cudaMemcpyAsync(&h_cnt, cnt, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                         cudaStreamSynchronize(s) != cudaSuccess))
         st = PG_ERR_CUDA;
+    g->knn_exact = h_cnt;
     if (st == PG_OK && h_cnt > 0) {
-        knn_exact_kernel<KP><<<pg_blocks(h_cnt, 128), 128, 0, s>>>(g->qpk, g->cell_start, g->m2c, g->c2m, redo, cnt,
-                                                                  g->k, g->level, g->r2_max, g->nbr);
+        knn_exact_kernel<KP><<<pg_blocks(h_cnt, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, redo, cnt, g->k,
+                                                                  g->level, g->r2_max, g->nbr);
         pg_count_launches(1);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     }
@@ -427,44 +441,52 @@ extern "C" pg_status pg_build_graph(const pg_vertices *v, int64_t n, const pg_bu
     pg_status st = PG_OK;
     int64_t ncells = (int64_t)1 << (3 * g->level);
     uint32_t *keys = nullptr;
-    uint64_t *qpk_c = nullptr;
+    int4 *qrec_c = nullptr;
+    int32_t *cell_start = nullptr;
 #define A(ptr, bytes) \
     if (st == PG_OK) st = pg_alloc(g, (void **)&(ptr), (bytes), s)
     A(g->flags, sizeof(int32_t) * 4);
     A(g->m2c, sizeof(int32_t) * n);
     A(g->c2m, sizeof(int32_t) * n);
-    A(g->qpk, sizeof(uint64_t) * n);
-    A(g->cell_start, sizeof(int32_t) * (ncells + 1));
+    A(g->qrec, sizeof(int4) * n);
+    A(g->cell_se, sizeof(int2) * ncells);
     A(g->nbr, sizeof(int32_t) * n * g->kp);
     if (st == PG_OK) st = pg_alloc(nullptr, (void **)&keys, sizeof(uint32_t) * (n > 0 ? n : 1), s);
-    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&qpk_c, sizeof(uint64_t) * (n > 0 ? n : 1), s);
+    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&qrec_c, sizeof(int4) * (n > 0 ? n : 1), s);
+    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&cell_start, sizeof(int32_t) * (ncells + 1), s);
 #undef A
     if (st == PG_OK) {
         if (cudaMemsetAsync(g->flags, 0, sizeof(int32_t) * 4, s) != cudaSuccess) st = PG_ERR_CUDA;
     }
     if (st == PG_OK && n > 0) {
         quantize_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(v->px, v->py, v->pz, n, g->lo[0], g->lo[1], g->lo[2],
-                                                          g->scale, g->level, keys, g->m2c, qpk_c, g->flags);
+                                                          g->scale, g->level, keys, g->m2c, qrec_c, g->flags);
         pg_count_launches(1);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
         if (st == PG_OK) st = pg_radix_sort(g, keys, g->m2c, n, 3 * g->level, s);
         if (st == PG_OK) {
-            permute_build_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(g->m2c, qpk_c, n, g->qpk, g->c2m);
+            permute_build_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(g->m2c, qrec_c, n, g->qrec, g->c2m);
             pg_count_launches(1);
             if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
         }
-        if (st == PG_OK && cudaMemsetAsync(g->cell_start, 0, sizeof(int32_t) * (ncells + 1), s) != cudaSuccess)
+        if (st == PG_OK && cudaMemsetAsync(cell_start, 0, sizeof(int32_t) * (ncells + 1), s) != cudaSuccess)
             st = PG_ERR_CUDA;
         if (st == PG_OK) {
-            cell_count_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(keys, n, g->cell_start);
+            cell_count_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(keys, n, cell_start);
             pg_count_launches(1);
             if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
         }
-        if (st == PG_OK) st = pg_scan_exclusive(g, g->cell_start, ncells + 1, nullptr, s);
+        if (st == PG_OK) st = pg_scan_exclusive(g, cell_start, ncells + 1, nullptr, s);
+        if (st == PG_OK) {
+            cell_table_kernel<<<pg_blocks(ncells, 256), 256, 0, s>>>(cell_start, ncells, g->level, g->cell_se);
+            pg_count_launches(1);
+            if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+        }
         if (st == PG_OK) st = pg_launch_knn(g, s);
     }
     if (keys) cudaFreeAsync(keys, s);
-    if (qpk_c) cudaFreeAsync(qpk_c, s);
+    if (qrec_c) cudaFreeAsync(qrec_c, s);
+    if (cell_start) cudaFreeAsync(cell_start, s);
     int32_t hflags = 0;
     if (st == PG_OK) {
         if (cudaMemcpyAsync(&hflags, g->flags, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -514,6 +536,7 @@ extern "C" pg_status pg_graph_get_info(const pg_graph *g, pg_graph_info *info) {
     info->device_bytes = g->bytes;
     info->weight_dtype = (int32_t)g->wdtype;
     info->history_iters = g->hist_iters;
+    info->knn_exact = g->knn_exact;
     return PG_OK;
 }
 
@@ -524,8 +547,8 @@ static pg_status graph_free_all(pg_graph *g) {
     pg_free(g, (void **)&g->flags, sizeof(int32_t) * 4);
     pg_free(g, (void **)&g->m2c, 4 * n);
     pg_free(g, (void **)&g->c2m, 4 * n);
-    pg_free(g, (void **)&g->qpk, 8 * n);
-    pg_free(g, (void **)&g->cell_start, 4 * ncells);
+    pg_free(g, (void **)&g->qrec, 16 * n);
+    pg_free(g, (void **)&g->cell_se, 8 * (ncells - 1));
     pg_free(g, (void **)&g->nbr, 4 * n * kp);
     pg_free(g, (void **)&g->m2r, 4 * n);
     pg_free(g, (void **)&g->r2m, 4 * n);

@@ -34,9 +34,10 @@ struct pg_graph {
     // ---- graph build (Morton order m) ----
     int32_t *m2c = nullptr;        // m -> caller index
     int32_t *c2m = nullptr;        // caller -> m
-    uint64_t *qpk = nullptr;       // packed quantised coordinates (x | y<<21 | z<<42), m order
-    int32_t *cell_start = nullptr; // 8^L + 1 offsets into m order
+    int4 *qrec = nullptr;          // (qx, qy, qz, caller index), m order
+    int2 *cell_se = nullptr;       // (start, count) per cell, index x + G (y + G z)
     int32_t *nbr = nullptr;        // [n][kp], m-space neighbour ids, -1 padded; slot 0 = self
+    int64_t knn_exact = 0;         // queries resolved by the exact neighbour kernel
 
     // ---- aggregation ----
     int aggregated = 0;
