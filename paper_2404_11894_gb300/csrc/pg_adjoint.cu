@@ -29,6 +29,24 @@ __device__ __forceinline__ float wload<__nv_bfloat16>(const __nv_bfloat16 *W, in
 template <>
 __device__ __forceinline__ float wload<__half>(const __half *W, int64_t i) { return __half2float(W[i]); }
 
+// weight <-> the 32-bit payload of a transposed entry
+template <typename WT>
+__device__ __forceinline__ int32_t wbits(WT w);
+template <>
+__device__ __forceinline__ int32_t wbits<float>(float w) { return __float_as_int(w); }
+template <>
+__device__ __forceinline__ int32_t wbits<__nv_bfloat16>(__nv_bfloat16 w) { return (int32_t)__bfloat16_as_ushort(w); }
+template <>
+__device__ __forceinline__ int32_t wbits<__half>(__half w) { return (int32_t)__half_as_ushort(w); }
+template <typename WT>
+__device__ __forceinline__ float wfrom(int32_t b);
+template <>
+__device__ __forceinline__ float wfrom<float>(int32_t b) { return __int_as_float(b); }
+template <>
+__device__ __forceinline__ float wfrom<__nv_bfloat16>(int32_t b) { return __bfloat162float(__ushort_as_bfloat16((unsigned short)b)); }
+template <>
+__device__ __forceinline__ float wfrom<__half>(int32_t b) { return __half2float(__ushort_as_half((unsigned short)b)); }
+
 template <typename WT>
 struct W4L;
 template <>
@@ -70,36 +88,29 @@ __global__ void tcount_kernel(const int32_t *__restrict__ col, int64_t n, int kp
 
 template <typename WT>
 __global__ void tfill_kernel(const int32_t *__restrict__ col, const WT *__restrict__ W, int64_t n, int kp,
-                             const int32_t *__restrict__ tptr, int32_t *__restrict__ fill, int32_t *__restrict__ trow,
-                             WT *__restrict__ tW) {
+                             const int32_t *__restrict__ tptr, int32_t *__restrict__ fill, int2 *__restrict__ tent) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n * kp) return;
     int32_t c = col[e];
     if (c >= n) return;
     int32_t pos = tptr[c] + atomicAdd(&fill[c], 1);
-    trow[pos] = (int32_t)(e / kp);
-    tW[pos] = W[e];
+    tent[pos] = make_int2((int32_t)(e / kp), wbits<WT>(W[e]));
 }
 
 // Order each column's entries by source row (a row appears once per column),
 // which makes the reverse sweep's summation order deterministic. Columns of
 // up to 32 entries (all of them for k <= 16 in practice) are sorted in
 // registers by a bitonic network; longer ones by insertion sort in memory.
-template <typename WT>
 __global__ void __launch_bounds__(128) tsort_kernel(const int32_t *__restrict__ tptr, int64_t ncols,
-                                                    int32_t *__restrict__ trow, WT *__restrict__ tW) {
+                                                    int2 *__restrict__ tent) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncols) return;
     const int32_t a = tptr[c], b = tptr[c + 1], len = b - a;
     if (len <= 1) return;
     if (len <= 32) {
-        int32_t kr[32];
-        WT kw[32];
+        int2 kv[32];
 #pragma unroll
-        for (int i = 0; i < 32; i++) {
-            kr[i] = i < len ? trow[a + i] : INT32_MAX;
-            kw[i] = i < len ? tW[a + i] : WT(0.0f);
-        }
+        for (int i = 0; i < 32; i++) kv[i] = i < len ? tent[a + i] : make_int2(INT32_MAX, 0);
 #pragma unroll
         for (int size = 2; size <= 32; size <<= 1) {
 #pragma unroll
@@ -109,9 +120,10 @@ __global__ void __launch_bounds__(128) tsort_kernel(const int32_t *__restrict__ 
                     const int j = i ^ stride;
                     if (j > i) {
                         const bool up = (i & size) == 0;
-                        if ((kr[i] > kr[j]) == up) {
-                            int32_t tr = kr[i]; kr[i] = kr[j]; kr[j] = tr;
-                            WT tw = kw[i]; kw[i] = kw[j]; kw[j] = tw;
+                        if ((kv[i].x > kv[j].x) == up) {
+                            int2 t = kv[i];
+                            kv[i] = kv[j];
+                            kv[j] = t;
                         }
                     }
                 }
@@ -119,23 +131,17 @@ __global__ void __launch_bounds__(128) tsort_kernel(const int32_t *__restrict__ 
         }
 #pragma unroll
         for (int i = 0; i < 32; i++)
-            if (i < len) {
-                trow[a + i] = kr[i];
-                tW[a + i] = kw[i];
-            }
+            if (i < len) tent[a + i] = kv[i];
         return;
     }
     for (int32_t i = a + 1; i < b; i++) {
-        int32_t r = trow[i];
-        WT w = tW[i];
+        const int2 v = tent[i];
         int32_t j = i - 1;
-        while (j >= a && trow[j] > r) {
-            trow[j + 1] = trow[j];
-            tW[j + 1] = tW[j];
+        while (j >= a && tent[j].x > v.x) {
+            tent[j + 1] = tent[j];
             j--;
         }
-        trow[j + 1] = r;
-        tW[j + 1] = w;
+        tent[j + 1] = v;
     }
 }
 
@@ -167,7 +173,7 @@ static constexpr int TS_PER_LANE = 8; // 4 lanes x 8 = 32 entries per column pas
 
 template <typename WT>
 __global__ void __launch_bounds__(TS_THREADS, 8) tsweep_kernel(
-    const int32_t *__restrict__ tptr, const int32_t *__restrict__ trow, const WT *__restrict__ tW,
+    const int32_t *__restrict__ tptr, const int2 *__restrict__ tent,
     const float *__restrict__ us_in, const float *__restrict__ mu_in, const float *__restrict__ y_t,
     const float *__restrict__ rscale, int64_t ncols, int write_out, float *__restrict__ mu_out,
     float *__restrict__ us_out, float *__restrict__ G, float *__restrict__ B) {
@@ -185,17 +191,15 @@ __global__ void __launch_bounds__(TS_THREADS, 8) tsweep_kernel(
             int32_t a = tptr[c];
             const int32_t b = tptr[c + 1];
             for (; a < b; a += TS_LPC * TS_PER_LANE) {
-                int32_t rr[TS_PER_LANE];
-                float ww[TS_PER_LANE];
+                int2 ent[TS_PER_LANE];
 #pragma unroll
                 for (int u = 0; u < TS_PER_LANE; u++) {
                     const int32_t e = a + q + TS_LPC * u;
-                    rr[u] = e < b ? trow[e] : -1;
-                    ww[u] = e < b ? wload<WT>(tW, e) : 0.0f;
+                    ent[u] = e < b ? __ldcs(tent + e) : make_int2(-1, 0);
                 }
 #pragma unroll
                 for (int u = 0; u < TS_PER_LANE; u++)
-                    if (rr[u] >= 0) acc = fmaf(ww[u], __ldg(us_in + rr[u]), acc);
+                    if (ent[u].x >= 0) acc = fmaf(wfrom<WT>(ent[u].y), __ldg(us_in + ent[u].x), acc);
             }
         }
 #pragma unroll
@@ -281,6 +285,7 @@ __global__ void __launch_bounds__(256) recompute_scatter_kernel(
     (void)unused;
     __shared__ float4 s_o[256];
     __shared__ float2 s_ab[256];
+    __shared__ float s_eo[256];
     const int lane = threadIdx.x & 31;
     const int j = lane & (KP - 1);
     const int gbase = threadIdx.x - j;
@@ -301,6 +306,8 @@ __global__ void __launch_bounds__(256) recompute_scatter_kernel(
     HGc hc = hg_consts(og.w);
     s_o[threadIdx.x] = make_float4(og.x, og.y, og.z, valid ? hc.C : 0.0f);
     s_ab[threadIdx.x] = make_float2(valid ? hc.a : 1.0f, valid ? hc.b2 : 0.0f);
+    s_eo[threadIdx.x] = unit_err(og.x, og.y, og.z);
+    const float ed = unit_err(dp.x, dp.y, dp.z);
     __syncwarp();
     if (__any_sync(0xffffffffu, live_row)) {
         float pm_d = 0.0f;
@@ -312,7 +319,7 @@ __global__ void __launch_bounds__(256) recompute_scatter_kernel(
             h.C = so.w;
             h.a = ab.x;
             h.b2 = ab.y;
-            pm_d += hg_eval(h, one_plus_dot(so.x, so.y, so.z, dp.x, dp.y, dp.z));
+            pm_d += hg_eval(h, one_plus_dot_u(so.x, so.y, so.z, s_eo[gbase + l], dp.x, dp.y, dp.z, ed));
         }
         const float4 so = s_o[gbase];
         const float2 sab = s_ab[gbase];
@@ -321,7 +328,7 @@ __global__ void __launch_bounds__(256) recompute_scatter_kernel(
         hs.a = sab.x;
         hs.b2 = sab.y;
         const float4 lvs = LV[m];
-        float rho_sd = hg_eval(hs, one_plus_dot(so.x, so.y, so.z, dp.x, dp.y, dp.z));
+        float rho_sd = hg_eval(hs, one_plus_dot_u(so.x, so.y, so.z, s_eo[gbase], dp.x, dp.y, dp.z, ed));
         if (live_row && valid && sj >= 0) {
             int32_t cl = m2r[sj];
             float Wt = lvs.w * (lvs.z * rho_sd / pm_d);
@@ -343,6 +350,7 @@ __global__ void __launch_bounds__(256) recompute_first_kernel(
     const float *__restrict__ yT, const float *__restrict__ D_m, float *__restrict__ G) {
     __shared__ float4 s_o[256];
     __shared__ float2 s_ab[256];
+    __shared__ float s_eo[256];
     const int lane = threadIdx.x & 31;
     const int j = lane & (KP - 1);
     const int gbase = threadIdx.x - j;
@@ -362,6 +370,8 @@ __global__ void __launch_bounds__(256) recompute_first_kernel(
     HGc hc = hg_consts(og.w);
     s_o[threadIdx.x] = make_float4(og.x, og.y, og.z, valid ? hc.C : 0.0f);
     s_ab[threadIdx.x] = make_float2(valid ? hc.a : 1.0f, valid ? hc.b2 : 0.0f);
+    s_eo[threadIdx.x] = unit_err(og.x, og.y, og.z);
+    const float ed = unit_err(dp.x, dp.y, dp.z);
     __syncwarp();
     float pm_d = 0.0f;
 #pragma unroll 4
@@ -372,7 +382,7 @@ __global__ void __launch_bounds__(256) recompute_first_kernel(
         h.C = so.w;
         h.a = ab.x;
         h.b2 = ab.y;
-        pm_d += hg_eval(h, one_plus_dot(so.x, so.y, so.z, dp.x, dp.y, dp.z));
+        pm_d += hg_eval(h, one_plus_dot_u(so.x, so.y, so.z, s_eo[gbase + l], dp.x, dp.y, dp.z, ed));
     }
     const float4 so = s_o[gbase];
     const float2 sab = s_ab[gbase];
@@ -381,7 +391,7 @@ __global__ void __launch_bounds__(256) recompute_first_kernel(
     hs.a = sab.x;
     hs.b2 = sab.y;
     const float4 lvs = row_ok ? LV[m] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float rho_sd = hg_eval(hs, one_plus_dot(so.x, so.y, so.z, dp.x, dp.y, dp.z));
+    float rho_sd = hg_eval(hs, one_plus_dot_u(so.x, so.y, so.z, s_eo[gbase], dp.x, dp.y, dp.z, ed));
     float term = 0.0f;
     if (row_ok && valid && sj >= 0) term = lvs.w * (lvs.z * rho_sd / pm_d) * yT[m2r[sj]];
 #pragma unroll
@@ -420,6 +430,8 @@ __global__ void __launch_bounds__(256) grad_g_kernel(
     __shared__ float4 s_o[256];   // (o_l, g_l)
     __shared__ float4 s_d[256];   // (d_j, coefficient for rho'_l(o_l, d_j))
     __shared__ float4 s_e[256];   // (e_j, coefficient for rho'_l(o_l, e_j))
+    __shared__ float s_eo[256];   // |o_l|^2 - 1
+    __shared__ float2 s_ede[256]; // (|d_j|^2 - 1, |e_j|^2 - 1)
     const int lane = threadIdx.x & 31;
     const int j = lane & (KP - 1);
     const int gbase = threadIdx.x - j;
@@ -437,6 +449,9 @@ __global__ void __launch_bounds__(256) grad_g_kernel(
         lv = LV[nj];
     }
     s_o[threadIdx.x] = og;
+    const float eo = unit_err(og.x, og.y, og.z), ed = unit_err(dp.x, dp.y, dp.z), ee = unit_err(ep.x, ep.y, ep.z);
+    s_eo[threadIdx.x] = eo;
+    s_ede[threadIdx.x] = make_float2(ed, ee);
     __syncwarp();
     const float K = (float)__popc(__ballot_sync(0xffffffffu, valid) &
                                   ((KP == 32) ? 0xffffffffu : (((1u << KP) - 1u) << src)));
@@ -448,8 +463,9 @@ __global__ void __launch_bounds__(256) grad_g_kernel(
         bool lv_ok = __shfl_sync(0xffffffffu, valid, src + l);
         if (lv_ok) {
             HGc h = hg_consts(so.w);
-            pm_d += hg_eval(h, one_plus_dot(so.x, so.y, so.z, dp.x, dp.y, dp.z));
-            pm_e += hg_eval(h, one_plus_dot(so.x, so.y, so.z, ep.x, ep.y, ep.z));
+            const float el = s_eo[gbase + l];
+            pm_d += hg_eval(h, one_plus_dot_u(so.x, so.y, so.z, el, dp.x, dp.y, dp.z, ed));
+            pm_e += hg_eval(h, one_plus_dot_u(so.x, so.y, so.z, el, ep.x, ep.y, ep.z, ee));
         }
     }
     const float4 os = s_o[gbase];
@@ -474,8 +490,9 @@ __global__ void __launch_bounds__(256) grad_g_kernel(
     const float gc = row_ok ? w_s * B[r] : 0.0f;
     const float gD = row_ok ? w_s * nu[r] : 0.0f;
     float drho_sd, drho_se, rho_sd, rho_se;
-    drho_sd = hg_eval_dg(os.w, one_plus_dot(os.x, os.y, os.z, dp.x, dp.y, dp.z), &rho_sd);
-    drho_se = hg_eval_dg(os.w, one_plus_dot(os.x, os.y, os.z, ep.x, ep.y, ep.z), &rho_se);
+    const float es = s_eo[gbase];
+    drho_sd = hg_eval_dg(os.w, one_plus_dot_u(os.x, os.y, os.z, es, dp.x, dp.y, dp.z, ed), &rho_sd);
+    drho_se = hg_eval_dg(os.w, one_plus_dot_u(os.x, os.y, os.z, es, ep.x, ep.y, ep.z, ee), &rho_se);
     const bool delta = ep.w < 0.0f;
     const float me = pm_e + K * ep.w;
     const float mph = pm_d + K * dp.w;
@@ -497,9 +514,12 @@ __global__ void __launch_bounds__(256) grad_g_kernel(
 #pragma unroll 4
         for (int jj = 0; jj < KP; jj++) {
             float4 sd = s_d[gbase + jj], se = s_e[gbase + jj];
+            const float2 ede = s_ede[gbase + jj];
             float dummy;
-            if (sd.w != 0.0f) acc += sd.w * hg_eval_dg(og.w, one_plus_dot(og.x, og.y, og.z, sd.x, sd.y, sd.z), &dummy);
-            if (se.w != 0.0f) acc += se.w * hg_eval_dg(og.w, one_plus_dot(og.x, og.y, og.z, se.x, se.y, se.z), &dummy);
+            if (sd.w != 0.0f)
+                acc += sd.w * hg_eval_dg(og.w, one_plus_dot_u(og.x, og.y, og.z, eo, sd.x, sd.y, sd.z, ede.x), &dummy);
+            if (se.w != 0.0f)
+                acc += se.w * hg_eval_dg(og.w, one_plus_dot_u(og.x, og.y, og.z, eo, se.x, se.y, se.z, ede.y), &dummy);
         }
     }
     // the row's own g_s: numerators and the non-aggregated direct term
@@ -545,13 +565,12 @@ static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
     PG_CUDA(cudaMemcpyAsync(&h_total, d_total, 4, cudaMemcpyDeviceToHost, s));
     PG_CUDA(cudaStreamSynchronize(s));
     g->nnz_t = h_total;
-    PG_TRY(pg_alloc(g, (void **)&g->t_row, 4 * (size_t)(h_total > 0 ? h_total : 1), s));
-    PG_TRY(pg_alloc(g, (void **)&g->t_W, sizeof(WT) * (size_t)(h_total > 0 ? h_total : 1), s));
+    PG_TRY(pg_alloc(g, (void **)&g->t_ent, 8 * (size_t)(h_total > 0 ? h_total : 1), s));
     tfill_kernel<WT><<<pg_blocks(n * kp, 256), 256, 0, s>>>(g->col, (const WT *)g->W, n, kp, g->t_ptr, fill,
-                                                            g->t_row, (WT *)g->t_W);
+                                                            g->t_ent);
     pg_count_launches(1);
     PG_LAUNCH_CHECK();
-    tsort_kernel<WT><<<pg_blocks(g->n_active, 128), 128, 0, s>>>(g->t_ptr, g->n_active, g->t_row, (WT *)g->t_W);
+    tsort_kernel<<<pg_blocks(g->n_active, 128), 128, 0, s>>>(g->t_ptr, g->n_active, g->t_ent);
     pg_count_launches(1);
     PG_LAUNCH_CHECK();
     cudaFreeAsync(fill, s);
@@ -574,13 +593,13 @@ static pg_status adjoint_store(pg_graph *g, float *us0, float *mu_a, float *mu_b
     auto mu_slot = [&](int t) { return muhist ? muhist + (int64_t)t * stride : ((t & 1) ? mu_b : mu_a); };
     float *us_cur = us_a, *us_nxt = us_b;
     // mu_T = W^T nu
-    tsweep_kernel<WT><<<tb, TS_THREADS, 0, s>>>(g->t_ptr, g->t_row, (const WT *)g->t_W, us0, nullptr, nullptr, rs, na, 1,
+    tsweep_kernel<WT><<<tb, TS_THREADS, 0, s>>>(g->t_ptr, g->t_ent, us0, nullptr, nullptr, rs, na, 1,
                                          mu_slot(T), us_cur, G, B);
     pg_count_launches(1);
     PG_LAUNCH_CHECK();
     for (int t = T; t >= 1; t--) {
         const float *y_t = g->hist + (int64_t)t * stride;
-        tsweep_kernel<WT><<<tb, TS_THREADS, 0, s>>>(g->t_ptr, g->t_row, (const WT *)g->t_W, us_cur, mu_slot(t), y_t, rs,
+        tsweep_kernel<WT><<<tb, TS_THREADS, 0, s>>>(g->t_ptr, g->t_ent, us_cur, mu_slot(t), y_t, rs,
                                              na, t > 1 ? 1 : 0, mu_slot(t - 1), us_nxt, G, B);
         pg_count_launches(1);
         PG_LAUNCH_CHECK();
@@ -822,8 +841,7 @@ extern "C" pg_status pg_graph_release_weights(pg_graph *g) {
     if (!g) return PG_ERR_INVALID_ARG;
     size_t wb = pg_wbytes(g->wdtype);
     pg_free(g, (void **)&g->W, wb * (size_t)g->n * (size_t)g->kp);
-    pg_free(g, (void **)&g->t_W, wb * (size_t)g->nnz_t);
-    pg_free(g, (void **)&g->t_row, 4 * (size_t)g->nnz_t);
+    pg_free(g, (void **)&g->t_ent, 8 * (size_t)g->nnz_t);
     pg_free(g, (void **)&g->t_ptr, 4 * (size_t)(g->n + 1));
     g->nnz_t = 0;
     return PG_OK;

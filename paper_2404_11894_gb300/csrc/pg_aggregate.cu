@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(256) aggregate_kernel(
     unsigned long long *__restrict__ nnz_counter) {
     __shared__ float4 s_o[256];   // (ox, oy, oz, C)
     __shared__ float2 s_ab[256];  // ((1-g)^2, 2g)
+    __shared__ float s_eo[256];   // |o|^2 - 1
     const int lane = threadIdx.x & 31;
     const int j = lane & (KP - 1);
     const int gbase = threadIdx.x - j; // first thread of this row's group
@@ -118,8 +119,11 @@ __global__ void __launch_bounds__(256) aggregate_kernel(
         sj = succ_m[nj];
     }
     HGc hc = hg_consts(og.w);
+    const float eo = unit_err(og.x, og.y, og.z);
+    const float ed = unit_err(dp.x, dp.y, dp.z), ee = unit_err(ep.x, ep.y, ep.z);
     s_o[threadIdx.x] = make_float4(og.x, og.y, og.z, valid ? hc.C : 0.0f);
     s_ab[threadIdx.x] = make_float2(valid ? hc.a : 1.0f, valid ? hc.b2 : 0.0f);
+    s_eo[threadIdx.x] = eo;
     __syncwarp();
     const unsigned gmask = (KP == 32) ? 0xffffffffu : (((1u << KP) - 1u) << (lane & ~(KP - 1)));
     const float K = (float)__popc(__ballot_sync(0xffffffffu, valid) & gmask);
@@ -134,8 +138,9 @@ __global__ void __launch_bounds__(256) aggregate_kernel(
         h.C = so.w;
         h.a = ab.x;
         h.b2 = ab.y;
-        pm_d += hg_eval(h, one_plus_dot(so.x, so.y, so.z, dp.x, dp.y, dp.z));
-        pm_e += hg_eval(h, one_plus_dot(so.x, so.y, so.z, ep.x, ep.y, ep.z));
+        const float el = s_eo[gbase + l];
+        pm_d += hg_eval(h, one_plus_dot_u(so.x, so.y, so.z, el, dp.x, dp.y, dp.z, ed));
+        pm_e += hg_eval(h, one_plus_dot_u(so.x, so.y, so.z, el, ep.x, ep.y, ep.z, ee));
     }
     // receiver s = slot 0 of the group
     const float4 so = s_o[gbase];
@@ -147,8 +152,9 @@ __global__ void __launch_bounds__(256) aggregate_kernel(
     const int src = lane & ~(KP - 1);
     const float sig_s = __shfl_sync(0xffffffffu, lv.z, src);
     const float w_s = __shfl_sync(0xffffffffu, lv.w, src);
-    float rho_sd = hg_eval(hs, one_plus_dot(so.x, so.y, so.z, dp.x, dp.y, dp.z));
-    float rho_se = hg_eval(hs, one_plus_dot(so.x, so.y, so.z, ep.x, ep.y, ep.z));
+    const float es = s_eo[gbase];
+    float rho_sd = hg_eval(hs, one_plus_dot_u(so.x, so.y, so.z, es, dp.x, dp.y, dp.z, ed));
+    float rho_se = hg_eval(hs, one_plus_dot_u(so.x, so.y, so.z, es, ep.x, ep.y, ep.z, ee));
     float A = 0.0f, term = 0.0f;
     if (valid) {
         A = sig_s * rho_sd / pm_d;
@@ -241,8 +247,7 @@ extern "C" pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype w
     // (re)allocate the aggregation buffers
     size_t wb_old = pg_wbytes(g->wdtype);
     pg_free(g, (void **)&g->W, wb_old * n * kp);
-    pg_free(g, (void **)&g->t_W, wb_old * (size_t)g->nnz_t);
-    pg_free(g, (void **)&g->t_row, 4 * (size_t)g->nnz_t);
+    pg_free(g, (void **)&g->t_ent, 8 * (size_t)g->nnz_t);
     pg_free(g, (void **)&g->t_ptr, 4 * (size_t)(n + 1));
     g->nnz_t = 0;
     g->aggregated = 0;

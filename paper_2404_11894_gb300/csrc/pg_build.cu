@@ -570,8 +570,7 @@ static pg_status graph_free_all(pg_graph *g) {
     pg_free(g, (void **)&g->d_ctrl, 16);
     pg_free(g, (void **)&g->d_partials, 16 * (size_t)g->partials_cap);
     pg_free(g, (void **)&g->t_ptr, 4 * (n + 1));
-    pg_free(g, (void **)&g->t_row, 4 * (size_t)g->nnz_t);
-    pg_free(g, (void **)&g->t_W, wb * (size_t)g->nnz_t);
+    pg_free(g, (void **)&g->t_ent, 8 * (size_t)g->nnz_t);
     return PG_OK;
 }
 

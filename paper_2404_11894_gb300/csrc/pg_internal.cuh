@@ -71,8 +71,7 @@ struct pg_graph {
 
     // ---- adjoint (lazily built) ----
     int32_t *t_ptr = nullptr;     // [n+1] transposed row pointers (by column)
-    int32_t *t_row = nullptr;     // [nnz_t] source row of each transposed entry
-    void *t_W = nullptr;          // [nnz_t] weight in transposed order (same dtype)
+    int2 *t_ent = nullptr;        // [nnz_t] (source row, weight bits) of each transposed entry
     int64_t nnz_t = 0;
     int32_t *flags = nullptr;     // validation flags (device)
 };
@@ -137,6 +136,27 @@ __device__ __forceinline__ float one_plus_dot(float ax, float ay, float az, floa
     two_sum(1.0f, p, s, q);
     return __fadd_rn(s, __fadd_rn(q, err));
 }
+// |v|^2 - 1 of a (nearly) unit vector, accurate to a few ulps of the result
+// (error-free products and sums; evaluated once per vector)
+__device__ __forceinline__ float unit_err(float x, float y, float z) {
+    const float p1 = __fmul_rn(x, x), p2 = __fmul_rn(y, y), p3 = __fmul_rn(z, z);
+    const float e1 = __fmaf_rn(x, x, -p1), e2 = __fmaf_rn(y, y, -p2), e3 = __fmaf_rn(z, z, -p3);
+    float s1, q1, s2, q2;
+    two_sum(p1, p2, s1, q1);
+    two_sum(s1, p3, s2, q2);
+    const float s3 = __fsub_rn(s2, 1.0f); // exact: s2 is close to 1
+    return __fadd_rn(s3, __fadd_rn(__fadd_rn(q1, q2), __fadd_rn(e1, __fadd_rn(e2, e3))));
+}
+// 1 + a.b from the vectors and their unit_err: 1 + a.b = (|a+b|^2 - ea - eb) / 2.
+// Near the forward peak a ~ -b, |a+b| is small and computed to full relative
+// precision, so this is as accurate as one_plus_dot at a third of the cost.
+__device__ __forceinline__ float one_plus_dot_u(float ax, float ay, float az, float ea, float bx, float by, float bz,
+                                                float eb) {
+    const float sx = ax + bx, sy = ay + by, sz = az + bz;
+    const float s2 = fmaf(sz, sz, fmaf(sy, sy, sx * sx));
+    return 0.5f * (s2 - (ea + eb));
+}
+
 // rsqrt refined by one Newton step (the hardware estimate alone is ~2 ulp)
 __device__ __forceinline__ float rsqrt_nr(float x) {
     float r = rsqrtf(x);
