@@ -217,17 +217,14 @@ __global__ void __launch_bounds__(128, 4) knn_kernel(const int4 *__restrict__ qr
     for (int pos = km1; pos < M; pos++) row[1 + pos] = -1;
 }
 
-// Ring search over all rings for queued queries. PACKED: entries are the
-// 64-bit keys of the fast pass (a list that ends up holding a saturated
-// distance is queued again, for PACKED = false); otherwise entries are
-// (int64 d2, caller id) compared lexicographically, exact for any input.
-template <int KP, bool PACKED>
-__global__ void __launch_bounds__(128, 4) knn_exact_kernel(const int4 *__restrict__ qrec,
+// Exact path for queued queries: entries (int64 d2, caller id) compared
+// lexicographically.
+template <int KP>
+__global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__ qrec,
                                                         const int2 *__restrict__ cell_se,
                                                         const int32_t *__restrict__ c2m, const int32_t *__restrict__ list,
                                                         const int32_t *__restrict__ d_count, int k, int level,
-                                                        int64_t r2_max, int32_t *__restrict__ nbr,
-                                                        int32_t *__restrict__ redo, int32_t *__restrict__ redo_count) {
+                                                        int64_t r2_max, int32_t *__restrict__ nbr) {
     constexpr int M = KP - 1;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= *d_count) return;
@@ -248,11 +245,7 @@ __global__ void __launch_bounds__(128, 4) knn_exact_kernel(const int4 *__restric
     int32_t bi[M > 0 ? M : 1];
 #pragma unroll
     for (int i = 0; i < M; i++) {
-        if (PACKED) {
-            bd[i] = i < pad ? 0 : (int64_t)UINT64_MAX;
-        } else {
-            bd[i] = i < pad ? (int64_t)-1 : INT64_MAX;
-        }
+        bd[i] = i < pad ? (int64_t)-1 : INT64_MAX;
         bi[i] = i < pad ? -1 : INT32_MAX;
     }
     int64_t worst_d = INT64_MAX;
@@ -293,22 +286,6 @@ __global__ void __launch_bounds__(128, 4) knn_exact_kernel(const int4 *__restric
                     if (d2 > worst_d) continue;
                     if (r2_max >= 0 && d2 > r2_max) continue;
                     const int32_t id = cq.w;
-                    if (PACKED) {
-                        // one 64-bit key per entry (bd holds keys, bi unused)
-                        const uint64_t dk = d2 < (int64_t)KNN_SAT ? (uint64_t)d2 : KNN_SAT;
-                        const uint64_t key = (dk << 31) | (uint64_t)(uint32_t)id;
-                        if (key >= (uint64_t)bd[M - 1]) continue;
-#pragma unroll
-                        for (int i = M - 1; i > 0; --i) {
-                            const uint64_t prev = (uint64_t)bd[i - 1];
-                            if (key < (uint64_t)bd[i]) bd[i] = (int64_t)(key < prev ? prev : key);
-                        }
-                        if (key < (uint64_t)bd[0]) bd[0] = (int64_t)key;
-                        found++;
-                        const uint64_t wk = (uint64_t)bd[M - 1];
-                        worst_d = wk == UINT64_MAX ? INT64_MAX : (int64_t)(wk >> 31);
-                        continue;
-                    }
                     if (!knn_less(d2, id, worst_d, worst_i)) continue;
                     // insert into the sorted list, shifting larger entries up
 #pragma unroll
@@ -357,30 +334,12 @@ __global__ void __launch_bounds__(128, 4) knn_exact_kernel(const int4 *__restric
             if (r2_max >= 0 && bnd2 > r2_max) break;            // nothing outside is in range
         }
     }
-    if (PACKED) {
-        bool saturated = false;
-#pragma unroll
-        for (int i = 0; i < M; i++)
-            if (i >= pad && (uint64_t)bd[i] != UINT64_MAX && ((uint64_t)bd[i] >> 31) >= KNN_SAT) saturated = true;
-        if (saturated) {
-            redo[atomicAdd(redo_count, 1)] = (int32_t)m;
-            return;
-        }
-    }
     int32_t *row = nbr + m * KP;
     row[0] = (int32_t)m;
 #pragma unroll
     for (int i = 0; i < M; i++) {
         int pos = i - pad; // rank among the k-1 others
-        if (pos >= 0) {
-            int32_t out = -1;
-            if (PACKED) {
-                if ((uint64_t)bd[i] != UINT64_MAX) out = c2m[(int32_t)((uint64_t)bd[i] & 0x7fffffffu)];
-            } else if (bi[i] != INT32_MAX) {
-                out = c2m[bi[i]];
-            }
-            row[1 + pos] = out;
-        }
+        if (pos >= 0) row[1 + pos] = bi[i] != INT32_MAX ? c2m[bi[i]] : -1;
     }
     for (int pos = km1; pos < M; pos++) row[1 + pos] = -1;
 }
@@ -410,27 +369,10 @@ static pg_status launch_knn_t(pg_graph *g, cudaStream_t s) {
         st = PG_ERR_CUDA;
     g->knn_exact = h_cnt;
     if (st == PG_OK && h_cnt > 0) {
-        // all rings with packed keys; lists holding a saturated distance go on
-        int32_t *redo2 = nullptr;
-        st = pg_alloc(nullptr, (void **)&redo2, 4 * (size_t)h_cnt, s);
-        if (st == PG_OK && cudaMemsetAsync(cnt + 1, 0, 4, s) != cudaSuccess) st = PG_ERR_CUDA;
-        if (st == PG_OK) {
-            knn_exact_kernel<KP, true><<<pg_blocks(h_cnt, 128), 128, 0, s>>>(
-                g->qrec, g->cell_se, g->c2m, redo, cnt, g->k, g->level, g->r2_max, g->nbr, redo2, cnt + 1);
-            pg_count_launches(1);
-            if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
-        }
-        int32_t h2 = 0;
-        if (st == PG_OK && (cudaMemcpyAsync(&h2, cnt + 1, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                            cudaStreamSynchronize(s) != cudaSuccess))
-            st = PG_ERR_CUDA;
-        if (st == PG_OK && h2 > 0) {
-            knn_exact_kernel<KP, false><<<pg_blocks(h2, 128), 128, 0, s>>>(
-                g->qrec, g->cell_se, g->c2m, redo2, cnt + 1, g->k, g->level, g->r2_max, g->nbr, nullptr, nullptr);
-            pg_count_launches(1);
-            if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
-        }
-        if (redo2) cudaFreeAsync(redo2, s);
+        knn_exact_kernel<KP><<<pg_blocks(h_cnt, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, redo, cnt, g->k,
+                                                                  g->level, g->r2_max, g->nbr);
+        pg_count_launches(1);
+        if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     }
     cudaFreeAsync(redo, s);
     cudaFreeAsync(cnt, s);
@@ -627,8 +569,7 @@ static pg_status graph_free_all(pg_graph *g) {
     pg_free(g, (void **)&g->d_resid, 8 * (size_t)g->resid_cap);
     pg_free(g, (void **)&g->d_ctrl, 16);
     pg_free(g, (void **)&g->d_partials, 16 * (size_t)g->partials_cap);
-    pg_free(g, (void **)&g->t_ptr, 4 * (n + 1));
-    pg_free(g, (void **)&g->t_ent, 8 * (size_t)g->nnz_t);
+    pg_free_transposes(g);
     return PG_OK;
 }
 
