@@ -79,20 +79,22 @@ __global__ void scale_rows_kernel(const float *__restrict__ mu, const float *__r
 }
 
 // ------------------------------------------------------------------ transpose build
-__global__ void tcount_kernel(const int32_t *__restrict__ col, int64_t n, int kp, int32_t *__restrict__ cnt) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n * kp) return;
+__global__ void tcount_kernel(const int32_t *__restrict__ col, int64_t r0, int64_t r1, int kp, int64_t ncols,
+                              int32_t *__restrict__ cnt) {
+    int64_t e = r0 * kp + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= r1 * kp) return;
     int32_t c = col[e];
-    if (c < n) atomicAdd(&cnt[c], 1);
+    if (c < ncols) atomicAdd(&cnt[c], 1);
 }
 
 template <typename WT>
-__global__ void tfill_kernel(const int32_t *__restrict__ col, const WT *__restrict__ W, int64_t n, int kp,
-                             const int32_t *__restrict__ tptr, int32_t *__restrict__ fill, int2 *__restrict__ tent) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n * kp) return;
+__global__ void tfill_kernel(const int32_t *__restrict__ col, const WT *__restrict__ W, int64_t r0, int64_t r1,
+                             int kp, int64_t ncols, const int32_t *__restrict__ tptr, int32_t *__restrict__ fill,
+                             int2 *__restrict__ tent) {
+    int64_t e = r0 * kp + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= r1 * kp) return;
     int32_t c = col[e];
-    if (c >= n) return;
+    if (c >= ncols) return;
     int32_t pos = tptr[c] + atomicAdd(&fill[c], 1);
     tent[pos] = make_int2((int32_t)(e / kp), wbits<WT>(W[e]));
 }
@@ -165,27 +167,47 @@ __global__ void seed_kernel(const int32_t *__restrict__ first, const float *__re
 // column's entries (rows ascending). Each lane loads all of its (up to 8)
 // entries before using them, so a column costs one round trip, and each
 // block walks one contiguous chunk of columns (neighbouring columns draw on
-// neighbouring rows). Also accumulates G[c] += mu_in[c] y_t[c] and
-// B[c] += mu_in[c] when y_t is given.
+// neighbouring rows). When y_t is given it also accumulates
+// G[c] += mu_in[c] y_t[c] (and B[c] += mu_in[c] when B is given); those
+// column scalars are loaded up front, one per lane, so they travel with the
+// entry loads. us_out (the next input, mu times the 16-bit row scale) is
+// written only when it differs from mu_out.
 static constexpr int TS_THREADS = 256;
-static constexpr int TS_LPC = 4;
-static constexpr int TS_PER_LANE = 8; // 4 lanes x 8 = 32 entries per column pass
 
-template <typename WT>
-__global__ void __launch_bounds__(TS_THREADS, 8) tsweep_kernel(
+template <typename WT, int TS_LPC, int TS_PER_LANE, int MINB>
+__global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_kernel(
     const int32_t *__restrict__ tptr, const int2 *__restrict__ tent,
     const float *__restrict__ us_in, const float *__restrict__ mu_in, const float *__restrict__ y_t,
     const float *__restrict__ rscale, int64_t ncols, int write_out, float *__restrict__ mu_out,
     float *__restrict__ us_out, float *__restrict__ G, float *__restrict__ B) {
     constexpr int CPB = TS_THREADS / TS_LPC; // columns per block per iteration
+    constexpr int SV = (4 + TS_LPC - 1) / TS_LPC; // column scalars per lane
     const int lane = threadIdx.x & 31;
     const int q = lane & (TS_LPC - 1);
+    const int lead = lane & ~(TS_LPC - 1);
+    const bool acc_g = y_t != nullptr;
     const int64_t chunk = ((ncols + gridDim.x - 1) / gridDim.x + CPB - 1) / CPB * CPB;
     const int64_t c0 = (int64_t)blockIdx.x * chunk;
     const int64_t c1 = min(ncols, c0 + chunk);
     for (int64_t base = c0; base < c1; base += CPB) {
         const int64_t c = base + threadIdx.x / TS_LPC;
         const bool ok = c < c1;
+        // column scalars k = 0 mu_in, 1 y_t, 2 G, 3 B: scalar k is loaded by
+        // lane k % LPC of the column into its slot k / LPC; lane 0 also loads
+        // the row scale
+        float sv[SV], rs = 1.0f;
+#pragma unroll
+        for (int i = 0; i < SV; i++) {
+            const int k = q + TS_LPC * i;
+            sv[i] = 0.0f;
+            if (ok && acc_g) {
+                if (k == 0) sv[i] = mu_in[c];
+                else if (k == 1) sv[i] = __ldcs(y_t + c);
+                else if (k == 2) sv[i] = G[c];
+                else if (k == 3 && B) sv[i] = B[c];
+            }
+        }
+        if (ok && rscale && write_out && q == 0) rs = __ldcs(rscale + c);
         float acc = 0.0f;
         if (ok && write_out) {
             int32_t a = tptr[c];
@@ -204,15 +226,16 @@ __global__ void __launch_bounds__(TS_THREADS, 8) tsweep_kernel(
         }
 #pragma unroll
         for (int o = TS_LPC / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (ok && q == 0) {
-            if (write_out) {
+        const float m = __shfl_sync(0xffffffffu, sv[0], lead);
+        const float yv = __shfl_sync(0xffffffffu, sv[1 / TS_LPC], lead + 1 % TS_LPC);
+        if (ok) {
+            if (q == 0 && write_out) {
                 mu_out[c] = acc;
-                us_out[c] = rscale ? acc * rscale[c] : acc;
+                if (us_out) us_out[c] = acc * rs;
             }
-            if (y_t) {
-                const float m = mu_in[c];
-                G[c] = fmaf(m, y_t[c], G[c]);
-                B[c] += m;
+            if (acc_g) {
+                if (q == 2 % TS_LPC) G[c] = fmaf(m, yv, sv[2 / TS_LPC]);
+                if (q == 3 % TS_LPC && B) B[c] = sv[3 / TS_LPC] + m;
             }
         }
     }
@@ -266,7 +289,7 @@ __global__ void __launch_bounds__(256) scatter_sweep_kernel(
     if (y_t && q == 0) {
         const float m = mu_in[row];
         G[row] = fmaf(m, y_t[row], G[row]);
-        B[row] += m;
+        if (B) B[row] += m;
     }
 }
 
@@ -337,7 +360,7 @@ __global__ void __launch_bounds__(256) recompute_scatter_kernel(
     }
     if (row_ok && j == 0 && y_t) {
         G[r] = fmaf(ur, y_t[r], G[r]);
-        B[r] += ur;
+        if (B) B[r] += ur;
     }
 }
 
@@ -545,37 +568,61 @@ __global__ void permute_m2c_kernel(const float *__restrict__ in_m, const int32_t
 }
 
 // ------------------------------------------------------------------ host
+// Two transposes of the stored weights: the active rows' (applied in every
+// reverse sweep) and the first-vertex rows' (applied once, to the output
+// adjoint nu), so the reverse sweeps never stream the first rows' entries.
 template <typename WT>
 static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
-    const int64_t n = g->n;
+    const int64_t n = g->n, na = g->n_active;
     const int kp = g->kp;
-    int32_t *cnt = nullptr, *fill = nullptr, *d_total = nullptr;
-    pg_status st = pg_alloc(g, (void **)&g->t_ptr, 4 * (size_t)(n + 1), s);
-    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&fill, 4 * (size_t)(n + 1), s);
+    pg_tcsr *ts[2] = {&g->tA, &g->tF};
+    const int64_t r0[2] = {0, na}, r1[2] = {na, n};
+    int32_t *fill = nullptr, *d_total = nullptr;
+    pg_status st = PG_OK;
+    for (int i = 0; i < 2 && st == PG_OK; i++) st = pg_alloc(g, (void **)&ts[i]->ptr, 4 * (size_t)(na + 1), s);
+    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&fill, 4 * (size_t)(na + 1), s);
     if (st == PG_OK) st = pg_alloc(nullptr, (void **)&d_total, 16, s);
-    if (st != PG_OK) return st;
-    cnt = g->t_ptr;
-    PG_CUDA(cudaMemsetAsync(cnt, 0, 4 * (size_t)(n + 1), s));
-    PG_CUDA(cudaMemsetAsync(fill, 0, 4 * (size_t)(n + 1), s));
-    tcount_kernel<<<pg_blocks(n * kp, 256), 256, 0, s>>>(g->col, n, kp, cnt);
-    pg_count_launches(1);
-    PG_LAUNCH_CHECK();
-    PG_TRY(pg_scan_exclusive(g, g->t_ptr, n + 1, d_total, s));
-    int32_t h_total = 0;
-    PG_CUDA(cudaMemcpyAsync(&h_total, d_total, 4, cudaMemcpyDeviceToHost, s));
+    if (st != PG_OK) {
+        if (fill) cudaFreeAsync(fill, s);
+        return st;
+    }
+    for (int i = 0; i < 2; i++) {
+        PG_CUDA(cudaMemsetAsync(ts[i]->ptr, 0, 4 * (size_t)(na + 1), s));
+        if (r1[i] > r0[i]) {
+            tcount_kernel<<<pg_blocks((r1[i] - r0[i]) * kp, 256), 256, 0, s>>>(g->col, r0[i], r1[i], kp, na,
+                                                                               ts[i]->ptr);
+            pg_count_launches(1);
+            PG_LAUNCH_CHECK();
+        }
+        PG_TRY(pg_scan_exclusive(g, ts[i]->ptr, na + 1, d_total + 2 * i, s));
+    }
+    int32_t h_total[4] = {0, 0, 0, 0};
+    PG_CUDA(cudaMemcpyAsync(h_total, d_total, 16, cudaMemcpyDeviceToHost, s));
     PG_CUDA(cudaStreamSynchronize(s));
-    g->nnz_t = h_total;
-    PG_TRY(pg_alloc(g, (void **)&g->t_ent, 8 * (size_t)(h_total > 0 ? h_total : 1), s));
-    tfill_kernel<WT><<<pg_blocks(n * kp, 256), 256, 0, s>>>(g->col, (const WT *)g->W, n, kp, g->t_ptr, fill,
-                                                            g->t_ent);
-    pg_count_launches(1);
-    PG_LAUNCH_CHECK();
-    tsort_kernel<<<pg_blocks(g->n_active, 128), 128, 0, s>>>(g->t_ptr, g->n_active, g->t_ent);
-    pg_count_launches(1);
-    PG_LAUNCH_CHECK();
+    for (int i = 0; i < 2; i++) {
+        ts[i]->nnz = h_total[2 * i];
+        PG_TRY(pg_alloc(g, (void **)&ts[i]->ent, 8 * (size_t)(ts[i]->nnz > 0 ? ts[i]->nnz : 1), s));
+        if (ts[i]->nnz == 0) continue;
+        PG_CUDA(cudaMemsetAsync(fill, 0, 4 * (size_t)(na + 1), s));
+        tfill_kernel<WT><<<pg_blocks((r1[i] - r0[i]) * kp, 256), 256, 0, s>>>(
+            g->col, (const WT *)g->W, r0[i], r1[i], kp, na, ts[i]->ptr, fill, ts[i]->ent);
+        pg_count_launches(1);
+        PG_LAUNCH_CHECK();
+        tsort_kernel<<<pg_blocks(na, 128), 128, 0, s>>>(ts[i]->ptr, na, ts[i]->ent);
+        pg_count_launches(1);
+        PG_LAUNCH_CHECK();
+    }
     cudaFreeAsync(fill, s);
     cudaFreeAsync(d_total, s);
     return PG_OK;
+}
+
+void pg_free_transposes(pg_graph *g) {
+    for (pg_tcsr *t : {&g->tA, &g->tF}) {
+        pg_free(g, (void **)&t->ent, 8 * (size_t)(t->nnz > 0 ? t->nnz : 1));
+        pg_free(g, (void **)&t->ptr, 4 * (size_t)(g->n_active + 1));
+        t->nnz = 0;
+    }
 }
 
 template <typename WT>
@@ -585,25 +632,38 @@ static pg_status adjoint_store(pg_graph *g, float *us0, float *mu_a, float *mu_b
     const int T = g->hist_iters;
     const int64_t stride = n + 1;
     const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
-    if (!g->t_ptr) PG_TRY(build_transpose<WT>(g, s));
-    int64_t need = (na * TS_LPC + TS_THREADS - 1) / TS_THREADS;
-    int64_t cap = (int64_t)pg_num_sms() * 8;
+    if (!g->tA.ptr) PG_TRY(build_transpose<WT>(g, s));
+    // four lanes per column, up to 8 entries per lane in flight; 40 registers
+    // (6 blocks of 256 per SM) keep the entries and column scalars unspilled
+    int64_t need = (na * 4 + TS_THREADS - 1) / TS_THREADS;
+    int64_t cap = (int64_t)pg_num_sms() * 6;
     const int tb = (int)(need < cap ? (need > 0 ? need : 1) : cap);
+    auto tsweep = [&](const pg_tcsr &t, const float *us_in, const float *mu_in, const float *y_t, int wo,
+                      float *mu_out, float *us_out) {
+        tsweep_kernel<WT, 4, 8, 6><<<tb, TS_THREADS, 0, s>>>(t.ptr, t.ent, us_in, mu_in, y_t, rs, na, wo, mu_out,
+                                                             us_out, G, B);
+    };
     // mu_t lives in slice t of the history when one is kept, else ping-pong
     auto mu_slot = [&](int t) { return muhist ? muhist + (int64_t)t * stride : ((t & 1) ? mu_b : mu_a); };
-    float *us_cur = us_a, *us_nxt = us_b;
-    // mu_T = W^T nu
-    tsweep_kernel<WT><<<tb, TS_THREADS, 0, s>>>(g->t_ptr, g->t_ent, us0, nullptr, nullptr, rs, na, 1,
-                                         mu_slot(T), us_cur, G, B);
+    // with FP32 weights us = mu, so the reverse iterate itself is the next input
+    float *us_cur = rs ? us_a : mu_slot(T), *us_nxt = us_b;
+    // mu_T = W^T nu (nu lives on the first-vertex rows)
+    tsweep(g->tF, us0, nullptr, nullptr, 1, mu_slot(T), rs ? us_cur : nullptr);
     pg_count_launches(1);
     PG_LAUNCH_CHECK();
     for (int t = T; t >= 1; t--) {
         const float *y_t = g->hist + (int64_t)t * stride;
-        tsweep_kernel<WT><<<tb, TS_THREADS, 0, s>>>(g->t_ptr, g->t_ent, us_cur, mu_slot(t), y_t, rs,
-                                             na, t > 1 ? 1 : 0, mu_slot(t - 1), us_nxt, G, B);
+        float *out_us = rs ? us_nxt : nullptr;
+        tsweep(g->tA, us_cur, mu_slot(t), y_t, t > 1 ? 1 : 0, mu_slot(t - 1), out_us);
         pg_count_launches(1);
         PG_LAUNCH_CHECK();
-        float *tu = us_cur; us_cur = us_nxt; us_nxt = tu;
+        if (rs) {
+            float *tu = us_cur;
+            us_cur = us_nxt;
+            us_nxt = tu;
+        } else {
+            us_cur = mu_slot(t - 1);
+        }
     }
     return PG_OK;
 }
@@ -730,8 +790,8 @@ extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const in
     T_ALLOC(us_a, vb);
     T_ALLOC(us_b, vb);
     T_ALLOC(G, vb);
-    T_ALLOC(B, vb);
     if (want_g) {
+        T_ALLOC(B, vb); // sum of the reverse iterates: only the g gradient uses it
         T_ALLOC(muhist, vb * (size_t)(g->hist_iters + 1)); // mu_t per reverse sweep
         T_ALLOC(gg_m, vb);
     }
@@ -740,7 +800,7 @@ extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const in
         cudaMemsetAsync(nu, 0, vb, s);
         cudaMemsetAsync(us0, 0, vb, s);
         cudaMemsetAsync(G, 0, vb, s);
-        cudaMemsetAsync(B, 0, vb, s);
+        if (B) cudaMemsetAsync(B, 0, vb, s);
         cudaMemsetAsync(mu_a, 0, vb, s);
         cudaMemsetAsync(mu_b, 0, vb, s);
         cudaMemsetAsync(us_a, 0, vb, s); // rows past n_active must read as zero
@@ -841,8 +901,6 @@ extern "C" pg_status pg_graph_release_weights(pg_graph *g) {
     if (!g) return PG_ERR_INVALID_ARG;
     size_t wb = pg_wbytes(g->wdtype);
     pg_free(g, (void **)&g->W, wb * (size_t)g->n * (size_t)g->kp);
-    pg_free(g, (void **)&g->t_ent, 8 * (size_t)g->nnz_t);
-    pg_free(g, (void **)&g->t_ptr, 4 * (size_t)(g->n + 1));
-    g->nnz_t = 0;
+    pg_free_transposes(g);
     return PG_OK;
 }

@@ -247,9 +247,7 @@ extern "C" pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype w
     // (re)allocate the aggregation buffers
     size_t wb_old = pg_wbytes(g->wdtype);
     pg_free(g, (void **)&g->W, wb_old * n * kp);
-    pg_free(g, (void **)&g->t_ent, 8 * (size_t)g->nnz_t);
-    pg_free(g, (void **)&g->t_ptr, 4 * (size_t)(n + 1));
-    g->nnz_t = 0;
+    pg_free_transposes(g);
     g->aggregated = 0;
     g->hist_iters = -1;
     g->wdtype = wdtype;

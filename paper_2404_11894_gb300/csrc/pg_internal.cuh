@@ -20,6 +20,14 @@ enum : int {
     PG_FLAG_BAD_RANGE = 8,
 };
 
+// Transposed weights by column (sweep row of the column's vertex), entries
+// sorted by source row: ptr[n_active + 1], ent[nnz] = (source row, weight bits).
+struct pg_tcsr {
+    int32_t *ptr = nullptr;
+    int2 *ent = nullptr;
+    int64_t nnz = 0;
+};
+
 struct pg_graph {
     int64_t n = 0;
     int32_t k = 0;
@@ -70,9 +78,8 @@ struct pg_graph {
     int32_t partials_cap = 0;
 
     // ---- adjoint (lazily built) ----
-    int32_t *t_ptr = nullptr;     // [n+1] transposed row pointers (by column)
-    int2 *t_ent = nullptr;        // [nnz_t] (source row, weight bits) of each transposed entry
-    int64_t nnz_t = 0;
+    pg_tcsr tA;                   // transpose of the active rows [0, n_active)
+    pg_tcsr tF;                   // transpose of the first-vertex rows [n_active, n)
     int32_t *flags = nullptr;     // validation flags (device)
 };
 
@@ -227,4 +234,5 @@ static inline size_t pg_wbytes(pg_wdtype t) { return t == PG_W_F32 ? 4 : 2; }
 
 // Launchers implemented in the per-stage translation units.
 pg_status pg_launch_knn(pg_graph *g, cudaStream_t s);
+void pg_free_transposes(pg_graph *g); // releases both transposes (weights changed)
 pg_status pg_launch_aggregate(pg_graph *g, float *c_out, float *D_out, cudaStream_t s);

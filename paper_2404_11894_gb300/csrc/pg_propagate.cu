@@ -8,6 +8,7 @@
 // and combine their four products with shuffles. The relative change of the
 // sweep is reduced in FP64 (per-block partials, then the last block), and a
 // sweep that finds the previous one converged returns at once.
+#include <algorithm>
 #include <mutex>
 
 #include "pg_internal.cuh"
@@ -49,8 +50,9 @@ __device__ __forceinline__ float wdec<__half>(const __half *W, int64_t i) { retu
 static constexpr int SWEEP_THREADS = 256;
 
 // Sum (a, b) over the block in FP64; result valid in thread 0.
+template <int NT>
 __device__ __forceinline__ void block_sum2(double &a, double &b) {
-    __shared__ double sa[SWEEP_THREADS / 32], sb[SWEEP_THREADS / 32];
+    __shared__ double sa[NT / 32], sb[NT / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -63,8 +65,8 @@ __device__ __forceinline__ void block_sum2(double &a, double &b) {
     }
     __syncthreads();
     if (wid == 0) {
-        a = lane < SWEEP_THREADS / 32 ? sa[lane] : 0.0;
-        b = lane < SWEEP_THREADS / 32 ? sb[lane] : 0.0;
+        a = lane < NT / 32 ? sa[lane] : 0.0;
+        b = lane < NT / 32 ? sb[lane] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -73,81 +75,13 @@ __device__ __forceinline__ void block_sum2(double &a, double &b) {
     }
 }
 
-template <int KP, typename WT>
-__global__ void __launch_bounds__(SWEEP_THREADS, 8) sweep_kernel(
-    const int32_t *__restrict__ col, const WT *__restrict__ W, const float *__restrict__ rscale,
-    const float *__restrict__ b, const float *__restrict__ yin, float *__restrict__ yout, int64_t n_active,
-    int32_t *__restrict__ ctrl, double2 *__restrict__ partials, double *__restrict__ resid, int t, double tol) {
-    if (*(volatile int32_t *)&ctrl[1]) return; // converged in an earlier sweep
-    constexpr int LPR = KP / 4;
-    const int lane = threadIdx.x & 31;
-    const int q = lane & (LPR - 1);
-    // Each block owns one contiguous chunk of rows and walks it in order:
-    // rows are in Morton order, so consecutive rows share most neighbour
-    // columns and their y gathers hit in this SM's L1. Every iteration
-    // handles two row groups, so each thread has both groups' streamed loads
-    // and gathers in flight before it does any arithmetic.
-    constexpr int RPB = SWEEP_THREADS / LPR; // rows per block per group
-    constexpr int U = 2;                     // row groups per iteration
-    const int64_t chunk = ((n_active + gridDim.x - 1) / gridDim.x + U * RPB - 1) / (U * RPB) * (U * RPB);
-    const int64_t r0 = (int64_t)blockIdx.x * chunk;
-    const int64_t r1 = min(n_active, r0 + chunk);
-    float rd = 0.0f, rn = 0.0f;
-    for (int64_t base = r0; base < r1; base += U * RPB) { // uniform across the block
-        int64_t row[U];
-        bool ok[U];
-        int4 c4[U];
-        float4 w4[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            row[u] = base + u * RPB + threadIdx.x / LPR;
-            ok[u] = row[u] < r1;
-            if (ok[u]) {
-                c4[u] = __ldcs(reinterpret_cast<const int4 *>(col + row[u] * KP) + q);
-                w4[u] = W4<WT>::load(W + row[u] * KP + q * 4);
-            } else {
-                c4[u] = make_int4(0, 0, 0, 0);
-                w4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
-        float g[U][4];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            g[u][0] = __ldg(yin + c4[u].x);
-            g[u][1] = __ldg(yin + c4[u].y);
-            g[u][2] = __ldg(yin + c4[u].z);
-            g[u][3] = __ldg(yin + c4[u].w);
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            // compensated sum of the row's products (the kernel is memory-bound,
-            // so the extra additions are free; they keep 30+ sweeps at albedo
-            // ~1 within float32 rounding of the exact iterate)
-            float acc, cmp, e;
-            two_sum(__fmul_rn(w4[u].x, g[u][0]), __fmul_rn(w4[u].y, g[u][1]), acc, cmp);
-            two_sum(acc, __fmul_rn(w4[u].z, g[u][2]), acc, e);
-            cmp = __fadd_rn(cmp, e);
-            two_sum(acc, __fmul_rn(w4[u].w, g[u][3]), acc, e);
-            cmp = __fadd_rn(cmp, e);
-#pragma unroll
-            for (int o = LPR / 2; o > 0; o >>= 1) {
-                float oa = __shfl_xor_sync(0xffffffffu, acc, o), oc = __shfl_xor_sync(0xffffffffu, cmp, o);
-                two_sum(acc, oa, acc, e);
-                cmp = __fadd_rn(cmp, __fadd_rn(oc, e));
-            }
-            acc = __fadd_rn(acc, cmp);
-            if (ok[u] && q == 0) {
-                const float sc = WTraits<WT>::id == PG_W_F32 ? 1.0f : rscale[row[u]];
-                const float yn = fmaf(acc, sc, b[row[u]]);
-                const float d = yn - yin[row[u]];
-                yout[row[u]] = yn;
-                rd = fmaf(d, d, rd);
-                rn = fmaf(yn, yn, rn);
-            }
-        }
-    }
+// Relative change of the sweep: per-block FP64 partials, then the last block
+// to finish (ticket in ctrl[2]) adds them up and sets the stop flag.
+template <int NT>
+__device__ __forceinline__ void sweep_residual(float rd, float rn, int32_t *ctrl, double2 *partials,
+                                               double *resid, int t, double tol) {
     double a = rd, bb = rn;
-    block_sum2(a, bb);
+    block_sum2<NT>(a, bb);
     __shared__ bool last;
     if (threadIdx.x == 0) {
         partials[blockIdx.x] = make_double2(a, bb);
@@ -163,7 +97,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 8) sweep_kernel(
         sa += pv[0];
         sb += pv[1];
     }
-    block_sum2(sa, sb);
+    block_sum2<NT>(sa, sb);
     if (threadIdx.x == 0) {
         double r = sb > 0.0 ? sqrt(sa) / sqrt(sb) : 0.0;
         resid[t - 1] = r;
@@ -171,6 +105,110 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 8) sweep_kernel(
         ctrl[2] = 0;
         if (tol > 0.0 && r < tol) ctrl[1] = 1;
     }
+}
+
+// Compensated sum of one row's products, four per lane, then over the row's
+// LPR lanes (the kernel is memory-bound, so the extra additions are free;
+// they keep 30+ sweeps at albedo ~1 within float32 rounding of the exact
+// iterate).
+template <int LPR>
+__device__ __forceinline__ float row_dot(const float4 &w, float g0, float g1, float g2, float g3) {
+    float acc, cmp, e;
+    two_sum(__fmul_rn(w.x, g0), __fmul_rn(w.y, g1), acc, cmp);
+    two_sum(acc, __fmul_rn(w.z, g2), acc, e);
+    cmp = __fadd_rn(cmp, e);
+    two_sum(acc, __fmul_rn(w.w, g3), acc, e);
+    cmp = __fadd_rn(cmp, e);
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) {
+        float oa = __shfl_xor_sync(0xffffffffu, acc, o), oc = __shfl_xor_sync(0xffffffffu, cmp, o);
+        two_sum(acc, oa, acc, e);
+        cmp = __fadd_rn(cmp, __fadd_rn(oc, e));
+    }
+    return __fadd_rn(acc, cmp);
+}
+
+template <int KP, typename WT, int NT, int MINB, bool HOIST, int U>
+__global__ void __launch_bounds__(NT, MINB) sweep_kernel(
+    const int32_t *__restrict__ col, const WT *__restrict__ W, const float *__restrict__ rscale,
+    const float *__restrict__ b, const float *__restrict__ yin, float *__restrict__ yout, int64_t n_active,
+    int32_t *__restrict__ ctrl, double2 *__restrict__ partials, double *__restrict__ resid, int t, double tol) {
+    if (*(volatile int32_t *)&ctrl[1]) return; // converged in an earlier sweep
+    constexpr int LPR = KP / 4;
+    constexpr bool W16 = WTraits<WT>::id != PG_W_F32;
+    const int lane = threadIdx.x & 31;
+    const int q = lane & (LPR - 1);
+    const int lead = lane & ~(LPR - 1);
+    static_assert(!HOIST || LPR >= (W16 ? 3 : 2), "row scalars need a lane each");
+    // Each block owns one contiguous chunk of rows and walks it in order:
+    // rows are in Morton order, so consecutive rows share most neighbour
+    // columns and their y gathers hit in this SM's L1. Every iteration
+    // handles U row groups, so each thread has all groups' streamed loads
+    // and gathers in flight before it does any arithmetic. With HOIST the
+    // row's scalars (b, its previous iterate, the 16-bit row scale) are
+    // loaded up front by different lanes of the row, so they travel with the
+    // streamed loads instead of costing a round trip after the gathers.
+    constexpr int RPB = NT / LPR; // rows per block per group
+    const int64_t chunk = ((n_active + gridDim.x - 1) / gridDim.x + U * RPB - 1) / (U * RPB) * (U * RPB);
+    const int64_t r0 = min((int64_t)blockIdx.x * chunk, n_active);
+    const int64_t r1 = min(n_active, r0 + chunk);
+    float rd = 0.0f, rn = 0.0f;
+    for (int64_t base = r0; base < r1; base += U * RPB) { // uniform across the block
+        int32_t row[U]; // row indices fit in 32 bits (n < 2^31); 64-bit only in element offsets
+        bool ok[U];
+        int4 c4[U];
+        float4 w4[U];
+        float sv[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            row[u] = (int32_t)(base + u * RPB + threadIdx.x / LPR);
+            ok[u] = row[u] < r1;
+            if (ok[u]) {
+                c4[u] = __ldcs(reinterpret_cast<const int4 *>(col + (int64_t)row[u] * KP) + q);
+                w4[u] = W4<WT>::load(W + (int64_t)row[u] * KP + q * 4);
+            } else {
+                c4[u] = make_int4(0, 0, 0, 0);
+                w4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            sv[u] = 0.0f;
+            if (HOIST && ok[u]) {
+                if (q == 0) sv[u] = __ldcs(b + row[u]);
+                else if (q == 1) sv[u] = yin[row[u]];
+                else if (W16 && q == 2) sv[u] = __ldcs(rscale + row[u]);
+            }
+        }
+        float g[U][4];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            g[u][0] = __ldg(yin + c4[u].x);
+            g[u][1] = __ldg(yin + c4[u].y);
+            g[u][2] = __ldg(yin + c4[u].z);
+            g[u][3] = __ldg(yin + c4[u].w);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const float acc = row_dot<LPR>(w4[u], g[u][0], g[u][1], g[u][2], g[u][3]);
+            float bv, yo, sc = 1.0f;
+            if (HOIST) {
+                bv = sv[u];
+                yo = __shfl_sync(0xffffffffu, sv[u], lead + 1);
+                if (W16) sc = __shfl_sync(0xffffffffu, sv[u], lead + 2);
+            }
+            if (ok[u] && q == 0) {
+                if (!HOIST) {
+                    if (W16) sc = rscale[row[u]];
+                    bv = b[row[u]];
+                    yo = yin[row[u]];
+                }
+                const float yn = fmaf(acc, sc, bv);
+                const float d = yn - yo;
+                yout[row[u]] = yn;
+                rd = fmaf(d, d, rd);
+                rn = fmaf(yn, yn, rn);
+            }
+        }
+    }
+    sweep_residual<NT>(rd, rn, ctrl, partials, resid, t, tol);
 }
 
 // y0[row of succ(v)] = L0[v]  (L+_v is the radiance that succ(v) sends back)
@@ -207,27 +245,55 @@ __global__ void finish_L_kernel(const int32_t *__restrict__ c2m, const int32_t *
     L[v] = s >= 0 ? y[m2r[s]] : 0.0f;
 }
 
+template <int KP, typename WT, int NT, int MINB, bool HOIST, int U>
+static void launch_sweep_cfg(const pg_graph *g, const float *b, const float *yin, float *yout, int32_t *ctrl,
+                             double2 *partials, double *resid, int t, double tol, cudaStream_t s) {
+    int64_t need = (g->n_active * (KP / 4) + NT - 1) / NT;
+    int64_t cap = (int64_t)pg_num_sms() * MINB;
+    int blocks = (int)std::max<int64_t>(1, std::min(need, cap));
+    sweep_kernel<KP, WT, NT, MINB, HOIST, U><<<blocks, NT, 0, s>>>(g->col, (const WT *)g->W, g->rscale, b, yin,
+                                                                  yout, g->n_active, ctrl, partials, resid, t, tol);
+}
+
+// Launch shapes (measured on the 8.7M-vertex cloud, k = 16): FP32 rows with
+// the row scalars loaded up front, one row group per iteration, 256 x 8 per
+// SM; 16-bit rows (whose streamed bytes are smaller, so the gathers weigh
+// more) in 1024-thread blocks, two per SM, so fewer distinct row chunks share
+// an SM's L1.
 template <int KP, typename WT>
-static pg_status launch_sweep(pg_graph *g, const float *b, const float *yin, float *yout, int t, double tol,
-                              int blocks, cudaStream_t s) {
-    sweep_kernel<KP, WT><<<blocks, SWEEP_THREADS, 0, s>>>(g->col, (const WT *)g->W, g->rscale, b, yin, yout,
-                                                          g->n_active, g->d_ctrl, (double2 *)g->d_partials,
-                                                          g->d_resid, t, tol);
+static pg_status launch_sweep(const pg_graph *g, const float *b, const float *yin, float *yout, int32_t *ctrl,
+                              double2 *partials, double *resid, int t, double tol, cudaStream_t s) {
+    if constexpr (WTraits<WT>::id == PG_W_F32 && KP >= 8)
+        launch_sweep_cfg<KP, WT, 256, 8, true, 1>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
+    else if constexpr (KP >= 16)
+        launch_sweep_cfg<KP, WT, 1024, 2, false, 2>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
+    else
+        launch_sweep_cfg<KP, WT, 1024, 2, false, 1>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
     pg_count_launches(1);
     PG_LAUNCH_CHECK();
     return PG_OK;
 }
 
 template <typename WT>
-static pg_status launch_sweep_k(pg_graph *g, const float *b, const float *yin, float *yout, int t, double tol,
-                                int blocks, cudaStream_t s) {
+static pg_status launch_sweep_k(const pg_graph *g, const float *b, const float *yin, float *yout, int32_t *ctrl,
+                                double2 *partials, double *resid, int t, double tol, cudaStream_t s) {
     switch (g->kp) {
-        case 4: return launch_sweep<4, WT>(g, b, yin, yout, t, tol, blocks, s);
-        case 8: return launch_sweep<8, WT>(g, b, yin, yout, t, tol, blocks, s);
-        case 16: return launch_sweep<16, WT>(g, b, yin, yout, t, tol, blocks, s);
-        case 32: return launch_sweep<32, WT>(g, b, yin, yout, t, tol, blocks, s);
+        case 4: return launch_sweep<4, WT>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
+        case 8: return launch_sweep<8, WT>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
+        case 16: return launch_sweep<16, WT>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
+        case 32: return launch_sweep<32, WT>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
         default: return PG_ERR_UNSUPPORTED;
     }
+}
+
+static pg_status launch_sweep_w(const pg_graph *g, const float *b, const float *yin, float *yout, int32_t *ctrl,
+                                double2 *partials, double *resid, int t, double tol, cudaStream_t s) {
+    switch (g->wdtype) {
+        case PG_W_F32: return launch_sweep_k<float>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
+        case PG_W_BF16: return launch_sweep_k<__nv_bfloat16>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
+        case PG_W_F16: return launch_sweep_k<__half>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
+    }
+    return PG_ERR_UNSUPPORTED;
 }
 
 int pg_sweep_blocks(const pg_graph *g) {
@@ -303,11 +369,7 @@ extern "C" pg_status pg_propagate(pg_graph *g, const float *c, const float *L0, 
     for (int t = 1; t <= iters && st == PG_OK; t++) {
         const float *yin = keep_history ? g->hist + (int64_t)(t - 1) * stride : g->ybuf[(t - 1) & 1];
         float *yout = keep_history ? g->hist + (int64_t)t * stride : g->ybuf[t & 1];
-        switch (g->wdtype) {
-            case PG_W_F32: st = launch_sweep_k<float>(g, b, yin, yout, t, tol, blocks, s); break;
-            case PG_W_BF16: st = launch_sweep_k<__nv_bfloat16>(g, b, yin, yout, t, tol, blocks, s); break;
-            case PG_W_F16: st = launch_sweep_k<__half>(g, b, yin, yout, t, tol, blocks, s); break;
-        }
+        st = launch_sweep_w(g, b, yin, yout, g->d_ctrl, (double2 *)g->d_partials, g->d_resid, t, tol, s);
     }
     if (st == PG_OK) {
         finish_L_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(g->c2m, g->succ_m, g->m2r, n, g->ybuf[0], g->ybuf[1],
@@ -372,25 +434,6 @@ static pg_status noalloc_scratch(unsigned char **out) {
     return PG_OK;
 }
 
-template <int KP, typename WT>
-static void na_sweep(const pg_graph *g, const float *yin, float *yout, int32_t *ctrl, double2 *partials,
-                     double *resid, int t, double tol, int blocks, cudaStream_t s) {
-    sweep_kernel<KP, WT><<<blocks, SWEEP_THREADS, 0, s>>>(g->col, (const WT *)g->W, g->rscale, g->b, yin, yout,
-                                                          g->n_active, ctrl, partials, resid, t, tol);
-    pg_count_launches(1);
-}
-
-template <typename WT>
-static void na_sweep_k(const pg_graph *g, const float *yin, float *yout, int32_t *ctrl, double2 *partials,
-                       double *resid, int t, double tol, int blocks, cudaStream_t s) {
-    switch (g->kp) {
-        case 4: na_sweep<4, WT>(g, yin, yout, ctrl, partials, resid, t, tol, blocks, s); break;
-        case 8: na_sweep<8, WT>(g, yin, yout, ctrl, partials, resid, t, tol, blocks, s); break;
-        case 16: na_sweep<16, WT>(g, yin, yout, ctrl, partials, resid, t, tol, blocks, s); break;
-        default: na_sweep<32, WT>(g, yin, yout, ctrl, partials, resid, t, tol, blocks, s); break;
-    }
-}
-
 extern "C" pg_status pg_propagate_noalloc(pg_graph *g, const float *L0, int32_t iters, double tol, float *L,
                                           pg_stream_t stream) {
     if (!g || iters < 0) return PG_ERR_INVALID_ARG;
@@ -399,8 +442,7 @@ extern "C" pg_status pg_propagate_noalloc(pg_graph *g, const float *L0, int32_t 
     const int64_t n = g->n;
     if (n == 0) return PG_OK;
     if (!L0 || !L) return PG_ERR_INVALID_ARG;
-    int blocks = pg_sweep_blocks(g);
-    if (blocks > NA_MAX_BLOCKS) blocks = NA_MAX_BLOCKS;
+    if (pg_num_sms() * 8 > NA_MAX_BLOCKS) return PG_ERR_UNSUPPORTED; // partials of one sweep
     unsigned char *base = nullptr;
     PG_TRY(noalloc_scratch(&base));
     cudaStream_t s = (cudaStream_t)stream;
@@ -418,11 +460,7 @@ extern "C" pg_status pg_propagate_noalloc(pg_graph *g, const float *L0, int32_t 
     for (int t = 1; t <= iters; t++) {
         const float *yin = (t & 1) ? y0 : y1;
         float *yout = (t & 1) ? y1 : y0;
-        switch (g->wdtype) {
-            case PG_W_F32: na_sweep_k<float>(g, yin, yout, ctrl, partials, resid, t, tol, blocks, s); break;
-            case PG_W_BF16: na_sweep_k<__nv_bfloat16>(g, yin, yout, ctrl, partials, resid, t, tol, blocks, s); break;
-            case PG_W_F16: na_sweep_k<__half>(g, yin, yout, ctrl, partials, resid, t, tol, blocks, s); break;
-        }
+        PG_TRY(launch_sweep_w(g, g->b, yin, yout, ctrl, partials, resid, t, tol, s));
     }
     finish_L_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(g->c2m, g->succ_m, g->m2r, n, y0, y1, nullptr, ctrl, L);
     pg_count_launches(1);
