@@ -67,7 +67,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
@@ -180,16 +180,27 @@ def run_gpu(args):
     stage_ms = {nm: float(np.mean([m[nm][0].elapsed_time(m[nm][1]) for m in marks_all if m[nm][0].query()]))
                 for nm in stage_names if not (args.no_adjoint and nm == "adjoint")}
 
-    # ---- sweep kernel roofline: propagation time minus its permutation prologue/epilogue
-    t0 = time.time()
-    prop_base = solver.time_propagate(0, reps=5)
-    prop_full = solver.time_propagate(sc.iters, reps=3)
-    sweep_ms = (prop_full - prop_base) / sc.iters
+    # ---- sweep kernel roofline: the propagate stage of the timed steps minus its
+    # prologue/epilogue (pg_propagate with zero sweeps), per sweep
+    prop_base = solver.time_propagate(0, reps=5, keep_history=not args.no_adjoint)
+    sweep_ms = (stage_ms["propagate"] - prop_base) / sc.iters
     wb = 4
     bytes_sweep = nnz * (4 + wb) + info["n_active"] * 12
     achieved = bytes_sweep / (sweep_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
     traffic = _profile_traffic("sweep_f32", n)
+    others = {}
+    if not args.no_adjoint and args.adjoint_mode == 0:
+        # transposed (reverse) sweep: adjoint time after T and after 1 forward sweeps
+        first_d = dev_in["first"]
+        a_T = solver.time_adjoint(sc.iters, sc.spp, sc.width, sc.height, first_d)
+        a_1 = solver.time_adjoint(1, sc.spp, sc.width, sc.height, first_d)
+        ts_ms = (a_T - a_1) / (sc.iters - 1)
+        ts_bytes = nnz * 8 + info["n_active"] * 24
+        others["tsweep_kernel<float,4,8,6>"] = {
+            "launch_ms": ts_ms, "algorithmic_bytes_per_launch": ts_bytes,
+            "achieved": ts_bytes / (ts_ms / 1e3) / 1e9, "frac": ts_bytes / (ts_ms / 1e3) / 1e9 / peak,
+            "launches_per_step": sc.iters + 1}
 
     # ---- the adjoint with the HG g gradient as well (not part of the step)
     adj_g_ms = None
@@ -258,7 +269,8 @@ def run_gpu(args):
         "propagate_edge_updates_per_s": nnz / (sweep_ms / 1e3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "sweep_kernel<16,float>",
-                     "sweep_ms": sweep_ms, "algorithmic_bytes_per_launch": bytes_sweep, "peak_kind": peak_kind},
+                     "sweep_ms": sweep_ms, "algorithmic_bytes_per_launch": bytes_sweep, "peak_kind": peak_kind,
+                     "other_kernels": others},
         "precision": prec,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -360,7 +372,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-adjoint", action="store_true")

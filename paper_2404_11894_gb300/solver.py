@@ -57,15 +57,32 @@ class Solver:
             mark("adjoint", 1)
         return img
 
-    def time_propagate(self, iters: int, reps: int = 3) -> float:
+    def time_propagate(self, iters: int, reps: int = 3, keep_history: bool = False) -> float:
         """Mean device time (ms) of pg_propagate on the current graph."""
         s = torch.cuda.current_stream()
         L = torch.empty_like(self._L0)
-        pg_propagate(self.graph, self._L0, iters, out=L)
+        pg_propagate(self.graph, self._L0, iters, out=L, keep_history=keep_history)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
         for _ in range(reps):
-            pg_propagate(self.graph, self._L0, iters, out=L)
+            pg_propagate(self.graph, self._L0, iters, out=L, keep_history=keep_history)
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def time_adjoint(self, iters: int, spp: int, width: int, height: int, first, reps: int = 2) -> float:
+        """Mean device time (ms) of pg_propagate_adjoint after a forward pass of
+        ``iters`` sweeps on the current graph (transposes already built)."""
+        s = torch.cuda.current_stream()
+        pg_propagate(self.graph, self._L0, iters, keep_history=True)
+        dI = torch.ones(width * height, dtype=torch.float32, device="cuda")
+        pg_propagate_adjoint(self.graph, dI, first, spp, width, height, want_g=False,
+                             recompute_weights=self.recompute_weights)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            pg_propagate_adjoint(self.graph, dI, first, spp, width, height, want_g=False,
+                                 recompute_weights=self.recompute_weights)
         e1.record(s)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
