@@ -99,44 +99,69 @@ __global__ void tfill_kernel(const int32_t *__restrict__ col, const WT *__restri
     tent[pos] = make_int2((int32_t)(e / kp), wbits<WT>(W[e]));
 }
 
-// Order each column's entries by source row (a row appears once per column),
-// which makes the reverse sweep's summation order deterministic. Columns of
-// up to 32 entries (all of them for k <= 16 in practice) are sorted in
-// registers by a bitonic network; longer ones by insertion sort in memory.
-__global__ void __launch_bounds__(128) tsort_kernel(const int32_t *__restrict__ tptr, int64_t ncols,
-                                                    int2 *__restrict__ tent) {
+// Column lengths rounded up to even, so that every column starts on a
+// 16-byte boundary and the reverse sweep loads its entries in pairs.
+__global__ void tround_kernel(int32_t *__restrict__ cnt, int64_t ncols) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncols) return;
-    const int32_t a = tptr[c], b = tptr[c + 1], len = b - a;
-    if (len <= 1) return;
-    if (len <= 32) {
-        int2 kv[32];
+    if (c < ncols) cnt[c] = (cnt[c] + 1) & ~1;
+}
+
+template <int N>
+__device__ __forceinline__ void bitonic_rows(int2 (&kv)[N]) {
 #pragma unroll
-        for (int i = 0; i < 32; i++) kv[i] = i < len ? tent[a + i] : make_int2(INT32_MAX, 0);
+    for (int size = 2; size <= N; size <<= 1) {
 #pragma unroll
-        for (int size = 2; size <= 32; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
 #pragma unroll
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-#pragma unroll
-                for (int i = 0; i < 32; i++) {
-                    const int j = i ^ stride;
-                    if (j > i) {
-                        const bool up = (i & size) == 0;
-                        if ((kv[i].x > kv[j].x) == up) {
-                            int2 t = kv[i];
-                            kv[i] = kv[j];
-                            kv[j] = t;
-                        }
+            for (int i = 0; i < N; i++) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    if ((kv[i].x > kv[j].x) == up) {
+                        int2 t = kv[i];
+                        kv[i] = kv[j];
+                        kv[j] = t;
                     }
                 }
             }
         }
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void sort_column(int2 *__restrict__ tent, int32_t a, int32_t len) {
+    int2 kv[N];
 #pragma unroll
-        for (int i = 0; i < 32; i++)
-            if (i < len) tent[a + i] = kv[i];
+    for (int i = 0; i < N; i++) kv[i] = i < len ? tent[a + i] : make_int2(INT32_MAX, 0);
+    bitonic_rows<N>(kv);
+#pragma unroll
+    for (int i = 0; i < N; i++)
+        if (i < len) tent[a + i] = kv[i];
+}
+
+// Order each column's entries by source row (a row appears once per column),
+// which makes the reverse sweep's summation order deterministic, and write
+// the column's pad entry (source row pad_row < 0, skipped by the sweep) when
+// its length was rounded up. Columns of up to 16 or 32 entries (all of them
+// for k <= 16 in practice) are sorted in registers by a bitonic network;
+// longer ones by insertion sort in memory.
+__global__ void __launch_bounds__(128) tsort_kernel(const int32_t *__restrict__ tptr,
+                                                    const int32_t *__restrict__ fill, int64_t ncols,
+                                                    int32_t pad_row, int2 *__restrict__ tent) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    const int32_t a = tptr[c], len = fill[c];
+    if (a + len < tptr[c + 1]) tent[a + len] = make_int2(pad_row, 0);
+    if (len <= 1) return;
+    if (len <= 16) {
+        sort_column<16>(tent, a, len);
         return;
     }
-    for (int32_t i = a + 1; i < b; i++) {
+    if (len <= 32) {
+        sort_column<32>(tent, a, len);
+        return;
+    }
+    for (int32_t i = a + 1; i < a + len; i++) {
         const int2 v = tent[i];
         int32_t j = i - 1;
         while (j >= a && tent[j].x > v.x) {
@@ -165,7 +190,8 @@ __global__ void seed_kernel(const int32_t *__restrict__ first, const float *__re
 // ------------------------------------------------------------------ reverse sweep (stored transpose)
 // Four lanes per column c: mu_out[c] = sum_e tW[e] us_in[trow[e]] over the
 // column's entries (rows ascending). Each lane loads all of its (up to 8)
-// entries before using them, so a column costs one round trip, and each
+// entries, two per 16-byte load, before using them, so a column costs one
+// round trip, and each
 // block walks one contiguous chunk of columns (neighbouring columns draw on
 // neighbouring rows). When y_t is given it also accumulates
 // G[c] += mu_in[c] y_t[c] (and B[c] += mu_in[c] when B is given); those
@@ -189,9 +215,25 @@ __global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_kernel(
     const int64_t chunk = ((ncols + gridDim.x - 1) / gridDim.x + CPB - 1) / CPB * CPB;
     const int64_t c0 = (int64_t)blockIdx.x * chunk;
     const int64_t c1 = min(ncols, c0 + chunk);
+    // each iteration prefetches the next one's column extents, so the entry
+    // loads never wait behind a load of the row pointers
+    int32_t pa = 0, pb = 0;
+    if (write_out && c0 + threadIdx.x / TS_LPC < c1) {
+        pa = tptr[c0 + threadIdx.x / TS_LPC];
+        pb = tptr[c0 + threadIdx.x / TS_LPC + 1];
+    }
     for (int64_t base = c0; base < c1; base += CPB) {
         const int64_t c = base + threadIdx.x / TS_LPC;
         const bool ok = c < c1;
+        int32_t ca = pa, cb = pb;
+        if (write_out) {
+            const int64_t cn = c + CPB;
+            pa = pb = 0;
+            if (cn < c1) {
+                pa = tptr[cn];
+                pb = tptr[cn + 1];
+            }
+        }
         // column scalars k = 0 mu_in, 1 y_t, 2 G, 3 B: scalar k is loaded by
         // lane k % LPC of the column into its slot k / LPC; lane 0 also loads
         // the row scale
@@ -210,18 +252,21 @@ __global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_kernel(
         if (ok && rscale && write_out && q == 0) rs = __ldcs(rscale + c);
         float acc = 0.0f;
         if (ok && write_out) {
-            int32_t a = tptr[c];
-            const int32_t b = tptr[c + 1];
+            int32_t a = ca;
+            const int32_t b = cb;
+            // columns start on even entries: lane q takes the pairs 2q + 2 LPC u
             for (; a < b; a += TS_LPC * TS_PER_LANE) {
-                int2 ent[TS_PER_LANE];
+                int4 ent[TS_PER_LANE / 2];
 #pragma unroll
-                for (int u = 0; u < TS_PER_LANE; u++) {
-                    const int32_t e = a + q + TS_LPC * u;
-                    ent[u] = e < b ? __ldcs(tent + e) : make_int2(-1, 0);
+                for (int u = 0; u < TS_PER_LANE / 2; u++) {
+                    const int32_t e = a + 2 * q + 2 * TS_LPC * u;
+                    ent[u] = e < b ? __ldcs(reinterpret_cast<const int4 *>(tent + e)) : make_int4(-1, 0, -1, 0);
                 }
 #pragma unroll
-                for (int u = 0; u < TS_PER_LANE; u++)
+                for (int u = 0; u < TS_PER_LANE / 2; u++) {
                     if (ent[u].x >= 0) acc = fmaf(wfrom<WT>(ent[u].y), __ldg(us_in + ent[u].x), acc);
+                    if (ent[u].z >= 0) acc = fmaf(wfrom<WT>(ent[u].w), __ldg(us_in + ent[u].z), acc);
+                }
             }
         }
 #pragma unroll
@@ -591,7 +636,8 @@ static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
         if (r1[i] > r0[i]) {
             tcount_kernel<<<pg_blocks((r1[i] - r0[i]) * kp, 256), 256, 0, s>>>(g->col, r0[i], r1[i], kp, na,
                                                                                ts[i]->ptr);
-            pg_count_launches(1);
+            tround_kernel<<<pg_blocks(na, 256), 256, 0, s>>>(ts[i]->ptr, na);
+            pg_count_launches(2);
             PG_LAUNCH_CHECK();
         }
         PG_TRY(pg_scan_exclusive(g, ts[i]->ptr, na + 1, d_total + 2 * i, s));
@@ -608,7 +654,7 @@ static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
             g->col, (const WT *)g->W, r0[i], r1[i], kp, na, ts[i]->ptr, fill, ts[i]->ent);
         pg_count_launches(1);
         PG_LAUNCH_CHECK();
-        tsort_kernel<<<pg_blocks(na, 128), 128, 0, s>>>(ts[i]->ptr, na, ts[i]->ent);
+        tsort_kernel<<<pg_blocks(na, 128), 128, 0, s>>>(ts[i]->ptr, fill, na, -1, ts[i]->ent);
         pg_count_launches(1);
         PG_LAUNCH_CHECK();
     }

@@ -128,7 +128,7 @@ __device__ __forceinline__ float row_dot(const float4 &w, float g0, float g1, fl
     return __fadd_rn(acc, cmp);
 }
 
-template <int KP, typename WT, int NT, int MINB, bool HOIST, int U>
+template <int KP, typename WT, int NT, int MINB, int U>
 __global__ void __launch_bounds__(NT, MINB) sweep_kernel(
     const int32_t *__restrict__ col, const WT *__restrict__ W, const float *__restrict__ rscale,
     const float *__restrict__ b, const float *__restrict__ yin, float *__restrict__ yout, int64_t n_active,
@@ -138,16 +138,11 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(
     constexpr bool W16 = WTraits<WT>::id != PG_W_F32;
     const int lane = threadIdx.x & 31;
     const int q = lane & (LPR - 1);
-    const int lead = lane & ~(LPR - 1);
-    static_assert(!HOIST || LPR >= (W16 ? 3 : 2), "row scalars need a lane each");
     // Each block owns one contiguous chunk of rows and walks it in order:
     // rows are in Morton order, so consecutive rows share most neighbour
     // columns and their y gathers hit in this SM's L1. Every iteration
     // handles U row groups, so each thread has all groups' streamed loads
-    // and gathers in flight before it does any arithmetic. With HOIST the
-    // row's scalars (b, its previous iterate, the 16-bit row scale) are
-    // loaded up front by different lanes of the row, so they travel with the
-    // streamed loads instead of costing a round trip after the gathers.
+    // and gathers in flight before it does any arithmetic.
     constexpr int RPB = NT / LPR; // rows per block per group
     const int64_t chunk = ((n_active + gridDim.x - 1) / gridDim.x + U * RPB - 1) / (U * RPB) * (U * RPB);
     const int64_t r0 = min((int64_t)blockIdx.x * chunk, n_active);
@@ -158,7 +153,6 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(
         bool ok[U];
         int4 c4[U];
         float4 w4[U];
-        float sv[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
             row[u] = (int32_t)(base + u * RPB + threadIdx.x / LPR);
@@ -169,12 +163,6 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(
             } else {
                 c4[u] = make_int4(0, 0, 0, 0);
                 w4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            sv[u] = 0.0f;
-            if (HOIST && ok[u]) {
-                if (q == 0) sv[u] = __ldcs(b + row[u]);
-                else if (q == 1) sv[u] = yin[row[u]];
-                else if (W16 && q == 2) sv[u] = __ldcs(rscale + row[u]);
             }
         }
         float g[U][4];
@@ -188,20 +176,10 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const float acc = row_dot<LPR>(w4[u], g[u][0], g[u][1], g[u][2], g[u][3]);
-            float bv, yo, sc = 1.0f;
-            if (HOIST) {
-                bv = sv[u];
-                yo = __shfl_sync(0xffffffffu, sv[u], lead + 1);
-                if (W16) sc = __shfl_sync(0xffffffffu, sv[u], lead + 2);
-            }
             if (ok[u] && q == 0) {
-                if (!HOIST) {
-                    if (W16) sc = rscale[row[u]];
-                    bv = b[row[u]];
-                    yo = yin[row[u]];
-                }
-                const float yn = fmaf(acc, sc, bv);
-                const float d = yn - yo;
+                const float sc = W16 ? rscale[row[u]] : 1.0f;
+                const float yn = fmaf(acc, sc, b[row[u]]);
+                const float d = yn - yin[row[u]];
                 yout[row[u]] = yn;
                 rd = fmaf(d, d, rd);
                 rn = fmaf(yn, yn, rn);
@@ -209,6 +187,79 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(
         }
     }
     sweep_residual<NT>(rd, rn, ctrl, partials, resid, t, tol);
+}
+
+// The same sweep, software-pipelined: one row group per iteration, with the
+// next group's streamed loads issued before this group's gathers, so the
+// DRAM round trip of one group overlaps the L2 round trip of the other. The
+// row's scalars (b, its previous iterate, the 16-bit row scale) are loaded
+// with the streamed loads by different lanes of the row and shuffled to the
+// row's first lane at the end, instead of costing a round trip after the
+// gathers.
+template <int KP, typename WT, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) sweep_pf_kernel(
+    const int32_t *__restrict__ col, const WT *__restrict__ W, const float *__restrict__ rscale,
+    const float *__restrict__ b, const float *__restrict__ yin, float *__restrict__ yout, int64_t n_active,
+    int32_t *__restrict__ ctrl, double2 *__restrict__ partials, double *__restrict__ resid, int t, double tol) {
+    if (*(volatile int32_t *)&ctrl[1]) return; // converged in an earlier sweep
+    constexpr int LPR = KP / 4;
+    constexpr bool W16 = WTraits<WT>::id != PG_W_F32;
+    static_assert(LPR >= (W16 ? 3 : 2), "row scalars need a lane each");
+    const int lane = threadIdx.x & 31;
+    const int q = lane & (LPR - 1);
+    const int lead = lane & ~(LPR - 1);
+    constexpr int RPB = NT / LPR;
+    const int64_t chunk = ((n_active + gridDim.x - 1) / gridDim.x + RPB - 1) / RPB * RPB;
+    const int64_t r0 = min((int64_t)blockIdx.x * chunk, n_active);
+    const int64_t r1 = min(n_active, r0 + chunk);
+    const int32_t lr = threadIdx.x / LPR;
+    auto load = [&](int64_t base, int4 &c4, float4 &w4, float &sv) {
+        const int64_t row = base + lr;
+        c4 = make_int4(0, 0, 0, 0);
+        w4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        sv = 0.0f;
+        if (row < r1) {
+            c4 = __ldcs(reinterpret_cast<const int4 *>(col + row * KP) + q);
+            w4 = W4<WT>::load(W + row * KP + q * 4);
+            if (q == 0) sv = __ldcs(b + row);
+            else if (q == 1) sv = yin[row];
+            else if (W16 && q == 2) sv = __ldcs(rscale + row);
+        }
+    };
+    float rd = 0.0f, rn = 0.0f;
+    int4 c4n;
+    float4 w4n;
+    float svn;
+    load(r0, c4n, w4n, svn);
+    for (int64_t base = r0; base < r1; base += RPB) { // uniform across the block
+        const int4 c4 = c4n;
+        const float4 w4 = w4n;
+        const float sv = svn;
+        if (base + RPB < r1) load(base + RPB, c4n, w4n, svn);
+        const float g0 = __ldg(yin + c4.x), g1 = __ldg(yin + c4.y), g2 = __ldg(yin + c4.z), g3 = __ldg(yin + c4.w);
+        const float acc = row_dot<LPR>(w4, g0, g1, g2, g3);
+        const float yo = __shfl_sync(0xffffffffu, sv, lead + 1);
+        const float sc = W16 ? __shfl_sync(0xffffffffu, sv, lead + 2) : 1.0f;
+        const int64_t row = base + lr;
+        if (row < r1 && q == 0) {
+            const float yn = fmaf(acc, sc, sv);
+            const float d = yn - yo;
+            yout[row] = yn;
+            rd = fmaf(d, d, rd);
+            rn = fmaf(yn, yn, rn);
+        }
+    }
+    sweep_residual<NT>(rd, rn, ctrl, partials, resid, t, tol);
+}
+
+template <int KP, typename WT, int NT, int MINB>
+static void launch_pf_cfg(const pg_graph *g, const float *b, const float *yin, float *yout, int32_t *ctrl,
+                          double2 *partials, double *resid, int t, double tol, cudaStream_t s) {
+    int64_t need = (g->n_active * (KP / 4) + NT - 1) / NT;
+    int64_t cap = (int64_t)pg_num_sms() * MINB;
+    int blocks = (int)std::max<int64_t>(1, std::min(need, cap));
+    sweep_pf_kernel<KP, WT, NT, MINB><<<blocks, NT, 0, s>>>(g->col, (const WT *)g->W, g->rscale, b, yin, yout,
+                                                            g->n_active, ctrl, partials, resid, t, tol);
 }
 
 // y0[row of succ(v)] = L0[v]  (L+_v is the radiance that succ(v) sends back)
@@ -245,30 +296,29 @@ __global__ void finish_L_kernel(const int32_t *__restrict__ c2m, const int32_t *
     L[v] = s >= 0 ? y[m2r[s]] : 0.0f;
 }
 
-template <int KP, typename WT, int NT, int MINB, bool HOIST, int U>
+template <int KP, typename WT, int NT, int MINB, int U>
 static void launch_sweep_cfg(const pg_graph *g, const float *b, const float *yin, float *yout, int32_t *ctrl,
                              double2 *partials, double *resid, int t, double tol, cudaStream_t s) {
     int64_t need = (g->n_active * (KP / 4) + NT - 1) / NT;
     int64_t cap = (int64_t)pg_num_sms() * MINB;
     int blocks = (int)std::max<int64_t>(1, std::min(need, cap));
-    sweep_kernel<KP, WT, NT, MINB, HOIST, U><<<blocks, NT, 0, s>>>(g->col, (const WT *)g->W, g->rscale, b, yin,
-                                                                  yout, g->n_active, ctrl, partials, resid, t, tol);
+    sweep_kernel<KP, WT, NT, MINB, U><<<blocks, NT, 0, s>>>(g->col, (const WT *)g->W, g->rscale, b, yin, yout,
+                                                            g->n_active, ctrl, partials, resid, t, tol);
 }
 
-// Launch shapes (measured on the 8.7M-vertex cloud, k = 16): FP32 rows with
-// the row scalars loaded up front, one row group per iteration, 256 x 8 per
-// SM; 16-bit rows (whose streamed bytes are smaller, so the gathers weigh
-// more) in 1024-thread blocks, two per SM, so fewer distinct row chunks share
-// an SM's L1.
+// Launch shapes (measured on the 8.7M-vertex cloud, k = 16): FP32 rows in the
+// pipelined kernel, one 1024-thread block per SM (one row chunk per L1);
+// 16-bit rows (whose streamed bytes are smaller, so the gathers weigh more)
+// in the two-group kernel, two 1024-thread blocks per SM.
 template <int KP, typename WT>
 static pg_status launch_sweep(const pg_graph *g, const float *b, const float *yin, float *yout, int32_t *ctrl,
                               double2 *partials, double *resid, int t, double tol, cudaStream_t s) {
     if constexpr (WTraits<WT>::id == PG_W_F32 && KP >= 8)
-        launch_sweep_cfg<KP, WT, 256, 8, true, 1>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
+        launch_pf_cfg<KP, WT, 1024, 1>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
     else if constexpr (KP >= 16)
-        launch_sweep_cfg<KP, WT, 1024, 2, false, 2>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
+        launch_sweep_cfg<KP, WT, 1024, 2, 2>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
     else
-        launch_sweep_cfg<KP, WT, 1024, 2, false, 1>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
+        launch_sweep_cfg<KP, WT, 1024, 2, 1>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
     pg_count_launches(1);
     PG_LAUNCH_CHECK();
     return PG_OK;
