@@ -268,7 +268,7 @@ def run_gpu(args):
         "adjoint_with_g_gradient_ms": adj_g_ms,
         "propagate_edge_updates_per_s": nnz / (sweep_ms / 1e3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "sweep_kernel<16,float>",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "sweep_pf_kernel<16,float,1024,1>",
                      "sweep_ms": sweep_ms, "algorithmic_bytes_per_launch": bytes_sweep, "peak_kind": peak_kind,
                      "other_kernels": others},
         "precision": prec,
@@ -294,6 +294,13 @@ def _profile_traffic(kind, n):
         d = json.load(f)
     e = d.get(kind)
     if not e:
+        return None
+    # counters describe the kernel as it was compiled then: null once its source changed
+    import hashlib
+
+    src = b"".join(open(os.path.join(ROOT, "paper_2404_11894_gb300", "csrc", f), "rb").read()
+                   for f in ("pg_propagate.cu", "pg_internal.cuh"))
+    if hashlib.sha256(src).hexdigest() != e.get("source_sha256"):
         return None
     return e["dram_bytes_per_launch"] * (n / e["vertices"]) if e.get("scale_with_n") else e["dram_bytes_per_launch"]
 
