@@ -6,5 +6,5 @@ shares no code with the CUDA library.
 """
 from .pathgraph import (  # noqa: F401
     adjoint, aggregate, dense_fixed_point, forward, gather, hg, hg_dg, image_loss,
-    knn, knn_brute, path_values, propagate, quantize, sweep, vertex_arrays,
+    knn, knn_brute, path_values, propagate, quantize, sample_marginals, sweep, vertex_arrays,
 )

@@ -18,12 +18,19 @@ notes):
     k-1 nearest others by squared integer distance, ties by smaller index) on
     21-bit quantised coordinates; the paper's clusters (Section 3.1) are the
     special case where every point's neighbourhood is its cluster;
-  * the marginal density of a sample (Eq. indirect-weight) is taken over the
-    receiver's own neighbourhood;
+  * the marginal density of a sample j (Eq. indirect-weight) is taken over the
+    points that use j, R(j) = {s : j in N(s)}: with clusters every member's
+    neighbourhood is the cluster, so R(j) is the cluster, and this is the
+    reading that keeps, for any neighbour graph, the identity that a sample's
+    MIS weights over the points aggregating it sum to one (which bounds the
+    column sums of P A+ by the albedo, so the iteration contracts);
   * the "K p_E(omega_j)" inside the direct marginal (Eq. ag-direct, the
     definition of p_m after it) is read as K p_e of the same direction;
   * a delta-light emitter sample cannot be produced by phase sampling, so its
-    balance-heuristic weight reduces to an average over the K emitter samples;
+    balance-heuristic weight reduces to an average over the receiver's K
+    emitter samples (K = |N(s)|); in the continuous-emitter and phase-sample
+    marginals of Eq. ag-direct, K is |R(j)|, the number of emitter samples
+    combined with the phase strategies of R(j);
   * Jacobi iteration (double-buffered), starting from the path tracer's
     estimate (Section 4, "Path graph solver"); sweep t=1 is the first
     aggregation + propagation;
@@ -187,26 +194,59 @@ def vertex_arrays(V):
 # --------------------------------------------------------------------------
 # Aggregation (Section 3.5)
 # --------------------------------------------------------------------------
-def aggregate(V, nbr, chunk=8192, sigma_s=None, g=None, rows=None):
-    """Aggregation weights of every row s with neighbourhood N(s) = nbr[s].
+def sample_marginals(V, nbr, cols=None, g=None, chunk=1 << 22):
+    """Marginal densities of every sample j over the points that use it.
 
-    With ``rows``, nbr[i] is the neighbourhood of vertex rows[i] and the
-    outputs are for those vertices only (sampled rows of a large graph).
+    R(j) = {r : j in N(r)}; K_j = |R(j)|;
+      pm_d[j] = sum_{r in R(j)} rho_r(o_r, d_j)   (phase sample of j)
+      pm_e[j] = sum_{r in R(j)} rho_r(o_r, e_j)   (emitter sample of j)
+    (Eq. indirect-weight's p_m, and the phase part of Eq. ag-direct's).
+    With ``cols`` only those samples' marginals are formed (the others are
+    zero). Parity: pinned by the MIS column sums (each sample's weights over
+    R(j) sum to one) and by the isotropic closed form.
+    """
+    X = vertex_arrays(V)
+    if g is not None:
+        X["g"] = np.asarray(g, np.float64)
+    n = len(X["g"])
+    mask = nbr >= 0
+    if cols is not None:
+        want = np.zeros(n, bool)
+        want[np.asarray(cols, np.int64)] = True
+        mask &= want[np.where(mask, nbr, 0)]
+    r_idx, i_idx = np.nonzero(mask)
+    pm_d = np.zeros(n)
+    pm_e = np.zeros(n)
+    K = np.zeros(n)
+    for a in range(0, len(r_idx), chunk):
+        r = r_idx[a:a + chunk]
+        j = nbr[r, i_idx[a:a + chunk]].astype(np.int64)
+        pm_d += np.bincount(j, weights=hg(X["o"][r], X["d"][j], X["g"][r]), minlength=n)
+        pm_e += np.bincount(j, weights=hg(X["o"][r], X["e"][j], X["g"][r]), minlength=n)
+        K += np.bincount(j, minlength=n)
+    return pm_d, pm_e, K
 
-    Returns a dict (all float64, caller order):
-      A   (n,k): A+_{s,j} = sigma_s(s) rho_s(o_s, d_j) / p_m(d_j),
-                 p_m(d_j) = sum_{l in N(s)} rho_l(o_l, d_j)
-                 (Eq. ag-indirect with the marginal of Eq. indirect-weight)
-      Ae  (n,k): A°_{s,2j}: emitter sample of j (Eq. ag-direct, first sum),
-                 sigma_s rho_s(o_s,e_j) / (sum_l rho_l(o_l,e_j) + K pe_e_j), or
-                 sigma_s rho_s(o_s,e_j) / K for a delta light
-      Aph (n,k): A°_{s,2j+1}: phase sample of j (Eq. ag-direct, second sum),
-                 sigma_s rho_s(o_s,d_j) / (sum_l rho_l(o_l,d_j) + K pe_ph_j)
-      c   (n):   (A°L°)_s = sum_j Ae_{s,j} Le_j + Aph_{s,j} Lph_j
-      D   (n):   the same with N(s) = {s} (non-aggregated direct, Section 4)
-      K   (n):   |N(s)|
+
+def aggregate(V, nbr, sigma_s=None, g=None, rows=None, marginals=None):
+    """Aggregation weights of the rows s (all, or ``rows``) of the neighbour
+    table ``nbr`` (all n rows: the marginals need every point that uses a
+    sample).
+
+    Returns a dict (all float64; rows in the order of ``rows``, else caller
+    order):
+      A   (m,k): A+_{s,j} = sigma_s(s) rho_s(o_s, d_j) / pm_d[j]
+                 (Eq. ag-indirect, marginal of Eq. indirect-weight over R(j))
+      Ae  (m,k): A°_{s,2j}: emitter sample of j (Eq. ag-direct, first sum),
+                 sigma_s rho_s(o_s,e_j) / (pm_e[j] + K_j pe_e_j), or
+                 sigma_s rho_s(o_s,e_j) / |N(s)| for a delta light
+      Aph (m,k): A°_{s,2j+1}: phase sample of j (Eq. ag-direct, second sum),
+                 sigma_s rho_s(o_s,d_j) / (pm_d[j] + K_j pe_ph_j)
+      c   (m):   (A°L°)_s = sum_j Ae_{s,j} Le_j + Aph_{s,j} Lph_j
+      D   (m):   the same with N(s) = {s} (non-aggregated direct, Section 4)
+      pm_d, pm_e, Kj (n): the marginals of :func:`sample_marginals`
     Entries for missing neighbours (-1) are 0. ``sigma_s``/``g`` override the
-    recorded per-vertex values (used by finite differences).
+    recorded per-vertex values (used by finite differences); ``marginals``
+    passes (pm_d, pm_e, Kj) already formed by :func:`sample_marginals`.
     Parity: pinned by the MIS column sums (Eq. indirect-weight), the isotropic
     closed form, and the K=1 reduction to the path tracer.
     """
@@ -215,44 +255,33 @@ def aggregate(V, nbr, chunk=8192, sigma_s=None, g=None, rows=None):
         X["sigma_s"] = np.asarray(sigma_s, np.float64)
     if g is not None:
         X["g"] = np.asarray(g, np.float64)
-    n, k = nbr.shape
-    recv = np.arange(n) if rows is None else np.asarray(rows, np.int64)
-    out = {name: np.zeros((n, k)) for name in ("A", "Ae", "Aph")}
-    out["c"] = np.zeros(n)
-    out["K"] = (nbr >= 0).sum(axis=1)
-    for a in range(0, n, chunk):
-        b = min(n, a + chunk)
-        nb = nbr[a:b]
-        valid = nb >= 0
-        j = np.where(valid, nb, 0)
-        K = valid.sum(axis=1).astype(np.float64)
-        o_l, g_l = X["o"][j], X["g"][j]              # (m,k,3), (m,k): strategies l
-        d_j, e_j = X["d"][j], X["e"][j]               # (m,k,3): samples j
-        s_idx = recv[a:b]
-        o_s, g_s, sig_s = X["o"][s_idx], X["g"][s_idx], X["sigma_s"][s_idx]
-        # rho_l(o_l, d_j) for all l (axis 1) and j (axis 2)
-        rho_ld = hg(o_l[:, :, None, :], d_j[:, None, :, :], g_l[:, :, None])
-        rho_le = hg(o_l[:, :, None, :], e_j[:, None, :, :], g_l[:, :, None])
-        vl = valid[:, :, None]
-        pm_d = np.where(vl, rho_ld, 0.0).sum(axis=1)  # sum over l -> (m,k)
-        pm_e = np.where(vl, rho_le, 0.0).sum(axis=1)
-        rho_sd = hg(o_s[:, None, :], d_j, g_s[:, None])
-        rho_se = hg(o_s[:, None, :], e_j, g_s[:, None])
-        A = sig_s[:, None] * rho_sd / pm_d
-        delta = X["delta"][j]
-        Ae_cont = sig_s[:, None] * rho_se / (pm_e + K[:, None] * X["pe_e"][j])
-        Ae_delta = sig_s[:, None] * rho_se / K[:, None]
-        Ae = np.where(delta, Ae_delta, Ae_cont)
-        Aph = sig_s[:, None] * rho_sd / (pm_d + K[:, None] * X["pe_ph"][j])
-        A, Ae, Aph = (np.where(valid, M, 0.0) for M in (A, Ae, Aph))
-        out["A"][a:b], out["Ae"][a:b], out["Aph"][a:b] = A, Ae, Aph
-        out["c"][a:b] = (Ae * X["Le"][j] + Aph * X["Lph"][j]).sum(axis=1)
+    recv = np.arange(len(nbr)) if rows is None else np.asarray(rows, np.int64)
+    nb = nbr[recv]
+    valid = nb >= 0
+    j = np.where(valid, nb, 0)
+    if marginals is None:
+        marginals = sample_marginals(V, nbr, cols=None if rows is None else np.unique(j[valid]), g=g)
+    pm_d, pm_e, Kj = marginals
+    Ks = valid.sum(axis=1).astype(np.float64)[:, None]
+    o_s, g_s, sig_s = X["o"][recv], X["g"][recv], X["sigma_s"][recv]
+    rho_sd = hg(o_s[:, None, :], X["d"][j], g_s[:, None])
+    rho_se = hg(o_s[:, None, :], X["e"][j], g_s[:, None])
+    pd, pe, K = pm_d[j], pm_e[j], Kj[j]
+    safe = lambda x: np.where(valid, x, 1.0)  # noqa: E731
+    A = sig_s[:, None] * rho_sd / safe(pd)
+    Ae_cont = sig_s[:, None] * rho_se / safe(pe + K * X["pe_e"][j])
+    Ae_delta = sig_s[:, None] * rho_se / Ks
+    Ae = np.where(X["delta"][j], Ae_delta, Ae_cont)
+    Aph = sig_s[:, None] * rho_sd / safe(pd + K * X["pe_ph"][j])
+    A, Ae, Aph = (np.where(valid, M, 0.0) for M in (A, Ae, Aph))
+    out = dict(A=A, Ae=Ae, Aph=Aph, pm_d=pm_d, pm_e=pm_e, Kj=Kj, K=Ks[:, 0])
+    out["c"] = (Ae * X["Le"][j] + Aph * X["Lph"][j]).sum(axis=1)
     # non-aggregated direct: K = 1, N(s) = {s}
     o, e, d, gg = X["o"][recv], X["e"][recv], X["d"][recv], X["g"][recv]
     rho_e = hg(o, e, gg)
     rho_d = hg(o, d, gg)
-    Le, pe, Lph, pph = X["Le"][recv], X["pe_e"][recv], X["Lph"][recv], X["pe_ph"][recv]
-    De = np.where(X["delta"][recv], rho_e * Le, rho_e * Le / (rho_e + pe))
+    Le, pe_, Lph, pph = X["Le"][recv], X["pe_e"][recv], X["Lph"][recv], X["pe_ph"][recv]
+    De = np.where(X["delta"][recv], rho_e * Le, rho_e * Le / (rho_e + pe_))
     Dp = rho_d * Lph / (rho_d + pph)
     out["D"] = X["sigma_s"][recv] * (De + Dp)
     return out
@@ -417,55 +446,62 @@ def adjoint(V, nbr, iters, L0, dI, first, bg, spp, width, height, voxel=None, n_
         lam_prev = np.zeros(n)
         np.add.at(lam_prev, j_idx[valid], (mu[:, None] * A)[valid])
         lam = lam_prev
-    # explicit derivatives of the aggregation formulas
+    # explicit derivatives of the aggregation formulas, per entry (s, j) with
+    # j in N(s) (equivalently s in R(j)):
+    #   A_sj  = sig_s rho_s(d_j) / pm_d[j]
+    #   Ae_sj = sig_s rho_s(e_j) / me[j]  (delta: / |N(s)|),  me  = pm_e + K_j pe_e
+    #   Aph_sj = sig_s rho_s(d_j) / mph[j],                    mph = pm_d + K_j pe_ph
+    # g_s enters the numerators rho_s(o_s, .) of row s and, through
+    # pm_d[j] and pm_e[j], the weights of every receiver of each j in N(s).
     grad_sig = np.zeros(n)
     grad_g = np.zeros(n)
     sig = X["sigma_s"]
+    pm_d, pm_e, Kj = agg["pm_d"], agg["pm_e"], agg["Kj"]
+    gpm_d = np.zeros(n)   # dLoss/dpm_d[j]
+    gpm_e = np.zeros(n)   # dLoss/dpm_e[j]
+    parts = []
     for a in range(0, n, chunk):
         b = min(n, a + chunk)
         nb = nbr[a:b]
         vm = nb >= 0
         j = np.where(vm, nb, 0)
-        K = vm.sum(axis=1).astype(np.float64)[:, None]
+        Ks = vm.sum(axis=1).astype(np.float64)[:, None]
         s_idx = np.arange(a, b)
-        o_l, g_l = X["o"][j], X["g"][j]
-        d_j, e_j = X["d"][j], X["e"][j]
         o_s, g_s = X["o"][s_idx], X["g"][s_idx]
         sg = sig[s_idx][:, None]
-        rho_ld = hg(o_l[:, :, None, :], d_j[:, None, :, :], g_l[:, :, None])
-        rho_le = hg(o_l[:, :, None, :], e_j[:, None, :, :], g_l[:, :, None])
-        drho_ld = hg_dg(o_l[:, :, None, :], d_j[:, None, :, :], g_l[:, :, None])
-        drho_le = hg_dg(o_l[:, :, None, :], e_j[:, None, :, :], g_l[:, :, None])
-        vl = vm[:, :, None]
-        rho_ld, rho_le = np.where(vl, rho_ld, 0.0), np.where(vl, rho_le, 0.0)
-        drho_ld, drho_le = np.where(vl, drho_ld, 0.0), np.where(vl, drho_le, 0.0)
-        pm_d, pm_e = rho_ld.sum(axis=1), rho_le.sum(axis=1)
+        d_j, e_j = X["d"][j], X["e"][j]
         rho_sd = hg(o_s[:, None, :], d_j, g_s[:, None])
         rho_se = hg(o_s[:, None, :], e_j, g_s[:, None])
-        drho_sd = hg_dg(o_s[:, None, :], d_j, g_s[:, None])
-        drho_se = hg_dg(o_s[:, None, :], e_j, g_s[:, None])
+        pd, pe, K = np.where(vm, pm_d[j], 1.0), np.where(vm, pm_e[j], 1.0), Kj[j]
         delta = X["delta"][j]
         Le, Lph = X["Le"][j], X["Lph"][j]
-        me = pm_e + K * X["pe_e"][j]
-        mph = pm_d + K * X["pe_ph"][j]
+        me = np.where(vm, pe + K * X["pe_e"][j], 1.0)
+        mph = np.where(vm, pd + K * X["pe_ph"][j], 1.0)
         gAc, gcc = gA[a:b], gc[a:b][:, None]
         # d/dsigma_s(s): every weight of row s is sigma_s(s) times a factor
-        fA = np.where(vm, rho_sd / pm_d, 0.0)
-        fe = np.where(vm, np.where(delta, rho_se / K, rho_se / me), 0.0)
+        fA = np.where(vm, rho_sd / pd, 0.0)
+        fe = np.where(vm, np.where(delta, rho_se / Ks, rho_se / me), 0.0)
         fph = np.where(vm, rho_sd / mph, 0.0)
         grad_sig[a:b] += (gAc * fA).sum(axis=1) + gcc[:, 0] * (fe * Le + fph * Lph).sum(axis=1)
-        # d/dg_l through the marginals (l ranges over N(s), axis 1)
-        # A_sj = sg rho_sd / pm_d -> dA/dg_l = -sg rho_sd drho_ld[l,j] / pm_d^2
-        coefA = np.where(vm, -sg * rho_sd / pm_d ** 2, 0.0) * gAc                        # (m,j)
-        coefE = np.where(vm & ~delta, -sg * rho_se * Le / me ** 2, 0.0) * gcc           # (m,j)
-        coefP = np.where(vm, -sg * rho_sd * Lph / mph ** 2, 0.0) * gcc
-        g_l_contrib = (drho_ld * (coefA + coefP)[:, None, :]).sum(axis=2) + (drho_le * coefE[:, None, :]).sum(axis=2)
-        np.add.at(grad_g, j[vm], g_l_contrib[vm])
-        # d/dg_s through the numerators rho_s(o_s, .)
-        numA = np.where(vm, sg * drho_sd / pm_d, 0.0) * gAc
-        numE = np.where(vm, np.where(delta, sg * drho_se * Le / K, sg * drho_se * Le / me), 0.0) * gcc
-        numP = np.where(vm, sg * drho_sd * Lph / mph, 0.0) * gcc
-        grad_g[a:b] += (numA + numE + numP).sum(axis=1)
+        # adjoints of the marginals of the samples j (summed over receivers s)
+        cd = np.where(vm, -sg * rho_sd * (gAc / pd ** 2 + gcc * Lph / mph ** 2), 0.0)
+        ce = np.where(vm & ~delta, -sg * rho_se * gcc * Le / me ** 2, 0.0)
+        np.add.at(gpm_d, j[vm], cd[vm])
+        np.add.at(gpm_e, j[vm], ce[vm])
+        # numerator factors of drho_s(o_s, d_j)/dg_s and drho_s(o_s, e_j)/dg_s
+        nd = np.where(vm, sg * (gAc / pd + gcc * Lph / mph), 0.0)
+        ne = np.where(vm, sg * gcc * Le * np.where(delta, 1.0 / Ks, 1.0 / me), 0.0)
+        parts.append((a, b, nd, ne))
+    for a, b, nd, ne in parts:
+        nb = nbr[a:b]
+        vm = nb >= 0
+        j = np.where(vm, nb, 0)
+        s_idx = np.arange(a, b)
+        o_s, g_s = X["o"][s_idx], X["g"][s_idx]
+        drho_sd = hg_dg(o_s[:, None, :], X["d"][j], g_s[:, None])
+        drho_se = hg_dg(o_s[:, None, :], X["e"][j], g_s[:, None])
+        tot = drho_sd * (nd + np.where(vm, gpm_d[j], 0.0)) + drho_se * (ne + np.where(vm, gpm_e[j], 0.0))
+        grad_g[a:b] += np.where(vm, tot, 0.0).sum(axis=1)
     # D_s = sigma_s (De + Dp) with K = 1
     rho_e = hg(X["o"], X["e"], X["g"])
     rho_d = hg(X["o"], X["d"], X["g"])

@@ -11,7 +11,8 @@ import oracle
 import oracle.pathgraph as opg
 import pgrec
 
-from test_oracle_pins import SMALL_SCENES, _cluster_graph, test_hg_forward_convention
+from test_oracle_pins import (SMALL_SCENES, _cluster_graph, test_hg_forward_convention,
+                              test_mis_weights_sum_to_one_on_knn_graphs)
 
 
 def _k1_image(scene):
@@ -78,3 +79,27 @@ def test_transposed_numerator_is_caught():
         pm = opg.hg(X["o"][js][:, None, :], X["d"][js][None, :, :], X["g"][js][:, None]).sum(axis=0)
         bad[s] = opg.hg(X["o"][js], X["d"][js], X["g"][js]) / pm  # rho_j(o_j, d_j): wrong operand
     assert not np.allclose(col_sums(bad), 1.0, rtol=1e-6)
+
+
+def test_receiver_neighbourhood_marginal_is_caught(monkeypatch):
+    """Taking sample j's marginal over the receiver's own neighbourhood N(s)
+    (the same thing on clusters) breaks the per-sample MIS sums on a kNN graph."""
+    good = opg.aggregate
+
+    def bad_aggregate(V, nbr, sigma_s=None, g=None, rows=None, marginals=None):
+        out = good(V, nbr, sigma_s=sigma_s, g=g, rows=rows, marginals=marginals)
+        X = opg.vertex_arrays(V)
+        recv = np.arange(len(nbr)) if rows is None else np.asarray(rows)
+        nb = nbr[recv]
+        valid = nb >= 0
+        j = np.where(valid, nb, 0)
+        rho_ld = opg.hg(X["o"][j][:, :, None, :], X["d"][j][:, None, :, :], X["g"][j][:, :, None])
+        pm = np.where(valid[:, :, None], rho_ld, 0.0).sum(axis=1)
+        rho_sd = opg.hg(X["o"][recv][:, None, :], X["d"][j], X["g"][recv][:, None])
+        out["A"] = np.where(valid, X["sigma_s"][recv][:, None] * rho_sd / pm, 0.0)
+        return out
+
+    monkeypatch.setattr(opg, "aggregate", bad_aggregate)
+    monkeypatch.setattr(oracle, "aggregate", bad_aggregate)
+    with pytest.raises(AssertionError):
+        test_mis_weights_sum_to_one_on_knn_graphs()

@@ -148,6 +148,77 @@ def test_mis_weights_sum_to_one():
             np.testing.assert_allclose(list(col.values()), 1.0, rtol=1e-13)
 
 
+def _knn_records(n=900, seed=12, k=8):
+    """Random records on a kNN graph (neighbourhoods overlap and differ), with
+    every emitter sample continuous and no emitter pdf mass, so the MIS sums
+    of the direct weights reduce to the phase strategies alone."""
+    V = synthetic.random_records(n, seed=seed)
+    V["e_delta"] = np.zeros(n, np.uint8)
+    V["pe_e"] = np.zeros(n, np.float32)
+    V["pe_ph"] = np.zeros(n, np.float32)
+    q = oracle.quantize(V["px"], V["py"], V["pz"], (0, 0, 0), (1, 1, 1))
+    return V, oracle.knn(q, k)
+
+
+def knn_column_sums(M, nbr):
+    """sum over the rows s that use sample j of M[s, slot of j]; and R(j)'s size."""
+    valid = nbr >= 0
+    n = nbr.shape[0]
+    return (np.bincount(nbr[valid], weights=M[valid], minlength=n),
+            np.bincount(nbr[valid], minlength=n))
+
+
+def test_mis_weights_sum_to_one_on_knn_graphs():
+    """Eq. indirect-weight on a neighbour graph that is not a set of clusters:
+    sample j's balance-heuristic weights over the points that aggregate it
+    (R(j), whose strategies form j's marginal) sum to one, so every column of
+    A+ / sigma_s sums to exactly 1 and P A+ cannot grow a vector."""
+    V, nbr = _knn_records()
+    agg = oracle.aggregate(V, nbr)
+    sig = V["sigma_s"].astype(np.float64)
+    for name in ("A", "Ae", "Aph"):
+        col, indeg = knn_column_sums(agg[name] / sig[:, None], nbr)
+        assert indeg.min() >= 1 and indeg.max() > indeg.min()  # R(j) sizes differ
+        np.testing.assert_allclose(col, 1.0, rtol=1e-13)
+    # the column sums of P A+ (row v, sample j: w_succ(v) A+_{succ(v), j}) are
+    # at most the largest albedo sigma_s / sigma_t
+    X = oracle.vertex_arrays(V)
+    a = X["sigma_s"] * X["w"]
+    colP, _ = knn_column_sums(a[:, None] * agg["A"] / sig[:, None], nbr)
+    assert colP.max() <= a.max() * (1 + 1e-13)
+
+
+def test_weights_isotropic_closed_form_on_knn_graphs():
+    """Isotropic rho = 1/(4 pi) on a kNN graph: A+_{s,j} = sigma_s / |R(j)|,
+    Aph_{s,j} = sigma_s / (|R(j)| (1 + 4 pi pe_ph_j)), and a delta light's
+    Ae_{s,j} = sigma_s / (4 pi |N(s)|)."""
+    V, nbr = _knn_records(seed=13)
+    V["g"] = np.zeros_like(V["g"])
+    V["pe_ph"] = np.full_like(V["pe_ph"], 0.03)
+    V["e_delta"] = np.ones_like(V["e_delta"])
+    agg = oracle.aggregate(V, nbr)
+    sig = V["sigma_s"].astype(np.float64)[:, None]
+    _, indeg = knn_column_sums(np.ones(nbr.shape), nbr)
+    Rj = indeg[nbr].astype(np.float64)
+    pph = np.float64(np.float32(0.03))
+    np.testing.assert_allclose(agg["A"], sig / Rj, rtol=1e-13)
+    np.testing.assert_allclose(agg["Aph"], sig / (Rj * (1 + 4 * np.pi * pph)), rtol=1e-13)
+    np.testing.assert_allclose(agg["Ae"], np.broadcast_to(sig / (4 * np.pi * nbr.shape[1]), nbr.shape), rtol=1e-13)
+
+
+def test_sampled_rows_match_all_rows():
+    """aggregate(rows=...) forms the same weights as the whole table (the
+    marginals of a sampled row's samples still span every receiver)."""
+    V, nbr = _knn_records(seed=14)
+    full = oracle.aggregate(V, nbr)
+    rows = np.array([0, 5, 17, 400, 899])
+    part = oracle.aggregate(V, nbr, rows=rows)
+    for name in ("A", "Ae", "Aph"):
+        np.testing.assert_allclose(part[name], full[name][rows], rtol=1e-15)
+    np.testing.assert_allclose(part["c"], full["c"][rows], rtol=1e-15)
+    np.testing.assert_allclose(part["D"], full["D"][rows], rtol=1e-15)
+
+
 def test_direct_weights_isotropic_closed_form():
     """Eq. ag-direct with isotropic rho = 1/(4 pi): the emitter sample's weight
     is sigma_s / (4 pi (K/(4 pi) + K pe)); a delta light's is sigma_s/(4 pi K)."""
