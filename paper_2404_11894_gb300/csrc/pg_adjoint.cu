@@ -340,70 +340,42 @@ __global__ void __launch_bounds__(256) scatter_sweep_kernel(
 
 // ------------------------------------------------------------------ recompute mode
 // Row s (Morton m) re-evaluates its weights W~[s][j] = w_s sigma_s rho_s(o_s,d_j)
-// / sum_l rho_l(o_l,d_j) and scatters u[r] W~ into out[col] with atomics.
-// Also accumulates G/B (y_t given) for rows with u != 0.
+// / pm_d[j] from the vertex records and the stored sample marginals, and
+// scatters u[r] W~ into out[col] with atomics. Also accumulates G/B (y_t
+// given) for the rows.
+__device__ __forceinline__ float recompute_weight(const float4 &os, const float4 &dp, float w_s, float sig_s,
+                                                  float pm_d) {
+    const HGc hs = hg_consts(os.w);
+    const float rho = hg_eval(hs, one_plus_dot_u(os.x, os.y, os.z, unit_err(os.x, os.y, os.z), dp.x, dp.y, dp.z,
+                                                  unit_err(dp.x, dp.y, dp.z)));
+    return w_s * (sig_s * rho / pm_d);
+}
+
 template <int KP>
 __global__ void __launch_bounds__(256) recompute_scatter_kernel(
     const int32_t *__restrict__ nbr, const float4 *__restrict__ OG, const float4 *__restrict__ DP,
-    const float4 *__restrict__ LV, const int32_t *__restrict__ succ_m, const int32_t *__restrict__ m2r,
-    const int32_t *__restrict__ r2m, int64_t r0, int64_t r1, int64_t n, const float *__restrict__ u,
-    const float *__restrict__ y_t, const float *__restrict__ y_prev, int write_out, float *__restrict__ out,
-    float *__restrict__ G, float *__restrict__ B, float *__restrict__ unused) {
-    (void)y_prev;
-    (void)unused;
-    __shared__ float4 s_o[256];
-    __shared__ float2 s_ab[256];
-    __shared__ float s_eo[256];
+    const float4 *__restrict__ LV, const int32_t *__restrict__ succ_m, const unsigned long long *__restrict__ pmd,
+    const int32_t *__restrict__ m2r, const int32_t *__restrict__ r2m, int64_t r0, int64_t r1,
+    const float *__restrict__ u, const float *__restrict__ y_t, int write_out, float *__restrict__ out,
+    float *__restrict__ G, float *__restrict__ B) {
     const int lane = threadIdx.x & 31;
     const int j = lane & (KP - 1);
-    const int gbase = threadIdx.x - j;
     const int64_t r = r0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / KP;
-    const bool row_ok = r < r1;
-    const int32_t m = row_ok ? r2m[r] : 0;
-    const float ur = row_ok ? u[r] : 0.0f;
-    const bool live_row = row_ok && ur != 0.0f;
-    int32_t nj = row_ok ? nbr[(int64_t)m * KP + j] : -1;
-    const bool valid = nj >= 0;
-    float4 og = make_float4(0.f, 0.f, 1.f, 0.f), dp = make_float4(0.f, 0.f, 1.f, 0.f);
-    int32_t sj = -1;
-    if (valid) {
-        og = OG[nj];
-        dp = DP[nj];
-        sj = succ_m[nj];
-    }
-    HGc hc = hg_consts(og.w);
-    s_o[threadIdx.x] = make_float4(og.x, og.y, og.z, valid ? hc.C : 0.0f);
-    s_ab[threadIdx.x] = make_float2(valid ? hc.a : 1.0f, valid ? hc.b2 : 0.0f);
-    s_eo[threadIdx.x] = unit_err(og.x, og.y, og.z);
-    const float ed = unit_err(dp.x, dp.y, dp.z);
-    __syncwarp();
-    if (__any_sync(0xffffffffu, live_row)) {
-        float pm_d = 0.0f;
-#pragma unroll 4
-        for (int l = 0; l < KP; l++) {
-            float4 so = s_o[gbase + l];
-            float2 ab = s_ab[gbase + l];
-            HGc h;
-            h.C = so.w;
-            h.a = ab.x;
-            h.b2 = ab.y;
-            pm_d += hg_eval(h, one_plus_dot_u(so.x, so.y, so.z, s_eo[gbase + l], dp.x, dp.y, dp.z, ed));
-        }
-        const float4 so = s_o[gbase];
-        const float2 sab = s_ab[gbase];
-        HGc hs;
-        hs.C = so.w;
-        hs.a = sab.x;
-        hs.b2 = sab.y;
-        const float4 lvs = LV[m];
-        float rho_sd = hg_eval(hs, one_plus_dot_u(so.x, so.y, so.z, s_eo[gbase], dp.x, dp.y, dp.z, ed));
-        if (live_row && valid && sj >= 0) {
-            int32_t cl = m2r[sj];
-            float Wt = lvs.w * (lvs.z * rho_sd / pm_d);
-            if (write_out) atomicAdd(out + cl, ur * Wt);
+    if (r >= r1) return; // whole groups leave together (r is uniform over a group)
+    const int32_t m = r2m[r];
+    const float ur = u[r];
+    if (write_out && ur != 0.0f) {
+        const int32_t nj = nbr[(int64_t)m * KP + j];
+        if (nj >= 0) {
+            const int32_t sj = succ_m[nj];
+            if (sj >= 0) {
+                const float4 lvs = LV[m];
+                const float Wt = recompute_weight(OG[m], DP[nj], lvs.w, lvs.z, pg_pm_float(pmd[nj]));
+                atomicAdd(out + m2r[sj], ur * Wt);
+            }
         }
     }
-    if (row_ok && j == 0 && y_t) {
+    if (j == 0 && y_t) {
         G[r] = fmaf(ur, y_t[r], G[r]);
         if (B) B[r] += ur;
     }
@@ -413,58 +385,24 @@ __global__ void __launch_bounds__(256) recompute_scatter_kernel(
 template <int KP>
 __global__ void __launch_bounds__(256) recompute_first_kernel(
     const int32_t *__restrict__ nbr, const float4 *__restrict__ OG, const float4 *__restrict__ DP,
-    const float4 *__restrict__ LV, const int32_t *__restrict__ succ_m, const int32_t *__restrict__ m2r,
-    const int32_t *__restrict__ r2m, int64_t r0, int64_t r1, const float *__restrict__ nu,
-    const float *__restrict__ yT, const float *__restrict__ D_m, float *__restrict__ G) {
-    __shared__ float4 s_o[256];
-    __shared__ float2 s_ab[256];
-    __shared__ float s_eo[256];
+    const float4 *__restrict__ LV, const int32_t *__restrict__ succ_m, const unsigned long long *__restrict__ pmd,
+    const int32_t *__restrict__ m2r, const int32_t *__restrict__ r2m, int64_t r0, int64_t r1,
+    const float *__restrict__ nu, const float *__restrict__ yT, const float *__restrict__ D_m,
+    float *__restrict__ G) {
     const int lane = threadIdx.x & 31;
     const int j = lane & (KP - 1);
-    const int gbase = threadIdx.x - j;
-    const int src = lane & ~(KP - 1);
     const int64_t r = r0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / KP;
     const bool row_ok = r < r1;
     const int32_t m = row_ok ? r2m[r] : 0;
-    int32_t nj = row_ok ? nbr[(int64_t)m * KP + j] : -1;
-    const bool valid = nj >= 0;
-    float4 og = make_float4(0.f, 0.f, 1.f, 0.f), dp = make_float4(0.f, 0.f, 1.f, 0.f);
-    int32_t sj = -1;
-    if (valid) {
-        og = OG[nj];
-        dp = DP[nj];
-        sj = succ_m[nj];
-    }
-    HGc hc = hg_consts(og.w);
-    s_o[threadIdx.x] = make_float4(og.x, og.y, og.z, valid ? hc.C : 0.0f);
-    s_ab[threadIdx.x] = make_float2(valid ? hc.a : 1.0f, valid ? hc.b2 : 0.0f);
-    s_eo[threadIdx.x] = unit_err(og.x, og.y, og.z);
-    const float ed = unit_err(dp.x, dp.y, dp.z);
-    __syncwarp();
-    float pm_d = 0.0f;
-#pragma unroll 4
-    for (int l = 0; l < KP; l++) {
-        float4 so = s_o[gbase + l];
-        float2 ab = s_ab[gbase + l];
-        HGc h;
-        h.C = so.w;
-        h.a = ab.x;
-        h.b2 = ab.y;
-        pm_d += hg_eval(h, one_plus_dot_u(so.x, so.y, so.z, s_eo[gbase + l], dp.x, dp.y, dp.z, ed));
-    }
-    const float4 so = s_o[gbase];
-    const float2 sab = s_ab[gbase];
-    HGc hs;
-    hs.C = so.w;
-    hs.a = sab.x;
-    hs.b2 = sab.y;
+    const int32_t nj = row_ok ? nbr[(int64_t)m * KP + j] : -1;
     const float4 lvs = row_ok ? LV[m] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float rho_sd = hg_eval(hs, one_plus_dot_u(so.x, so.y, so.z, s_eo[gbase], dp.x, dp.y, dp.z, ed));
     float term = 0.0f;
-    if (row_ok && valid && sj >= 0) term = lvs.w * (lvs.z * rho_sd / pm_d) * yT[m2r[sj]];
+    if (nj >= 0) {
+        const int32_t sj = succ_m[nj];
+        if (sj >= 0) term = recompute_weight(OG[m], DP[nj], lvs.w, lvs.z, pg_pm_float(pmd[nj])) * yT[m2r[sj]];
+    }
 #pragma unroll
     for (int o = KP / 2; o > 0; o >>= 1) term += __shfl_xor_sync(0xffffffffu, term, o);
-    (void)src;
     if (row_ok && j == 0) G[r] += nu[r] * (term + lvs.w * D_m[m]);
 }
 
@@ -485,124 +423,106 @@ __global__ void grad_sigma_kernel(const float *__restrict__ G, const int32_t *__
     }
 }
 
-// d/dg of every weight of row s (Morton m) given the edge adjoints
-// Gamma (dLoss/dW~), beta (dLoss/db) and nu (dLoss/d(w D)); contributions to
-// g_l of every l in N(s) are added atomically into gg (Morton order).
+// d/dg through the aggregation, given the edge adjoints Gamma (dLoss/dW~),
+// beta (dLoss/db) and nu (dLoss/d(w D)). Per entry (s, j), j in N(s):
+//   A_sj = sig_s rho_s(d_j)/pm_d[j], Ae_sj = sig_s rho_s(e_j)/me[j] (delta:
+//   /|N(s)|), Aph_sj = sig_s rho_s(d_j)/mph[j], me = pm_e + K_j pe_e,
+//   mph = pm_d + K_j pe_ph, and pm_d[j] = sum over the rows r using j of
+//   rho_r(o_r, d_j) (pm_e likewise), so g_s enters row s's numerators and the
+//   marginals of every sample s uses. Pass 1 forms each entry's numerator
+//   factors and adds its share of dLoss/dpm_d[j], dLoss/dpm_e[j] (atomics);
+//   pass 2 takes drho_s/dg_s times (numerator factor + marginal adjoint) over
+//   the row's entries, plus the non-aggregated direct term.
 template <int KP>
-__global__ void __launch_bounds__(256) grad_g_kernel(
+__global__ void __launch_bounds__(256) grad_g_marg_kernel(
     const int32_t *__restrict__ nbr, const float4 *__restrict__ OG, const float4 *__restrict__ DP,
     const float4 *__restrict__ EP, const float4 *__restrict__ LV, const int32_t *__restrict__ m2r, int64_t n,
     int64_t n_active, const int32_t *__restrict__ col, const float *__restrict__ yhist,
     const float *__restrict__ muhist, int T, const float *__restrict__ B, const float *__restrict__ nu,
-    float *__restrict__ gg) {
-    __shared__ float4 s_o[256];   // (o_l, g_l)
-    __shared__ float4 s_d[256];   // (d_j, coefficient for rho'_l(o_l, d_j))
-    __shared__ float4 s_e[256];   // (e_j, coefficient for rho'_l(o_l, e_j))
-    __shared__ float s_eo[256];   // |o_l|^2 - 1
-    __shared__ float2 s_ede[256]; // (|d_j|^2 - 1, |e_j|^2 - 1)
+    const unsigned long long *__restrict__ pmd, const unsigned long long *__restrict__ pme,
+    const uint32_t *__restrict__ kin, float *__restrict__ gpm_d, float *__restrict__ gpm_e,
+    float2 *__restrict__ num) {
     const int lane = threadIdx.x & 31;
     const int j = lane & (KP - 1);
-    const int gbase = threadIdx.x - j;
     const int src = lane & ~(KP - 1);
     const int64_t m = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / KP;
     const bool row_ok = m < n;
-    int32_t nj = row_ok ? nbr[m * KP + j] : -1;
+    const int32_t nj = row_ok ? nbr[m * KP + j] : -1;
     const bool valid = nj >= 0;
-    float4 og = make_float4(0.f, 0.f, 1.f, 0.f), dp = make_float4(0.f, 0.f, 1.f, 0.f),
-           ep = make_float4(0.f, 0.f, 1.f, 0.f), lv = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (valid) {
-        og = OG[nj];
-        dp = DP[nj];
-        ep = EP[nj];
-        lv = LV[nj];
+    const unsigned gmask = (KP == 32) ? 0xffffffffu : (((1u << KP) - 1u) << src);
+    const float Ks = (float)__popc(__ballot_sync(0xffffffffu, valid) & gmask);
+    const float4 lvs = row_ok ? LV[m] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!valid) {
+        if (row_ok) num[m * KP + j] = make_float2(0.f, 0.f);
+        return;
     }
-    s_o[threadIdx.x] = og;
-    const float eo = unit_err(og.x, og.y, og.z), ed = unit_err(dp.x, dp.y, dp.z), ee = unit_err(ep.x, ep.y, ep.z);
-    s_eo[threadIdx.x] = eo;
-    s_ede[threadIdx.x] = make_float2(ed, ee);
-    __syncwarp();
-    const float K = (float)__popc(__ballot_sync(0xffffffffu, valid) &
-                                  ((KP == 32) ? 0xffffffffu : (((1u << KP) - 1u) << src)));
-    // marginals of this lane's samples
-    float pm_d = 0.0f, pm_e = 0.0f;
-#pragma unroll 4
-    for (int l = 0; l < KP; l++) {
-        float4 so = s_o[gbase + l];
-        bool lv_ok = __shfl_sync(0xffffffffu, valid, src + l);
-        if (lv_ok) {
-            HGc h = hg_consts(so.w);
-            const float el = s_eo[gbase + l];
-            pm_d += hg_eval(h, one_plus_dot_u(so.x, so.y, so.z, el, dp.x, dp.y, dp.z, ed));
-            pm_e += hg_eval(h, one_plus_dot_u(so.x, so.y, so.z, el, ep.x, ep.y, ep.z, ee));
-        }
-    }
-    const float4 os = s_o[gbase];
-    const float sig = __shfl_sync(0xffffffffu, lv.z, src);
-    const float w_s = __shfl_sync(0xffffffffu, lv.w, src);
-    const int64_t r = row_ok ? m2r[m] : 0;
+    const float4 os = OG[m], dp = DP[nj], ep = EP[nj], lv = LV[nj];
+    const float sig = lvs.z, w_s = lvs.w;
+    const int64_t r = m2r[m];
     // edge adjoint Gamma = dLoss/dW~ of this entry: sum over the sweeps that
     // used it (mu_t of the row times the iterate it multiplied), or the output
     // term nu y_T for a path's first vertex
     float Gam = 0.0f;
-    if (row_ok && valid) {
-        const int32_t cl = col[r * KP + j];
-        const int64_t stride = n + 1;
-        if (r < n_active) {
-            for (int t = 1; t <= T; t++) Gam = fmaf(muhist[t * stride + r], yhist[(t - 1) * stride + cl], Gam);
-        } else {
-            Gam = nu[r] * yhist[(int64_t)T * stride + cl];
-        }
+    const int32_t cl = col[r * KP + j];
+    const int64_t stride = n + 1;
+    if (r < n_active) {
+        for (int t = 1; t <= T; t++) Gam = fmaf(muhist[t * stride + r], yhist[(t - 1) * stride + cl], Gam);
+    } else {
+        Gam = nu[r] * yhist[(int64_t)T * stride + cl];
     }
-    // adjoints w.r.t. A+ (per entry), c and D of this row
-    const float gA = w_s * Gam;
-    const float gc = row_ok ? w_s * B[r] : 0.0f;
-    const float gD = row_ok ? w_s * nu[r] : 0.0f;
-    float drho_sd, drho_se, rho_sd, rho_se;
-    const float es = s_eo[gbase];
-    drho_sd = hg_eval_dg(os.w, one_plus_dot_u(os.x, os.y, os.z, es, dp.x, dp.y, dp.z, ed), &rho_sd);
-    drho_se = hg_eval_dg(os.w, one_plus_dot_u(os.x, os.y, os.z, es, ep.x, ep.y, ep.z, ee), &rho_se);
+    const float gA = w_s * Gam;      // dLoss/dA+ of this entry
+    const float gc = w_s * B[r];     // dLoss/dc of the row
+    const HGc hs = hg_consts(os.w);
+    const float es = unit_err(os.x, os.y, os.z);
+    const float rho_sd = hg_eval(hs, one_plus_dot_u(os.x, os.y, os.z, es, dp.x, dp.y, dp.z, unit_err(dp.x, dp.y, dp.z)));
+    const float rho_se = hg_eval(hs, one_plus_dot_u(os.x, os.y, os.z, es, ep.x, ep.y, ep.z, unit_err(ep.x, ep.y, ep.z)));
+    const float pm_d = pg_pm_float(pmd[nj]), pm_e = pg_pm_float(pme[nj]), kj = (float)kin[nj];
     const bool delta = ep.w < 0.0f;
-    const float me = pm_e + K * ep.w;
-    const float mph = pm_d + K * dp.w;
-    float cd = 0.0f, ce = 0.0f, num = 0.0f;
-    if (valid && row_ok) {
-        // marginal terms: coefficient of rho'_l(o_l, d_j) and rho'_l(o_l, e_j)
-        cd = -sig * rho_sd * (gA / (pm_d * pm_d) + gc * lv.y / (mph * mph));
-        ce = delta ? 0.0f : -sig * rho_se * gc * lv.x / (me * me);
-        // numerator terms: derivatives w.r.t. g_s of rho_s(o_s, .)
-        num = sig * drho_sd * (gA / pm_d + gc * lv.y / mph) +
-              sig * drho_se * gc * lv.x / (delta ? K : me);
-    }
-    s_d[threadIdx.x] = make_float4(dp.x, dp.y, dp.z, cd);
-    s_e[threadIdx.x] = make_float4(ep.x, ep.y, ep.z, ce);
-    __syncwarp();
-    // lane l: contribution to g_l = sum_j cd_j rho'_l(o_l,d_j) + ce_j rho'_l(o_l,e_j)
+    const float me = fmaf(kj, ep.w, pm_e), mph = fmaf(kj, dp.w, pm_d);
+    const float cd = -sig * rho_sd * (gA / (pm_d * pm_d) + gc * lv.y / (mph * mph));
+    const float ce = delta ? 0.0f : -sig * rho_se * gc * lv.x / (me * me);
+    if (cd != 0.0f) atomicAdd(gpm_d + nj, cd);
+    if (ce != 0.0f) atomicAdd(gpm_e + nj, ce);
+    const float nd = sig * (gA / pm_d + gc * lv.y / mph);
+    const float ne = sig * gc * lv.x / (delta ? Ks : me);
+    num[m * KP + j] = make_float2(nd, ne);
+}
+
+template <int KP>
+__global__ void __launch_bounds__(256) grad_g_kernel(
+    const int32_t *__restrict__ nbr, const float4 *__restrict__ OG, const float4 *__restrict__ DP,
+    const float4 *__restrict__ EP, const float4 *__restrict__ LV, const int32_t *__restrict__ m2r, int64_t n,
+    const float *__restrict__ nu, const float *__restrict__ gpm_d, const float *__restrict__ gpm_e,
+    const float2 *__restrict__ num, float *__restrict__ gg) {
+    const int lane = threadIdx.x & 31;
+    const int j = lane & (KP - 1);
+    const int64_t m = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / KP;
+    const bool row_ok = m < n;
+    const int32_t nj = row_ok ? nbr[m * KP + j] : -1;
     float acc = 0.0f;
-    if (valid && row_ok) {
-#pragma unroll 4
-        for (int jj = 0; jj < KP; jj++) {
-            float4 sd = s_d[gbase + jj], se = s_e[gbase + jj];
-            const float2 ede = s_ede[gbase + jj];
-            float dummy;
-            if (sd.w != 0.0f)
-                acc += sd.w * hg_eval_dg(og.w, one_plus_dot_u(og.x, og.y, og.z, eo, sd.x, sd.y, sd.z, ede.x), &dummy);
-            if (se.w != 0.0f)
-                acc += se.w * hg_eval_dg(og.w, one_plus_dot_u(og.x, og.y, og.z, eo, se.x, se.y, se.z, ede.y), &dummy);
-        }
-    }
-    // the row's own g_s: numerators and the non-aggregated direct term
-    float nsum = num;
-#pragma unroll
-    for (int o = KP / 2; o > 0; o >>= 1) nsum += __shfl_xor_sync(0xffffffffu, nsum, o);
-    if (valid && row_ok) {
+    if (nj >= 0) {
+        const float4 os = OG[m], dp = DP[nj], ep = EP[nj];
+        const float es = unit_err(os.x, os.y, os.z);
+        float rho_sd, rho_se;
+        const float drho_sd =
+            hg_eval_dg(os.w, one_plus_dot_u(os.x, os.y, os.z, es, dp.x, dp.y, dp.z, unit_err(dp.x, dp.y, dp.z)), &rho_sd);
+        const float drho_se =
+            hg_eval_dg(os.w, one_plus_dot_u(os.x, os.y, os.z, es, ep.x, ep.y, ep.z, unit_err(ep.x, ep.y, ep.z)), &rho_se);
+        const float2 nde = num[m * KP + j];
+        acc = drho_sd * (nde.x + gpm_d[nj]) + drho_se * (nde.y + gpm_e[nj]);
         if (j == 0) {
             // D_s = sigma_s (De + Dp) with K = 1, own samples (slot 0 = s)
-            float dDe = delta ? drho_se * lv.x : drho_se * lv.x * ep.w / ((rho_se + ep.w) * (rho_se + ep.w));
-            float dDp = drho_sd * lv.y * dp.w / ((rho_sd + dp.w) * (rho_sd + dp.w));
-            acc += nsum + gD * sig * (dDe + dDp);
+            const float4 lv = LV[m];
+            const float gD = lv.w * nu[m2r[m]];
+            const bool delta = ep.w < 0.0f;
+            const float dDe = delta ? drho_se * lv.x : drho_se * lv.x * ep.w / ((rho_se + ep.w) * (rho_se + ep.w));
+            const float dDp = drho_sd * lv.y * dp.w / ((rho_sd + dp.w) * (rho_sd + dp.w));
+            acc += gD * lv.z * (dDe + dDp);
         }
-        if (acc != 0.0f) atomicAdd(gg + nj, acc);
     }
+#pragma unroll
+    for (int o = KP / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (row_ok && j == 0) gg[m] = acc;
 }
 
 __global__ void permute_m2c_kernel(const float *__restrict__ in_m, const int32_t *__restrict__ c2m, int64_t n,
@@ -772,23 +692,21 @@ static pg_status adjoint_recompute(pg_graph *g, float *nu, float *mu_a, float *m
     PG_CUDA(cudaMemsetAsync(mu_slot(T), 0, 4 * (size_t)(n + 1), s));
     const float *yT = g->hist + (int64_t)T * stride;
     recompute_scatter_kernel<KP><<<pg_blocks((n - na) * KP, 256), 256, 0, s>>>(
-        g->nbr, g->OG, g->DP, g->LV, g->succ_m, g->m2r, g->r2m, na, n, n, nu, nullptr, yT, 1, mu_slot(T), G, B,
-        nullptr);
+        g->nbr, g->OG, g->DP, g->LV, g->succ_m, g->pmd, g->m2r, g->r2m, na, n, nu, nullptr, 1, mu_slot(T), G, B);
     pg_count_launches(1);
     PG_LAUNCH_CHECK();
     for (int t = T; t >= 1; t--) {
         if (t > 1) PG_CUDA(cudaMemsetAsync(mu_slot(t - 1), 0, 4 * (size_t)(n + 1), s));
         const float *y_t = g->hist + (int64_t)t * stride;
-        const float *y_p = g->hist + (int64_t)(t - 1) * stride;
         recompute_scatter_kernel<KP><<<pg_blocks(na * KP, 256), 256, 0, s>>>(
-            g->nbr, g->OG, g->DP, g->LV, g->succ_m, g->m2r, g->r2m, 0, na, n, mu_slot(t), y_t, y_p, t > 1 ? 1 : 0,
-            mu_slot(t - 1), G, B, nullptr);
+            g->nbr, g->OG, g->DP, g->LV, g->succ_m, g->pmd, g->m2r, g->r2m, 0, na, mu_slot(t), y_t, t > 1 ? 1 : 0,
+            mu_slot(t - 1), G, B);
         pg_count_launches(1);
         PG_LAUNCH_CHECK();
     }
     // output term of first-vertex rows
     recompute_first_kernel<KP><<<pg_blocks((n - na) * KP, 256), 256, 0, s>>>(
-        g->nbr, g->OG, g->DP, g->LV, g->succ_m, g->m2r, g->r2m, na, n, nu, yT, g->D_m, G);
+        g->nbr, g->OG, g->DP, g->LV, g->succ_m, g->pmd, g->m2r, g->r2m, na, n, nu, yT, g->D_m, G);
     pg_count_launches(1);
     PG_LAUNCH_CHECK();
     return PG_OK;
@@ -797,12 +715,24 @@ static pg_status adjoint_recompute(pg_graph *g, float *nu, float *mu_a, float *m
 template <int KP>
 static pg_status launch_grad_g(pg_graph *g, const float *muhist, const float *B, const float *nu, float *gg_m,
                                cudaStream_t s) {
-    grad_g_kernel<KP><<<pg_blocks(g->n * KP, 256), 256, 0, s>>>(g->nbr, g->OG, g->DP, g->EP, g->LV, g->m2r, g->n,
-                                                               g->n_active, g->col, g->hist, muhist,
-                                                               g->hist_iters, B, nu, gg_m);
-    pg_count_launches(1);
-    PG_LAUNCH_CHECK();
-    return PG_OK;
+    const int64_t n = g->n;
+    float *gpm = nullptr;
+    float2 *num = nullptr;
+    PG_TRY(pg_alloc(nullptr, (void **)&gpm, 8 * (size_t)n, s));
+    pg_status st = pg_alloc(nullptr, (void **)&num, 8 * (size_t)n * KP, s);
+    if (st == PG_OK && cudaMemsetAsync(gpm, 0, 8 * (size_t)n, s) != cudaSuccess) st = PG_ERR_CUDA;
+    if (st == PG_OK) {
+        grad_g_marg_kernel<KP><<<pg_blocks(n * KP, 256), 256, 0, s>>>(
+            g->nbr, g->OG, g->DP, g->EP, g->LV, g->m2r, n, g->n_active, g->col, g->hist, muhist, g->hist_iters, B,
+            nu, g->pmd, g->pme, g->kin, gpm, gpm + n, num);
+        grad_g_kernel<KP><<<pg_blocks(n * KP, 256), 256, 0, s>>>(g->nbr, g->OG, g->DP, g->EP, g->LV, g->m2r, n, nu,
+                                                                 gpm, gpm + n, num, gg_m);
+        pg_count_launches(2);
+        if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+    }
+    if (gpm) cudaFreeAsync(gpm, s);
+    if (num) cudaFreeAsync(num, s);
+    return st;
 }
 
 extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const int32_t *first, int64_t n_paths,

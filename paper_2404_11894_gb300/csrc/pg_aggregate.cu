@@ -1,6 +1,9 @@
 // Aggregation (Section 3.5): the MIS edge weights A+ of Eq. ag-indirect, the
 // direct term A°L° of Eq. ag-direct, and the non-aggregated direct light D
-// used at output (Section 4, "Handling direct light").
+// used at output (Section 4, "Handling direct light"). A sample's marginal
+// density is summed over the rows that aggregate it, so that its balance
+// weights over those rows sum to one (as within one of the paper's clusters)
+// and the sweep matrix's column sums stay below the albedo.
 //
 // Layout produced for the propagation sweep (Eq. rte-mff, L+ = P A+ L+ + P c):
 // the sweep works on y_s = (tau/p_t)_s (A+ L+ + c)_s, the radiance that s
@@ -85,82 +88,82 @@ __device__ __forceinline__ float from_w<__nv_bfloat16>(__nv_bfloat16 x) { return
 template <>
 __device__ __forceinline__ float from_w<__half>(__half x) { return __half2float(x); }
 
-// One group of KP lanes per row s (Morton order m); lane j owns neighbour
-// slot j of N(s). Strategy data (o_l, HG constants of g_l) of the row's
-// neighbours are shared through shared memory; each lane sums the k pdfs
-// rho_l(o_l, d_j) and rho_l(o_l, e_j) for its own samples (the two marginal
-// densities), then forms its weights.
+// Pass 1: the marginal densities of every sample over the rows that use it
+// (Eq. indirect-weight read on a neighbour graph: sample j is combined by the
+// strategies of R(j) = {r : j in N(r)}, so pm_d[j] = sum_{r in R(j)}
+// rho_r(o_r, d_j), pm_e[j] likewise for e_j, and kin[j] = |R(j)|). One group
+// of KP lanes per row r; lane i adds row r's two phase-function values for
+// its sample nbr[r][i] with exact fixed-point atomics.
+template <int KP>
+__global__ void __launch_bounds__(256) marginal_kernel(const int32_t *__restrict__ nbr,
+                                                       const float4 *__restrict__ OG,
+                                                       const float4 *__restrict__ DP,
+                                                       const float4 *__restrict__ EP, int64_t n,
+                                                       unsigned long long *__restrict__ pmd,
+                                                       unsigned long long *__restrict__ pme,
+                                                       uint32_t *__restrict__ kin) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t m = t / KP;
+    if (m >= n) return;
+    const int32_t nj = nbr[t];
+    if (nj < 0) return;
+    const float4 og = OG[m], dp = DP[nj], ep = EP[nj];
+    const HGc h = hg_consts(og.w);
+    const float eo = unit_err(og.x, og.y, og.z);
+    const float rd = hg_eval(h, one_plus_dot_u(og.x, og.y, og.z, eo, dp.x, dp.y, dp.z, unit_err(dp.x, dp.y, dp.z)));
+    const float re = hg_eval(h, one_plus_dot_u(og.x, og.y, og.z, eo, ep.x, ep.y, ep.z, unit_err(ep.x, ep.y, ep.z)));
+    atomicAdd(pmd + nj, pg_pm_fix(rd));
+    atomicAdd(pme + nj, pg_pm_fix(re));
+    atomicAdd(kin + nj, 1u);
+}
+
+// Pass 2: one group of KP lanes per row s (Morton order m); lane j owns
+// neighbour slot j of N(s) and forms that sample's weights from the
+// receiver's phase function and the sample's marginals.
 template <int KP, typename WT>
 __global__ void __launch_bounds__(256) aggregate_kernel(
     const int32_t *__restrict__ nbr, const float4 *__restrict__ OG, const float4 *__restrict__ DP,
     const float4 *__restrict__ EP, const float4 *__restrict__ LV, const int32_t *__restrict__ succ_m,
-    const int32_t *__restrict__ m2r, const int32_t *__restrict__ m2c, int64_t n, int64_t n_active,
-    WT *__restrict__ W, float *__restrict__ rscale, int32_t *__restrict__ col, float *__restrict__ b,
-    float *__restrict__ c_m, float *__restrict__ D_m, float *__restrict__ c_out, float *__restrict__ D_out,
-    unsigned long long *__restrict__ nnz_counter) {
-    __shared__ float4 s_o[256];   // (ox, oy, oz, C)
-    __shared__ float2 s_ab[256];  // ((1-g)^2, 2g)
-    __shared__ float s_eo[256];   // |o|^2 - 1
+    const unsigned long long *__restrict__ pmd, const unsigned long long *__restrict__ pme,
+    const uint32_t *__restrict__ kin, const int32_t *__restrict__ m2r, const int32_t *__restrict__ m2c, int64_t n,
+    int64_t n_active, WT *__restrict__ W, float *__restrict__ rscale, int32_t *__restrict__ col,
+    float *__restrict__ b, float *__restrict__ c_m, float *__restrict__ D_m, float *__restrict__ c_out,
+    float *__restrict__ D_out, unsigned long long *__restrict__ nnz_counter) {
     const int lane = threadIdx.x & 31;
     const int j = lane & (KP - 1);
-    const int gbase = threadIdx.x - j; // first thread of this row's group
+    const int src = lane & ~(KP - 1); // lane of slot 0 (the receiver itself)
     const int64_t m = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / KP;
     const bool row_ok = m < n;
-    int32_t nj = row_ok ? nbr[m * KP + j] : -1;
+    const int32_t nj = row_ok ? nbr[m * KP + j] : -1;
     const bool valid = nj >= 0;
-    float4 og = make_float4(0.f, 0.f, 1.f, 0.f), dp = make_float4(0.f, 0.f, 1.f, 0.f),
-           ep = make_float4(0.f, 0.f, 1.f, 0.f), lv = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 os = row_ok ? OG[m] : make_float4(0.f, 0.f, 1.f, 0.f);
+    float4 dp = make_float4(0.f, 0.f, 1.f, 0.f), ep = make_float4(0.f, 0.f, 1.f, 0.f),
+           lv = make_float4(0.f, 0.f, 0.f, 0.f);
     int32_t sj = -1;
+    float pm_d = 1.0f, pm_e = 1.0f, kj = 1.0f;
     if (valid) {
-        og = OG[nj];
         dp = DP[nj];
         ep = EP[nj];
         lv = LV[nj];
         sj = succ_m[nj];
+        pm_d = pg_pm_float(pmd[nj]);
+        pm_e = pg_pm_float(pme[nj]);
+        kj = (float)kin[nj];
     }
-    HGc hc = hg_consts(og.w);
-    const float eo = unit_err(og.x, og.y, og.z);
-    const float ed = unit_err(dp.x, dp.y, dp.z), ee = unit_err(ep.x, ep.y, ep.z);
-    s_o[threadIdx.x] = make_float4(og.x, og.y, og.z, valid ? hc.C : 0.0f);
-    s_ab[threadIdx.x] = make_float2(valid ? hc.a : 1.0f, valid ? hc.b2 : 0.0f);
-    s_eo[threadIdx.x] = eo;
-    __syncwarp();
-    const unsigned gmask = (KP == 32) ? 0xffffffffu : (((1u << KP) - 1u) << (lane & ~(KP - 1)));
-    const float K = (float)__popc(__ballot_sync(0xffffffffu, valid) & gmask);
-
-    // marginal densities of this lane's two samples over the row's strategies
-    float pm_d = 0.0f, pm_e = 0.0f;
-#pragma unroll 4
-    for (int l = 0; l < KP; l++) {
-        float4 so = s_o[gbase + l];
-        float2 ab = s_ab[gbase + l];
-        HGc h;
-        h.C = so.w;
-        h.a = ab.x;
-        h.b2 = ab.y;
-        const float el = s_eo[gbase + l];
-        pm_d += hg_eval(h, one_plus_dot_u(so.x, so.y, so.z, el, dp.x, dp.y, dp.z, ed));
-        pm_e += hg_eval(h, one_plus_dot_u(so.x, so.y, so.z, el, ep.x, ep.y, ep.z, ee));
-    }
-    // receiver s = slot 0 of the group
-    const float4 so = s_o[gbase];
-    const float2 sab = s_ab[gbase];
-    HGc hs;
-    hs.C = so.w;
-    hs.a = sab.x;
-    hs.b2 = sab.y;
-    const int src = lane & ~(KP - 1);
+    const unsigned gmask = (KP == 32) ? 0xffffffffu : (((1u << KP) - 1u) << src);
+    const float Ks = (float)__popc(__ballot_sync(0xffffffffu, valid) & gmask); // |N(s)|
+    const HGc hs = hg_consts(os.w);
+    const float es = unit_err(os.x, os.y, os.z);
+    const float rho_sd = hg_eval(hs, one_plus_dot_u(os.x, os.y, os.z, es, dp.x, dp.y, dp.z, unit_err(dp.x, dp.y, dp.z)));
+    const float rho_se = hg_eval(hs, one_plus_dot_u(os.x, os.y, os.z, es, ep.x, ep.y, ep.z, unit_err(ep.x, ep.y, ep.z)));
     const float sig_s = __shfl_sync(0xffffffffu, lv.z, src);
     const float w_s = __shfl_sync(0xffffffffu, lv.w, src);
-    const float es = s_eo[gbase];
-    float rho_sd = hg_eval(hs, one_plus_dot_u(so.x, so.y, so.z, es, dp.x, dp.y, dp.z, ed));
-    float rho_se = hg_eval(hs, one_plus_dot_u(so.x, so.y, so.z, es, ep.x, ep.y, ep.z, ee));
+    const bool delta = ep.w < 0.0f;
     float A = 0.0f, term = 0.0f;
     if (valid) {
         A = sig_s * rho_sd / pm_d;
-        bool delta = ep.w < 0.0f;
-        float Ae = delta ? sig_s * rho_se / K : sig_s * rho_se / fmaf(K, ep.w, pm_e);
-        float Aph = sig_s * rho_sd / fmaf(K, dp.w, pm_d);
+        const float Ae = delta ? sig_s * rho_se / Ks : sig_s * rho_se / fmaf(kj, ep.w, pm_e);
+        const float Aph = sig_s * rho_sd / fmaf(kj, dp.w, pm_d);
         term = fmaf(Ae, lv.x, Aph * lv.y);
     }
     // c_s: sum over the group's lanes (fixed butterfly order)
@@ -170,14 +173,13 @@ __global__ void __launch_bounds__(256) aggregate_kernel(
     // D_s from slot 0's own samples (K = 1)
     float Dterm = 0.0f;
     if (j == 0 && valid) {
-        bool delta = ep.w < 0.0f;
-        float De = delta ? rho_se * lv.x : rho_se * lv.x / (rho_se + ep.w);
-        float Dp = rho_sd * lv.y / (rho_sd + dp.w);
+        const float De = delta ? rho_se * lv.x : rho_se * lv.x / (rho_se + ep.w);
+        const float Dp = rho_sd * lv.y / (rho_sd + dp.w);
         Dterm = sig_s * (De + Dp);
     }
-    float Wt = w_s * A;
-    int32_t r = row_ok ? m2r[m] : 0;
-    int32_t cl = (valid && sj >= 0) ? m2r[sj] : (int32_t)n;
+    const float Wt = w_s * A;
+    const int32_t r = row_ok ? m2r[m] : 0;
+    const int32_t cl = (valid && sj >= 0) ? m2r[sj] : (int32_t)n;
     float scale = 1.0f;
     if (WTraits<WT>::id != PG_W_F32) {
         float mx = Wt;
@@ -197,24 +199,29 @@ __global__ void __launch_bounds__(256) aggregate_kernel(
             if (WTraits<WT>::id != PG_W_F32) rscale[r] = scale;
             c_m[m] = c;
             D_m[m] = Dterm;
-            int32_t ci = m2c[m];
+            const int32_t ci = m2c[m];
             if (c_out) c_out[ci] = c;
             if (D_out) D_out[ci] = Dterm;
         }
     }
     // edge updates per sweep: real entries of rows that have a predecessor
-    bool counted = row_ok && valid && sj >= 0 && r < n_active;
-    unsigned cnt = __popc(__ballot_sync(0xffffffffu, counted));
+    const bool counted = row_ok && valid && sj >= 0 && r < n_active;
+    const unsigned cnt = __popc(__ballot_sync(0xffffffffu, counted));
     if (lane == 0 && cnt) atomicAdd(nnz_counter, (unsigned long long)cnt);
 }
 
 template <int KP, typename WT>
 static pg_status launch_agg(pg_graph *g, float *c_out, float *D_out, unsigned long long *cnt, cudaStream_t s) {
     int64_t threads = g->n * KP;
+    PG_CUDA(cudaMemsetAsync(g->pmd, 0, 8 * (size_t)g->n, s));
+    PG_CUDA(cudaMemsetAsync(g->pme, 0, 8 * (size_t)g->n, s));
+    PG_CUDA(cudaMemsetAsync(g->kin, 0, 4 * (size_t)g->n, s));
+    marginal_kernel<KP><<<pg_blocks(threads, 256), 256, 0, s>>>(g->nbr, g->OG, g->DP, g->EP, g->n, g->pmd, g->pme,
+                                                                g->kin);
     aggregate_kernel<KP, WT><<<pg_blocks(threads, 256), 256, 0, s>>>(
-        g->nbr, g->OG, g->DP, g->EP, g->LV, g->succ_m, g->m2r, g->m2c, g->n, g->n_active, (WT *)g->W, g->rscale,
-        g->col, g->b, g->c_m, g->D_m, c_out, D_out, cnt);
-    pg_count_launches(1);
+        g->nbr, g->OG, g->DP, g->EP, g->LV, g->succ_m, g->pmd, g->pme, g->kin, g->m2r, g->m2c, g->n, g->n_active,
+        (WT *)g->W, g->rscale, g->col, g->b, g->c_m, g->D_m, c_out, D_out, cnt);
+    pg_count_launches(2);
     PG_LAUNCH_CHECK();
     return PG_OK;
 }
@@ -267,6 +274,9 @@ extern "C" pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype w
     A(g->b, 4 * (size_t)(n + 1));
     A(g->c_m, 4 * (size_t)n);
     A(g->D_m, 4 * (size_t)n);
+    A(g->pmd, 8 * (size_t)n);
+    A(g->pme, 8 * (size_t)n);
+    A(g->kin, 4 * (size_t)n);
 #undef A
     if (st != PG_OK) return st;
     if (n == 0) {

@@ -569,6 +569,9 @@ static pg_status graph_free_all(pg_graph *g) {
     pg_free(g, (void **)&g->d_resid, 8 * (size_t)g->resid_cap);
     pg_free(g, (void **)&g->d_ctrl, 16);
     pg_free(g, (void **)&g->d_partials, 16 * (size_t)g->partials_cap);
+    pg_free(g, (void **)&g->pmd, 8 * n);
+    pg_free(g, (void **)&g->pme, 8 * n);
+    pg_free(g, (void **)&g->kin, 4 * n);
     pg_free_transposes(g);
     return PG_OK;
 }
