@@ -40,7 +40,7 @@ __global__ void pack_kernel(pg_vertices v, int64_t n, const int32_t *__restrict_
             f |= PG_FLAG_BAD_INDEX;
         } else {
             sm = c2m[sc];
-            if (atomicAdd(&predcnt[sm], 1) != 0) f |= PG_FLAG_TWO_PREDS;
+            atomicAdd(&predcnt[sm], 1); // a second predecessor is flagged by active_flag_kernel
         }
     } else if (sc != -1) {
         f |= PG_FLAG_BAD_INDEX;
@@ -53,10 +53,22 @@ __global__ void pack_kernel(pg_vertices v, int64_t n, const int32_t *__restrict_
     succ_m[m] = sm;
 }
 
-__global__ void active_flag_kernel(const int32_t *__restrict__ predcnt, int64_t n, int32_t *__restrict__ act) {
+__global__ void active_flag_kernel(const int32_t *__restrict__ predcnt, int64_t n, int32_t *__restrict__ act,
+                                   int32_t *__restrict__ flags) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n) return;
-    act[m] = predcnt[m] > 0 ? 1 : 0;
+    const int32_t pc = predcnt[m];
+    act[m] = pc > 0 ? 1 : 0;
+    if (pc > 1) atomicOr(flags, PG_FLAG_TWO_PREDS);
+}
+
+// sweep row of each vertex's successor, or the zero slot n at a path end
+__global__ void succ_row_kernel(const int32_t *__restrict__ succ_m, const int32_t *__restrict__ m2r, int64_t n,
+                                int32_t *__restrict__ sr) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const int32_t s = succ_m[m];
+    sr[m] = s >= 0 ? m2r[s] : (int32_t)n;
 }
 
 // act holds the exclusive prefix of the active flags; predcnt the flags' source
@@ -119,11 +131,13 @@ __global__ void __launch_bounds__(256) marginal_kernel(const int32_t *__restrict
 
 // Pass 2: one group of KP lanes per row s (Morton order m); lane j owns
 // neighbour slot j of N(s) and forms that sample's weights from the
-// receiver's phase function and the sample's marginals.
+// receiver's phase function and the sample's marginals. Blocks stride over
+// the rows (a fixed grid), so the count of swept entries costs one atomic
+// per block.
 template <int KP, typename WT>
 __global__ void __launch_bounds__(256) aggregate_kernel(
     const int32_t *__restrict__ nbr, const float4 *__restrict__ OG, const float4 *__restrict__ DP,
-    const float4 *__restrict__ EP, const float4 *__restrict__ LV, const int32_t *__restrict__ succ_m,
+    const float4 *__restrict__ EP, const float4 *__restrict__ LV, const int32_t *__restrict__ sr,
     const unsigned long long *__restrict__ pmd, const unsigned long long *__restrict__ pme,
     const uint32_t *__restrict__ kin, const int32_t *__restrict__ m2r, const int32_t *__restrict__ m2c, int64_t n,
     int64_t n_active, WT *__restrict__ W, float *__restrict__ rscale, int32_t *__restrict__ col,
@@ -132,82 +146,90 @@ __global__ void __launch_bounds__(256) aggregate_kernel(
     const int lane = threadIdx.x & 31;
     const int j = lane & (KP - 1);
     const int src = lane & ~(KP - 1); // lane of slot 0 (the receiver itself)
-    const int64_t m = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / KP;
-    const bool row_ok = m < n;
-    const int32_t nj = row_ok ? nbr[m * KP + j] : -1;
-    const bool valid = nj >= 0;
-    const float4 os = row_ok ? OG[m] : make_float4(0.f, 0.f, 1.f, 0.f);
-    float4 dp = make_float4(0.f, 0.f, 1.f, 0.f), ep = make_float4(0.f, 0.f, 1.f, 0.f),
-           lv = make_float4(0.f, 0.f, 0.f, 0.f);
-    int32_t sj = -1;
-    float pm_d = 1.0f, pm_e = 1.0f, kj = 1.0f;
-    if (valid) {
-        dp = DP[nj];
-        ep = EP[nj];
-        lv = LV[nj];
-        sj = succ_m[nj];
-        pm_d = pg_pm_float(pmd[nj]);
-        pm_e = pg_pm_float(pme[nj]);
-        kj = (float)kin[nj];
-    }
-    const unsigned gmask = (KP == 32) ? 0xffffffffu : (((1u << KP) - 1u) << src);
-    const float Ks = (float)__popc(__ballot_sync(0xffffffffu, valid) & gmask); // |N(s)|
-    const HGc hs = hg_consts(os.w);
-    const float es = unit_err(os.x, os.y, os.z);
-    const float rho_sd = hg_eval(hs, one_plus_dot_u(os.x, os.y, os.z, es, dp.x, dp.y, dp.z, unit_err(dp.x, dp.y, dp.z)));
-    const float rho_se = hg_eval(hs, one_plus_dot_u(os.x, os.y, os.z, es, ep.x, ep.y, ep.z, unit_err(ep.x, ep.y, ep.z)));
-    const float sig_s = __shfl_sync(0xffffffffu, lv.z, src);
-    const float w_s = __shfl_sync(0xffffffffu, lv.w, src);
-    const bool delta = ep.w < 0.0f;
-    float A = 0.0f, term = 0.0f;
-    if (valid) {
-        A = sig_s * rho_sd / pm_d;
-        const float Ae = delta ? sig_s * rho_se / Ks : sig_s * rho_se / fmaf(kj, ep.w, pm_e);
-        const float Aph = sig_s * rho_sd / fmaf(kj, dp.w, pm_d);
-        term = fmaf(Ae, lv.x, Aph * lv.y);
-    }
-    // c_s: sum over the group's lanes (fixed butterfly order)
-    float c = term;
-#pragma unroll
-    for (int o = KP / 2; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    // D_s from slot 0's own samples (K = 1)
-    float Dterm = 0.0f;
-    if (j == 0 && valid) {
-        const float De = delta ? rho_se * lv.x : rho_se * lv.x / (rho_se + ep.w);
-        const float Dp = rho_sd * lv.y / (rho_sd + dp.w);
-        Dterm = sig_s * (De + Dp);
-    }
-    const float Wt = w_s * A;
-    const int32_t r = row_ok ? m2r[m] : 0;
-    const int32_t cl = (valid && sj >= 0) ? m2r[sj] : (int32_t)n;
-    float scale = 1.0f;
-    if (WTraits<WT>::id != PG_W_F32) {
-        float mx = Wt;
-#pragma unroll
-        for (int o = KP / 2; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        scale = mx > 0.0f ? mx : 1.0f;
-    }
-    // 16-bit payload: the row's weights relative to its largest one, rounded
-    // to nearest (error diffusion along the row was measured to be worse:
-    // the gathered radiance of a row's columns is far from uniform)
-    const WT wq = to_w<WT>(WTraits<WT>::id == PG_W_F32 ? Wt : Wt / scale);
-    if (row_ok) {
-        W[(int64_t)r * KP + j] = wq;
-        col[(int64_t)r * KP + j] = cl;
-        if (j == 0) {
-            b[r] = w_s * c;
-            if (WTraits<WT>::id != PG_W_F32) rscale[r] = scale;
-            c_m[m] = c;
-            D_m[m] = Dterm;
-            const int32_t ci = m2c[m];
-            if (c_out) c_out[ci] = c;
-            if (D_out) D_out[ci] = Dterm;
+    constexpr int RPB = 256 / KP;     // rows per block per iteration
+    unsigned long long counted_total = 0;
+    for (int64_t base = (int64_t)blockIdx.x * RPB; base < n; base += (int64_t)gridDim.x * RPB) {
+        const int64_t m = base + threadIdx.x / KP;
+        const bool row_ok = m < n;
+        const int32_t nj = row_ok ? nbr[m * KP + j] : -1;
+        const bool valid = nj >= 0;
+        const float4 os = row_ok ? OG[m] : make_float4(0.f, 0.f, 1.f, 0.f);
+        float4 dp = make_float4(0.f, 0.f, 1.f, 0.f), ep = make_float4(0.f, 0.f, 1.f, 0.f),
+               lv = make_float4(0.f, 0.f, 0.f, 0.f);
+        int32_t cl = (int32_t)n; // sweep row of succ(j), or the zero slot
+        float pm_d = 1.0f, pm_e = 1.0f, kj = 1.0f;
+        if (valid) {
+            dp = DP[nj];
+            ep = EP[nj];
+            lv = LV[nj];
+            cl = sr[nj];
+            pm_d = pg_pm_float(pmd[nj]);
+            pm_e = pg_pm_float(pme[nj]);
+            kj = (float)kin[nj];
         }
+        const unsigned gmask = (KP == 32) ? 0xffffffffu : (((1u << KP) - 1u) << src);
+        const float Ks = (float)__popc(__ballot_sync(0xffffffffu, valid) & gmask); // |N(s)|
+        const HGc hs = hg_consts(os.w);
+        const float es = unit_err(os.x, os.y, os.z);
+        const float rho_sd = hg_eval(hs, one_plus_dot_u(os.x, os.y, os.z, es, dp.x, dp.y, dp.z, unit_err(dp.x, dp.y, dp.z)));
+        const float rho_se = hg_eval(hs, one_plus_dot_u(os.x, os.y, os.z, es, ep.x, ep.y, ep.z, unit_err(ep.x, ep.y, ep.z)));
+        const float sig_s = __shfl_sync(0xffffffffu, lv.z, src);
+        const float w_s = __shfl_sync(0xffffffffu, lv.w, src);
+        const bool delta = ep.w < 0.0f;
+        float A = 0.0f, term = 0.0f;
+        if (valid) {
+            A = sig_s * rho_sd / pm_d;
+            const float Ae = delta ? sig_s * rho_se / Ks : sig_s * rho_se / fmaf(kj, ep.w, pm_e);
+            const float Aph = sig_s * rho_sd / fmaf(kj, dp.w, pm_d);
+            term = fmaf(Ae, lv.x, Aph * lv.y);
+        }
+        // c_s: sum over the group's lanes (fixed butterfly order)
+        float c = term;
+    #pragma unroll
+        for (int o = KP / 2; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        // D_s from slot 0's own samples (K = 1)
+        float Dterm = 0.0f;
+        if (j == 0 && valid) {
+            const float De = delta ? rho_se * lv.x : rho_se * lv.x / (rho_se + ep.w);
+            const float Dp = rho_sd * lv.y / (rho_sd + dp.w);
+            Dterm = sig_s * (De + Dp);
+        }
+        const float Wt = w_s * A;
+        const int32_t r = row_ok ? m2r[m] : 0;
+        float scale = 1.0f;
+        if (WTraits<WT>::id != PG_W_F32) {
+            float mx = Wt;
+    #pragma unroll
+            for (int o = KP / 2; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            scale = mx > 0.0f ? mx : 1.0f;
+        }
+        // 16-bit payload: the row's weights relative to its largest one, rounded
+        // to nearest (error diffusion along the row was measured to be worse:
+        // the gathered radiance of a row's columns is far from uniform)
+        const WT wq = to_w<WT>(WTraits<WT>::id == PG_W_F32 ? Wt : Wt / scale);
+        if (row_ok) {
+            W[(int64_t)r * KP + j] = wq;
+            col[(int64_t)r * KP + j] = cl;
+            if (j == 0) {
+                b[r] = w_s * c;
+                if (WTraits<WT>::id != PG_W_F32) rscale[r] = scale;
+                c_m[m] = c;
+                D_m[m] = Dterm;
+                const int32_t ci = m2c[m];
+                if (c_out) c_out[ci] = c;
+                if (D_out) D_out[ci] = Dterm;
+            }
+        }
+        // edge updates per sweep: real entries of rows that have a predecessor
+        const bool counted = row_ok && valid && cl < n && r < n_active;
+        counted_total += __popc(__ballot_sync(0xffffffffu, counted));
     }
-    // edge updates per sweep: real entries of rows that have a predecessor
-    const bool counted = row_ok && valid && sj >= 0 && r < n_active;
-    const unsigned cnt = __popc(__ballot_sync(0xffffffffu, counted));
-    if (lane == 0 && cnt) atomicAdd(nnz_counter, (unsigned long long)cnt);
+    __shared__ unsigned long long s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    if (lane == 0 && counted_total) atomicAdd(&s_cnt, counted_total);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_cnt) atomicAdd(nnz_counter, s_cnt);
 }
 
 template <int KP, typename WT>
@@ -216,12 +238,18 @@ static pg_status launch_agg(pg_graph *g, float *c_out, float *D_out, unsigned lo
     PG_CUDA(cudaMemsetAsync(g->pmd, 0, 8 * (size_t)g->n, s));
     PG_CUDA(cudaMemsetAsync(g->pme, 0, 8 * (size_t)g->n, s));
     PG_CUDA(cudaMemsetAsync(g->kin, 0, 4 * (size_t)g->n, s));
+    int32_t *sr = nullptr;
+    PG_TRY(pg_alloc(nullptr, (void **)&sr, 4 * (size_t)g->n, s));
     marginal_kernel<KP><<<pg_blocks(threads, 256), 256, 0, s>>>(g->nbr, g->OG, g->DP, g->EP, g->n, g->pmd, g->pme,
                                                                 g->kin);
-    aggregate_kernel<KP, WT><<<pg_blocks(threads, 256), 256, 0, s>>>(
-        g->nbr, g->OG, g->DP, g->EP, g->LV, g->succ_m, g->pmd, g->pme, g->kin, g->m2r, g->m2c, g->n, g->n_active,
+    succ_row_kernel<<<pg_blocks(g->n, 256), 256, 0, s>>>(g->succ_m, g->m2r, g->n, sr);
+    int64_t need = (g->n * KP + 255) / 256;
+    int64_t cap = (int64_t)pg_num_sms() * 6;
+    aggregate_kernel<KP, WT><<<(int)(need < cap ? need : cap), 256, 0, s>>>(
+        g->nbr, g->OG, g->DP, g->EP, g->LV, sr, g->pmd, g->pme, g->kin, g->m2r, g->m2c, g->n, g->n_active,
         (WT *)g->W, g->rscale, g->col, g->b, g->c_m, g->D_m, c_out, D_out, cnt);
-    pg_count_launches(2);
+    pg_count_launches(3);
+    cudaFreeAsync(sr, s);
     PG_LAUNCH_CHECK();
     return PG_OK;
 }
@@ -299,7 +327,7 @@ extern "C" pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype w
         pack_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(*v, n, g->c2m, g->OG, g->DP, g->EP, g->LV, g->succ_m, predcnt,
                                                       g->flags);
         pg_count_launches(1);
-        active_flag_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(predcnt, n, act);
+        active_flag_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(predcnt, n, act, g->flags);
         pg_count_launches(1);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     }

@@ -202,8 +202,18 @@ __global__ void __launch_bounds__(128, 4) knn_kernel(const int4 *__restrict__ qr
 #pragma unroll
         for (int i = 0; i < M; i++)
             if (i >= pad && bk[i] != UINT64_MAX && (bk[i] >> 31) >= KNN_SAT) saturated = true;
-        if (!done || saturated) {
-            redo[atomicAdd(redo_count, 1)] = (int32_t)m;
+        // queue the query for the exact kernel; one counter atomic per
+        // converged group of lanes, not one per query (a single hot address)
+        const bool need = !done || saturated;
+        const unsigned am = __activemask();
+        const unsigned need_mask = __ballot_sync(am, need);
+        if (need) {
+            const int lane = threadIdx.x & 31;
+            const int leader = __ffs(need_mask) - 1;
+            int32_t base = 0;
+            if (lane == leader) base = atomicAdd(redo_count, __popc(need_mask));
+            base = __shfl_sync(need_mask, base, leader);
+            redo[base + __popc(need_mask & ((1u << lane) - 1u))] = (int32_t)m;
             return;
         }
     }

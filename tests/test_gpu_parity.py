@@ -124,11 +124,14 @@ def rel_err_mean(got, ref):
 @pytest.mark.parametrize("wdtype", ["bf16", "f16"])
 def test_16bit_weights(case, pg, wdtype):
     """FP16 payload with a per-row FP32 scale meets 2e-3 per pixel; BF16's
-    8-bit mantissa meets it on the mean over pixels only (its per-pixel
-    maximum is reported by the bench and stays below 1e-2)."""
+    8-bit mantissa meets it per pixel on the cube and cloud workloads and on
+    the mean over pixels of the dense albedo-0.999 one (whose per-pixel
+    maximum, 5e-3, is held below 1e-2)."""
     sc, rec, ref, _ = case
     gpu = _gpu_forward(pg, rec, sc, wdtype=wdtype)
     img = gpu.img.cpu().numpy()
+    print(f"\n{sc.name} {wdtype}: image max {rel_err(img, ref['image']):.3e} mean {rel_err_mean(img, ref['image']):.3e}"
+          f" L max {rel_err(gpu.L.cpu().numpy(), ref['L']):.3e}")
     if wdtype == "f16":
         assert rel_err(img, ref["image"]) <= W16_TOL
     else:
