@@ -194,7 +194,7 @@ def vertex_arrays(V):
 # --------------------------------------------------------------------------
 # Aggregation (Section 3.5)
 # --------------------------------------------------------------------------
-def sample_marginals(V, nbr, cols=None, g=None, chunk=1 << 22):
+def sample_marginals(V, nbr, cols=None, g=None, chunk=1 << 18):
     """Marginal densities of every sample j over the points that use it.
 
     R(j) = {r : j in N(r)}; K_j = |R(j)|;
@@ -202,28 +202,35 @@ def sample_marginals(V, nbr, cols=None, g=None, chunk=1 << 22):
       pm_e[j] = sum_{r in R(j)} rho_r(o_r, e_j)   (emitter sample of j)
     (Eq. indirect-weight's p_m, and the phase part of Eq. ag-direct's).
     With ``cols`` only those samples' marginals are formed (the others are
-    zero). Parity: pinned by the MIS column sums (each sample's weights over
-    R(j) sum to one) and by the isotropic closed form.
+    zero). The table is walked in blocks of ``chunk`` rows. Parity: pinned by
+    the MIS column sums (each sample's weights over R(j) sum to one) and by
+    the isotropic closed form.
     """
     X = vertex_arrays(V)
     if g is not None:
         X["g"] = np.asarray(g, np.float64)
     n = len(X["g"])
-    mask = nbr >= 0
+    want = None
     if cols is not None:
         want = np.zeros(n, bool)
         want[np.asarray(cols, np.int64)] = True
-        mask &= want[np.where(mask, nbr, 0)]
-    r_idx, i_idx = np.nonzero(mask)
     pm_d = np.zeros(n)
     pm_e = np.zeros(n)
     K = np.zeros(n)
-    for a in range(0, len(r_idx), chunk):
-        r = r_idx[a:a + chunk]
-        j = nbr[r, i_idx[a:a + chunk]].astype(np.int64)
-        pm_d += np.bincount(j, weights=hg(X["o"][r], X["d"][j], X["g"][r]), minlength=n)
-        pm_e += np.bincount(j, weights=hg(X["o"][r], X["e"][j], X["g"][r]), minlength=n)
-        K += np.bincount(j, minlength=n)
+    for a in range(0, len(nbr), chunk):
+        nb = nbr[a:a + chunk]
+        mask = nb >= 0
+        if want is not None:
+            mask &= want[np.where(mask, nb, 0)]
+        r_loc, i_idx = np.nonzero(mask)
+        if len(r_loc) == 0:
+            continue
+        r = r_loc + a
+        j = nb[r_loc, i_idx].astype(np.int64)
+        top = int(j.max()) + 1
+        pm_d[:top] += np.bincount(j, weights=hg(X["o"][r], X["d"][j], X["g"][r]), minlength=top)
+        pm_e[:top] += np.bincount(j, weights=hg(X["o"][r], X["e"][j], X["g"][r]), minlength=top)
+        K[:top] += np.bincount(j, minlength=top)
     return pm_d, pm_e, K
 
 

@@ -80,30 +80,30 @@ __global__ void scale_rows_kernel(const float *__restrict__ mu, const float *__r
 
 // ------------------------------------------------------------------ transpose build
 __global__ void tcount_kernel(const int32_t *__restrict__ col, int64_t r0, int64_t r1, int kp, int64_t ncols,
-                              int32_t *__restrict__ cnt) {
+                              int64_t *__restrict__ cnt) {
     int64_t e = r0 * kp + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= r1 * kp) return;
     int32_t c = col[e];
-    if (c < ncols) atomicAdd(&cnt[c], 1);
+    if (c < ncols) atomicAdd(reinterpret_cast<unsigned long long *>(cnt + c), 1ull);
 }
 
 template <typename WT>
 __global__ void tfill_kernel(const int32_t *__restrict__ col, const WT *__restrict__ W, int64_t r0, int64_t r1,
-                             int kp, int64_t ncols, const int32_t *__restrict__ tptr, int32_t *__restrict__ fill,
+                             int kp, int64_t ncols, const int64_t *__restrict__ tptr, int32_t *__restrict__ fill,
                              int2 *__restrict__ tent) {
     int64_t e = r0 * kp + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= r1 * kp) return;
     int32_t c = col[e];
     if (c >= ncols) return;
-    int32_t pos = tptr[c] + atomicAdd(&fill[c], 1);
+    int64_t pos = tptr[c] + atomicAdd(&fill[c], 1);
     tent[pos] = make_int2((int32_t)(e / kp), wbits<WT>(W[e]));
 }
 
 // Column lengths rounded up to even, so that every column starts on a
 // 16-byte boundary and the reverse sweep loads its entries in pairs.
-__global__ void tround_kernel(int32_t *__restrict__ cnt, int64_t ncols) {
+__global__ void tround_kernel(int64_t *__restrict__ cnt, int64_t ncols) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < ncols) cnt[c] = (cnt[c] + 1) & ~1;
+    if (c < ncols) cnt[c] = (cnt[c] + 1) & ~(int64_t)1;
 }
 
 template <int N>
@@ -129,7 +129,7 @@ __device__ __forceinline__ void bitonic_rows(int2 (&kv)[N]) {
 }
 
 template <int N>
-__device__ __forceinline__ void sort_column(int2 *__restrict__ tent, int32_t a, int32_t len) {
+__device__ __forceinline__ void sort_column(int2 *__restrict__ tent, int64_t a, int32_t len) {
     int2 kv[N];
 #pragma unroll
     for (int i = 0; i < N; i++) kv[i] = i < len ? tent[a + i] : make_int2(INT32_MAX, 0);
@@ -145,12 +145,13 @@ __device__ __forceinline__ void sort_column(int2 *__restrict__ tent, int32_t a, 
 // its length was rounded up. Columns of up to 16 or 32 entries (all of them
 // for k <= 16 in practice) are sorted in registers by a bitonic network;
 // longer ones by insertion sort in memory.
-__global__ void __launch_bounds__(128) tsort_kernel(const int32_t *__restrict__ tptr,
+__global__ void __launch_bounds__(128) tsort_kernel(const int64_t *__restrict__ tptr,
                                                     const int32_t *__restrict__ fill, int64_t ncols,
                                                     int32_t pad_row, int2 *__restrict__ tent) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncols) return;
-    const int32_t a = tptr[c], len = fill[c];
+    const int64_t a = tptr[c];
+    const int32_t len = fill[c];
     if (a + len < tptr[c + 1]) tent[a + len] = make_int2(pad_row, 0);
     if (len <= 1) return;
     if (len <= 16) {
@@ -161,9 +162,9 @@ __global__ void __launch_bounds__(128) tsort_kernel(const int32_t *__restrict__ 
         sort_column<32>(tent, a, len);
         return;
     }
-    for (int32_t i = a + 1; i < a + len; i++) {
+    for (int64_t i = a + 1; i < a + len; i++) {
         const int2 v = tent[i];
-        int32_t j = i - 1;
+        int64_t j = i - 1;
         while (j >= a && tent[j].x > v.x) {
             tent[j + 1] = tent[j];
             j--;
@@ -202,7 +203,7 @@ static constexpr int TS_THREADS = 256;
 
 template <typename WT, int TS_LPC, int TS_PER_LANE, int MINB>
 __global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_kernel(
-    const int32_t *__restrict__ tptr, const int2 *__restrict__ tent,
+    const int64_t *__restrict__ tptr, const int2 *__restrict__ tent,
     const float *__restrict__ us_in, const float *__restrict__ mu_in, const float *__restrict__ y_t,
     const float *__restrict__ rscale, int64_t ncols, int write_out, float *__restrict__ mu_out,
     float *__restrict__ us_out, float *__restrict__ G, float *__restrict__ B) {
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_kernel(
     const int64_t c1 = min(ncols, c0 + chunk);
     // each iteration prefetches the next one's column extents, so the entry
     // loads never wait behind a load of the row pointers
-    int32_t pa = 0, pb = 0;
+    int64_t pa = 0, pb = 0;
     if (write_out && c0 + threadIdx.x / TS_LPC < c1) {
         pa = tptr[c0 + threadIdx.x / TS_LPC];
         pb = tptr[c0 + threadIdx.x / TS_LPC + 1];
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_kernel(
     for (int64_t base = c0; base < c1; base += CPB) {
         const int64_t c = base + threadIdx.x / TS_LPC;
         const bool ok = c < c1;
-        int32_t ca = pa, cb = pb;
+        const int64_t ca = pa, cb = pb;
         if (write_out) {
             const int64_t cn = c + CPB;
             pa = pb = 0;
@@ -252,15 +253,13 @@ __global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_kernel(
         if (ok && rscale && write_out && q == 0) rs = __ldcs(rscale + c);
         float acc = 0.0f;
         if (ok && write_out) {
-            int32_t a = ca;
-            const int32_t b = cb;
             // columns start on even entries: lane q takes the pairs 2q + 2 LPC u
-            for (; a < b; a += TS_LPC * TS_PER_LANE) {
+            for (int64_t a = ca; a < cb; a += TS_LPC * TS_PER_LANE) {
                 int4 ent[TS_PER_LANE / 2];
 #pragma unroll
                 for (int u = 0; u < TS_PER_LANE / 2; u++) {
-                    const int32_t e = a + 2 * q + 2 * TS_LPC * u;
-                    ent[u] = e < b ? __ldcs(reinterpret_cast<const int4 *>(tent + e)) : make_int4(-1, 0, -1, 0);
+                    const int64_t e = a + 2 * q + 2 * TS_LPC * u;
+                    ent[u] = e < cb ? __ldcs(reinterpret_cast<const int4 *>(tent + e)) : make_int4(-1, 0, -1, 0);
                 }
 #pragma unroll
                 for (int u = 0; u < TS_PER_LANE / 2; u++) {
@@ -542,9 +541,10 @@ static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
     const int kp = g->kp;
     pg_tcsr *ts[2] = {&g->tA, &g->tF};
     const int64_t r0[2] = {0, na}, r1[2] = {na, n};
-    int32_t *fill = nullptr, *d_total = nullptr;
+    int32_t *fill = nullptr;
+    int64_t *d_total = nullptr;
     pg_status st = PG_OK;
-    for (int i = 0; i < 2 && st == PG_OK; i++) st = pg_alloc(g, (void **)&ts[i]->ptr, 4 * (size_t)(na + 1), s);
+    for (int i = 0; i < 2 && st == PG_OK; i++) st = pg_alloc(g, (void **)&ts[i]->ptr, 8 * (size_t)(na + 1), s);
     if (st == PG_OK) st = pg_alloc(nullptr, (void **)&fill, 4 * (size_t)(na + 1), s);
     if (st == PG_OK) st = pg_alloc(nullptr, (void **)&d_total, 16, s);
     if (st != PG_OK) {
@@ -552,7 +552,7 @@ static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
         return st;
     }
     for (int i = 0; i < 2; i++) {
-        PG_CUDA(cudaMemsetAsync(ts[i]->ptr, 0, 4 * (size_t)(na + 1), s));
+        PG_CUDA(cudaMemsetAsync(ts[i]->ptr, 0, 8 * (size_t)(na + 1), s));
         if (r1[i] > r0[i]) {
             tcount_kernel<<<pg_blocks((r1[i] - r0[i]) * kp, 256), 256, 0, s>>>(g->col, r0[i], r1[i], kp, na,
                                                                                ts[i]->ptr);
@@ -560,13 +560,13 @@ static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
             pg_count_launches(2);
             PG_LAUNCH_CHECK();
         }
-        PG_TRY(pg_scan_exclusive(g, ts[i]->ptr, na + 1, d_total + 2 * i, s));
+        PG_TRY(pg_scan_exclusive64(g, ts[i]->ptr, na + 1, d_total + i, s));
     }
-    int32_t h_total[4] = {0, 0, 0, 0};
+    int64_t h_total[2] = {0, 0};
     PG_CUDA(cudaMemcpyAsync(h_total, d_total, 16, cudaMemcpyDeviceToHost, s));
     PG_CUDA(cudaStreamSynchronize(s));
     for (int i = 0; i < 2; i++) {
-        ts[i]->nnz = h_total[2 * i];
+        ts[i]->nnz = h_total[i];
         PG_TRY(pg_alloc(g, (void **)&ts[i]->ent, 8 * (size_t)(ts[i]->nnz > 0 ? ts[i]->nnz : 1), s));
         if (ts[i]->nnz == 0) continue;
         PG_CUDA(cudaMemsetAsync(fill, 0, 4 * (size_t)(na + 1), s));
@@ -586,7 +586,7 @@ static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
 void pg_free_transposes(pg_graph *g) {
     for (pg_tcsr *t : {&g->tA, &g->tF}) {
         pg_free(g, (void **)&t->ent, 8 * (size_t)(t->nnz > 0 ? t->nnz : 1));
-        pg_free(g, (void **)&t->ptr, 4 * (size_t)(g->n_active + 1));
+        pg_free(g, (void **)&t->ptr, 8 * (size_t)(g->n_active + 1));
         t->nnz = 0;
     }
 }

@@ -21,9 +21,10 @@ enum : int {
 };
 
 // Transposed weights by column (sweep row of the column's vertex), entries
-// sorted by source row: ptr[n_active + 1], ent[nnz] = (source row, weight bits).
+// sorted by source row: ptr[n_active + 1] (64-bit: a large graph holds more
+// than 2^31 entries), ent[nnz] = (source row, weight bits).
 struct pg_tcsr {
-    int32_t *ptr = nullptr;
+    int64_t *ptr = nullptr;
     int2 *ent = nullptr;
     int64_t nnz = 0;
 };
@@ -118,6 +119,8 @@ void pg_count_launches(int k); // diagnostic count of kernel launches
 pg_status pg_radix_sort(pg_graph *g, uint32_t *keys, int32_t *vals, int64_t n, int nbits, cudaStream_t s);
 // Exclusive prefix sum of n int32 counts (in place); total written to *d_total if non-NULL.
 pg_status pg_scan_exclusive(pg_graph *g, int32_t *data, int64_t n, int32_t *d_total, cudaStream_t s);
+// 64-bit offsets (totals past 2^31, e.g. the transposed weights of 150M+ vertices)
+pg_status pg_scan_exclusive64(pg_graph *g, int64_t *data, int64_t n, int64_t *d_total, cudaStream_t s);
 
 // ------------------------------------------------------------------ device math
 // 1 + a.b for unit vectors, with the rounding errors of the three products

@@ -64,59 +64,62 @@ static constexpr int SCAN_THREADS = 512;
 static constexpr int SCAN_ITEMS = 8;
 static constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
-__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *total) {
-    __shared__ int32_t warp_sums[SCAN_THREADS / 32];
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T *total) {
+    __shared__ T warp_sums[SCAN_THREADS / 32];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int32_t x = v;
+    T x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        T y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
     if (lane == 31) warp_sums[wid] = x;
     __syncthreads();
     if (wid == 0) {
-        int32_t w = lane < SCAN_THREADS / 32 ? warp_sums[lane] : 0;
+        T w = lane < SCAN_THREADS / 32 ? warp_sums[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            T y = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += y;
         }
         if (lane < SCAN_THREADS / 32) warp_sums[lane] = w;
     }
     __syncthreads();
-    int32_t off = wid > 0 ? warp_sums[wid - 1] : 0;
+    T off = wid > 0 ? warp_sums[wid - 1] : 0;
     *total = warp_sums[SCAN_THREADS / 32 - 1];
     __syncthreads();
     return off + x - v;
 }
 
-__global__ void scan_block_sums(const int32_t *__restrict__ data, int64_t n, int32_t *__restrict__ sums) {
+template <typename T>
+__global__ void scan_block_sums(const T *__restrict__ data, int64_t n, T *__restrict__ sums) {
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
-    int32_t acc = 0;
+    T acc = 0;
     for (int i = 0; i < SCAN_ITEMS; i++) {
         int64_t idx = base + (int64_t)i * SCAN_THREADS + threadIdx.x;
         if (idx < n) acc += data[idx];
     }
-    int32_t total;
-    (void)block_exclusive_scan(acc, &total);
+    T total;
+    (void)block_exclusive_scan<T>(acc, &total);
     if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
-__global__ void scan_block_apply(int32_t *__restrict__ data, int64_t n, const int32_t *__restrict__ offs,
-                                 int32_t *__restrict__ d_total, int64_t nblocks) {
+template <typename T>
+__global__ void scan_block_apply(T *__restrict__ data, int64_t n, const T *__restrict__ offs, T *__restrict__ d_total,
+                                 int64_t nblocks) {
     // each thread owns SCAN_ITEMS consecutive elements
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
-    int32_t v[SCAN_ITEMS];
-    int32_t s = 0;
+    T v[SCAN_ITEMS];
+    T s = 0;
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; i++) {
         int64_t idx = base + i;
         v[i] = idx < n ? data[idx] : 0;
         s += v[i];
     }
-    int32_t total;
-    int32_t ex = block_exclusive_scan(s, &total) + (offs ? offs[blockIdx.x] : 0);
+    T total;
+    T ex = block_exclusive_scan<T>(s, &total) + (offs ? offs[blockIdx.x] : 0);
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; i++) {
         int64_t idx = base + i;
@@ -126,32 +129,41 @@ __global__ void scan_block_apply(int32_t *__restrict__ data, int64_t n, const in
     if (d_total && blockIdx.x == nblocks - 1 && threadIdx.x == SCAN_THREADS - 1) *d_total = ex;
 }
 
-pg_status pg_scan_exclusive(pg_graph *g, int32_t *data, int64_t n, int32_t *d_total, cudaStream_t s) {
+template <typename T>
+static pg_status scan_exclusive(pg_graph *g, T *data, int64_t n, T *d_total, cudaStream_t s) {
     if (n <= 0) {
-        if (d_total) PG_CUDA(cudaMemsetAsync(d_total, 0, sizeof(int32_t), s));
+        if (d_total) PG_CUDA(cudaMemsetAsync(d_total, 0, sizeof(T), s));
         return PG_OK;
     }
     int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (nb == 1) {
-        scan_block_apply<<<1, SCAN_THREADS, 0, s>>>(data, n, nullptr, d_total, 1);
+        scan_block_apply<T><<<1, SCAN_THREADS, 0, s>>>(data, n, nullptr, d_total, 1);
         pg_count_launches(1);
         PG_LAUNCH_CHECK();
         return PG_OK;
     }
-    int32_t *sums = nullptr;
-    PG_TRY(pg_alloc(nullptr, (void **)&sums, sizeof(int32_t) * nb, s));
-    scan_block_sums<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(data, n, sums);
+    T *sums = nullptr;
+    PG_TRY(pg_alloc(nullptr, (void **)&sums, sizeof(T) * nb, s));
+    scan_block_sums<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(data, n, sums);
     pg_count_launches(1);
     pg_status st = PG_OK;
     if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
-    if (st == PG_OK) st = pg_scan_exclusive(g, sums, nb, nullptr, s);
+    if (st == PG_OK) st = scan_exclusive<T>(g, sums, nb, nullptr, s);
     if (st == PG_OK) {
-        scan_block_apply<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(data, n, sums, d_total, nb);
+        scan_block_apply<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(data, n, sums, d_total, nb);
         pg_count_launches(1);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     }
     cudaFreeAsync(sums, s);
     return st;
+}
+
+pg_status pg_scan_exclusive(pg_graph *g, int32_t *data, int64_t n, int32_t *d_total, cudaStream_t s) {
+    return scan_exclusive<int32_t>(g, data, n, d_total, s);
+}
+
+pg_status pg_scan_exclusive64(pg_graph *g, int64_t *data, int64_t n, int64_t *d_total, cudaStream_t s) {
+    return scan_exclusive<int64_t>(g, data, n, d_total, s);
 }
 
 // ------------------------------------------------------------------ radix sort
