@@ -155,3 +155,20 @@ def test_autograd_function(pg):
     ref = oracle.adjoint(rec, nbr, 6, rec["L0"], dI, rec["first"], rec["bg"], sc.spp, sc.width, sc.height)
     assert adj_err(sig.grad.cpu().numpy(), ref["grad_sigma_s"]) <= ADJ_TOL
     assert adj_err(g.grad.cpu().numpy(), ref["grad_g"]) <= ADJ_TOL
+
+
+def test_adjoint_dense_forward_scattering(pg):
+    """The dense workload's regime (albedo 0.999, g = 0.9, area light plus
+    environment) at a size the FP64 oracle's adjoint runs in seconds."""
+    sc = pgrec.CLOUD256_DENSE.with_(grid_res=48, width=24, height=24, spp=2, iters=20, max_depth=64)
+    T = sc.iters
+    rec = pgrec.trace(sc)
+    q = oracle.quantize(rec["px"], rec["py"], rec["pz"], (0, 0, 0), (1, 1, 1))
+    nbr = oracle.knn(q, sc.k)
+    base = oracle.forward(rec, rec["first"], rec["bg"], sc.spp, sc.width, sc.height, sc.k, T, nbr=nbr)
+    _, dI = oracle.image_loss(base["image"], 0.9 * base["image"])
+    ref = oracle.adjoint(rec, nbr, T, rec["L0"], dI, rec["first"], rec["bg"], sc.spp, sc.width, sc.height)
+    for mode in (0, 2):
+        got = _gpu_adjoint(pg, rec, sc, T, dI, recompute=mode, want_g=True)
+        assert adj_err(got["grad_sigma_s"], ref["grad_sigma_s"]) <= ADJ_TOL
+        assert adj_err(got["grad_g"], ref["grad_g"]) <= ADJ_TOL
