@@ -196,8 +196,8 @@ def run_gpu(args):
         a_T = solver.time_adjoint(sc.iters, sc.spp, sc.width, sc.height, first_d)
         a_1 = solver.time_adjoint(1, sc.spp, sc.width, sc.height, first_d)
         ts_ms = (a_T - a_1) / (sc.iters - 1)
-        ts_bytes = nnz * 8 + info["n_active"] * 24
-        others["tsweep_kernel<float,4,8,6>"] = {
+        ts_bytes = nnz * 8 + info["n_active"] * 28
+        others["tsweep_pf_kernel<float,4>"] = {
             "launch_ms": ts_ms, "algorithmic_bytes_per_launch": ts_bytes,
             "achieved": ts_bytes / (ts_ms / 1e3) / 1e9, "frac": ts_bytes / (ts_ms / 1e3) / 1e9 / peak,
             "launches_per_step": sc.iters + 1}

@@ -190,10 +190,8 @@ __global__ void seed_kernel(const int32_t *__restrict__ first, const float *__re
 
 // ------------------------------------------------------------------ reverse sweep (stored transpose)
 // Four lanes per column c: mu_out[c] = sum_e tW[e] us_in[trow[e]] over the
-// column's entries (rows ascending). Each lane loads all of its (up to 8)
-// entries, two per 16-byte load, before using them, so a column costs one
-// round trip, and each
-// block walks one contiguous chunk of columns (neighbouring columns draw on
+// column's entries (rows ascending), two entries per 16-byte load, each block
+// walking one contiguous chunk of columns (neighbouring columns draw on
 // neighbouring rows). When y_t is given it also accumulates
 // G[c] += mu_in[c] y_t[c] (and B[c] += mu_in[c] when B is given); those
 // column scalars are loaded up front, one per lane, so they travel with the
@@ -201,85 +199,101 @@ __global__ void seed_kernel(const int32_t *__restrict__ first, const float *__re
 // written only when it differs from mu_out.
 static constexpr int TS_THREADS = 256;
 
-template <typename WT, int TS_LPC, int TS_PER_LANE, int MINB>
-__global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_kernel(
+// The sweep is software-pipelined: the first pass of entries
+// (up to 32) of the next column group is loaded before this group's gathers,
+// with the column extents two groups ahead, so a column's DRAM round trip
+// overlaps the previous one's L2 round trip. Columns longer than 32 entries
+// take their remaining passes unpipelined.
+template <typename WT, int MINB>
+__global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_pf_kernel(
     const int64_t *__restrict__ tptr, const int2 *__restrict__ tent,
     const float *__restrict__ us_in, const float *__restrict__ mu_in, const float *__restrict__ y_t,
     const float *__restrict__ rscale, int64_t ncols, int write_out, float *__restrict__ mu_out,
     float *__restrict__ us_out, float *__restrict__ G, float *__restrict__ B) {
-    constexpr int CPB = TS_THREADS / TS_LPC; // columns per block per iteration
-    constexpr int SV = (4 + TS_LPC - 1) / TS_LPC; // column scalars per lane
+    constexpr int LPC = 4, PAIRS = 4; // 4 lanes x 4 pairs = 32 entries per pass
+    constexpr int CPB = TS_THREADS / LPC;
     const int lane = threadIdx.x & 31;
-    const int q = lane & (TS_LPC - 1);
-    const int lead = lane & ~(TS_LPC - 1);
+    const int q = lane & (LPC - 1);
+    const int lead = lane & ~(LPC - 1);
     const bool acc_g = y_t != nullptr;
     const int64_t chunk = ((ncols + gridDim.x - 1) / gridDim.x + CPB - 1) / CPB * CPB;
     const int64_t c0 = (int64_t)blockIdx.x * chunk;
     const int64_t c1 = min(ncols, c0 + chunk);
-    // each iteration prefetches the next one's column extents, so the entry
-    // loads never wait behind a load of the row pointers
-    int64_t pa = 0, pb = 0;
-    if (write_out && c0 + threadIdx.x / TS_LPC < c1) {
-        pa = tptr[c0 + threadIdx.x / TS_LPC];
-        pb = tptr[c0 + threadIdx.x / TS_LPC + 1];
+    const int cl = threadIdx.x / LPC;
+    auto extent = [&](int64_t c, int64_t &a, int64_t &b) {
+        a = b = 0;
+        if (write_out && c < c1) {
+            a = tptr[c];
+            b = tptr[c + 1];
+        }
+    };
+    auto first_pass = [&](int64_t a, int64_t b, int4 (&ent)[PAIRS]) {
+#pragma unroll
+        for (int u = 0; u < PAIRS; u++) {
+            const int64_t e = a + 2 * q + 2 * LPC * u;
+            ent[u] = e < b ? __ldcs(reinterpret_cast<const int4 *>(tent + e)) : make_int4(-1, 0, -1, 0);
+        }
+    };
+    int64_t a1, b1, a2, b2; // extents of the next group and the one after
+    int4 en[PAIRS];         // first pass of the next group
+    {
+        int64_t a0, b0;
+        extent(c0 + cl, a0, b0);
+        first_pass(a0, b0, en);
+        extent(c0 + CPB + cl, a1, b1);
+        // the current group's extent travels with its entries
+        a2 = a0;
+        b2 = b0;
     }
     for (int64_t base = c0; base < c1; base += CPB) {
-        const int64_t c = base + threadIdx.x / TS_LPC;
+        const int64_t c = base + cl;
         const bool ok = c < c1;
-        const int64_t ca = pa, cb = pb;
-        if (write_out) {
-            const int64_t cn = c + CPB;
-            pa = pb = 0;
-            if (cn < c1) {
-                pa = tptr[cn];
-                pb = tptr[cn + 1];
-            }
-        }
-        // column scalars k = 0 mu_in, 1 y_t, 2 G, 3 B: scalar k is loaded by
-        // lane k % LPC of the column into its slot k / LPC; lane 0 also loads
-        // the row scale
-        float sv[SV], rs = 1.0f;
+        const int64_t ca = a2, cb = b2; // this group's extent
+        int4 ent[PAIRS];
 #pragma unroll
-        for (int i = 0; i < SV; i++) {
-            const int k = q + TS_LPC * i;
-            sv[i] = 0.0f;
-            if (ok && acc_g) {
-                if (k == 0) sv[i] = mu_in[c];
-                else if (k == 1) sv[i] = __ldcs(y_t + c);
-                else if (k == 2) sv[i] = G[c];
-                else if (k == 3 && B) sv[i] = B[c];
-            }
+        for (int u = 0; u < PAIRS; u++) ent[u] = en[u];
+        // next group's first pass, and the extent of the group after it
+        first_pass(a1, b1, en);
+        a2 = a1;
+        b2 = b1;
+        extent(base + 2 * CPB + cl, a1, b1);
+        float sv = 0.0f, rs = 1.0f; // column scalars: lane 0 mu_in, 1 y_t, 2 G, 3 B
+        if (ok && acc_g) {
+            if (q == 0) sv = mu_in[c];
+            else if (q == 1) sv = __ldcs(y_t + c);
+            else if (q == 2) sv = G[c];
+            else if (B) sv = B[c];
         }
         if (ok && rscale && write_out && q == 0) rs = __ldcs(rscale + c);
         float acc = 0.0f;
         if (ok && write_out) {
-            // columns start on even entries: lane q takes the pairs 2q + 2 LPC u
-            for (int64_t a = ca; a < cb; a += TS_LPC * TS_PER_LANE) {
-                int4 ent[TS_PER_LANE / 2];
 #pragma unroll
-                for (int u = 0; u < TS_PER_LANE / 2; u++) {
-                    const int64_t e = a + 2 * q + 2 * TS_LPC * u;
-                    ent[u] = e < cb ? __ldcs(reinterpret_cast<const int4 *>(tent + e)) : make_int4(-1, 0, -1, 0);
-                }
+            for (int u = 0; u < PAIRS; u++) {
+                if (ent[u].x >= 0) acc = fmaf(wfrom<WT>(ent[u].y), __ldg(us_in + ent[u].x), acc);
+                if (ent[u].z >= 0) acc = fmaf(wfrom<WT>(ent[u].w), __ldg(us_in + ent[u].z), acc);
+            }
+            for (int64_t a = ca + 2 * LPC * PAIRS; a < cb; a += 2 * LPC * PAIRS) {
+                int4 more[PAIRS];
+                first_pass(a, cb, more);
 #pragma unroll
-                for (int u = 0; u < TS_PER_LANE / 2; u++) {
-                    if (ent[u].x >= 0) acc = fmaf(wfrom<WT>(ent[u].y), __ldg(us_in + ent[u].x), acc);
-                    if (ent[u].z >= 0) acc = fmaf(wfrom<WT>(ent[u].w), __ldg(us_in + ent[u].z), acc);
+                for (int u = 0; u < PAIRS; u++) {
+                    if (more[u].x >= 0) acc = fmaf(wfrom<WT>(more[u].y), __ldg(us_in + more[u].x), acc);
+                    if (more[u].z >= 0) acc = fmaf(wfrom<WT>(more[u].w), __ldg(us_in + more[u].z), acc);
                 }
             }
         }
 #pragma unroll
-        for (int o = TS_LPC / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        const float m = __shfl_sync(0xffffffffu, sv[0], lead);
-        const float yv = __shfl_sync(0xffffffffu, sv[1 / TS_LPC], lead + 1 % TS_LPC);
+        for (int o = LPC / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const float m = __shfl_sync(0xffffffffu, sv, lead);
+        const float yv = __shfl_sync(0xffffffffu, sv, lead + 1);
         if (ok) {
             if (q == 0 && write_out) {
                 mu_out[c] = acc;
                 if (us_out) us_out[c] = acc * rs;
             }
             if (acc_g) {
-                if (q == 2 % TS_LPC) G[c] = fmaf(m, yv, sv[2 / TS_LPC]);
-                if (q == 3 % TS_LPC && B) B[c] = sv[3 / TS_LPC] + m;
+                if (q == 2) G[c] = fmaf(m, yv, sv);
+                if (q == 3 && B) B[c] = sv + m;
             }
         }
     }
@@ -599,15 +613,16 @@ static pg_status adjoint_store(pg_graph *g, float *us0, float *mu_a, float *mu_b
     const int64_t stride = n + 1;
     const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
     if (!g->tA.ptr) PG_TRY(build_transpose<WT>(g, s));
-    // four lanes per column, up to 8 entries per lane in flight; 40 registers
-    // (6 blocks of 256 per SM) keep the entries and column scalars unspilled
+    // four lanes per column, software-pipelined (next group's first 32
+    // entries in flight during this group's gathers); 64 registers, 4 blocks
+    // of 256 per SM
     int64_t need = (na * 4 + TS_THREADS - 1) / TS_THREADS;
-    int64_t cap = (int64_t)pg_num_sms() * 6;
+    int64_t cap = (int64_t)pg_num_sms() * 4;
     const int tb = (int)(need < cap ? (need > 0 ? need : 1) : cap);
     auto tsweep = [&](const pg_tcsr &t, const float *us_in, const float *mu_in, const float *y_t, int wo,
                       float *mu_out, float *us_out) {
-        tsweep_kernel<WT, 4, 8, 6><<<tb, TS_THREADS, 0, s>>>(t.ptr, t.ent, us_in, mu_in, y_t, rs, na, wo, mu_out,
-                                                             us_out, G, B);
+        tsweep_pf_kernel<WT, 4><<<tb, TS_THREADS, 0, s>>>(t.ptr, t.ent, us_in, mu_in, y_t, rs, na, wo, mu_out, us_out,
+                                                          G, B);
     };
     // mu_t lives in slice t of the history when one is kept, else ping-pong
     auto mu_slot = [&](int t) { return muhist ? muhist + (int64_t)t * stride : ((t & 1) ? mu_b : mu_a); };
