@@ -181,8 +181,9 @@ def run_gpu(args):
                 for nm in stage_names if not (args.no_adjoint and nm == "adjoint")}
 
     # ---- sweep kernel roofline: the propagate stage of the timed steps minus its
-    # prologue/epilogue (pg_propagate with zero sweeps), per sweep
-    prop_base = solver.time_propagate(0, reps=5, keep_history=not args.no_adjoint)
+    # prologue/epilogue (pg_propagate with zero sweeps, started on an idle
+    # device as in the step, where the aggregation synchronised), per sweep
+    prop_base = solver.time_propagate(0, reps=5, keep_history=not args.no_adjoint, from_idle=True)
     sweep_ms = (stage_ms["propagate"] - prop_base) / sc.iters
     wb = 4
     bytes_sweep = nnz * (4 + wb) + info["n_active"] * 12

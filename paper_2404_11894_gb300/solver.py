@@ -57,12 +57,25 @@ class Solver:
             mark("adjoint", 1)
         return img
 
-    def time_propagate(self, iters: int, reps: int = 3, keep_history: bool = False) -> float:
-        """Mean device time (ms) of pg_propagate on the current graph."""
+    def time_propagate(self, iters: int, reps: int = 3, keep_history: bool = False, from_idle: bool = False) -> float:
+        """Mean device time (ms) of pg_propagate on the current graph. With
+        ``from_idle`` each call starts on an idle device, as it does inside a
+        step (after the aggregation's synchronisation), so the time includes
+        the same wait for the host to issue the call's first work."""
         s = torch.cuda.current_stream()
         L = torch.empty_like(self._L0)
         pg_propagate(self.graph, self._L0, iters, out=L, keep_history=keep_history)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if from_idle:
+            tot = 0.0
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                e0.record(s)
+                pg_propagate(self.graph, self._L0, iters, out=L, keep_history=keep_history)
+                e1.record(s)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            return tot / reps
         e0.record(s)
         for _ in range(reps):
             pg_propagate(self.graph, self._L0, iters, out=L, keep_history=keep_history)
