@@ -35,6 +35,15 @@ UNIT = "edge-updates/s"
 L2_BYTES = 129 * 2 ** 20
 
 
+WORKLOADS = ("cloud128", "dense256")
+
+
+def _scene(name):
+    import pgrec
+
+    return {"cloud128": pgrec.CLOUD128, "dense256": pgrec.CLOUD256_DENSE}[name]
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -118,7 +127,8 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     from paper_2404_11894_gb300.dist import combine_throughput, rank_seed
 
-    sc = pgrec.CLOUD128
+    sc = _scene(args.workload)
+    wdtype = sc.weight_dtypes[0] if sc.weight_dtypes else "f32"
     if args.scale != 1.0:  # smaller image of the same scene (profiling captures)
         sc = sc.with_(width=int(sc.width * args.scale), height=int(sc.height * args.scale))
     if world > 1:  # independent renders (replicas), one per rank
@@ -140,7 +150,7 @@ def run_gpu(args):
     dev_in = {k: v.to(dev) for k, v in host.items()}
     dev_target = host_target.to(dev)
     V = pg.Vertices({k: dev_in[k] for k in pg.VERTEX_F32 + ("e_delta", "succ")})
-    solver = pg.Solver(k=sc.k, iters=sc.iters, wdtype="f32", adjoint=not args.no_adjoint,
+    solver = pg.Solver(k=sc.k, iters=sc.iters, wdtype=wdtype, adjoint=not args.no_adjoint,
                        recompute_weights=args.adjoint_mode, want_g=False)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
@@ -185,11 +195,16 @@ def run_gpu(args):
     # device as in the step, where the aggregation synchronised), per sweep
     prop_base = solver.time_propagate(0, reps=5, keep_history=not args.no_adjoint, from_idle=True)
     sweep_ms = (stage_ms["propagate"] - prop_base) / sc.iters
-    wb = 4
-    bytes_sweep = nnz * (4 + wb) + info["n_active"] * 12
+    # the same kernel outside the step, back to back (a diagnostic beside the in-step figure)
+    iso = {}
+    for hist in (False, True):
+        iso["history" if hist else "ping_pong"] = (solver.time_propagate(sc.iters, reps=3, keep_history=hist)
+                                                   - solver.time_propagate(0, reps=5, keep_history=hist)) / sc.iters
+    w16 = wdtype != "f32"
+    bytes_sweep = nnz * (4 + (2 if w16 else 4)) + info["n_active"] * (16 if w16 else 12)
     achieved = bytes_sweep / (sweep_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
-    traffic = _profile_traffic("sweep_f32", n)
+    traffic = _profile_traffic("sweep_f32", n) if not w16 else None
     others = {}
     if not args.no_adjoint and args.adjoint_mode == 0:
         # transposed (reverse) sweep: adjoint time after T and after 1 forward sweeps
@@ -197,8 +212,8 @@ def run_gpu(args):
         a_T = solver.time_adjoint(sc.iters, sc.spp, sc.width, sc.height, first_d)
         a_1 = solver.time_adjoint(1, sc.spp, sc.width, sc.height, first_d)
         ts_ms = (a_T - a_1) / (sc.iters - 1)
-        ts_bytes = nnz * 8 + info["n_active"] * 28
-        others["tsweep_pf_kernel<float,4>"] = {
+        ts_bytes = nnz * 8 + info["n_active"] * (32 if w16 else 28)
+        others["tsweep_pf_kernel<%s,4>" % ("float" if not w16 else wdtype)] = {
             "launch_ms": ts_ms, "algorithmic_bytes_per_launch": ts_bytes,
             "achieved": ts_bytes / (ts_ms / 1e3) / 1e9, "frac": ts_bytes / (ts_ms / 1e3) / 1e9 / peak,
             "launches_per_step": sc.iters + 1}
@@ -219,7 +234,7 @@ def run_gpu(args):
 
     # ---- 16-bit weights: propagation rate and error against FP32 (same inputs)
     prec = {}
-    if not args.quick:
+    if not args.quick and not w16:
         img32 = solver.last_image.clone()
         for wd in ("bf16", "f16"):
             s16 = pg.Solver(k=sc.k, iters=sc.iters, wdtype=wd, adjoint=False)
@@ -257,7 +272,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": sc.name, "vertices": n, "paths": P, "k": sc.k, "iters": sc.iters,
-                   "weights": "f32", "nnz_per_sweep": nnz, "n_active": info["n_active"],
+                   "weights": wdtype, "nnz_per_sweep": nnz, "n_active": info["n_active"],
                    "sweeps_per_step": sweeps_per_step, "edge_updates_per_step": edge_updates_step,
                    "step": "build+aggregate+propagate(history)+gather" + (
                        "" if args.no_adjoint else "+adjoint(sigma_s, per-voxel albedo)"),
@@ -268,9 +283,15 @@ def run_gpu(args):
         "stages_ms": stage_ms,
         "adjoint_with_g_gradient_ms": adj_g_ms,
         "propagate_edge_updates_per_s": nnz / (sweep_ms / 1e3),
+        "build_vertices_per_s": n / (stage_ms["build"] / 1e3),
+        # two phase-function evaluations per neighbour entry in each of the two
+        # aggregation passes, and two per row for the non-aggregated direct term
+        "aggregate_hg_evals_per_s": (4 * info["k"] * n + 2 * n) / (stage_ms["aggregate"] / 1e3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "sweep_pf_kernel<16,float,1024,1>",
-                     "sweep_ms": sweep_ms, "algorithmic_bytes_per_launch": bytes_sweep, "peak_kind": peak_kind,
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "sweep_kernel<16,%s,1024,2,2>" % wdtype if w16 else "sweep_pf_kernel<16,float,1024,1>",
+                     "sweep_ms": sweep_ms, "sweep_ms_outside_step": iso,
+                     "algorithmic_bytes_per_launch": bytes_sweep, "peak_kind": peak_kind,
                      "other_kernels": others},
         "precision": prec,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -388,6 +409,9 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the 16-bit weight runs")
     ap.add_argument("--oracle-stride", type=int, default=10)
     ap.add_argument("--scale", type=float, default=1.0, help="image resolution factor (profiling only)")
+    ap.add_argument("--workload", default="cloud128", choices=WORKLOADS,
+                    help="cloud128: the headline workload; dense256: the 158.7M-vertex BF16 workload "
+                         "(stage times at scale, not the headline line)")
     ap.add_argument("--adjoint-mode", type=int, default=0, choices=[0, 1, 2],
                     help="reverse sweep: 0 transposed copy, 1 recomputed weights, 2 atomic scatter")
     args = ap.parse_args()

@@ -262,6 +262,12 @@ static void launch_pf_cfg(const pg_graph *g, const float *b, const float *yin, f
                                                             g->n_active, ctrl, partials, resid, t, tol);
 }
 
+// slot n of each of `slices` vectors of n+1 floats
+__global__ void zero_slots_kernel(float *__restrict__ v, int64_t n, int64_t slices) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < slices) v[t * (n + 1) + n] = 0.0f;
+}
+
 // y0[row of succ(v)] = L0[v]  (L+_v is the radiance that succ(v) sends back)
 __global__ void init_y_kernel(const float *__restrict__ L0, const int32_t *__restrict__ c2m,
                               const int32_t *__restrict__ succ_m, const int32_t *__restrict__ m2r, int64_t n,
@@ -391,7 +397,12 @@ extern "C" pg_status pg_propagate(pg_graph *g, const float *c, const float *L0, 
         pg_free(g, (void **)&g->hist, 4 * (size_t)(n + 1) * (size_t)(g->hist_cap + 1));
         g->hist_cap = -1;
         PG_TRY(pg_alloc(g, (void **)&g->hist, 4 * (size_t)(n + 1) * (size_t)(iters + 1), s));
-        PG_CUDA(cudaMemsetAsync(g->hist, 0, 4 * (size_t)(n + 1) * (size_t)(iters + 1), s));
+        // only each slice's zero slot needs a value up front: a sweep writes
+        // rows [0, n_active) of its slice, init_y those of slice 0, and no
+        // reader touches rows [n_active, n)
+        zero_slots_kernel<<<pg_blocks(iters + 1, 256), 256, 0, s>>>(g->hist, n, iters + 1);
+        pg_count_launches(1);
+        PG_LAUNCH_CHECK();
         g->hist_cap = iters;
     }
     g->hist_iters = -1;
