@@ -146,6 +146,126 @@ def knn(q, k, r2_max=None, workers=1):
 
 
 # --------------------------------------------------------------------------
+# Cluster neighbourhoods (Section 3.1, Section 4 "Path graph solver")
+# --------------------------------------------------------------------------
+GOLDEN_GAMMA = 0x9E3779B97F4A7C15
+
+
+def splitmix64(seed, i):
+    """Output i (0-based) of the SplitMix64 generator started from ``seed``:
+    z = seed + (i + 1) * 0x9E3779B97F4A7C15 (mod 2^64) through the published
+    finaliser (xor-shift 30, multiply, xor-shift 27, multiply, xor-shift 31).
+    Vectorised over i. Pinned by the generator's published first outputs."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (np.asarray(i, np.uint64) + np.uint64(1)) * np.uint64(GOLDEN_GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def morton_order(q, level):
+    """Vertex indices ordered by the Morton code of their hash-grid cell at
+    ``level`` (2^level cells per axis; cell = q >> (21 - level); bit b of
+    x, y, z goes to bit 3b, 3b+1, 3b+2 of the code), ties by caller index."""
+    cell = np.asarray(q, np.int64) >> (QBITS - level)
+    key = np.zeros(len(cell), np.int64)
+    for b in range(level):
+        for a in range(3):
+            key |= ((cell[:, a] >> b) & 1) << (3 * b + a)
+    return np.lexsort((np.arange(len(cell)), key))
+
+
+def nearest_centre(q, centres):
+    """Index into ``centres`` of each vertex's nearest centre: smallest exact
+    int64 squared distance, ties by the smaller caller index of the centre.
+    A k-d tree (library kNN primitive) proposes candidates; each set is
+    re-ordered exactly and widened until it provably holds every centre that
+    ties with the nearest. Pinned against brute force."""
+    from scipy.spatial import cKDTree
+
+    q = np.asarray(q, np.int64)
+    centres = np.asarray(centres, np.int64)
+    m = len(centres)
+    out = np.empty(len(q), np.int64)
+    tree = cKDTree(q[centres].astype(np.float64))
+    todo = np.arange(len(q))
+    kk = min(m, 4)
+    while todo.size:
+        _, cand = tree.query(q[todo].astype(np.float64), k=kk)
+        cand = np.asarray(cand, np.int64).reshape(len(todo), kk)
+        d2 = ((q[centres[cand]] - q[todo][:, None, :]) ** 2).sum(axis=2)
+        order = np.lexsort((centres[cand], d2), axis=1)
+        best = np.take_along_axis(cand, order[:, :1], axis=1)[:, 0]
+        dbest = np.take_along_axis(d2, order[:, :1], axis=1)[:, 0]
+        ok = (kk == m) | (d2.max(axis=1) > dbest)
+        out[todo[ok]] = best[ok]
+        todo = todo[~ok]
+        kk = min(m, kk * 2)
+    return out
+
+
+def nearest_centre_brute(q, centres):
+    """Definition of :func:`nearest_centre` by brute force (O(n m))."""
+    q = np.asarray(q, np.int64)
+    centres = np.asarray(centres, np.int64)
+    out = np.empty(len(q), np.int64)
+    for v in range(len(q)):
+        d2 = ((q[centres] - q[v]) ** 2).sum(axis=1)
+        out[v] = np.lexsort((centres, d2))[0]
+    return out
+
+
+def cluster_graph(q, k, K, seed, level):
+    """Neighbourhoods from the paper's disjoint clusters (Section 3.1: about
+    N/K centres, every point joins the nearest one, large clusters are split
+    until the sizes are even; Section 4: centres drawn at random, nearest-
+    centre search on the hash grid), read as:
+      1. vertex v is a centre iff splitmix64(seed, v) < floor((2^64 - 1) / K)
+         (expected n/K centres); with none drawn, vertex 0 is the centre;
+      2. every vertex joins its nearest centre (:func:`nearest_centre`);
+      3. a cluster of S > k members is cut into P = ceil(S / k) parts: with
+         its members in Morton order (:func:`morton_order` at ``level``) the
+         i-th (0-based) goes to part floor(i P / S), so sizes differ by at
+         most one and none exceeds k;
+      4. N(s) = s, then the other members of s's part in Morton order, -1
+         padded to width k.
+    Returns (nbr, part) with part[v] an id shared by the members of a part.
+    Pinned by the partition invariants, brute-force nearest centres and the
+    generator's published outputs."""
+    q = np.asarray(q, np.int64)
+    n = len(q)
+    nbr = -np.ones((n, k), np.int64)
+    if n == 0:
+        return nbr, np.zeros(0, np.int64)
+    thr = np.uint64((2 ** 64 - 1) // K)
+    centres = np.nonzero(splitmix64(seed, np.arange(n)) < thr)[0]
+    if len(centres) == 0:
+        centres = np.array([0])
+    owner = nearest_centre(q, centres)            # index into centres
+    rank = np.empty(n, np.int64)
+    order = morton_order(q, level)
+    rank[order] = np.arange(n)                    # Morton position of each vertex
+    members = np.lexsort((rank, owner))           # by cluster, then Morton order
+    bounds = np.flatnonzero(np.r_[True, owner[members][1:] != owner[members][:-1], True])
+    part = np.empty(n, np.int64)
+    next_id = 0
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        mem = members[a:b]
+        S = b - a
+        P = -(-S // k)
+        pidx = (np.arange(S) * P) // S
+        for p in range(P):
+            grp = mem[pidx == p]
+            part[grp] = next_id
+            next_id += 1
+            for s in grp:
+                others = grp[grp != s]
+                nbr[s, 0] = s
+                nbr[s, 1:1 + len(others)] = others
+    return nbr, part
+
+
+# --------------------------------------------------------------------------
 # Henyey-Greenstein phase function (Eq. standard-RTE's rho)
 # --------------------------------------------------------------------------
 def hg(o, d, g):

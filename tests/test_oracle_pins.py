@@ -346,3 +346,74 @@ def test_adjoint_matches_central_differences():
         sm[m] -= h * st[m]
         fd = (_loss(rec, nbr, T, target, sc, sigma_s=sp)[0] - _loss(rec, nbr, T, target, sc, sigma_s=sm)[0]) / (2 * h)
         assert adj["grad_albedo"][vx] == pytest.approx(fd, rel=1e-6, abs=1e-12)
+
+
+# ---------------------------------------------------------------- cluster neighbourhoods
+def test_splitmix64_published_output():
+    """The generator's first output from seed 0 is the published 0xE220A8397B1DCDAF;
+    its top bits over many indices are uniform (the centre draw relies on it)."""
+    assert int(oracle.splitmix64(0, 0)) == 0xE220A8397B1DCDAF
+    top = oracle.splitmix64(12345, np.arange(1 << 16)) >> np.uint64(56)
+    counts = np.bincount(top.astype(np.int64), minlength=256)
+    assert counts.min() > 160 and counts.max() < 360  # mean 256, sd 16
+
+
+def test_morton_order_matches_bit_interleave():
+    rng = np.random.default_rng(8)
+    q = rng.integers(0, 1 << 21, size=(300, 3))
+    for level in (1, 3, 7):
+        cell = q >> (21 - level)
+
+        def code(c):
+            out = 0
+            for b in range(level):
+                for a in range(3):
+                    out |= ((int(c[a]) >> b) & 1) << (3 * b + a)
+            return out
+
+        keys = [code(c) for c in cell]
+        want = sorted(range(len(q)), key=lambda i: (keys[i], i))
+        np.testing.assert_array_equal(oracle.morton_order(q, level), want)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_nearest_centre_matches_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    for hi, n in ((5, 300), (1 << 21, 500)):
+        q = rng.integers(0, hi, size=(n, 3))  # the first case is full of ties
+        centres = np.sort(rng.choice(n, max(1, n // 9), replace=False))
+        np.testing.assert_array_equal(oracle.nearest_centre(q, centres), oracle.nearest_centre_brute(q, centres))
+
+
+@pytest.mark.parametrize("K,k", [(4, 8), (8, 8), (16, 16), (40, 16)])
+def test_cluster_graph_partition(K, k):
+    """Section 3.1's clusters as neighbourhoods: a partition into parts of at
+    most k points whose members share one neighbourhood (the part), each part
+    inside the cluster of its points' nearest centre, the parts of one cluster
+    even in size, about n/K centres."""
+    rng = np.random.default_rng(K)
+    n = 2000
+    q = rng.integers(0, 1 << 21, size=(n, 3))
+    level = 4
+    nbr, part = oracle.cluster_graph(q, k, K, seed=77, level=level)
+    thr = np.uint64((2 ** 64 - 1) // K)
+    centres = np.nonzero(oracle.splitmix64(77, np.arange(n)) < thr)[0]
+    assert abs(len(centres) - n / K) < 5 * np.sqrt(n / K)
+    owner = oracle.nearest_centre_brute(q, centres)
+    assert (nbr[:, 0] == np.arange(n)).all()
+    for p in np.unique(part):
+        mem = np.nonzero(part == p)[0]
+        assert 1 <= len(mem) <= k
+        assert len(np.unique(owner[mem])) == 1
+        for s in mem:
+            row = nbr[s][nbr[s] >= 0]
+            assert sorted(row.tolist()) == sorted(mem.tolist())
+            # others in Morton order
+            rank = np.empty(n, np.int64)
+            rank[oracle.morton_order(q, level)] = np.arange(n)
+            assert np.all(np.diff(rank[row[1:]]) > 0)
+    for c in np.unique(owner):
+        sizes = np.bincount(part[owner == c])
+        sizes = sizes[sizes > 0]
+        assert sizes.max() - sizes.min() <= 1
+        assert len(sizes) == -(-int((owner == c).sum()) // k)
