@@ -151,6 +151,7 @@ def run_gpu(args):
     dev_target = host_target.to(dev)
     V = pg.Vertices({k: dev_in[k] for k in pg.VERTEX_F32 + ("e_delta", "succ")})
     solver = pg.Solver(k=sc.k, iters=sc.iters, wdtype=wdtype, adjoint=not args.no_adjoint,
+                       cluster_size=args.clusters, cluster_seed=sc.seed,
                        recompute_weights=args.adjoint_mode, want_g=False)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
@@ -189,6 +190,9 @@ def run_gpu(args):
                                               device=dev)
     stage_ms = {nm: float(np.mean([m[nm][0].elapsed_time(m[nm][1]) for m in marks_all if m[nm][0].query()]))
                 for nm in stage_names if not (args.no_adjoint and nm == "adjoint")}
+
+    pt = rec["pt_image"].astype(np.float64)
+    solver_img_ratio = float(solver.last_image.double().mean()) / float(pt.mean()) if pt.mean() > 0 else None
 
     # ---- sweep kernel roofline: the propagate stage of the timed steps minus its
     # prologue/epilogue (pg_propagate with zero sweeps, started on an idle
@@ -277,10 +281,12 @@ def run_gpu(args):
                    "step": "build+aggregate+propagate(history)+gather" + (
                        "" if args.no_adjoint else "+adjoint(sigma_s, per-voxel albedo)"),
                    "adjoint_mode": ["transposed", "recompute", "scatter"][args.adjoint_mode],
+                   "neighbourhoods": "clusters K=%d" % args.clusters if args.clusters else "kNN",
                    "l2": "inputs larger than L2 (vertex records %.0f MB > 129 MB)" % (
                        sum(int(v.numel() * v.element_size()) for v in dev_in.values()) / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "stages_ms": stage_ms,
+        "image_mean_over_path_tracer": solver_img_ratio,
         "adjoint_with_g_gradient_ms": adj_g_ms,
         "propagate_edge_updates_per_s": nnz / (sweep_ms / 1e3),
         "build_vertices_per_s": n / (stage_ms["build"] / 1e3),
@@ -409,6 +415,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the 16-bit weight runs")
     ap.add_argument("--oracle-stride", type=int, default=10)
     ap.add_argument("--scale", type=float, default=1.0, help="image resolution factor (profiling only)")
+    ap.add_argument("--clusters", type=int, default=0, metavar="K",
+                    help="neighbourhoods from the paper's disjoint clusters of expected size K (0: kNN)")
     ap.add_argument("--workload", default="cloud128", choices=WORKLOADS,
                     help="cloud128: the headline workload; dense256: the 158.7M-vertex BF16 workload "
                          "(stage times at scale, not the headline line)")

@@ -100,6 +100,19 @@ typedef struct {
                            > r2_max; negative = no radius limit */
     int32_t grid_level; /* hash-grid cells per axis = 2^grid_level (1..10);
                            0 = chosen from n and k */
+    int32_t cluster_size; /* 0: kNN neighbourhoods (below). K > 0: the paper's
+                           disjoint clusters of expected size K instead
+                           (Section 3.1, Section 4 "Path graph solver"):
+                           caller vertex v is a centre iff SplitMix64 output v
+                           of cluster_seed is below floor((2^64-1)/K) (caller
+                           vertex 0 if none is), every vertex joins its nearest
+                           centre (squared quantised distance, ties by the
+                           smaller caller index), and a cluster of S > k
+                           members, in Morton order, is cut into ceil(S/k)
+                           parts, member i going to part floor(i P / S);
+                           N(s) = s, then the other members of s's part in
+                           Morton order. r2_max is ignored. */
+    uint64_t cluster_seed;
 } pg_build_params;
 
 /* Neighbour edges E_N (Section 3.1: points exchange information with their
@@ -134,6 +147,7 @@ typedef struct {
     int64_t knn_exact;   /* queries the graph build resolved with its exact
                             (slow) neighbour search: sparse surroundings,
                             large distances or dense ties */
+    int64_t clusters;    /* cluster mode: number of neighbourhoods (parts) */
 } pg_graph_info;
 
 pg_status pg_graph_get_info(const pg_graph *g, pg_graph_info *info);

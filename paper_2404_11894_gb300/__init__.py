@@ -92,7 +92,9 @@ class Graph:
 
 
 def pg_build_graph(verts: Vertices, k: int, bbox_lo=(0.0, 0.0, 0.0), bbox_hi=(1.0, 1.0, 1.0), r2_max: int = -1,
-                   grid_level: int = 0, stream=None) -> Graph:
+                   grid_level: int = 0, cluster_size: int = 0, cluster_seed: int = 0, stream=None) -> Graph:
+    """kNN neighbourhoods, or with ``cluster_size`` K > 0 the paper's disjoint
+    clusters of expected size K (parts of at most k points)."""
     p = PgBuildParams()
     p.k = k
     for a in range(3):
@@ -100,6 +102,8 @@ def pg_build_graph(verts: Vertices, k: int, bbox_lo=(0.0, 0.0, 0.0), bbox_hi=(1.
         p.bbox_hi[a] = bbox_hi[a]
     p.r2_max = r2_max
     p.grid_level = grid_level
+    p.cluster_size = cluster_size
+    p.cluster_seed = cluster_seed
     h = ctypes.c_void_p()
     check(_LIB.pg_build_graph(ctypes.byref(verts.struct), verts.n, ctypes.byref(p), _stream_ptr(stream),
                               ctypes.byref(h)), "pg_build_graph")

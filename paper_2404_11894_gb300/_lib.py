@@ -24,14 +24,15 @@ class PgVertices(ctypes.Structure):
 
 class PgBuildParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("bbox_lo", ctypes.c_float * 3), ("bbox_hi", ctypes.c_float * 3),
-                ("r2_max", ctypes.c_int64), ("grid_level", ctypes.c_int32)]
+                ("r2_max", ctypes.c_int64), ("grid_level", ctypes.c_int32), ("cluster_size", ctypes.c_int32),
+                ("cluster_seed", ctypes.c_uint64)]
 
 
 class PgGraphInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("k", ctypes.c_int32), ("row_width", ctypes.c_int32),
                 ("grid_level", ctypes.c_int32), ("aggregated", ctypes.c_int32), ("n_active", ctypes.c_int64),
                 ("nnz_swept", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("weight_dtype", ctypes.c_int32),
-                ("history_iters", ctypes.c_int32), ("knn_exact", ctypes.c_int64)]
+                ("history_iters", ctypes.c_int32), ("knn_exact", ctypes.c_int64), ("clusters", ctypes.c_int64)]
 
 
 EXPORTS = ("pg_build_graph", "pg_graph_neighbors", "pg_graph_get_info", "pg_aggregate", "pg_propagate",

@@ -425,6 +425,7 @@ extern "C" pg_status pg_build_graph(const pg_vertices *v, int64_t n, const pg_bu
     if (n < 0 || n >= INT32_MAX) return PG_ERR_INVALID_ARG;
     if (p->k < 1 || p->k > PG_MAX_K) return PG_ERR_UNSUPPORTED;
     if (p->grid_level < 0 || p->grid_level > 10) return PG_ERR_UNSUPPORTED;
+    if (p->cluster_size < 0) return PG_ERR_INVALID_ARG;
     if (n > 0 && (!v || !v->px || !v->py || !v->pz)) return PG_ERR_INVALID_ARG;
     float span = 0.0f;
     for (int a = 0; a < 3; a++) {
@@ -492,7 +493,9 @@ extern "C" pg_status pg_build_graph(const pg_vertices *v, int64_t n, const pg_bu
             pg_count_launches(1);
             if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
         }
-        if (st == PG_OK) st = pg_launch_knn(g, s);
+        if (st == PG_OK)
+            st = p->cluster_size > 0 ? pg_launch_clusters(g, keys, p->cluster_size, p->cluster_seed, s)
+                                     : pg_launch_knn(g, s);
     }
     if (keys) cudaFreeAsync(keys, s);
     if (qrec_c) cudaFreeAsync(qrec_c, s);
@@ -547,6 +550,7 @@ extern "C" pg_status pg_graph_get_info(const pg_graph *g, pg_graph_info *info) {
     info->weight_dtype = (int32_t)g->wdtype;
     info->history_iters = g->hist_iters;
     info->knn_exact = g->knn_exact;
+    info->clusters = g->clusters;
     return PG_OK;
 }
 

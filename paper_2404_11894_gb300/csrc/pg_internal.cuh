@@ -47,6 +47,7 @@ struct pg_graph {
     int2 *cell_se = nullptr;       // (start, count) per cell, index x + G (y + G z)
     int32_t *nbr = nullptr;        // [n][kp], m-space neighbour ids, -1 padded; slot 0 = self
     int64_t knn_exact = 0;         // queries resolved by the exact neighbour kernel
+    int64_t clusters = 0;          // cluster mode: number of parts (neighbourhoods)
 
     // ---- aggregation ----
     int aggregated = 0;
@@ -254,5 +255,7 @@ static inline size_t pg_wbytes(pg_wdtype t) { return t == PG_W_F32 ? 4 : 2; }
 
 // Launchers implemented in the per-stage translation units.
 pg_status pg_launch_knn(pg_graph *g, cudaStream_t s);
+// cluster neighbourhoods (keys: the vertices' sorted Morton cell keys)
+pg_status pg_launch_clusters(pg_graph *g, const uint32_t *keys, int32_t K, uint64_t seed, cudaStream_t s);
 void pg_free_transposes(pg_graph *g); // releases both transposes (weights changed)
 pg_status pg_launch_aggregate(pg_graph *g, float *c_out, float *D_out, cudaStream_t s);

@@ -12,13 +12,16 @@ class Solver:
 
     k: neighbours per vertex (self included); iters: propagation sweeps;
     wdtype: 'f32' | 'bf16' | 'f16' edge weights; adjoint: also run
-    pg_propagate_adjoint for the loss 1/2 |image - target|^2.
+    pg_propagate_adjoint for the loss 1/2 |image - target|^2;
+    cluster_size: 0 for kNN neighbourhoods, K > 0 for the paper's disjoint
+    clusters of expected size K (parts of at most k points).
     """
 
     def __init__(self, k: int, iters: int, wdtype: str = "f32", adjoint: bool = True,
                  bbox_lo=(0.0, 0.0, 0.0), bbox_hi=(1.0, 1.0, 1.0), recompute_weights: int = 0,
-                 want_g: bool = True):
+                 want_g: bool = True, cluster_size: int = 0, cluster_seed: int = 0):
         self.k, self.iters, self.wdtype, self.adjoint = k, iters, wdtype, adjoint
+        self.cluster_size, self.cluster_seed = cluster_size, cluster_seed
         self.bbox_lo, self.bbox_hi = bbox_lo, bbox_hi
         self.recompute_weights = int(recompute_weights)
         self.want_g = want_g
@@ -35,7 +38,8 @@ class Solver:
         if self.graph is not None:
             self.graph.close()
         mark("build", 0)
-        self.graph = pg_build_graph(V, self.k, self.bbox_lo, self.bbox_hi)
+        self.graph = pg_build_graph(V, self.k, self.bbox_lo, self.bbox_hi, cluster_size=self.cluster_size,
+                                    cluster_seed=self.cluster_seed)
         mark("build", 1)
         mark("aggregate", 0)
         self._c, self.D = pg_aggregate(self.graph, V, self.wdtype)
