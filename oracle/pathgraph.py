@@ -98,31 +98,35 @@ def knn_brute(q, k, r2_max=None):
     return nbr
 
 
-def knn(q, k, r2_max=None, workers=1):
+def knn(q, k, r2_max=None, workers=1, rows=None):
     """Same neighbourhoods as :func:`knn_brute`, found with a k-d tree.
 
     scipy's cKDTree (a library kNN primitive) proposes candidate sets; each is
     re-ordered with exact int64 squared distances and index ties, and widened
     until the candidate set provably holds every point that can tie with the
-    last kept entry. Pinned against :func:`knn_brute`.
+    last kept entry. With ``rows`` only those query points are answered (row i
+    of the result is point rows[i]'s neighbourhood among all points). Pinned
+    against :func:`knn_brute`.
     """
     from scipy.spatial import cKDTree
 
     n = len(q)
-    nbr = -np.ones((n, k), np.int64)
-    if n == 0 or k == 0:
+    qi = np.arange(n) if rows is None else np.asarray(rows, np.int64)
+    nbr = -np.ones((len(qi), k), np.int64)
+    if n == 0 or k == 0 or len(qi) == 0:
         return nbr
-    nbr[:, 0] = np.arange(n)
+    nbr[:, 0] = qi
     if k == 1 or n == 1:
         return nbr
     tree = cKDTree(q.astype(np.float64))
-    todo = np.arange(n)
+    todo = np.arange(len(qi))
     kk = min(n, k + 8)
     while todo.size:
-        _, cand = tree.query(q[todo].astype(np.float64), k=kk, workers=workers)
+        pts = qi[todo]
+        _, cand = tree.query(q[pts].astype(np.float64), k=kk, workers=workers)
         cand = np.asarray(cand, np.int64).reshape(len(todo), kk)
-        d2 = ((q[cand] - q[todo][:, None, :]) ** 2).sum(axis=2)
-        self_mask = cand == todo[:, None]
+        d2 = ((q[cand] - q[pts][:, None, :]) ** 2).sum(axis=2)
+        self_mask = cand == pts[:, None]
         d2s = np.where(self_mask, np.iinfo(np.int64).max, d2)
         # sort candidates by (d2, index), self last
         order = np.lexsort((cand, d2s), axis=1)
@@ -132,14 +136,13 @@ def knn(q, k, r2_max=None, workers=1):
         m = min(k - 1, n - 1)  # others wanted (all of them when n <= k-1)
         last = d2_sorted[:, m - 1]
         ok = (kk == n) | (last < d2_far)
-        rows = todo[ok]
         take = cand_sorted[ok, :m]
         dt = d2_sorted[ok, :m]
         take = np.where(dt == np.iinfo(np.int64).max, -1, take)  # never self
         if r2_max is not None:
             take = np.where(dt <= r2_max, take, -1)
         ncols = take.shape[1]
-        nbr[rows, 1:1 + ncols] = take
+        nbr[todo[ok], 1:1 + ncols] = take
         todo = todo[~ok]
         kk = min(n, kk * 2)
     return nbr
@@ -459,26 +462,106 @@ def propagate(V, nbr, A, c, L0, iters, keep_history=False):
     return L, hist, np.array(res)
 
 
-def path_values(V, nbr, A, L, D, first, bg):
+def path_values(V, nbr, A, L, D, first, bg, Dpath=None):
     """Radiance each path carries into the camera (Section 4, "Final output").
 
     For a path whose first vertex is f: (tau/p_t)_f * (sum_{j in N(f)} A+_{f,j} L+_j + D_f),
     with the non-aggregated direct D_f ("Handling direct light"); plus the
     background seen by a camera ray that left the medium (bg, 0 otherwise).
+    ``Dpath`` (per path) replaces D_f, e.g. by :func:`extra_direct`.
     """
     first = np.asarray(first, np.int64)
     bg = np.asarray(bg, np.float64)
     w = np.asarray(V["w_prop"], np.float64)
     Lj = np.where(nbr >= 0, L[np.where(nbr >= 0, nbr, 0)], 0.0)
-    Lbar = (A * Lj).sum(axis=1) + D
     f = np.where(first >= 0, first, 0)
-    return bg + np.where(first >= 0, w[f] * Lbar[f], 0.0)
+    Lbar = (A * Lj).sum(axis=1)[f]
+    Lbar = Lbar + (D[f] if Dpath is None else np.asarray(Dpath, np.float64))
+    return bg + np.where(first >= 0, w[f] * Lbar, 0.0)
 
 
-def gather(V, nbr, A, L, D, first, bg, spp, width, height):
+def gather(V, nbr, A, L, D, first, bg, spp, width, height, Dpath=None):
     """Pixel = mean of its spp path values (box filter, one pixel per path)."""
-    vals = path_values(V, nbr, A, L, D, first, bg)
+    vals = path_values(V, nbr, A, L, D, first, bg, Dpath)
     return vals.reshape(height, width, spp).mean(axis=2)
+
+
+def extra_direct(V, first, X, M):
+    """Direct light at each path's first vertex from M extra emitter samples
+    (Section 4, "Handling direct light": a few extra emitter samples at the
+    first bounce replace the non-aggregated direct light in the output).
+
+    Reading: the M emitter samples and the path's own phase sample at f are
+    combined by the balance heuristic, with M samples of the emitter strategy
+    and one of the phase strategy:
+      D^x_f = sigma_s(f) [ sum_m rho_f(o_f,e_m) Le_m / (M pe_m + rho_f(o_f,e_m))
+                           + rho_f(o_f,d_f) Lph_f / (M pe_ph_f + rho_f(o_f,d_f)) ]
+    where a delta-light sample m (which phase sampling cannot produce)
+    contributes sigma_s rho_f(o_f,e_m) Le_m / M instead. With M = 1 and the
+    path's own emitter sample this is D_f. X holds x_ex, x_ey, x_ez, x_Le,
+    x_pe, x_delta (M per path, path p's at [p*M, (p+1)*M)). Returns one value
+    per path (0 where the path has no vertex). Parity: pinned by the M = 1
+    reduction to D and by the expectation under a closed-form light field.
+    """
+    P = len(first)
+    first = np.asarray(first, np.int64)
+    Xv = vertex_arrays(V)
+    has = first >= 0
+    f = np.where(has, first, 0)
+    o, g = Xv["o"][f], Xv["g"][f]
+    e = np.stack([np.asarray(X[c], np.float64).reshape(P, M) for c in ("x_ex", "x_ey", "x_ez")], axis=2)
+    Le = np.asarray(X["x_Le"], np.float64).reshape(P, M)
+    pe = np.asarray(X["x_pe"], np.float64).reshape(P, M)
+    delta = np.asarray(X["x_delta"]).astype(bool).reshape(P, M)
+    rho_e = hg(o[:, None, :], e, g[:, None])
+    term = np.where(delta, rho_e * Le / M, rho_e * Le / (M * pe + rho_e))
+    rho_d = hg(o, Xv["d"][f], g)
+    ph = rho_d * Xv["Lph"][f] / (M * Xv["pe_ph"][f] + rho_d)
+    return np.where(has, Xv["sigma_s"][f] * (term.sum(axis=1) + ph), 0.0)
+
+
+def final_gather(V, q, L, first, bg, kfg, D=None, Dpath=None, chunk=1 << 14):
+    """Per-path output through a final gather: one more aggregation, at the
+    first vertices only, after the iteration (the optional final gather of
+    the Fig. 2 caption, which decorrelates neighbouring pixels).
+
+    Reading: path p with first vertex f aggregates over its own neighbourhood
+    N_fg(f) = the kfg nearest vertices of f (same rule as the graph build:
+    self first, then by squared quantised distance, ties by index), with the
+    balance heuristic of f over the phase strategies of N_fg(f):
+      A^fg_{f,j} = sigma_s(f) rho_f(o_f,d_j) / sum_{l in N_fg(f)} rho_l(o_l,d_j)
+      val_p = bg_p + (tau/p_t)_f (sum_{j in N_fg(f)} A^fg_{f,j} L+_j + D_f)
+    (val_p = bg_p without a vertex); ``Dpath`` (per path) replaces D_f.
+    ``q``: quantised positions (:func:`quantize`). Returns (values per path,
+    neighbour table of the paths (-1 rows for paths without a vertex)).
+    Parity: pinned by the kfg = 1 reduction to the path tracer, the isotropic
+    closed form, and the expectation under a closed-form radiance field.
+    """
+    first = np.asarray(first, np.int64)
+    bg = np.asarray(bg, np.float64)
+    has = first >= 0
+    Xv = vertex_arrays(V)
+    P = len(first)
+    nb = -np.ones((P, kfg), np.int64)
+    if has.any():
+        nb[has] = knn(q, kfg, rows=first[has])
+    L = np.asarray(L, np.float64)
+    f_all = np.where(has, first, 0)
+    direct = np.asarray(D, np.float64)[f_all] if Dpath is None else np.asarray(Dpath, np.float64)
+    indirect = np.zeros(P)
+    for a in range(0, P, chunk):
+        valid = nb[a:a + chunk] >= 0
+        j = np.where(valid, nb[a:a + chunk], 0)
+        f = f_all[a:a + chunk]
+        d_j = Xv["d"][j]                                   # [p, j, xyz]
+        # marginal of each sample j over the receiver's neighbourhood: [p, l, j]
+        rho_lj = hg(Xv["o"][j][:, :, None, :], d_j[:, None, :, :], Xv["g"][j][:, :, None])
+        pm = (rho_lj * valid[:, :, None]).sum(axis=1)
+        rho_fj = hg(Xv["o"][f][:, None, :], d_j, Xv["g"][f][:, None])
+        A = np.where(valid, Xv["sigma_s"][f][:, None] * rho_fj / np.where(valid, pm, 1.0), 0.0)
+        indirect[a:a + chunk] = (A * np.where(valid, L[j], 0.0)).sum(axis=1)
+    vals = bg + np.where(has, Xv["w"][f_all] * (indirect + direct), 0.0)
+    return vals, nb
 
 
 def forward(V, first, bg, spp, width, height, k, iters, lo=(0, 0, 0), hi=(1, 1, 1),

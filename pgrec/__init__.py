@@ -55,7 +55,7 @@ class _Config(ctypes.Structure):
         ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("spp", ctypes.c_int32),
         ("max_depth", ctypes.c_int32),
         ("cam_pos", ctypes.c_float * 3), ("cam_target", ctypes.c_float * 3),
-        ("cam_fov_deg", ctypes.c_float),
+        ("cam_fov_deg", ctypes.c_float), ("extra_direct", ctypes.c_int32),
     ]
 
 
@@ -75,6 +75,7 @@ def _load():
         lib.pgrec_copy_vertices.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)] + [ctypes.c_void_p] * 4
         lib.pgrec_copy_paths.argtypes = [ctypes.c_void_p] * 4
         lib.pgrec_copy_medium.argtypes = [ctypes.c_void_p] * 3
+        lib.pgrec_copy_extra.argtypes = [ctypes.c_void_p] * 7
         lib.pgrec_free.argtypes = [ctypes.c_void_p]
         _lib = lib
     return _lib
@@ -114,6 +115,7 @@ class Scene:
     cam_pos: tuple = (0.5, 0.5, -1.6)
     cam_target: tuple = (0.5, 0.5, 0.5)
     cam_fov_deg: float = 26.0
+    extra_direct: int = 0       # extra emitter samples per path at its first vertex
     weight_dtypes: tuple = ("f32",)
     extra: dict = field(default_factory=dict)
 
@@ -156,6 +158,7 @@ CLOUD256_DENSE = Scene(
 
 SCENES = {s.name: s for s in (CUBE_CONST, CLOUD128, CLOUD64_GRAD, CLOUD256_DENSE)}
 
+EXTRA_F32 = ("x_ex", "x_ey", "x_ez", "x_Le", "x_pe")
 F32_FIELDS = ("px", "py", "pz", "ox", "oy", "oz", "dx", "dy", "dz", "ex", "ey", "ez",
               "g", "sigma_s", "sigma_t", "w_prop", "Le", "pe_e", "Lph", "pe_ph", "L0")
 
@@ -166,6 +169,10 @@ def trace(scene: Scene, nthreads: int = 0, albedo_grid: np.ndarray | None = None
 
     ``alloc(shape, dtype)`` may supply the output buffers (e.g. pinned host
     tensors viewed as numpy); the default is ``np.empty``.
+    With ``scene.extra_direct`` = M > 0 also the extra emitter samples drawn
+    at each path's first vertex: ``x_ex, x_ey, x_ez, x_Le, x_pe`` (float32)
+    and ``x_delta`` (uint8), M per path, path p's at [p*M, (p+1)*M) (paths
+    without a vertex hold Le = 0).
     Keys: the per-vertex float32 fields in ``F32_FIELDS``, ``L0_f64``,
     ``e_delta`` (uint8), ``succ`` and ``voxel`` (int32); per path ``first``
     (int32), ``bg`` (float32) and ``pt_value`` (float64); the medium
@@ -200,6 +207,13 @@ def trace(scene: Scene, nthreads: int = 0, albedo_grid: np.ndarray | None = None
         out["albedo_grid"] = np.empty(G ** 3, np.float32)
         lib.pgrec_copy_medium(h, out["density"].ctypes.data, out["albedo_grid"].ctypes.data)
         out["majorant"] = lib.pgrec_majorant(h)
+        M = int(scene.extra_direct)
+        if M > 0:
+            for f in EXTRA_F32:
+                out[f] = alloc((P * M,), np.float32)
+            out["x_delta"] = alloc((P * M,), np.uint8)
+            lib.pgrec_copy_extra(h, *[out[f].ctypes.data for f in EXTRA_F32], out["x_delta"].ctypes.data)
+        out["extra_direct"] = M
     finally:
         lib.pgrec_free(h)
     out["n"] = int(n)
@@ -209,6 +223,17 @@ def trace(scene: Scene, nthreads: int = 0, albedo_grid: np.ndarray | None = None
     out["width"] = scene.width
     out["height"] = scene.height
     return out
+
+
+def _copy_extra(rec: dict, out: dict, paths) -> None:
+    """Extra first-vertex samples of the chosen paths, in their new order."""
+    M = int(rec.get("extra_direct", 0))
+    out["extra_direct"] = M
+    if M == 0:
+        return
+    q = (np.asarray(paths, np.int64)[:, None] * M + np.arange(M)[None, :]).reshape(-1)
+    for f in EXTRA_F32 + ("x_delta",):
+        out[f] = np.ascontiguousarray(rec[f][q])
 
 
 def subset_paths(rec: dict, path_lo: int, path_hi: int) -> dict:
@@ -235,6 +260,7 @@ def subset_paths(rec: dict, path_lo: int, path_hi: int) -> dict:
     out["first"] = np.where(first >= 0, first - v0, -1).astype(np.int32)
     out["bg"] = np.ascontiguousarray(rec["bg"][path_lo:path_hi])
     out["pt_value"] = np.ascontiguousarray(rec["pt_value"][path_lo:path_hi])
+    _copy_extra(rec, out, np.arange(path_lo, path_hi))
     for k in ("density", "albedo_grid", "majorant", "spp"):
         out[k] = rec[k]
     out["n"] = v1 - v0
@@ -278,6 +304,7 @@ def sample_pixels(rec: dict, width: int, height: int, spp: int, stride: int) -> 
     out["first"] = new_first
     out["bg"] = np.ascontiguousarray(rec["bg"][paths])
     out["pt_value"] = np.ascontiguousarray(rec["pt_value"][paths])
+    _copy_extra(rec, out, paths)
     for k in ("density", "albedo_grid", "majorant"):
         out[k] = rec[k]
     out["spp"] = spp

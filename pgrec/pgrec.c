@@ -68,6 +68,8 @@ typedef struct {
     float cam_pos[3];
     float cam_target[3];
     float cam_fov_deg;      /* vertical field of view */
+    int32_t extra_direct;   /* extra emitter samples recorded at each path's first
+                               vertex (Section 4, "Handling direct light"); 0 = none */
 } pgrec_config;
 
 typedef struct {
@@ -92,6 +94,9 @@ typedef struct {
     int32_t *path_thread;
     float *bg;
     double *val;
+    float *x_e;          /* n_paths * extra_direct * 3 extra emitter-sample directions */
+    float *x_Le, *x_pe;  /* their radiance and pdf (as Le / pe_e of a vertex) */
+    uint8_t *x_delta;    /* 1 for a delta-light sample */
     int64_t n_vertices;
     int64_t *thread_offset;
     double majorant;     /* max sigma_t over the grid (delta-tracking bound) */
@@ -335,6 +340,47 @@ static void continuous_emission(const pgrec_config *c, double p_cont, const doub
     *pdf = p_cont * pdf_;
 }
 
+/* One draw of the emitter-sampling strategy at x: the sun (a delta light)
+ * with probability p_sun, else a continuous light (area light or sky, chosen
+ * by p_area) sampled by solid angle. Returns the direction toward the light,
+ * the radiance it delivers (transmittance to the medium box included; for the
+ * sun divided by p_sun) and the continuous strategy's pdf of that direction
+ * (selection included; 0 for the sun). */
+static void sample_emitter(const pgrec_state *st, rng_t *r, const double x[3], const double sun_to[3], int has_cont,
+                           double e[3], double *Le_out, double *pe_out, int *delta_out) {
+    const pgrec_config *c = &st->cfg;
+    double Le = 0.0, pe = 0.0;
+    int delta = 0;
+    double u = rnd(r);
+    if (u < st->p_sun) {
+        e[0] = sun_to[0]; e[1] = sun_to[1]; e[2] = sun_to[2];
+        delta = 1;
+        Le = c->sun_irradiance / st->p_sun * ratio_track(st, r, x, e, 1e300);
+    } else if (has_cont) {
+        int has_area = c->area_radiance > 0, has_sky = c->sky_radiance > 0;
+        double pa = has_area ? (has_sky ? c->p_area : 1.0) : 0.0;
+        if (rnd(r) < pa) {
+            double a = 2.0 * rnd(r) - 1.0, bb = 2.0 * rnd(r) - 1.0, y[3];
+            for (int i = 0; i < 3; i++) y[i] = c->area_center[i] + a * c->area_u[i] + bb * c->area_v[i];
+            for (int i = 0; i < 3; i++) e[i] = y[i] - x[i];
+            normalize3(e);
+        } else {
+            double z = 1.0 - 2.0 * rnd(r), ph = 2.0 * PI_D * rnd(r), s = sqrt(fmax(0.0, 1.0 - z * z));
+            e[0] = s * cos(ph); e[1] = s * sin(ph); e[2] = z;
+        }
+        double Lc, pc;
+        continuous_emission(c, 1.0 - st->p_sun, x, e, &Lc, &pc);
+        pe = pc;
+        /* the lights sit outside the medium box: transmittance to the box exit */
+        Le = Lc > 0 ? Lc * ratio_track(st, r, x, e, 1e300) : 0.0;
+    } else {
+        e[0] = sun_to[0]; e[1] = sun_to[1]; e[2] = sun_to[2];
+    }
+    *Le_out = Le;
+    *pe_out = pe;
+    *delta_out = delta;
+}
+
 static void vbuf_grow(vbuf *b) {
     int64_t nc = b->cap ? b->cap * 2 : 4096;
 #define GROW(f, T) b->f = (T *)realloc(b->f, sizeof(T) * nc)
@@ -376,6 +422,12 @@ static double trace_path(pgrec_state *st, int64_t pi, vbuf *b, int64_t *first_lo
 
     *first_local = -1;
     *bg_out = 0.0f;
+    const int M = c->extra_direct > 0 ? c->extra_direct : 0;
+    for (int i = 0; i < M; i++) { /* paths without a vertex keep empty extra samples */
+        int64_t q = pi * M + i;
+        st->x_e[3 * q] = 0.0f; st->x_e[3 * q + 1] = 0.0f; st->x_e[3 * q + 2] = 1.0f;
+        st->x_Le[q] = 0.0f; st->x_pe[q] = 0.0f; st->x_delta[q] = 0;
+    }
     if (!delta_track(st, &r, pos, dir, x)) {
         double L, pdf;
         continuous_emission(c, 1.0 - st->p_sun, pos, dir, &L, &pdf);
@@ -383,11 +435,11 @@ static double trace_path(pgrec_state *st, int64_t pi, vbuf *b, int64_t *first_lo
         return (double)(float)L;
     }
     int64_t start = b->n;
-    double p_sun = st->p_sun;
     int has_cont = c->sky_radiance > 0 || c->area_radiance > 0;
     double sun_to[3] = {-c->sun_dir[0], -c->sun_dir[1], -c->sun_dir[2]};
     normalize3(sun_to);
     double o[3] = {-dir[0], -dir[1], -dir[2]};
+    const double x_first[3] = {x[0], x[1], x[2]};
     for (int depth = 0; depth < c->max_depth; depth++) {
         if (b->n == b->cap) vbuf_grow(b);
         int64_t v = b->n++;
@@ -402,33 +454,9 @@ static double trace_path(pgrec_state *st, int64_t pi, vbuf *b, int64_t *first_lo
         b->w_prop[v] = (float)(1.0 / sig_t); /* tau / p_t under delta tracking */
         b->voxel[v] = (int32_t)vox;
         /* emitter sample */
-        double e[3], Le = 0.0, pe = 0.0;
-        int delta = 0;
-        double u = rnd(&r);
-        if (u < p_sun) {
-            e[0] = sun_to[0]; e[1] = sun_to[1]; e[2] = sun_to[2];
-            delta = 1;
-            Le = c->sun_irradiance / p_sun * ratio_track(st, &r, x, e, 1e300);
-        } else if (has_cont) {
-            int has_area = c->area_radiance > 0, has_sky = c->sky_radiance > 0;
-            double pa = has_area ? (has_sky ? c->p_area : 1.0) : 0.0;
-            if (rnd(&r) < pa) {
-                double a = 2.0 * rnd(&r) - 1.0, bb = 2.0 * rnd(&r) - 1.0, y[3];
-                for (int i = 0; i < 3; i++) y[i] = c->area_center[i] + a * c->area_u[i] + bb * c->area_v[i];
-                for (int i = 0; i < 3; i++) e[i] = y[i] - x[i];
-                normalize3(e);
-            } else {
-                double z = 1.0 - 2.0 * rnd(&r), ph = 2.0 * PI_D * rnd(&r), s = sqrt(fmax(0.0, 1.0 - z * z));
-                e[0] = s * cos(ph); e[1] = s * sin(ph); e[2] = z;
-            }
-            double Lc, pc;
-            continuous_emission(c, 1.0 - st->p_sun, x, e, &Lc, &pc);
-            pe = pc;
-            /* the lights sit outside the medium box: transmittance to the box exit */
-            Le = Lc > 0 ? Lc * ratio_track(st, &r, x, e, 1e300) : 0.0;
-        } else {
-            e[0] = sun_to[0]; e[1] = sun_to[1]; e[2] = sun_to[2];
-        }
+        double e[3], Le, pe;
+        int delta;
+        sample_emitter(st, &r, x, sun_to, has_cont, e, &Le, &pe, &delta);
         b->ex[v] = (float)e[0]; b->ey[v] = (float)e[1]; b->ez[v] = (float)e[2];
         b->Le[v] = (float)Le;
         b->pe_e[v] = (float)pe;
@@ -456,6 +484,23 @@ static double trace_path(pgrec_state *st, int64_t pi, vbuf *b, int64_t *first_lo
         o[0] = -d[0]; o[1] = -d[1]; o[2] = -d[2];
     }
     *first_local = start;
+
+    /* extra emitter samples at the first vertex, from a random stream of
+     * their own so that the path above is the same with or without them */
+    if (M > 0) {
+        rng_t rx;
+        rx.s = mix64(c->seed ^ mix64((uint64_t)pi + 0xD1B54A32D192ED03ULL) ^ 0x8CB92BA72F3D8DD7ULL);
+        for (int i = 0; i < M; i++) {
+            double e[3], Le, pe;
+            int delta;
+            sample_emitter(st, &rx, x_first, sun_to, has_cont, e, &Le, &pe, &delta);
+            int64_t q = pi * M + i;
+            st->x_e[3 * q] = (float)e[0]; st->x_e[3 * q + 1] = (float)e[1]; st->x_e[3 * q + 2] = (float)e[2];
+            st->x_Le[q] = (float)Le;
+            st->x_pe[q] = (float)pe;
+            st->x_delta[q] = (uint8_t)delta;
+        }
+    }
 
     /* Path-tracing estimate from the stored (float32) records, in double:
      * scattered direct radiance per vertex by one-sample balance-heuristic
@@ -517,6 +562,13 @@ void *pgrec_trace(const pgrec_config *cfg, const float *albedo_grid, int32_t nth
     st->path_thread = (int32_t *)malloc(sizeof(int32_t) * st->n_paths);
     st->bg = (float *)malloc(sizeof(float) * st->n_paths);
     st->val = (double *)malloc(sizeof(double) * st->n_paths);
+    if (cfg->extra_direct > 0) {
+        int64_t nx = st->n_paths * cfg->extra_direct;
+        st->x_e = (float *)malloc(sizeof(float) * 3 * nx);
+        st->x_Le = (float *)malloc(sizeof(float) * nx);
+        st->x_pe = (float *)malloc(sizeof(float) * nx);
+        st->x_delta = (uint8_t *)malloc(nx);
+    }
     int64_t np = st->n_paths;
 #pragma omp parallel num_threads(nthreads)
     {
@@ -578,6 +630,22 @@ void pgrec_copy_paths(void *h, int32_t *first, float *bg, double *val) {
     }
 }
 
+/* Extra emitter samples at the first vertices (extra_direct per path, path
+ * p's at [p * extra_direct, (p + 1) * extra_direct)); directions split into
+ * x, y, z arrays. */
+void pgrec_copy_extra(void *h, float *ex, float *ey, float *ez, float *Le, float *pe, uint8_t *delta) {
+    pgrec_state *st = (pgrec_state *)h;
+    int64_t nx = st->n_paths * (st->cfg.extra_direct > 0 ? st->cfg.extra_direct : 0);
+    for (int64_t q = 0; q < nx; q++) {
+        ex[q] = st->x_e[3 * q];
+        ey[q] = st->x_e[3 * q + 1];
+        ez[q] = st->x_e[3 * q + 2];
+        Le[q] = st->x_Le[q];
+        pe[q] = st->x_pe[q];
+        delta[q] = st->x_delta[q];
+    }
+}
+
 void pgrec_copy_medium(void *h, float *density, float *albedo) {
     pgrec_state *st = (pgrec_state *)h;
     int64_t G = st->cfg.grid_res, nv = G * G * G;
@@ -600,6 +668,10 @@ void pgrec_free(void *h) {
     free(st->path_thread);
     free(st->bg);
     free(st->val);
+    free(st->x_e);
+    free(st->x_Le);
+    free(st->x_pe);
+    free(st->x_delta);
     free(st->thread_offset);
     free(st->density);
     free(st->albedo_grid);

@@ -103,3 +103,46 @@ def test_receiver_neighbourhood_marginal_is_caught(monkeypatch):
     monkeypatch.setattr(oracle, "aggregate", bad_aggregate)
     with pytest.raises(AssertionError):
         test_mis_weights_sum_to_one_on_knn_graphs()
+
+
+def test_extra_direct_missing_sample_count_is_caught(monkeypatch):
+    """Combining the M extra emitter samples as if each were alone (weight
+    pe / (pe + rho) instead of M pe / (M pe + rho)) over-counts them."""
+    from test_oracle_output_pins import test_extra_direct_expectation
+
+    def bad_extra(V, first, X, M):
+        X1 = {k: np.asarray(v) for k, v in X.items()}
+        P = len(first)
+        tot = np.zeros(P)
+        for m in range(M):
+            sub = {k: v.reshape(P, M)[:, m] for k, v in X1.items()}
+            tot += good(V, first, sub, 1)
+        return tot
+
+    good = opg.extra_direct
+    monkeypatch.setattr(oracle, "extra_direct", bad_extra)
+    with pytest.raises(AssertionError):
+        test_extra_direct_expectation(3)
+
+
+def test_final_gather_marginal_without_receiver_is_caught(monkeypatch):
+    """Leaving each sample's own strategy out of its marginal in the final
+    gather biases the estimate."""
+    from test_oracle_output_pins import test_final_gather_expectation
+
+    good_hg = opg.hg
+    calls = {"n": 0}
+
+    def bad_hg(o, d, g):
+        r = good_hg(o, d, g)
+        calls["n"] += 1
+        # the first phase evaluation of each chunk is the [p, l, j] marginal table
+        if calls["n"] % 2 == 1 and np.ndim(r) == 3 and r.shape[1] == r.shape[2]:
+            r = r.copy()
+            idx = np.arange(r.shape[1])
+            r[:, idx, idx] = 0.0
+        return r
+
+    monkeypatch.setattr(opg, "hg", bad_hg)
+    with pytest.raises(AssertionError):
+        test_final_gather_expectation()
