@@ -36,6 +36,7 @@ L2_BYTES = 129 * 2 ** 20
 
 
 WORKLOADS = ("cloud128", "dense256")
+EXTRA_M = 4  # extra emitter samples per path for the output-option timings
 
 
 def _scene(name):
@@ -133,7 +134,9 @@ def run_gpu(args):
         sc = sc.with_(width=int(sc.width * args.scale), height=int(sc.height * args.scale))
     if world > 1:  # independent renders (replicas), one per rank
         sc = sc.with_(seed=rank_seed(sc.seed, rank))
-    rec = pgrec.trace(sc)
+    # the extra first-vertex samples come from a random stream of their own:
+    # the path records are the same with or without them
+    rec = pgrec.trace(sc if args.quick else sc.with_(extra_direct=EXTRA_M))
     n, P = rec["n"], rec["n_paths"]
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
@@ -257,6 +260,33 @@ def run_gpu(args):
                         "mean_rel_err_vs_f32": float(((a - b).abs() / den).mean())}
             s16.close()
 
+    # ---- output options on the step's graph and L (not part of the step):
+    # extra first-vertex emitter samples and the final gather
+    outopt = {}
+    if not args.quick:
+        xs = pg.extra_from_records(rec)
+
+        def t_out(reps=5, **kw):
+            def f():
+                return pg.pg_gather_ex(solver.graph, solver.L, solver.D, dev_in["first"], dev_in["bg"], sc.spp,
+                                       sc.width, sc.height, **kw)
+            img = f()
+            torch.cuda.synchronize()
+            a, b = ev(), ev()
+            a.record(stream)
+            for _ in range(reps):
+                f()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return {"ms": a.elapsed_time(b) / reps,
+                    "image_mean_over_path_tracer": float(img.double().mean()) / float(pt.mean())}
+
+        outopt["gather"] = t_out()
+        outopt["extra_direct_m%d" % EXTRA_M] = t_out(extra=xs)
+        for kf in (8, 16, 32):
+            outopt["final_gather_k%d" % kf] = t_out(final_gather_k=kf)
+        outopt["final_gather_k16_extra_m%d" % EXTRA_M] = t_out(final_gather_k=16, extra=xs)
+
     # ---- end to end through the public API: host records -> image on the host
     e2e_t = []
     h2d = sum(int(v.numel() * v.element_size()) for v in host.values()) + host_target.numel() * 4
@@ -300,6 +330,7 @@ def run_gpu(args):
                      "algorithmic_bytes_per_launch": bytes_sweep, "peak_kind": peak_kind,
                      "other_kernels": others},
         "precision": prec,
+        "output_options_ms": outopt,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,

@@ -11,6 +11,9 @@
  *                         with P from Eq. volume-propagation
  *   pg_gather             per-path output into pixels (Section 4, "Final
  *                         output", "Handling direct light")
+ *   pg_gather_ex          the same with the output options: extra emitter
+ *                         samples at the first vertices (Section 4, "Handling
+ *                         direct light") and a final gather (Fig. 2 caption)
  *   pg_propagate_adjoint  reverse-mode gradients of an image loss through the
  *                         fixed graph (the paper has no adjoint; this follows
  *                         from differentiating the maps above)
@@ -199,6 +202,59 @@ pg_status pg_propagate(pg_graph *g, const float *c, const float *L0, int32_t ite
  * n_paths must equal width*height*spp. Errors: PG_ERR_STATE, PG_ERR_INVALID_ARG. */
 pg_status pg_gather(const pg_graph *g, const float *L, const float *D, const int32_t *first, const float *bg,
                     int64_t n_paths, int32_t spp, int32_t width, int32_t height, float *image, pg_stream_t stream);
+
+/* Extra emitter samples recorded at each path's first vertex (Section 4,
+ * "Handling direct light": a few extra emitter samples at the first bounce
+ * stand in for the non-aggregated direct light in the output). m samples per
+ * path, path p's at [p*m, (p+1)*m); device arrays of n_paths*m entries with
+ * the meaning of the vertex fields of the same name (e unit direction toward
+ * the light, Le delivered radiance with transmittance, for a delta light
+ * divided by its selection probability, pe_e the continuous strategy's pdf,
+ * e_delta 1 for a delta light). Entries of paths without a vertex are
+ * ignored. */
+typedef struct {
+    int32_t m;
+    const float *ex, *ey, *ez;
+    const float *Le, *pe_e;
+    const uint8_t *e_delta;
+} pg_extra_samples;
+
+typedef struct {
+    /* 0: aggregate over N(f) with the graph's weights (pg_gather).
+     * 1..32: final gather, one more aggregation at the first vertices only
+     * (the optional final gather of the Fig. 2 caption): N_fg(f) = the
+     * final_gather_k nearest vertices of f under the graph build's rule
+     * (self first, squared quantised distance, ties by caller index, no
+     * radius limit; in both neighbourhood modes), weighted by f's balance
+     * heuristic over the phase strategies of N_fg(f):
+     *   A^fg_{f,j} = sigma_s(f) rho_f(o_f,d_j) / sum_{l in N_fg(f)} rho_l(o_l,d_j) */
+    int32_t final_gather_k;
+    /* NULL: the output's direct term is D_f. Otherwise the M = extra->m
+     * samples and the path's own phase sample, by the balance heuristic:
+     *   D^x_f = sigma_s(f) [ sum_m rho_f(o_f,e_m) Le_m / (M pe_m + rho_f(o_f,e_m))
+     *                        + rho_f(o_f,d_f) Lph_f / (M pe_ph_f + rho_f(o_f,d_f)) ]
+     * where a delta-light sample contributes sigma_s rho_f(o_f,e_m) Le_m / M. */
+    const pg_extra_samples *extra;
+    /* optional out (device, n_paths*final_gather_k int32): N_fg(f) of each
+     * path in caller indices, -1 padded (all -1 for a path without a vertex);
+     * NULL to skip. Ignored when final_gather_k = 0. */
+    int32_t *fg_nbr;
+} pg_output_params;
+
+/* pg_gather with output options (params NULL = pg_gather). Path p with first
+ * vertex f carries
+ *   val_p = bg_p + (tau/p_t)_f * ( sum_{j} A_{f,j} L_j + Dir_p )
+ * with (j, A) from N(f) and A+ (final_gather_k = 0) or from N_fg(f) and
+ * A^fg, and Dir_p = D_f or D^x_f; image as in pg_gather. D may be NULL when
+ * extra samples are given. Synchronises `stream` once when extra samples are
+ * given (to report their validation). Temporary device memory: n_paths *
+ * (4 + 4 * row width) bytes for a final gather, 8 * n_paths otherwise.
+ * Errors: PG_ERR_STATE, PG_ERR_INVALID_ARG (sizes, NULL arrays, m < 1,
+ * negative Le or pe_e), PG_ERR_UNSUPPORTED (final_gather_k > 32),
+ * PG_ERR_NONFINITE (an extra sample). */
+pg_status pg_gather_ex(const pg_graph *g, const float *L, const float *D, const int32_t *first, const float *bg,
+                       int64_t n_paths, int32_t spp, int32_t width, int32_t height, const pg_output_params *params,
+                       float *image, pg_stream_t stream);
 
 /* Adjoint of pg_aggregate -> pg_propagate -> pg_gather for a fixed graph,
  * fixed samples, fixed tau/p_t and a detached L0. Needs the last

@@ -520,7 +520,7 @@ def extra_direct(V, first, X, M):
     return np.where(has, Xv["sigma_s"][f] * (term.sum(axis=1) + ph), 0.0)
 
 
-def final_gather(V, q, L, first, bg, kfg, D=None, Dpath=None, chunk=1 << 14):
+def final_gather(V, q, L, first, bg, kfg, D=None, Dpath=None, chunk=None):
     """Per-path output through a final gather: one more aggregation, at the
     first vertices only, after the iteration (the optional final gather of
     the Fig. 2 caption, which decorrelates neighbouring pixels).
@@ -546,6 +546,7 @@ def final_gather(V, q, L, first, bg, kfg, D=None, Dpath=None, chunk=1 << 14):
     if has.any():
         nb[has] = knn(q, kfg, rows=first[has])
     L = np.asarray(L, np.float64)
+    chunk = chunk or max(64, (1 << 20) // (kfg * kfg))  # paths per block: [p, l, j] tables stay ~100 MB
     f_all = np.where(has, first, 0)
     direct = np.asarray(D, np.float64)[f_all] if Dpath is None else np.asarray(Dpath, np.float64)
     indirect = np.zeros(P)

@@ -142,6 +142,41 @@ def pg_gather(graph: Graph, L: torch.Tensor, D: torch.Tensor, first: torch.Tenso
     return img
 
 
+EXTRA_FIELDS = ("ex", "ey", "ez", "Le", "pe_e", "e_delta")
+
+
+def pg_gather_ex(graph: Graph, L: torch.Tensor, D: torch.Tensor | None, first: torch.Tensor, bg: torch.Tensor,
+                 spp: int, width: int, height: int, final_gather_k: int = 0, extra: dict | None = None,
+                 want_fg_nbr: bool = False, out: torch.Tensor | None = None, stream=None):
+    """pg_gather with the output options of include/pg.h: a final gather over
+    the ``final_gather_k`` nearest vertices of each first vertex, and/or the
+    direct term from ``extra`` = {"m": M, "ex", "ey", "ez", "Le", "pe_e",
+    "e_delta": device tensors of n_paths*M entries}. Returns the image, and
+    with ``want_fg_nbr`` also the final gather's neighbour table."""
+    img = out if out is not None else torch.empty((height, width), dtype=torch.float32, device="cuda")
+    xs = None
+    if extra is not None:
+        xs = _lib.PgExtraSamples(m=int(extra["m"]), **{k: extra[k].data_ptr() for k in EXTRA_FIELDS})
+        for k in EXTRA_FIELDS:
+            _ptr(extra[k])
+    fg = torch.empty((first.numel(), final_gather_k), dtype=torch.int32, device="cuda") \
+        if want_fg_nbr and final_gather_k > 0 else None
+    p = _lib.PgOutputParams(final_gather_k=final_gather_k, extra=ctypes.pointer(xs) if xs is not None else None,
+                            fg_nbr=fg.data_ptr() if fg is not None else None)
+    check(_LIB.pg_gather_ex(graph.handle, _ptr(L), _ptr(D), _ptr(first), _ptr(bg), first.numel(), spp, width,
+                            height, ctypes.byref(p), _ptr(img), _stream_ptr(stream)), "pg_gather_ex")
+    return (img, fg) if want_fg_nbr else img
+
+
+def extra_from_records(rec: dict, device="cuda") -> dict:
+    """The recorder's extra first-vertex samples (x_ex ... x_delta) as the
+    device tensors pg_gather_ex takes."""
+    names = {"ex": "x_ex", "ey": "x_ey", "ez": "x_ez", "Le": "x_Le", "pe_e": "x_pe", "e_delta": "x_delta"}
+    out = {k: torch.from_numpy(np.ascontiguousarray(rec[v])).to(device) for k, v in names.items()}
+    out["m"] = int(rec["extra_direct"])
+    return out
+
+
 def pg_propagate_adjoint(graph: Graph, dI: torch.Tensor, first: torch.Tensor, spp: int, width: int, height: int,
                          want_sigma_s: bool = True, want_g: bool = True, voxel: torch.Tensor | None = None,
                          sigma_t: torch.Tensor | None = None, n_vox: int = 0, recompute_weights: int = 0,
@@ -173,5 +208,5 @@ def launch_count() -> int:
 
 from .solver import Solver  # noqa: E402
 
-__all__ = ["Solver", "launch_count", "Vertices", "Graph", "PgError", "pg_build_graph", "pg_aggregate", "pg_propagate", "pg_gather",
-           "pg_propagate_adjoint"]
+__all__ = ["Solver", "launch_count", "Vertices", "Graph", "PgError", "pg_build_graph", "pg_aggregate", "pg_propagate",
+           "pg_gather", "pg_gather_ex", "extra_from_records", "pg_propagate_adjoint", "pg_propagate_noalloc"]

@@ -35,9 +35,18 @@ class PgGraphInfo(ctypes.Structure):
                 ("history_iters", ctypes.c_int32), ("knn_exact", ctypes.c_int64), ("clusters", ctypes.c_int64)]
 
 
+class PgExtraSamples(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32)] + [(name, ctypes.c_void_p) for name in ("ex", "ey", "ez", "Le", "pe_e", "e_delta")]
+
+
+class PgOutputParams(ctypes.Structure):
+    _fields_ = [("final_gather_k", ctypes.c_int32), ("extra", ctypes.POINTER(PgExtraSamples)),
+                ("fg_nbr", ctypes.c_void_p)]
+
+
 EXPORTS = ("pg_build_graph", "pg_graph_neighbors", "pg_graph_get_info", "pg_aggregate", "pg_propagate",
            "pg_gather", "pg_propagate_adjoint", "pg_graph_release_weights", "pg_graph_destroy",
-           "pg_status_string", "pg_launch_count", "pg_propagate_noalloc")
+           "pg_status_string", "pg_launch_count", "pg_propagate_noalloc", "pg_gather_ex")
 
 _lib = None
 
@@ -58,6 +67,7 @@ def load(path: str = LIB_PATH):
     lib.pg_aggregate.argtypes = [vp, ctypes.POINTER(PgVertices), ctypes.c_int, vp, vp, vp]
     lib.pg_propagate.argtypes = [vp, vp, vp, i32, f64, i32, vp, vp, vp, vp]
     lib.pg_gather.argtypes = [vp, vp, vp, vp, vp, i64, i32, i32, i32, vp, vp]
+    lib.pg_gather_ex.argtypes = [vp, vp, vp, vp, vp, i64, i32, i32, i32, ctypes.POINTER(PgOutputParams), vp, vp]
     lib.pg_propagate_adjoint.argtypes = [vp, vp, vp, i64, i32, i32, i32, vp, vp, vp, vp, vp, i64, i32, vp]
     lib.pg_graph_release_weights.argtypes = [vp]
     lib.pg_graph_destroy.argtypes = [vp]

@@ -11,6 +11,8 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <mutex>
+
 #include "pg_internal.cuh"
 
 __global__ void quantize_kernel(const float *__restrict__ px, const float *__restrict__ py,
@@ -228,17 +230,24 @@ __global__ void __launch_bounds__(128, 4) knn_kernel(const int4 *__restrict__ qr
 }
 
 // Exact path for queued queries: entries (int64 d2, caller id) compared
-// lexicographically.
-template <int KP>
+// lexicographically. QUERY = false: the build's redo list (*d_count
+// entries), row m of nbr. QUERY = true: nq query points list[t] (Morton
+// index, or -1 for none), row t of nbr.
+template <int KP, bool QUERY>
 __global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__ qrec,
                                                         const int2 *__restrict__ cell_se,
                                                         const int32_t *__restrict__ c2m, const int32_t *__restrict__ list,
-                                                        const int32_t *__restrict__ d_count, int k, int level,
-                                                        int64_t r2_max, int32_t *__restrict__ nbr) {
+                                                        const int32_t *__restrict__ d_count, int64_t nq, int k,
+                                                        int level, int64_t r2_max, int32_t *__restrict__ nbr) {
     constexpr int M = KP - 1;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= *d_count) return;
+    if (t >= (QUERY ? nq : (int64_t)*d_count)) return;
     const int64_t m = list[t];
+    int32_t *row = nbr + (QUERY ? t : m) * KP;
+    if (QUERY && m < 0) {
+        for (int i = 0; i < KP; i++) row[i] = -1;
+        return;
+    }
     const int4 qr = qrec[m];
     const int32_t qx = qr.x, qy = qr.y, qz = qr.z;
     const int sh = PG_QBITS - level;
@@ -344,7 +353,6 @@ __global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__
             if (r2_max >= 0 && bnd2 > r2_max) break;            // nothing outside is in range
         }
     }
-    int32_t *row = nbr + m * KP;
     row[0] = (int32_t)m;
 #pragma unroll
     for (int i = 0; i < M; i++) {
@@ -379,8 +387,8 @@ static pg_status launch_knn_t(pg_graph *g, cudaStream_t s) {
         st = PG_ERR_CUDA;
     g->knn_exact = h_cnt;
     if (st == PG_OK && h_cnt > 0) {
-        knn_exact_kernel<KP><<<pg_blocks(h_cnt, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, redo, cnt, g->k,
-                                                                  g->level, g->r2_max, g->nbr);
+        knn_exact_kernel<KP, false><<<pg_blocks(h_cnt, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, redo, cnt, 0,
+                                                                         g->k, g->level, g->r2_max, g->nbr);
         pg_count_launches(1);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     }
@@ -389,15 +397,38 @@ static pg_status launch_knn_t(pg_graph *g, cudaStream_t s) {
     return st;
 }
 
-pg_status pg_launch_knn(pg_graph *g, cudaStream_t s) {
-    static bool table_ready = false; // per process; set on the first build (any device)
+static pg_status upload_ring1(cudaStream_t s) {
+    static std::once_flag once;
     static int ring[26];
-    if (!table_ready) {
-        ring1_table(ring);
-        table_ready = true;
-    }
+    std::call_once(once, [] { ring1_table(ring); });
     // the constant lives per device: copy it before every launch (26 ints)
     PG_CUDA(cudaMemcpyToSymbolAsync(c_ring1, ring, sizeof(ring), 0, cudaMemcpyHostToDevice, s));
+    return PG_OK;
+}
+
+pg_status pg_launch_knn_queries(const pg_graph *g, const int32_t *qm, int64_t nq, int k, int32_t *out,
+                                cudaStream_t s) {
+    if (nq <= 0) return PG_OK;
+    PG_TRY(upload_ring1(s));
+    const int kp = pg_row_width(k);
+#define Q(KP)                                                                                                   \
+    knn_exact_kernel<KP, true><<<pg_blocks(nq, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, qm, nullptr, nq, k, \
+                                                                 g->level, -1, out)
+    switch (kp) {
+        case 4: Q(4); break;
+        case 8: Q(8); break;
+        case 16: Q(16); break;
+        case 32: Q(32); break;
+        default: return PG_ERR_UNSUPPORTED;
+    }
+#undef Q
+    pg_count_launches(1);
+    PG_LAUNCH_CHECK();
+    return PG_OK;
+}
+
+pg_status pg_launch_knn(pg_graph *g, cudaStream_t s) {
+    PG_TRY(upload_ring1(s));
     switch (g->kp) {
         case 4: return launch_knn_t<4>(g, s);
         case 8: return launch_knn_t<8>(g, s);
@@ -439,7 +470,7 @@ extern "C" pg_status pg_build_graph(const pg_vertices *v, int64_t n, const pg_bu
     g->stream = s;
     g->n = n;
     g->k = p->k;
-    g->kp = p->k <= 4 ? 4 : p->k <= 8 ? 8 : p->k <= 16 ? 16 : 32;
+    g->kp = pg_row_width(p->k);
     g->level = p->grid_level ? p->grid_level : auto_level(n, p->k);
     for (int a = 0; a < 3; a++) g->lo[a] = p->bbox_lo[a];
     {

@@ -252,9 +252,16 @@ __device__ __forceinline__ float pg_pm_float(unsigned long long a) {
 }
 
 static inline size_t pg_wbytes(pg_wdtype t) { return t == PG_W_F32 ? 4 : 2; }
+// stored row width for k entries: 4, 8, 16 or 32 (128-bit aligned rows)
+static inline int pg_row_width(int k) { return k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32; }
 
 // Launchers implemented in the per-stage translation units.
 pg_status pg_launch_knn(pg_graph *g, cudaStream_t s);
+// exact k nearest vertices (self first) of nq query points qm[t] (Morton
+// index or -1) among all the graph's vertices, no radius limit: out row t
+// (row width pg_row_width(k), Morton ids, -1 padded; all -1 for qm[t] < 0)
+pg_status pg_launch_knn_queries(const pg_graph *g, const int32_t *qm, int64_t nq, int k, int32_t *out,
+                                cudaStream_t s);
 // cluster neighbourhoods (keys: the vertices' sorted Morton cell keys)
 pg_status pg_launch_clusters(pg_graph *g, const uint32_t *keys, int32_t K, uint64_t seed, cudaStream_t s);
 void pg_free_transposes(pg_graph *g); // releases both transposes (weights changed)

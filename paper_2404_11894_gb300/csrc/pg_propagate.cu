@@ -1,5 +1,4 @@
-// Propagation (Eq. rte-mff with P from Eq. volume-propagation) and the
-// per-path output (Section 4, "Final output").
+// Propagation (Eq. rte-mff with P from Eq. volume-propagation).
 //
 // One Jacobi sweep, in sweep-row order r over the rows that have a
 // predecessor:   y'_r = scale_r * sum_i W[r][i] * y[col[r][i]] + b_r
@@ -37,15 +36,6 @@ struct W4<__half> {
         return make_float4(fa.x, fa.y, fb.x, fb.y);
     }
 };
-
-template <typename WT>
-__device__ __forceinline__ float wdec(const WT *W, int64_t i);
-template <>
-__device__ __forceinline__ float wdec<float>(const float *W, int64_t i) { return W[i]; }
-template <>
-__device__ __forceinline__ float wdec<__nv_bfloat16>(const __nv_bfloat16 *W, int64_t i) { return __bfloat162float(W[i]); }
-template <>
-__device__ __forceinline__ float wdec<__half>(const __half *W, int64_t i) { return __half2float(W[i]); }
 
 static constexpr int SWEEP_THREADS = 256;
 
@@ -525,72 +515,6 @@ extern "C" pg_status pg_propagate_noalloc(pg_graph *g, const float *L0, int32_t 
     }
     finish_L_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(g->c2m, g->succ_m, g->m2r, n, y0, y1, nullptr, ctrl, L);
     pg_count_launches(1);
-    PG_LAUNCH_CHECK();
-    return PG_OK;
-}
-
-// ------------------------------------------------------------------ gather
-template <typename WT>
-__global__ void gather_kernel(const int32_t *__restrict__ first, const float *__restrict__ bg,
-                              const float *__restrict__ L, const float *__restrict__ D,
-                              const int32_t *__restrict__ c2m, const int32_t *__restrict__ m2c,
-                              const int32_t *__restrict__ m2r, const int32_t *__restrict__ nbr,
-                              const WT *__restrict__ W, const float *__restrict__ rscale,
-                              const float4 *__restrict__ LV, int kp, int spp, int64_t npix, int64_t n,
-                              float *__restrict__ image) {
-    int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pix >= npix) return;
-    float acc = 0.0f;
-    for (int sidx = 0; sidx < spp; sidx++) {
-        int64_t p = pix * spp + sidx;
-        float val = bg[p];
-        int32_t f = first[p];
-        if (f >= 0 && f < n) { // out-of-range entries are treated as -1
-            int32_t m = c2m[f];
-            int64_t r = m2r[m];
-            float sc = WTraits<WT>::id == PG_W_F32 ? 1.0f : rscale[r];
-            float sum = 0.0f;
-            for (int i = 0; i < kp; i++) {
-                int32_t j = nbr[(int64_t)m * kp + i];
-                if (j >= 0) sum = fmaf(wdec<WT>(W, r * kp + i), L[m2c[j]], sum);
-            }
-            val += fmaf(sum, sc, LV[m].w * D[f]);
-        }
-        acc += val;
-    }
-    image[pix] = acc / (float)spp;
-}
-
-extern "C" pg_status pg_gather(const pg_graph *g, const float *L, const float *D, const int32_t *first,
-                               const float *bg, int64_t n_paths, int32_t spp, int32_t width, int32_t height,
-                               float *image, pg_stream_t stream) {
-    if (!g || spp <= 0 || width < 0 || height < 0) return PG_ERR_INVALID_ARG;
-    if (n_paths != (int64_t)width * height * spp) return PG_ERR_INVALID_ARG;
-    if (!g->aggregated || !g->W) return PG_ERR_STATE;
-    int64_t npix = (int64_t)width * height;
-    if (npix == 0) return PG_OK;
-    if (!first || !bg || !image || (g->n > 0 && (!L || !D))) return PG_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
-    switch (g->wdtype) {
-        case PG_W_F32:
-            gather_kernel<float><<<pg_blocks(npix, 128), 128, 0, s>>>(first, bg, L, D, g->c2m, g->m2c, g->m2r, g->nbr,
-                                                                     (const float *)g->W, g->rscale, g->LV, g->kp,
-                                                                     spp, npix, g->n, image);
-            pg_count_launches(1);
-            break;
-        case PG_W_BF16:
-            gather_kernel<__nv_bfloat16><<<pg_blocks(npix, 128), 128, 0, s>>>(
-                first, bg, L, D, g->c2m, g->m2c, g->m2r, g->nbr, (const __nv_bfloat16 *)g->W, g->rscale, g->LV,
-                g->kp, spp, npix, g->n, image);
-            pg_count_launches(1);
-            break;
-        case PG_W_F16:
-            gather_kernel<__half><<<pg_blocks(npix, 128), 128, 0, s>>>(first, bg, L, D, g->c2m, g->m2c, g->m2r,
-                                                                      g->nbr, (const __half *)g->W, g->rscale,
-                                                                      g->LV, g->kp, spp, npix, g->n, image);
-            pg_count_launches(1);
-            break;
-    }
     PG_LAUNCH_CHECK();
     return PG_OK;
 }

@@ -111,3 +111,16 @@ def random_records(n: int, seed: int = 0, *, n_paths: int | None = None, max_len
     V["first"] = first
     V["bg"] = np.where(first < 0, rng.uniform(0.0, 1.0, n_paths), 0.0).astype(np.float32)
     return V
+
+
+def random_extra(n_paths: int, M: int, seed: int = 0) -> dict:
+    """Random extra first-vertex emitter samples, M per path (the recorder's
+    x_* arrays): random directions, about half of them delta lights."""
+    rng = np.random.default_rng(seed)
+    q = n_paths * M
+    e = unit_vectors(rng, q)
+    delta = (rng.uniform(size=q) < 0.5).astype(np.uint8)
+    return {"x_ex": np.ascontiguousarray(e[:, 0]), "x_ey": np.ascontiguousarray(e[:, 1]),
+            "x_ez": np.ascontiguousarray(e[:, 2]), "x_Le": rng.uniform(0.0, 2.0, q).astype(np.float32),
+            "x_pe": np.where(delta == 1, 0.0, rng.uniform(0.01, 1.0, q)).astype(np.float32),
+            "x_delta": delta, "extra_direct": M}

@@ -68,6 +68,7 @@ def test_argument_errors_without_gpu(lib):
     assert lib.pg_aggregate(None, None, 0, None, None, None) == 1
     assert lib.pg_propagate(None, None, None, 1, 0.0, 0, None, None, None, None) == 1
     assert lib.pg_gather(None, None, None, None, None, 0, 1, 0, 0, None, None) == 1
+    assert lib.pg_gather_ex(None, None, None, None, None, 0, 1, 0, 0, None, None, None) == 1
     assert lib.pg_graph_release_weights(None) == 1
     lib.pg_graph_destroy(None)
     assert lib.pg_status_string(4) == b"non-finite input"
