@@ -136,7 +136,9 @@ def run_gpu(args):
         sc = sc.with_(seed=rank_seed(sc.seed, rank))
     # the extra first-vertex samples come from a random stream of their own:
     # the path records are the same with or without them
+    t_tr = time.perf_counter()
     rec = pgrec.trace(sc if args.quick else sc.with_(extra_direct=EXTRA_M))
+    host_trace_s = time.perf_counter() - t_tr
     n, P = rec["n"], rec["n_paths"]
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
@@ -287,6 +289,45 @@ def run_gpu(args):
             outopt["final_gather_k%d" % kf] = t_out(final_gather_k=kf)
         outopt["final_gather_k16_extra_m%d" % EXTRA_M] = t_out(final_gather_k=16, extra=xs)
 
+    # ---- how the output changes with the number of sweeps (the paper's study
+    # of path-graph iterations): image after T sweeps against the image after
+    # the step's sweep count, on the step's graph
+    iter_study = None
+    if not args.quick:
+        Ts = [t for t in (0, 1, 2, 3, 5, 10, 15, 20, 30, 50) if t <= sc.iters]
+        imgs = {}
+        for T in Ts:
+            L_T = pg.pg_propagate(solver.graph, dev_in["L0"], T)
+            imgs[T] = pg.pg_gather(solver.graph, L_T, solver.D, dev_in["first"], dev_in["bg"], sc.spp, sc.width,
+                                   sc.height).double()
+        ref_img = imgs[Ts[-1]]
+        den = float(ref_img.norm())
+        _, res_hist, _ = pg.pg_propagate(solver.graph, dev_in["L0"], sc.iters, want_residual=True)
+        iter_study = {"sweeps": Ts,
+                      "image_rel_l2_change_vs_last": [float((imgs[T] - ref_img).norm()) / den for T in Ts],
+                      "image_mean_over_path_tracer": [float(imgs[T].mean()) / float(pt.mean()) for T in Ts],
+                      "residual_per_sweep": [float(x) for x in res_hist]}
+        del imgs
+
+    # ---- the path recorder on the GPU (not part of the step: the step starts
+    # from recorded paths), against the host recorder's wall time above
+    recorder = None
+    if not args.quick:
+        dens, alb = (torch.from_numpy(a).to(dev) for a in pgrec.medium(sc))
+        scx = sc.with_(extra_direct=EXTRA_M)
+        g_rec = pg.pg_record(scx, dens, alb)
+        torch.cuda.synchronize()
+        same = g_rec["n"] == n and bool(torch.equal(g_rec["px"].cpu(), torch.from_numpy(rec["px"])))
+        del g_rec
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(3):
+            pg.pg_record(scx, dens, alb)
+        b.record(stream)
+        torch.cuda.synchronize()
+        recorder = {"gpu_ms": a.elapsed_time(b) / 3, "host_s": host_trace_s, "host_threads": os.cpu_count(),
+                    "vertices": n, "extra_samples_per_path": EXTRA_M, "same_records_as_host": same}
+
     # ---- end to end through the public API: host records -> image on the host
     e2e_t = []
     h2d = sum(int(v.numel() * v.element_size()) for v in host.values()) + host_target.numel() * 4
@@ -331,6 +372,8 @@ def run_gpu(args):
                      "other_kernels": others},
         "precision": prec,
         "output_options_ms": outopt,
+        "path_recorder": recorder,
+        "iteration_study": iter_study,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,

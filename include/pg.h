@@ -11,6 +11,10 @@
  *                         with P from Eq. volume-propagation
  *   pg_gather             per-path output into pixels (Section 4, "Final
  *                         output", "Handling direct light")
+ *   pg_record_count,      the instrumented path tracer on the GPU (Section 4,
+ *   pg_record_fill        "Instrumented path tracer"): the per-vertex records
+ *                         the calls above take, from a voxel medium, lights
+ *                         and a pinhole camera
  *   pg_gather_ex          the same with the output options: extra emitter
  *                         samples at the first vertices (Section 4, "Handling
  *                         direct light") and a final gather (Fig. 2 caption)
@@ -279,6 +283,10 @@ pg_status pg_gather_ex(const pg_graph *g, const float *L, const float *D, const 
  *             2: from the stored weights in their forward row layout, with
  *                atomic adds into the reverse iterate (no transposed copy).
  *             Modes 1 and 2 sum in a non-deterministic order (float atomics).
+ *             grad_sigma_s of mode 0 is bitwise reproducible;
+ *             grad_g (its marginal terms) and grad_albedo_vox (the sum over a
+ *             voxel's vertices) are summed with float atomics, so repeated
+ *             calls agree to float rounding, not bitwise.
  * With grad_g, the reverse iterates of every sweep are kept for the call
  * ((iters + 1) * (n + 1) floats of temporary memory).
  * Gradients of vertices with sigma_s = 0 are reported as 0.
@@ -292,6 +300,72 @@ pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const int32_t *firs
  * pass, when memory is tight); pg_propagate then returns PG_ERR_STATE and
  * pg_propagate_adjoint needs recompute_weights = 1. */
 pg_status pg_graph_release_weights(pg_graph *g);
+
+/* ------------------------------------------------------------------------
+ * GPU path recorder (Section 4, "Instrumented path tracer": during path
+ * tracing each shading point's emitter-sampling and phase-sampling records
+ * and its incoming indirect radiance are recorded, a path's points stored
+ * contiguously in path order). One camera path per pixel sample through a
+ * pinhole camera into the unit cube [0,1]^3 holding a piecewise-constant
+ * voxel medium (nearest voxel); free flights by delta tracking against the
+ * grid's largest sigma_t, emitter samples with ratio-tracking transmittance,
+ * exact Henyey-Greenstein phase sampling, no Russian roulette (max_depth
+ * truncates). Records as described for pg_vertices, plus L0 (the path
+ * tracer's incoming indirect radiance along d, the propagation's start) and
+ * per path first / bg / the path tracer's value. Double precision inside,
+ * deterministic: the same scene and seed give the same records on every run
+ * (and the same as the repository's host recorder, which evaluates the same
+ * operations in the same order). */
+typedef struct {
+    int32_t grid_res;        /* voxels per axis */
+    const float *density;    /* device, grid_res^3 sigma_t >= 0, index x + G (y + G z) */
+    const float *albedo;     /* device, grid_res^3 albedo >= 0 */
+    float g;                 /* Henyey-Greenstein asymmetry, |g| < 1 */
+    float sun_dir[3];        /* direction the sunlight travels (a delta light) */
+    float sun_irradiance;    /* 0 = no sun */
+    float sky_radiance;      /* constant environment, 0 = none */
+    float area_radiance;     /* one-sided rectangle emitting toward +(u x v); 0 = none */
+    float area_center[3], area_u[3], area_v[3]; /* centre and half-edge vectors */
+    float p_sun;             /* probability that an emitter sample picks the sun
+                                (used when both the sun and a continuous light exist) */
+    float p_area;            /* share of the area light among the continuous lights */
+    int32_t width, height, spp, max_depth;
+    float cam_pos[3], cam_target[3], cam_fov_deg; /* vertical field of view */
+    uint64_t seed;
+    int32_t extra_direct;    /* extra emitter samples per path at its first vertex
+                                (pg_extra_samples), 0 = none */
+} pg_scene;
+
+/* Caller-allocated device outputs of pg_record_fill: n = the vertex count
+ * from pg_record_count entries per vertex array (caller order), n_paths =
+ * width*height*spp per path array, n_paths*extra_direct per extra array.
+ * voxel and val may be NULL; the rest are required (x_* only with
+ * extra_direct > 0). */
+typedef struct {
+    float *px, *py, *pz, *ox, *oy, *oz, *dx, *dy, *dz, *ex, *ey, *ez;
+    float *g, *sigma_s, *sigma_t, *w_prop, *Le, *pe_e, *Lph, *pe_ph, *L0;
+    double *L0_f64;
+    uint8_t *e_delta;
+    int32_t *succ, *voxel;
+    int32_t *first;         /* first vertex of each path, or -1 */
+    float *bg;              /* radiance of a camera ray that left the medium */
+    double *val;            /* the path tracer's value of each path */
+    float *x_ex, *x_ey, *x_ez, *x_Le, *x_pe;
+    uint8_t *x_delta;
+} pg_recording;
+
+/* Pass 1: trace every path and count its vertices. path_offsets (device,
+ * n_paths + 1 int64) receives the exclusive scan of the counts (path p's
+ * vertices are [path_offsets[p], path_offsets[p+1])); *n_vertices (host) the
+ * total. Synchronises `stream`. Errors: PG_ERR_INVALID_ARG (scene fields, a
+ * negative or non-finite grid value), PG_ERR_UNSUPPORTED (2^31 - 1 vertices
+ * or more). */
+pg_status pg_record_count(const pg_scene *scene, int64_t *path_offsets, int64_t *n_vertices, pg_stream_t stream);
+
+/* Pass 2: trace the same paths again and write their records at the offsets
+ * pass 1 produced (same scene, same seed). Asynchronous. */
+pg_status pg_record_fill(const pg_scene *scene, const int64_t *path_offsets, const pg_recording *out,
+                         pg_stream_t stream);
 
 void pg_graph_destroy(pg_graph *g);
 const char *pg_status_string(pg_status s);

@@ -177,6 +177,59 @@ def extra_from_records(rec: dict, device="cuda") -> dict:
     return out
 
 
+SCENE_FIELDS = tuple(f for f, _ in _lib.PgScene._fields_ if f not in ("density", "albedo"))
+
+
+def pg_record(scene, density: torch.Tensor, albedo: torch.Tensor, stream=None) -> dict:
+    """The GPU path recorder (pg_record_count + pg_record_fill). ``scene``:
+    any object (or dict) carrying the pg_scene fields by name; ``density``,
+    ``albedo``: device float32 grids of grid_res^3 voxels. Returns device
+    tensors keyed like the host recorder's output: the per-vertex fields,
+    ``L0_f64``, ``e_delta``, ``succ``, ``voxel``; per path ``first``, ``bg``,
+    ``pt_value``; the extra first-vertex samples ``x_*`` when requested; and
+    ``n``, ``n_paths``, ``extra_direct``."""
+    get = (lambda k: scene[k]) if isinstance(scene, dict) else (lambda k: getattr(scene, k))  # noqa: E731
+    sc = _lib.PgScene()
+    for f in SCENE_FIELDS:
+        v = get(f)
+        if isinstance(v, (tuple, list)):
+            arr = getattr(sc, f)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(sc, f, v)
+    sc.density, sc.albedo = _ptr(density).value, _ptr(albedo).value
+    P = int(sc.width) * int(sc.height) * int(sc.spp)
+    offsets = torch.empty(P + 1, dtype=torch.int64, device="cuda")
+    n = ctypes.c_int64(0)
+    check(_LIB.pg_record_count(ctypes.byref(sc), _ptr(offsets), ctypes.byref(n), _stream_ptr(stream)),
+          "pg_record_count")
+    n = int(n.value)
+    M = int(sc.extra_direct)
+    dev = torch.device("cuda")
+    nb = max(n, 1)  # never a NULL vertex array, even when no ray hits the medium
+    out = {k: torch.empty(nb, dtype=torch.float32, device=dev) for k in _lib.RECORD_VERTEX_F32}
+    out["L0_f64"] = torch.empty(nb, dtype=torch.float64, device=dev)
+    out["e_delta"] = torch.empty(nb, dtype=torch.uint8, device=dev)
+    out["succ"] = torch.empty(nb, dtype=torch.int32, device=dev)
+    out["voxel"] = torch.empty(nb, dtype=torch.int32, device=dev)
+    out["first"] = torch.empty(P, dtype=torch.int32, device=dev)
+    out["bg"] = torch.empty(P, dtype=torch.float32, device=dev)
+    out["pt_value"] = torch.empty(P, dtype=torch.float64, device=dev)
+    if M > 0:
+        for k in _lib.RECORD_EXTRA_F32:
+            out[k] = torch.empty(P * M, dtype=torch.float32, device=dev)
+        out["x_delta"] = torch.empty(P * M, dtype=torch.uint8, device=dev)
+    rec = _lib.PgRecording(**{k: out[k].data_ptr() for k in out if k != "pt_value"}, val=out["pt_value"].data_ptr())
+    check(_LIB.pg_record_fill(ctypes.byref(sc), _ptr(offsets), ctypes.byref(rec), _stream_ptr(stream)),
+          "pg_record_fill")
+    if n == 0:
+        for k in list(_lib.RECORD_VERTEX_F32) + ["L0_f64", "e_delta", "succ", "voxel"]:
+            out[k] = out[k][:0]
+    out["n"], out["n_paths"], out["extra_direct"] = n, P, M
+    return out
+
+
 def pg_propagate_adjoint(graph: Graph, dI: torch.Tensor, first: torch.Tensor, spp: int, width: int, height: int,
                          want_sigma_s: bool = True, want_g: bool = True, voxel: torch.Tensor | None = None,
                          sigma_t: torch.Tensor | None = None, n_vox: int = 0, recompute_weights: int = 0,
@@ -209,4 +262,5 @@ def launch_count() -> int:
 from .solver import Solver  # noqa: E402
 
 __all__ = ["Solver", "launch_count", "Vertices", "Graph", "PgError", "pg_build_graph", "pg_aggregate", "pg_propagate",
-           "pg_gather", "pg_gather_ex", "extra_from_records", "pg_propagate_adjoint", "pg_propagate_noalloc"]
+           "pg_gather", "pg_gather_ex", "extra_from_records", "pg_propagate_adjoint", "pg_propagate_noalloc",
+           "pg_record"]

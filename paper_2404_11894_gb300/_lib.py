@@ -44,9 +44,32 @@ class PgOutputParams(ctypes.Structure):
                 ("fg_nbr", ctypes.c_void_p)]
 
 
+class PgScene(ctypes.Structure):
+    _fields_ = [("grid_res", ctypes.c_int32), ("density", ctypes.c_void_p), ("albedo", ctypes.c_void_p),
+                ("g", ctypes.c_float), ("sun_dir", ctypes.c_float * 3), ("sun_irradiance", ctypes.c_float),
+                ("sky_radiance", ctypes.c_float), ("area_radiance", ctypes.c_float),
+                ("area_center", ctypes.c_float * 3), ("area_u", ctypes.c_float * 3), ("area_v", ctypes.c_float * 3),
+                ("p_sun", ctypes.c_float), ("p_area", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("spp", ctypes.c_int32), ("max_depth", ctypes.c_int32),
+                ("cam_pos", ctypes.c_float * 3), ("cam_target", ctypes.c_float * 3), ("cam_fov_deg", ctypes.c_float),
+                ("seed", ctypes.c_uint64), ("extra_direct", ctypes.c_int32)]
+
+
+RECORD_VERTEX_F32 = ("px", "py", "pz", "ox", "oy", "oz", "dx", "dy", "dz", "ex", "ey", "ez", "g", "sigma_s",
+                     "sigma_t", "w_prop", "Le", "pe_e", "Lph", "pe_ph", "L0")
+RECORD_EXTRA_F32 = ("x_ex", "x_ey", "x_ez", "x_Le", "x_pe")
+
+
+class PgRecording(ctypes.Structure):
+    _fields_ = ([(k, ctypes.c_void_p) for k in RECORD_VERTEX_F32]
+                + [(k, ctypes.c_void_p) for k in ("L0_f64", "e_delta", "succ", "voxel", "first", "bg", "val")]
+                + [(k, ctypes.c_void_p) for k in RECORD_EXTRA_F32 + ("x_delta",)])
+
+
 EXPORTS = ("pg_build_graph", "pg_graph_neighbors", "pg_graph_get_info", "pg_aggregate", "pg_propagate",
            "pg_gather", "pg_propagate_adjoint", "pg_graph_release_weights", "pg_graph_destroy",
-           "pg_status_string", "pg_launch_count", "pg_propagate_noalloc", "pg_gather_ex")
+           "pg_status_string", "pg_launch_count", "pg_propagate_noalloc", "pg_gather_ex",
+           "pg_record_count", "pg_record_fill")
 
 _lib = None
 
@@ -67,6 +90,8 @@ def load(path: str = LIB_PATH):
     lib.pg_aggregate.argtypes = [vp, ctypes.POINTER(PgVertices), ctypes.c_int, vp, vp, vp]
     lib.pg_propagate.argtypes = [vp, vp, vp, i32, f64, i32, vp, vp, vp, vp]
     lib.pg_gather.argtypes = [vp, vp, vp, vp, vp, i64, i32, i32, i32, vp, vp]
+    lib.pg_record_count.argtypes = [ctypes.POINTER(PgScene), vp, ctypes.POINTER(i64), vp]
+    lib.pg_record_fill.argtypes = [ctypes.POINTER(PgScene), vp, ctypes.POINTER(PgRecording), vp]
     lib.pg_gather_ex.argtypes = [vp, vp, vp, vp, vp, i64, i32, i32, i32, ctypes.POINTER(PgOutputParams), vp, vp]
     lib.pg_propagate_adjoint.argtypes = [vp, vp, vp, i64, i32, i32, i32, vp, vp, vp, vp, vp, i64, i32, vp]
     lib.pg_graph_release_weights.argtypes = [vp]

@@ -22,6 +22,11 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contra
               "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
 
 
+# translation units that must not contract a*b+c into FMAs (their double
+# arithmetic reproduces a host computation operation for operation)
+PER_FILE_FLAGS = {"pg_record.cu": ["-fmad=false"]}
+
+
 def nvcc() -> str:
     cand = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(cand):
@@ -53,7 +58,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     def compile_one(job):
         s, o = job
-        cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra_flags, "-c", s, "-o", o]
+        cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *PER_FILE_FLAGS.get(os.path.basename(s), []), *extra_flags, "-c", s,
+               "-o", o]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {os.path.basename(s)}:\n{r.stderr}")

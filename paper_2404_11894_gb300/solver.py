@@ -29,8 +29,11 @@ class Solver:
         self.last_image = None
         self.grads = None
 
-    def step(self, V: Vertices, L0, first, bg, spp, width, height, target=None, marks=None):
-        """One pass; ``marks`` maps stage names to (start, end) CUDA events."""
+    def step(self, V: Vertices, L0, first, bg, spp, width, height, target=None, marks=None, ready=None):
+        """One pass; ``marks`` maps stage names to (start, end) CUDA events.
+        ``ready``: a CUDA event the stream waits for after the graph build
+        (the build reads only positions; everything else may still be in
+        flight until then)."""
         def mark(name, i):
             if marks is not None and name in marks:
                 marks[name][i].record(torch.cuda.current_stream())
@@ -41,6 +44,8 @@ class Solver:
         self.graph = pg_build_graph(V, self.k, self.bbox_lo, self.bbox_hi, cluster_size=self.cluster_size,
                                     cluster_seed=self.cluster_seed)
         mark("build", 1)
+        if ready is not None:
+            torch.cuda.current_stream().wait_event(ready)
         mark("aggregate", 0)
         self._c, self.D = pg_aggregate(self.graph, V, self.wdtype)
         mark("aggregate", 1)
@@ -104,12 +109,34 @@ class Solver:
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
+    POSITIONS = ("px", "py", "pz")
+
     def solve_host(self, host: dict, host_target, spp, width, height):
-        """End to end from pinned host records to the image on the host."""
-        dev = {k: v.to("cuda", non_blocking=True) for k, v in host.items()}
-        tgt = host_target.to("cuda", non_blocking=True) if host_target is not None else None
+        """End to end from pinned host records to the image on the host.
+
+        The positions are copied first on the compute stream; every other
+        record is copied on a side stream while the graph is built (the build
+        reads only positions), and the aggregation waits for those copies."""
+        main = torch.cuda.current_stream()
+        if getattr(self, "_copy_stream", None) is None:
+            self._copy_stream = torch.cuda.Stream()
+        side = self._copy_stream
+        side.wait_stream(main)  # the caller's earlier work on the host buffers' device copies is done
+        dev = {k: host[k].to("cuda", non_blocking=True) for k in self.POSITIONS}
+        with torch.cuda.stream(side):
+            for k, v in host.items():
+                if k not in self.POSITIONS:
+                    dev[k] = v.to("cuda", non_blocking=True)
+            tgt = host_target.to("cuda", non_blocking=True) if host_target is not None else None
+            ready = torch.cuda.Event()
+            ready.record(side)
+        for k, t in dev.items():
+            if k not in self.POSITIONS:
+                t.record_stream(main)
+        if tgt is not None:
+            tgt.record_stream(main)
         V = Vertices({k: dev[k] for k in dev if k not in ("L0", "first", "bg")})
-        img = self.step(V, dev["L0"], dev["first"], dev["bg"], spp, width, height, tgt)
+        img = self.step(V, dev["L0"], dev["first"], dev["bg"], spp, width, height, tgt, ready=ready)
         return img.to("cpu")
 
     def close(self):

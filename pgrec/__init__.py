@@ -76,9 +76,40 @@ def _load():
         lib.pgrec_copy_paths.argtypes = [ctypes.c_void_p] * 4
         lib.pgrec_copy_medium.argtypes = [ctypes.c_void_p] * 3
         lib.pgrec_copy_extra.argtypes = [ctypes.c_void_p] * 7
+        lib.pgrec_build_medium.argtypes = [ctypes.POINTER(_Config), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.pgrec_log.argtypes = [ctypes.c_float]
+        lib.pgrec_log.restype = ctypes.c_float
+        lib.pgrec_sincos_2pi.argtypes = [ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]
         lib.pgrec_free.argtypes = [ctypes.c_void_p]
         _lib = lib
     return _lib
+
+
+def medium(scene: "Scene", albedo_grid: np.ndarray | None = None) -> tuple:
+    """The scene's (density, albedo) voxel grids, float32, grid_res^3 each
+    (index x + G (y + G z)), as :func:`trace` builds them."""
+    lib = _load()
+    G = scene.grid_res
+    dens = np.empty(G ** 3, np.float32)
+    alb = np.empty(G ** 3, np.float32)
+    ag = None
+    if albedo_grid is not None:
+        ag = np.ascontiguousarray(albedo_grid, dtype=np.float32)
+    cfg = scene._cstruct()
+    lib.pgrec_build_medium(ctypes.byref(cfg), ag.ctypes.data if ag is not None else None, dens.ctypes.data,
+                           alb.ctypes.data)
+    return dens, alb
+
+
+def elementary(name: str, x: float):
+    """The recorder's own single-precision log (``"log"``) or (sin, cos) of
+    2 pi x (``"sincos_2pi"``), x rounded to float32 first."""
+    lib = _load()
+    if name == "log":
+        return lib.pgrec_log(x)
+    s, c = ctypes.c_float(), ctypes.c_float()
+    lib.pgrec_sincos_2pi(x, ctypes.byref(s), ctypes.byref(c))
+    return s.value, c.value
 
 
 @dataclass(frozen=True)

@@ -38,6 +38,7 @@
 #endif
 
 #define PI_D 3.14159265358979323846
+#define PG_INV_4PI 0.07957746833562851f /* 1/(4 pi), float */
 
 typedef struct {
     /* medium: [0,1]^3 voxel grid, nearest-voxel lookup */
@@ -99,8 +100,9 @@ typedef struct {
     uint8_t *x_delta;    /* 1 for a delta-light sample */
     int64_t n_vertices;
     int64_t *thread_offset;
-    double majorant;     /* max sigma_t over the grid (delta-tracking bound) */
-    double p_sun;        /* probability that the emitter sample picks the sun */
+    float majorant;      /* max sigma_t over the grid (delta-tracking bound) */
+    float p_sun;         /* probability that the emitter sample picks the sun */
+    float tan_half_fov;  /* tan of half the vertical field of view */
 } pgrec_state;
 
 /* ---------------- random numbers ---------------- */
@@ -110,9 +112,70 @@ static inline uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
     return z ^ (z >> 31);
 }
-static inline double rnd(rng_t *r) {
+/* uniform on [0, 1) with 24 random bits (exact in float) */
+static inline float rnd(rng_t *r) {
     r->s += 0x9E3779B97F4A7C15ULL;
-    return (double)(mix64(r->s) >> 11) * (1.0 / 9007199254740992.0);
+    return (float)(mix64(r->s) >> 40) * (1.0f / 16777216.0f);
+}
+
+/* ---------------- elementary functions ----------------
+ * The path tracing runs in single precision with its own logarithm and
+ * sin/cos (rather than the C library's), built without FMA contraction, so
+ * that the GPU recorder, which evaluates the same formulas in the same order,
+ * produces bit-identical paths: both use only IEEE-rounded +, -, *, /, sqrt
+ * and exact operations (frexp, floor, scaling by powers of two).
+ *
+ * pg_log: x = m 2^e with m in [1/sqrt2, sqrt2); log m = 2 artanh(s),
+ * s = (m - 1)/(m + 1), |s| <= 0.1716, by its odd power series to s^11
+ * (remainder below 1e-10); log x = e ln2 + log m with ln2 split into a
+ * 12-bit head (e * head exact) and a tail. */
+static const float PG_LN2_HI = 0.693115234375f, PG_LN2_LO = 3.194618329871446e-05f;
+static const float PG_ATANH_C[5] = {0.3333333432674408f, 0.20000000298023224f, 0.1428571492433548f,
+                                    0.1111111119389534f, 0.09090909361839294f}; /* 1/3, 1/5, ..., 1/11 */
+static float pg_log(float x) {
+    int e;
+    float m = frexpf(x, &e);
+    if (m < 0.7071067690849304f) {
+        m = m * 2.0f;
+        e = e - 1;
+    }
+    float s = (m - 1.0f) / (m + 1.0f);
+    float s2 = s * s;
+    float p = PG_ATANH_C[4];
+    for (int k = 3; k >= 0; k--) p = p * s2 + PG_ATANH_C[k];
+    p = p * s2 + 1.0f;
+    float lm = 2.0f * s * p;
+    return (float)e * PG_LN2_HI + ((float)e * PG_LN2_LO + lm);
+}
+
+/* pg_sincos_2pi: sin and cos of 2 pi u for u in [0, 1). 4u = q + f
+ * (quadrant q, f in [0, 1), both exact), a = f pi/2 in [0, pi/2), Taylor
+ * series of sin a to a^13 and cos a to a^12 (remainder below 1e-8), then the
+ * quadrant's symmetry. */
+static const float PG_HALF_PI = 1.5707963705062866f;
+static const float PG_SIN_C[6] = {-0.1666666716337204f, 0.008333333767950535f, -0.00019841270113829523f,
+                                  2.7557318844628753e-06f, -2.5052107943679403e-08f,
+                                  1.6059044372074283e-10f}; /* (-1)^k/(2k+1)! */
+static const float PG_COS_C[6] = {-0.5f, 0.0416666679084301f, -0.0013888889225199819f, 2.4801587642286904e-05f,
+                                  -2.755731998149713e-07f, 2.0876755879584152e-09f}; /* (-1)^k/(2k)! */
+static void pg_sincos_2pi(float u, float *s_out, float *c_out) {
+    float t = 4.0f * u;
+    float q = floorf(t);
+    float f = t - q;
+    float a = f * PG_HALF_PI;
+    float a2 = a * a;
+    float ps = PG_SIN_C[5], pc = PG_COS_C[5];
+    for (int k = 4; k >= 0; k--) {
+        ps = ps * a2 + PG_SIN_C[k];
+        pc = pc * a2 + PG_COS_C[k];
+    }
+    float sa = a + a * (a2 * ps);
+    float ca = 1.0f + a2 * pc;
+    int qi = (int)q & 3;
+    if (qi == 0) { *s_out = sa; *c_out = ca; }
+    else if (qi == 1) { *s_out = ca; *c_out = -sa; }
+    else if (qi == 2) { *s_out = -sa; *c_out = -ca; }
+    else { *s_out = -ca; *c_out = sa; }
 }
 
 /* ---------------- value noise ---------------- */
@@ -179,9 +242,10 @@ static void build_medium(pgrec_state *st, const float *albedo_grid) {
     }
 }
 
-static inline int64_t voxel_of(const pgrec_config *c, double x, double y, double z) {
+static inline int64_t voxel_of(const pgrec_config *c, float x, float y, float z) {
     int64_t G = c->grid_res;
-    int64_t ix = (int64_t)floor(x * G), iy = (int64_t)floor(y * G), iz = (int64_t)floor(z * G);
+    float Gf = (float)c->grid_res;
+    int64_t ix = (int64_t)floorf(x * Gf), iy = (int64_t)floorf(y * Gf), iz = (int64_t)floorf(z * Gf);
     if (ix < 0) ix = 0;
     if (iy < 0) iy = 0;
     if (iz < 0) iz = 0;
@@ -192,42 +256,43 @@ static inline int64_t voxel_of(const pgrec_config *c, double x, double y, double
 }
 
 /* ray / unit-box slab test; returns 0 if missed */
-static int box_hit(const double o[3], const double d[3], double *t0, double *t1) {
-    double tn = -1e300, tf = 1e300;
+static int box_hit(const float o[3], const float d[3], float *t0, float *t1) {
+    float tn = -1e30f, tf = 1e30f;
     for (int a = 0; a < 3; a++) {
-        if (fabs(d[a]) < 1e-300) {
-            if (o[a] < 0.0 || o[a] > 1.0) return 0;
+        if (fabsf(d[a]) < 1e-30f) {
+            if (o[a] < 0.0f || o[a] > 1.0f) return 0;
             continue;
         }
-        double inv = 1.0 / d[a];
-        double ta = (0.0 - o[a]) * inv, tb = (1.0 - o[a]) * inv;
-        if (ta > tb) { double tmp = ta; ta = tb; tb = tmp; }
+        float inv = 1.0f / d[a];
+        float ta = (0.0f - o[a]) * inv, tb = (1.0f - o[a]) * inv;
+        if (ta > tb) { float tmp = ta; ta = tb; tb = tmp; }
         if (ta > tn) tn = ta;
         if (tb < tf) tf = tb;
     }
     if (tn > tf) return 0;
     *t0 = tn;
     *t1 = tf;
-    return tf > 0.0;
+    return tf > 0.0f;
 }
 
-static inline double sigma_t_at(const pgrec_state *st, double x, double y, double z) {
+static inline float sigma_t_at(const pgrec_state *st, float x, float y, float z) {
     return st->density[voxel_of(&st->cfg, x, y, z)];
 }
 
 /* delta tracking from p along d (p inside or outside the box).
  * Returns 1 and the collision point if a real collision happens. */
-static int delta_track(const pgrec_state *st, rng_t *r, const double p[3], const double d[3], double out[3]) {
-    double t0, t1;
-    double majorant = st->majorant;
-    if (majorant <= 0.0) return 0;
+static int delta_track(const pgrec_state *st, rng_t *r, const float p[3], const float d[3], float out[3]) {
+    float t0, t1;
+    float majorant = st->majorant;
+    if (majorant <= 0.0f) return 0;
     if (!box_hit(p, d, &t0, &t1)) return 0;
-    double t = t0 > 0.0 ? t0 : 0.0;
+    float inv_maj = 1.0f / majorant;
+    float t = t0 > 0.0f ? t0 : 0.0f;
     for (;;) {
-        t -= log(1.0 - rnd(r)) / majorant;
+        t = t - pg_log(1.0f - rnd(r)) * inv_maj;
         if (t >= t1) return 0;
-        double x = p[0] + t * d[0], y = p[1] + t * d[1], z = p[2] + t * d[2];
-        double s = sigma_t_at(st, x, y, z);
+        float x = p[0] + t * d[0], y = p[1] + t * d[1], z = p[2] + t * d[2];
+        float s = sigma_t_at(st, x, y, z);
         if (rnd(r) * majorant < s) {
             out[0] = x; out[1] = y; out[2] = z;
             return 1;
@@ -235,33 +300,34 @@ static int delta_track(const pgrec_state *st, rng_t *r, const double p[3], const
     }
 }
 
-/* ratio-tracking transmittance estimate from p along d up to distance tmax */
-static double ratio_track(const pgrec_state *st, rng_t *r, const double p[3], const double d[3], double tmax) {
-    double t0, t1;
-    double majorant = st->majorant;
-    if (majorant <= 0.0) return 1.0;
-    if (!box_hit(p, d, &t0, &t1)) return 1.0;
-    if (t1 > tmax) t1 = tmax;
-    double t = t0 > 0.0 ? t0 : 0.0, T = 1.0;
+/* ratio-tracking transmittance estimate from p along d to the box exit */
+static float ratio_track(const pgrec_state *st, rng_t *r, const float p[3], const float d[3]) {
+    float t0, t1;
+    float majorant = st->majorant;
+    if (majorant <= 0.0f) return 1.0f;
+    if (!box_hit(p, d, &t0, &t1)) return 1.0f;
+    float inv_maj = 1.0f / majorant;
+    float t = t0 > 0.0f ? t0 : 0.0f, T = 1.0f;
     for (;;) {
-        t -= log(1.0 - rnd(r)) / majorant;
+        t = t - pg_log(1.0f - rnd(r)) * inv_maj;
         if (t >= t1) return T;
-        double s = sigma_t_at(st, p[0] + t * d[0], p[1] + t * d[1], p[2] + t * d[2]);
-        T *= 1.0 - s / majorant;
+        float s = sigma_t_at(st, p[0] + t * d[0], p[1] + t * d[1], p[2] + t * d[2]);
+        T = T * (1.0f - s * inv_maj);
     }
 }
 
-static inline void normalize3(double v[3]) {
-    double l = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+static inline void normalize3(float v[3]) {
+    float l = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     v[0] /= l; v[1] /= l; v[2] /= l;
 }
-static inline void cross3(const double a[3], const double b[3], double c[3]) {
+static inline void cross3(const float a[3], const float b[3], float c[3]) {
     c[0] = a[1] * b[2] - a[2] * b[1];
     c[1] = a[2] * b[0] - a[0] * b[2];
     c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-/* Henyey-Greenstein density for outgoing direction o and light direction d */
+/* Henyey-Greenstein density for outgoing direction o and light direction d
+ * (double: the path tracer's own estimate below) */
 static inline double hg_eval(double g, const double o[3], const double d[3]) {
     double od = o[0] * d[0] + o[1] * d[1] + o[2] * d[2];
     double den = 1.0 + g * g + 2.0 * g * od;
@@ -269,71 +335,72 @@ static inline double hg_eval(double g, const double o[3], const double d[3]) {
 }
 
 /* sample d ~ HG around the travel direction w = -o */
-static void hg_sample(double g, const double o[3], rng_t *r, double d[3]) {
-    double u1 = rnd(r), u2 = rnd(r), ct;
-    if (fabs(g) < 1e-6) {
-        ct = 1.0 - 2.0 * u1;
+static void hg_sample(float g, const float o[3], rng_t *r, float d[3]) {
+    float u1 = rnd(r), u2 = rnd(r), ct;
+    if (fabsf(g) < 1e-6f) {
+        ct = 1.0f - 2.0f * u1;
     } else {
-        double s = (1.0 - g * g) / (1.0 - g + 2.0 * g * u1);
-        ct = (1.0 + g * g - s * s) / (2.0 * g);
+        float s = (1.0f - g * g) / (1.0f - g + 2.0f * g * u1);
+        ct = (1.0f + g * g - s * s) / (2.0f * g);
     }
-    if (ct > 1.0) ct = 1.0;
-    if (ct < -1.0) ct = -1.0;
-    double st_ = sqrt(1.0 - ct * ct), ph = 2.0 * PI_D * u2;
-    double w[3] = {-o[0], -o[1], -o[2]}, a[3], u[3], v[3];
-    if (fabs(w[0]) > 0.9) { a[0] = 0; a[1] = 1; a[2] = 0; } else { a[0] = 1; a[1] = 0; a[2] = 0; }
+    if (ct > 1.0f) ct = 1.0f;
+    if (ct < -1.0f) ct = -1.0f;
+    float st_ = sqrtf(1.0f - ct * ct), sp, cp;
+    pg_sincos_2pi(u2, &sp, &cp);
+    float w[3] = {-o[0], -o[1], -o[2]}, a[3], u[3], v[3];
+    if (fabsf(w[0]) > 0.9f) { a[0] = 0; a[1] = 1; a[2] = 0; } else { a[0] = 1; a[1] = 0; a[2] = 0; }
     cross3(w, a, u); normalize3(u);
     cross3(w, u, v);
-    for (int i = 0; i < 3; i++) d[i] = st_ * cos(ph) * u[i] + st_ * sin(ph) * v[i] + ct * w[i];
+    for (int i = 0; i < 3; i++) d[i] = st_ * cp * u[i] + st_ * sp * v[i] + ct * w[i];
     normalize3(d);
 }
 
 /* area light: ray from p along d; returns distance to the rectangle or -1 */
-static double area_hit(const pgrec_config *c, const double p[3], const double d[3], double *cos_l) {
-    double u[3] = {c->area_u[0], c->area_u[1], c->area_u[2]};
-    double v[3] = {c->area_v[0], c->area_v[1], c->area_v[2]};
-    double n[3];
+static float area_hit(const pgrec_config *c, const float p[3], const float d[3], float *cos_l) {
+    float u[3] = {c->area_u[0], c->area_u[1], c->area_u[2]};
+    float v[3] = {c->area_v[0], c->area_v[1], c->area_v[2]};
+    float n[3];
     cross3(u, v, n);
     normalize3(n);
-    double dn = d[0] * n[0] + d[1] * n[1] + d[2] * n[2];
-    if (dn >= 0.0) return -1.0; /* one-sided: visible only from its +n side */
-    double q[3] = {c->area_center[0] - p[0], c->area_center[1] - p[1], c->area_center[2] - p[2]};
-    double t = (q[0] * n[0] + q[1] * n[1] + q[2] * n[2]) / dn;
-    if (t <= 0.0) return -1.0;
-    double h[3] = {p[0] + t * d[0] - c->area_center[0], p[1] + t * d[1] - c->area_center[1],
-                   p[2] + t * d[2] - c->area_center[2]};
-    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2], vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-    double a = (h[0] * u[0] + h[1] * u[1] + h[2] * u[2]) / uu;
-    double b = (h[0] * v[0] + h[1] * v[1] + h[2] * v[2]) / vv;
-    if (fabs(a) > 1.0 || fabs(b) > 1.0) return -1.0;
+    float dn = d[0] * n[0] + d[1] * n[1] + d[2] * n[2];
+    if (dn >= 0.0f) return -1.0f; /* one-sided: visible only from its +n side */
+    float q[3] = {c->area_center[0] - p[0], c->area_center[1] - p[1], c->area_center[2] - p[2]};
+    float t = (q[0] * n[0] + q[1] * n[1] + q[2] * n[2]) / dn;
+    if (t <= 0.0f) return -1.0f;
+    float h[3] = {p[0] + t * d[0] - c->area_center[0], p[1] + t * d[1] - c->area_center[1],
+                  p[2] + t * d[2] - c->area_center[2]};
+    float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2], vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    float a = (h[0] * u[0] + h[1] * u[1] + h[2] * u[2]) / uu;
+    float b = (h[0] * v[0] + h[1] * v[1] + h[2] * v[2]) / vv;
+    if (fabsf(a) > 1.0f || fabsf(b) > 1.0f) return -1.0f;
     *cos_l = -dn;
     return t;
 }
 
-static double area_size(const pgrec_config *c) {
-    double u[3] = {c->area_u[0], c->area_u[1], c->area_u[2]};
-    double v[3] = {c->area_v[0], c->area_v[1], c->area_v[2]}, n[3];
+static float area_size(const pgrec_config *c) {
+    float u[3] = {c->area_u[0], c->area_u[1], c->area_u[2]};
+    float v[3] = {c->area_v[0], c->area_v[1], c->area_v[2]}, n[3];
     cross3(u, v, n);
-    return 4.0 * sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    return 4.0f * sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
 }
 
 /* continuous-emitter radiance seen from p along d (ignoring the medium) and
  * the selection-weighted solid-angle pdf of the continuous strategy */
-static void continuous_emission(const pgrec_config *c, double p_cont, const double p[3], const double d[3], double *L,
-                                double *pdf) {
+static void continuous_emission(const pgrec_config *c, float p_cont, const float p[3], const float d[3], float *L,
+                                float *pdf) {
     int has_area = c->area_radiance > 0, has_sky = c->sky_radiance > 0;
-    double pa = has_area ? (has_sky ? c->p_area : 1.0) : 0.0;
-    double L_ = 0.0, pdf_ = 0.0;
+    float pa = has_area ? (has_sky ? c->p_area : 1.0f) : 0.0f;
+    float L_ = 0.0f, pdf_ = 0.0f;
     if (has_sky) {
-        L_ += c->sky_radiance;
-        pdf_ += (1.0 - pa) / (4.0 * PI_D);
+        L_ = L_ + c->sky_radiance;
+        pdf_ = pdf_ + (1.0f - pa) * PG_INV_4PI;
     }
     if (has_area) {
-        double cl;
-        double t = area_hit(c, p, d, &cl);
+        float cl;
+        float t = area_hit(c, p, d, &cl);
         if (t > 0) {
-            L_ += c->area_radiance;
-            pdf_ += pa * t * t / (area_size(c) * cl);
+            L_ = L_ + c->area_radiance;
+            pdf_ = pdf_ + pa * t * t / (area_size(c) * cl);
         }
     }
     *L = L_;
@@ -346,33 +413,34 @@ static void continuous_emission(const pgrec_config *c, double p_cont, const doub
  * the radiance it delivers (transmittance to the medium box included; for the
  * sun divided by p_sun) and the continuous strategy's pdf of that direction
  * (selection included; 0 for the sun). */
-static void sample_emitter(const pgrec_state *st, rng_t *r, const double x[3], const double sun_to[3], int has_cont,
-                           double e[3], double *Le_out, double *pe_out, int *delta_out) {
+static void sample_emitter(const pgrec_state *st, rng_t *r, const float x[3], const float sun_to[3], int has_cont,
+                           float e[3], float *Le_out, float *pe_out, int *delta_out) {
     const pgrec_config *c = &st->cfg;
-    double Le = 0.0, pe = 0.0;
+    float Le = 0.0f, pe = 0.0f;
     int delta = 0;
-    double u = rnd(r);
+    float u = rnd(r);
     if (u < st->p_sun) {
         e[0] = sun_to[0]; e[1] = sun_to[1]; e[2] = sun_to[2];
         delta = 1;
-        Le = c->sun_irradiance / st->p_sun * ratio_track(st, r, x, e, 1e300);
+        Le = c->sun_irradiance / st->p_sun * ratio_track(st, r, x, e);
     } else if (has_cont) {
         int has_area = c->area_radiance > 0, has_sky = c->sky_radiance > 0;
-        double pa = has_area ? (has_sky ? c->p_area : 1.0) : 0.0;
+        float pa = has_area ? (has_sky ? c->p_area : 1.0f) : 0.0f;
         if (rnd(r) < pa) {
-            double a = 2.0 * rnd(r) - 1.0, bb = 2.0 * rnd(r) - 1.0, y[3];
+            float a = 2.0f * rnd(r) - 1.0f, bb = 2.0f * rnd(r) - 1.0f, y[3];
             for (int i = 0; i < 3; i++) y[i] = c->area_center[i] + a * c->area_u[i] + bb * c->area_v[i];
             for (int i = 0; i < 3; i++) e[i] = y[i] - x[i];
             normalize3(e);
         } else {
-            double z = 1.0 - 2.0 * rnd(r), ph = 2.0 * PI_D * rnd(r), s = sqrt(fmax(0.0, 1.0 - z * z));
-            e[0] = s * cos(ph); e[1] = s * sin(ph); e[2] = z;
+            float z = 1.0f - 2.0f * rnd(r), sp, cp, s = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+            pg_sincos_2pi(rnd(r), &sp, &cp);
+            e[0] = s * cp; e[1] = s * sp; e[2] = z;
         }
-        double Lc, pc;
-        continuous_emission(c, 1.0 - st->p_sun, x, e, &Lc, &pc);
+        float Lc, pc;
+        continuous_emission(c, 1.0f - st->p_sun, x, e, &Lc, &pc);
         pe = pc;
         /* the lights sit outside the medium box: transmittance to the box exit */
-        Le = Lc > 0 ? Lc * ratio_track(st, r, x, e, 1e300) : 0.0;
+        Le = Lc > 0 ? Lc * ratio_track(st, r, x, e) : 0.0f;
     } else {
         e[0] = sun_to[0]; e[1] = sun_to[1]; e[2] = sun_to[2];
     }
@@ -406,19 +474,19 @@ static double trace_path(pgrec_state *st, int64_t pi, vbuf *b, int64_t *first_lo
     int64_t pix = pi / c->spp;
     int64_t px_ = pix % c->width, py_ = pix / c->width;
     /* pinhole camera */
-    double fwd[3] = {c->cam_target[0] - c->cam_pos[0], c->cam_target[1] - c->cam_pos[1], c->cam_target[2] - c->cam_pos[2]};
+    float fwd[3] = {c->cam_target[0] - c->cam_pos[0], c->cam_target[1] - c->cam_pos[1], c->cam_target[2] - c->cam_pos[2]};
     normalize3(fwd);
-    double up0[3] = {0, 1, 0}, right[3], up[3];
+    float up0[3] = {0, 1, 0}, right[3], up[3];
     cross3(fwd, up0, right); normalize3(right);
     cross3(right, fwd, up);
-    double th = tan(0.5 * c->cam_fov_deg * PI_D / 180.0);
-    double aspect = (double)c->width / c->height;
-    double sx = ((px_ + rnd(&r)) / c->width * 2.0 - 1.0) * th * aspect;
-    double sy = (1.0 - (py_ + rnd(&r)) / c->height * 2.0) * th;
-    double dir[3];
+    float th = st->tan_half_fov;
+    float aspect = (float)c->width / (float)c->height;
+    float sx = (((float)px_ + rnd(&r)) / (float)c->width * 2.0f - 1.0f) * th * aspect;
+    float sy = (1.0f - ((float)py_ + rnd(&r)) / (float)c->height * 2.0f) * th;
+    float dir[3];
     for (int i = 0; i < 3; i++) dir[i] = fwd[i] + sx * right[i] + sy * up[i];
     normalize3(dir);
-    double pos[3] = {c->cam_pos[0], c->cam_pos[1], c->cam_pos[2]}, x[3];
+    float pos[3] = {c->cam_pos[0], c->cam_pos[1], c->cam_pos[2]}, x[3];
 
     *first_local = -1;
     *bg_out = 0.0f;
@@ -429,52 +497,52 @@ static double trace_path(pgrec_state *st, int64_t pi, vbuf *b, int64_t *first_lo
         st->x_Le[q] = 0.0f; st->x_pe[q] = 0.0f; st->x_delta[q] = 0;
     }
     if (!delta_track(st, &r, pos, dir, x)) {
-        double L, pdf;
-        continuous_emission(c, 1.0 - st->p_sun, pos, dir, &L, &pdf);
-        *bg_out = (float)L;
-        return (double)(float)L;
+        float L, pdf;
+        continuous_emission(c, 1.0f - st->p_sun, pos, dir, &L, &pdf);
+        *bg_out = L;
+        return (double)L;
     }
     int64_t start = b->n;
     int has_cont = c->sky_radiance > 0 || c->area_radiance > 0;
-    double sun_to[3] = {-c->sun_dir[0], -c->sun_dir[1], -c->sun_dir[2]};
+    float sun_to[3] = {-c->sun_dir[0], -c->sun_dir[1], -c->sun_dir[2]};
     normalize3(sun_to);
-    double o[3] = {-dir[0], -dir[1], -dir[2]};
-    const double x_first[3] = {x[0], x[1], x[2]};
+    float o[3] = {-dir[0], -dir[1], -dir[2]};
+    const float x_first[3] = {x[0], x[1], x[2]};
     for (int depth = 0; depth < c->max_depth; depth++) {
         if (b->n == b->cap) vbuf_grow(b);
         int64_t v = b->n++;
         int64_t vox = voxel_of(c, x[0], x[1], x[2]);
-        double sig_t = st->density[vox];
-        double alb = st->albedo_grid[vox];
-        b->px[v] = (float)x[0]; b->py[v] = (float)x[1]; b->pz[v] = (float)x[2];
-        b->ox[v] = (float)o[0]; b->oy[v] = (float)o[1]; b->oz[v] = (float)o[2];
+        float sig_t = st->density[vox];
+        float alb = st->albedo_grid[vox];
+        b->px[v] = x[0]; b->py[v] = x[1]; b->pz[v] = x[2];
+        b->ox[v] = o[0]; b->oy[v] = o[1]; b->oz[v] = o[2];
         b->g[v] = c->g;
-        b->sigma_t[v] = (float)sig_t;
-        b->sigma_s[v] = (float)(alb * sig_t);
-        b->w_prop[v] = (float)(1.0 / sig_t); /* tau / p_t under delta tracking */
+        b->sigma_t[v] = sig_t;
+        b->sigma_s[v] = alb * sig_t;
+        b->w_prop[v] = 1.0f / sig_t; /* tau / p_t under delta tracking */
         b->voxel[v] = (int32_t)vox;
         /* emitter sample */
-        double e[3], Le, pe;
+        float e[3], Le, pe;
         int delta;
         sample_emitter(st, &r, x, sun_to, has_cont, e, &Le, &pe, &delta);
-        b->ex[v] = (float)e[0]; b->ey[v] = (float)e[1]; b->ez[v] = (float)e[2];
-        b->Le[v] = (float)Le;
-        b->pe_e[v] = (float)pe;
+        b->ex[v] = e[0]; b->ey[v] = e[1]; b->ez[v] = e[2];
+        b->Le[v] = Le;
+        b->pe_e[v] = pe;
         b->e_delta[v] = (uint8_t)delta;
         /* phase sample and the continuation */
-        double d[3], xn[3];
+        float d[3], xn[3];
         hg_sample(c->g, o, &r, d);
-        b->dx[v] = (float)d[0]; b->dy[v] = (float)d[1]; b->dz[v] = (float)d[2];
+        b->dx[v] = d[0]; b->dy[v] = d[1]; b->dz[v] = d[2];
         b->succ_local[v] = -1;
         b->Lph[v] = 0.0f;
         b->pe_ph[v] = 0.0f;
         int hit = delta_track(st, &r, x, d, xn);
         if (!hit) {
             if (has_cont) {
-                double Lc, pc;
-                continuous_emission(c, 1.0 - st->p_sun, x, d, &Lc, &pc);
-                b->Lph[v] = (float)Lc;
-                b->pe_ph[v] = (float)pc;
+                float Lc, pc;
+                continuous_emission(c, 1.0f - st->p_sun, x, d, &Lc, &pc);
+                b->Lph[v] = Lc;
+                b->pe_ph[v] = pc;
             }
             break;
         }
@@ -491,13 +559,13 @@ static double trace_path(pgrec_state *st, int64_t pi, vbuf *b, int64_t *first_lo
         rng_t rx;
         rx.s = mix64(c->seed ^ mix64((uint64_t)pi + 0xD1B54A32D192ED03ULL) ^ 0x8CB92BA72F3D8DD7ULL);
         for (int i = 0; i < M; i++) {
-            double e[3], Le, pe;
+            float e[3], Le, pe;
             int delta;
             sample_emitter(st, &rx, x_first, sun_to, has_cont, e, &Le, &pe, &delta);
             int64_t q = pi * M + i;
-            st->x_e[3 * q] = (float)e[0]; st->x_e[3 * q + 1] = (float)e[1]; st->x_e[3 * q + 2] = (float)e[2];
-            st->x_Le[q] = (float)Le;
-            st->x_pe[q] = (float)pe;
+            st->x_e[3 * q] = e[0]; st->x_e[3 * q + 1] = e[1]; st->x_e[3 * q + 2] = e[2];
+            st->x_Le[q] = Le;
+            st->x_pe[q] = pe;
             st->x_delta[q] = (uint8_t)delta;
         }
     }
@@ -546,15 +614,16 @@ void *pgrec_trace(const pgrec_config *cfg, const float *albedo_grid, int32_t nth
 #endif
     build_medium(st, albedo_grid);
     int64_t G = cfg->grid_res, nv = G * G * G;
-    double mx = 0.0;
+    float mx = 0.0f;
     for (int64_t i = 0; i < nv; i++) mx = st->density[i] > mx ? st->density[i] : mx;
     st->majorant = mx;
     {
         int has_cont = cfg->sky_radiance > 0 || cfg->area_radiance > 0;
-        if (cfg->sun_irradiance <= 0) st->p_sun = 0.0;
-        else if (!has_cont) st->p_sun = 1.0;
+        if (cfg->sun_irradiance <= 0) st->p_sun = 0.0f;
+        else if (!has_cont) st->p_sun = 1.0f;
         else st->p_sun = cfg->p_sun;
     }
+    st->tan_half_fov = (float)tan(0.5 * cfg->cam_fov_deg * PI_D / 180.0);
     st->n_paths = (int64_t)cfg->width * cfg->height * cfg->spp;
     st->nthreads = nthreads;
     st->bufs = (vbuf *)calloc(nthreads, sizeof(vbuf));
@@ -677,3 +746,20 @@ void pgrec_free(void *h) {
     free(st->albedo_grid);
     free(st);
 }
+
+/* the medium grids alone (grid_res^3 sigma_t and albedo), as pgrec_trace builds them */
+void pgrec_build_medium(const pgrec_config *cfg, const float *albedo_grid, float *density_out, float *albedo_out) {
+    pgrec_state st;
+    memset(&st, 0, sizeof(st));
+    st.cfg = *cfg;
+    build_medium(&st, albedo_grid);
+    int64_t G = cfg->grid_res, nv = G * G * G;
+    memcpy(density_out, st.density, sizeof(float) * nv);
+    memcpy(albedo_out, st.albedo_grid, sizeof(float) * nv);
+    free(st.density);
+    free(st.albedo_grid);
+}
+
+/* the recorder's elementary functions, exported for their tests */
+float pgrec_log(float x) { return pg_log(x); }
+void pgrec_sincos_2pi(float u, float *s, float *c) { pg_sincos_2pi(u, s, c); }
