@@ -204,12 +204,18 @@ static constexpr int TS_THREADS = 256;
 // with the column extents two groups ahead, so a column's DRAM round trip
 // overlaps the previous one's L2 round trip. Columns longer than 32 entries
 // take their remaining passes unpipelined.
-template <typename WT, int MINB>
+// Column schedules as in the forward sweep: contiguous chunks per block, or
+// (FRONT) tiles of TS_TILE_GROUPS column groups dealt round-robin to the
+// blocks, so all blocks work in one window of the column order and the
+// gathered reverse iterates of that window stay in L2.
+static constexpr int TS_TILE_GROUPS = 64;
+
+template <typename WT, int MINB, bool FRONT>
 __global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_pf_kernel(
     const int64_t *__restrict__ tptr, const int2 *__restrict__ tent,
     const float *__restrict__ us_in, const float *__restrict__ mu_in, const float *__restrict__ y_t,
     const float *__restrict__ rscale, int64_t ncols, int write_out, float *__restrict__ mu_out,
-    float *__restrict__ us_out, float *__restrict__ G, float *__restrict__ B) {
+    float *__restrict__ us_out, float *__restrict__ G, float *__restrict__ B, int tile_groups) {
     constexpr int LPC = 4, PAIRS = 4; // 4 lanes x 4 pairs = 32 entries per pass
     constexpr int CPB = TS_THREADS / LPC;
     const int lane = threadIdx.x & 31;
@@ -217,8 +223,13 @@ __global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_pf_kernel(
     const int lead = lane & ~(LPC - 1);
     const bool acc_g = y_t != nullptr;
     const int64_t chunk = ((ncols + gridDim.x - 1) / gridDim.x + CPB - 1) / CPB * CPB;
-    const int64_t c0 = (int64_t)blockIdx.x * chunk;
-    const int64_t c1 = min(ncols, c0 + chunk);
+    const int64_t c0 = FRONT ? 0 : (int64_t)blockIdx.x * chunk;
+    const int64_t c1 = FRONT ? ncols : min(ncols, c0 + chunk);
+    auto gbase = [&](int64_t k) -> int64_t {
+        if (!FRONT) return c0 + k * CPB;
+        const int64_t tile = k / tile_groups;
+        return (tile * gridDim.x + blockIdx.x) * ((int64_t)CPB * tile_groups) + (k - tile * tile_groups) * CPB;
+    };
     const int cl = threadIdx.x / LPC;
     auto extent = [&](int64_t c, int64_t &a, int64_t &b) {
         a = b = 0;
@@ -238,14 +249,14 @@ __global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_pf_kernel(
     int4 en[PAIRS];         // first pass of the next group
     {
         int64_t a0, b0;
-        extent(c0 + cl, a0, b0);
+        extent(gbase(0) + cl, a0, b0);
         first_pass(a0, b0, en);
-        extent(c0 + CPB + cl, a1, b1);
+        extent(gbase(1) + cl, a1, b1);
         // the current group's extent travels with its entries
         a2 = a0;
         b2 = b0;
     }
-    for (int64_t base = c0; base < c1; base += CPB) {
+    for (int64_t k = 0, base = gbase(0); base < c1; base = gbase(++k)) {
         const int64_t c = base + cl;
         const bool ok = c < c1;
         const int64_t ca = a2, cb = b2; // this group's extent
@@ -256,7 +267,7 @@ __global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_pf_kernel(
         first_pass(a1, b1, en);
         a2 = a1;
         b2 = b1;
-        extent(base + 2 * CPB + cl, a1, b1);
+        extent(gbase(k + 2) + cl, a1, b1);
         float sv = 0.0f, rs = 1.0f; // column scalars: lane 0 mu_in, 1 y_t, 2 G, 3 B
         if (ok && acc_g) {
             if (q == 0) sv = mu_in[c];
@@ -619,10 +630,16 @@ static pg_status adjoint_store(pg_graph *g, float *us0, float *mu_a, float *mu_b
     int64_t need = (na * 4 + TS_THREADS - 1) / TS_THREADS;
     int64_t cap = (int64_t)pg_num_sms() * 4;
     const int tb = (int)(need < cap ? (need > 0 ? need : 1) : cap);
+    const bool front = pg_sweep_front(na);
+    const int tgr = TS_TILE_GROUPS;
     auto tsweep = [&](const pg_tcsr &t, const float *us_in, const float *mu_in, const float *y_t, int wo,
                       float *mu_out, float *us_out) {
-        tsweep_pf_kernel<WT, 4><<<tb, TS_THREADS, 0, s>>>(t.ptr, t.ent, us_in, mu_in, y_t, rs, na, wo, mu_out, us_out,
-                                                          G, B);
+        if (front)
+            tsweep_pf_kernel<WT, 4, true><<<tb, TS_THREADS, 0, s>>>(t.ptr, t.ent, us_in, mu_in, y_t, rs, na, wo, mu_out,
+                                                                    us_out, G, B, tgr);
+        else
+            tsweep_pf_kernel<WT, 4, false><<<tb, TS_THREADS, 0, s>>>(t.ptr, t.ent, us_in, mu_in, y_t, rs, na, wo,
+                                                                     mu_out, us_out, G, B, tgr);
     };
     // mu_t lives in slice t of the history when one is kept, else ping-pong
     auto mu_slot = [&](int t) { return muhist ? muhist + (int64_t)t * stride : ((t & 1) ? mu_b : mu_a); };

@@ -265,4 +265,7 @@ pg_status pg_launch_knn_queries(const pg_graph *g, const int32_t *qm, int64_t nq
 // cluster neighbourhoods (keys: the vertices' sorted Morton cell keys)
 pg_status pg_launch_clusters(pg_graph *g, const uint32_t *keys, int32_t K, uint64_t seed, cudaStream_t s);
 void pg_free_transposes(pg_graph *g); // releases both transposes (weights changed)
+// whether the sweeps deal their rows / columns to the blocks in round-robin
+// tiles (a window of the Morton order at a time) rather than in chunks
+bool pg_sweep_front(int64_t n_active);
 pg_status pg_launch_aggregate(pg_graph *g, float *c_out, float *D_out, cudaStream_t s);

@@ -124,3 +124,33 @@ def test_adjoint_modes_agree(big):
         grads.append(out["grad_sigma_s"].cpu().numpy().astype(np.float64))
     fl = 1e-3 * np.abs(grads[0]).max()
     assert (np.abs(grads[1] - grads[0]) / np.maximum(np.abs(grads[0]), fl)).max() <= 1e-4
+
+
+def test_fp32_sweep_rows(big):
+    """FP32 weights on the same graph (the sweeps deal rows to the blocks in
+    round-robin tiles at this size): one sweep of sampled rows against the
+    oracle's row, L_T[v] = w_s (sum_j A+_{s,j} L_{T-1}[j] + c_s), within the
+    FP32 tolerance; then the reverse sweeps in both schedules-independent
+    modes agree. Runs last: it re-aggregates the module's graph."""
+    pg = big.pg
+    c, D = pg.pg_aggregate(big.graph, big.V, "f32")
+    Lp = pg.pg_propagate(big.graph, big.L0, 9).cpu().numpy().astype(np.float64)
+    L = pg.pg_propagate(big.graph, big.L0, 10, keep_history=True).cpu().numpy().astype(np.float64)
+    succ = big.rec["succ"].astype(np.int64)
+    s = succ[big.S]
+    ref = oracle.aggregate(big.rec, big.nbr, rows=s)
+    nb = big.nbr[s]
+    Lj = np.where(nb >= 0, Lp[np.where(nb >= 0, nb, 0)], 0.0)
+    w = big.rec["w_prop"].astype(np.float64)[s]
+    expect = w * ((ref["A"] * Lj).sum(axis=1) + ref["c"])
+    err = np.abs(L[big.S] - expect) / np.maximum(np.abs(expect), 1e-3 * np.abs(expect).mean())
+    assert err.max() <= FP32_TOL
+    img = pg.pg_gather(big.graph, torch.from_numpy(L.astype(np.float32)).cuda(), D, big.first, big.bg, SC.spp,
+                       SC.width, SC.height)
+    dI = (0.1 * img).reshape(-1).contiguous()
+    g0 = pg.pg_propagate_adjoint(big.graph, dI, big.first, SC.spp, SC.width, SC.height, want_g=False,
+                                 recompute_weights=0)["grad_sigma_s"].cpu().numpy().astype(np.float64)
+    g2 = pg.pg_propagate_adjoint(big.graph, dI, big.first, SC.spp, SC.width, SC.height, want_g=False,
+                                 recompute_weights=2)["grad_sigma_s"].cpu().numpy().astype(np.float64)
+    fl = 1e-3 * np.abs(g0).max()
+    assert (np.abs(g2 - g0) / np.maximum(np.abs(g0), fl)).max() <= 1e-4
