@@ -296,6 +296,15 @@ pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const int32_t *firs
                                const int32_t *voxel, const float *sigma_t, float *grad_albedo_vox, int64_t n_vox,
                                int32_t recompute_weights, pg_stream_t stream);
 
+/* Build the transposed copy of the stored weights that pg_propagate_adjoint
+ * with recompute_weights = 0 applies (otherwise built by its first call), on
+ * `stream`, without a host round trip. It reads only the weights, so it may
+ * run on a second stream concurrently with pg_propagate; order
+ * pg_propagate_adjoint after it (same stream, or an event). No-op when the
+ * copy exists for the current weights. Errors: PG_ERR_STATE (no
+ * pg_aggregate or weights released), PG_ERR_OOM. */
+pg_status pg_prepare_adjoint(pg_graph *g, pg_stream_t stream);
+
 /* Free the stored edge weights and the transposed copy (after the forward
  * pass, when memory is tight); pg_propagate then returns PG_ERR_STATE and
  * pg_propagate_adjoint needs recompute_weights = 1. */

@@ -245,6 +245,12 @@ def pg_propagate_adjoint(graph: Graph, dI: torch.Tensor, first: torch.Tensor, sp
     return {"grad_sigma_s": gs, "grad_g": gg, "grad_albedo": ga}
 
 
+def pg_prepare_adjoint(graph: Graph, stream=None) -> None:
+    """Build the transposed weights for pg_propagate_adjoint on ``stream``
+    (e.g. a side stream while pg_propagate runs); see include/pg.h."""
+    check(_LIB.pg_prepare_adjoint(graph.handle, _stream_ptr(stream)), "pg_prepare_adjoint")
+
+
 def pg_propagate_noalloc(graph: Graph, L0: torch.Tensor, iters: int, out: torch.Tensor, tol: float = 0.0,
                          stream=None) -> torch.Tensor:
     """pg_propagate without device allocation (scratch in a static device
@@ -263,4 +269,4 @@ from .solver import Solver  # noqa: E402
 
 __all__ = ["Solver", "launch_count", "Vertices", "Graph", "PgError", "pg_build_graph", "pg_aggregate", "pg_propagate",
            "pg_gather", "pg_gather_ex", "extra_from_records", "pg_propagate_adjoint", "pg_propagate_noalloc",
-           "pg_record"]
+           "pg_record", "pg_prepare_adjoint"]

@@ -69,7 +69,7 @@ class PgRecording(ctypes.Structure):
 EXPORTS = ("pg_build_graph", "pg_graph_neighbors", "pg_graph_get_info", "pg_aggregate", "pg_propagate",
            "pg_gather", "pg_propagate_adjoint", "pg_graph_release_weights", "pg_graph_destroy",
            "pg_status_string", "pg_launch_count", "pg_propagate_noalloc", "pg_gather_ex",
-           "pg_record_count", "pg_record_fill")
+           "pg_record_count", "pg_record_fill", "pg_prepare_adjoint")
 
 _lib = None
 
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
     lib.pg_gather_ex.argtypes = [vp, vp, vp, vp, vp, i64, i32, i32, i32, ctypes.POINTER(PgOutputParams), vp, vp]
     lib.pg_propagate_adjoint.argtypes = [vp, vp, vp, i64, i32, i32, i32, vp, vp, vp, vp, vp, i64, i32, vp]
     lib.pg_graph_release_weights.argtypes = [vp]
+    lib.pg_prepare_adjoint.argtypes = [vp, vp]
     lib.pg_graph_destroy.argtypes = [vp]
     lib.pg_graph_destroy.restype = None
     lib.pg_status_string.argtypes = [ctypes.c_int]

@@ -587,13 +587,13 @@ static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
         }
         PG_TRY(pg_scan_exclusive64(g, ts[i]->ptr, na + 1, d_total + i, s));
     }
-    int64_t h_total[2] = {0, 0};
-    PG_CUDA(cudaMemcpyAsync(h_total, d_total, 16, cudaMemcpyDeviceToHost, s));
-    PG_CUDA(cudaStreamSynchronize(s));
+    // No host round trip for the totals: each transpose gets room for every
+    // entry its rows can hold plus one pad per column (at most 1 + 1/k of the
+    // live entries), so the build can be queued behind other work.
     for (int i = 0; i < 2; i++) {
-        ts[i]->nnz = h_total[i];
-        PG_TRY(pg_alloc(g, (void **)&ts[i]->ent, 8 * (size_t)(ts[i]->nnz > 0 ? ts[i]->nnz : 1), s));
-        if (ts[i]->nnz == 0) continue;
+        ts[i]->nnz = (r1[i] - r0[i]) * kp + na + 1;
+        PG_TRY(pg_alloc(g, (void **)&ts[i]->ent, 8 * (size_t)ts[i]->nnz, s));
+        if (r1[i] == r0[i]) continue;
         PG_CUDA(cudaMemsetAsync(fill, 0, 4 * (size_t)(na + 1), s));
         tfill_kernel<WT><<<pg_blocks((r1[i] - r0[i]) * kp, 256), 256, 0, s>>>(
             g->col, (const WT *)g->W, r0[i], r1[i], kp, na, ts[i]->ptr, fill, ts[i]->ent);
@@ -610,7 +610,7 @@ static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
 
 void pg_free_transposes(pg_graph *g) {
     for (pg_tcsr *t : {&g->tA, &g->tF}) {
-        pg_free(g, (void **)&t->ent, 8 * (size_t)(t->nnz > 0 ? t->nnz : 1));
+        pg_free(g, (void **)&t->ent, 8 * (size_t)t->nnz);
         pg_free(g, (void **)&t->ptr, 8 * (size_t)(g->n_active + 1));
         t->nnz = 0;
     }
@@ -765,6 +765,19 @@ static pg_status launch_grad_g(pg_graph *g, const float *muhist, const float *B,
     if (gpm) cudaFreeAsync(gpm, s);
     if (num) cudaFreeAsync(num, s);
     return st;
+}
+
+extern "C" pg_status pg_prepare_adjoint(pg_graph *g, pg_stream_t stream) {
+    if (!g) return PG_ERR_INVALID_ARG;
+    if (!g->aggregated || !g->W) return PG_ERR_STATE;
+    if (g->tA.ptr || g->n == 0) return PG_OK; // built for the current weights, or nothing to build
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (g->wdtype) {
+        case PG_W_F32: return build_transpose<float>(g, s);
+        case PG_W_BF16: return build_transpose<__nv_bfloat16>(g, s);
+        case PG_W_F16: return build_transpose<__half>(g, s);
+    }
+    return PG_ERR_INVALID_ARG;
 }
 
 extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const int32_t *first, int64_t n_paths,

@@ -26,7 +26,7 @@ enum : int {
 struct pg_tcsr {
     int64_t *ptr = nullptr;
     int2 *ent = nullptr;
-    int64_t nnz = 0;
+    int64_t nnz = 0; // entries allocated (the live ones are [ptr[0], ptr[ncols]))
 };
 
 struct pg_graph {

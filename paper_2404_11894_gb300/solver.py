@@ -50,8 +50,8 @@ class Solver:
         self._c, self.D = pg_aggregate(self.graph, V, self.wdtype)
         mark("aggregate", 1)
         self._L0 = L0
-        mark("propagate", 0)
         use_adj = self.adjoint and target is not None
+        mark("propagate", 0)
         self.L = pg_propagate(self.graph, L0, self.iters, keep_history=use_adj)
         mark("propagate", 1)
         mark("gather", 0)

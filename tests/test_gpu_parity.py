@@ -268,3 +268,33 @@ def test_solver_host_path_equals_device_path(pg):
     a, b = gh["grad_g"].double(), solver.grads["grad_g"].double()
     assert float((a - b).abs().max()) <= 1e-5 * float(b.abs().max())
     solver.close()
+
+
+def test_prepared_transpose_on_a_side_stream(pg):
+    """pg_prepare_adjoint on a second stream, concurrent with the forward
+    sweeps, gives the same reverse sweeps as the transpose built inside
+    pg_propagate_adjoint (bitwise: mode 0 sums in a fixed order)."""
+    sc = pgrec.CLOUD128.with_(width=48, height=48, spp=4)
+    rec = pgrec.trace(sc)
+    V = pg.Vertices.from_records(rec)
+    L0 = torch.from_numpy(rec["L0"]).cuda()
+    first = torch.from_numpy(rec["first"]).cuda()
+    dI = torch.from_numpy(rec["pt_image"].astype(np.float32).reshape(-1)).cuda()
+    grads = []
+    for prepared in (False, True):
+        graph = pg.pg_build_graph(V, sc.k)
+        pg.pg_aggregate(graph, V, "bf16")
+        main = torch.cuda.current_stream()
+        side = torch.cuda.Stream()
+        if prepared:
+            side.wait_stream(main)
+            pg.pg_prepare_adjoint(graph, side)
+            done = torch.cuda.Event()
+            done.record(side)
+        pg.pg_propagate(graph, L0, sc.iters, keep_history=True)
+        if prepared:
+            main.wait_event(done)
+        out = pg.pg_propagate_adjoint(graph, dI, first, sc.spp, sc.width, sc.height, want_g=False)
+        grads.append(out["grad_sigma_s"].cpu())
+        graph.close()
+    assert torch.equal(grads[0], grads[1])
