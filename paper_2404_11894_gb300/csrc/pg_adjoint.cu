@@ -210,13 +210,13 @@ static constexpr int TS_THREADS = 256;
 // gathered reverse iterates of that window stay in L2.
 static constexpr int TS_TILE_GROUPS = 64;
 
-template <typename WT, int MINB, bool FRONT>
+template <typename WT, int MINB, bool FRONT, int LPC, int PAIRS>
 __global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_pf_kernel(
     const int64_t *__restrict__ tptr, const int2 *__restrict__ tent,
     const float *__restrict__ us_in, const float *__restrict__ mu_in, const float *__restrict__ y_t,
     const float *__restrict__ rscale, int64_t ncols, int write_out, float *__restrict__ mu_out,
-    float *__restrict__ us_out, float *__restrict__ G, float *__restrict__ B, int tile_groups) {
-    constexpr int LPC = 4, PAIRS = 4; // 4 lanes x 4 pairs = 32 entries per pass
+    float *__restrict__ us_out, float *__restrict__ G, float *__restrict__ B) {
+    static_assert(LPC == 2 || LPC == 4, "two or four lanes per column");
     constexpr int CPB = TS_THREADS / LPC;
     const int lane = threadIdx.x & 31;
     const int q = lane & (LPC - 1);
@@ -227,8 +227,8 @@ __global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_pf_kernel(
     const int64_t c1 = FRONT ? ncols : min(ncols, c0 + chunk);
     auto gbase = [&](int64_t k) -> int64_t {
         if (!FRONT) return c0 + k * CPB;
-        const int64_t tile = k / tile_groups;
-        return (tile * gridDim.x + blockIdx.x) * ((int64_t)CPB * tile_groups) + (k - tile * tile_groups) * CPB;
+        const int64_t tile = k / TS_TILE_GROUPS;
+        return (tile * gridDim.x + blockIdx.x) * ((int64_t)CPB * TS_TILE_GROUPS) + (k - tile * TS_TILE_GROUPS) * CPB;
     };
     const int cl = threadIdx.x / LPC;
     auto extent = [&](int64_t c, int64_t &a, int64_t &b) {
@@ -268,12 +268,18 @@ __global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_pf_kernel(
         a2 = a1;
         b2 = b1;
         extent(gbase(k + 2) + cl, a1, b1);
-        float sv = 0.0f, rs = 1.0f; // column scalars: lane 0 mu_in, 1 y_t, 2 G, 3 B
+        // column scalars: four lanes hold mu_in, y_t, G, B; two lanes hold
+        // (mu_in, G) and (y_t, B)
+        float sv = 0.0f, sv2 = 0.0f, rs = 1.0f;
         if (ok && acc_g) {
             if (q == 0) sv = mu_in[c];
             else if (q == 1) sv = __ldcs(y_t + c);
             else if (q == 2) sv = G[c];
             else if (B) sv = B[c];
+            if constexpr (LPC == 2) {
+                if (q == 0) sv2 = G[c];
+                else if (B) sv2 = B[c];
+            }
         }
         if (ok && rscale && write_out && q == 0) rs = __ldcs(rscale + c);
         float acc = 0.0f;
@@ -303,8 +309,13 @@ __global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_pf_kernel(
                 if (us_out) us_out[c] = acc * rs;
             }
             if (acc_g) {
-                if (q == 2) G[c] = fmaf(m, yv, sv);
-                if (q == 3 && B) B[c] = sv + m;
+                if constexpr (LPC == 4) {
+                    if (q == 2) G[c] = fmaf(m, yv, sv);
+                    if (q == 3 && B) B[c] = sv + m;
+                } else {
+                    if (q == 0) G[c] = fmaf(m, yv, sv2);
+                    if (q == 1 && B) B[c] = sv2 + m;
+                }
             }
         }
     }
@@ -624,22 +635,24 @@ static pg_status adjoint_store(pg_graph *g, float *us0, float *mu_a, float *mu_b
     const int64_t stride = n + 1;
     const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
     if (!g->tA.ptr) PG_TRY(build_transpose<WT>(g, s));
-    // four lanes per column, software-pipelined (next group's first 32
-    // entries in flight during this group's gathers); 64 registers, 4 blocks
-    // of 256 per SM
-    int64_t need = (na * 4 + TS_THREADS - 1) / TS_THREADS;
+    // four lanes per column (two with the round-robin tiles, where they were
+    // 11 % faster on the 151 M-column dense medium and 16 % slower on the
+    // 7.8 M-column cloud in chunks), software-pipelined (next group's first
+    // pass of entries in flight during this group's gathers); 64 registers,
+    // 4 blocks of 256 per SM
+    const bool front = pg_sweep_front(na);
+    const int lpc = front ? 2 : 4;
+    int64_t need = (na * lpc + TS_THREADS - 1) / TS_THREADS;
     int64_t cap = (int64_t)pg_num_sms() * 4;
     const int tb = (int)(need < cap ? (need > 0 ? need : 1) : cap);
-    const bool front = pg_sweep_front(na);
-    const int tgr = TS_TILE_GROUPS;
     auto tsweep = [&](const pg_tcsr &t, const float *us_in, const float *mu_in, const float *y_t, int wo,
                       float *mu_out, float *us_out) {
         if (front)
-            tsweep_pf_kernel<WT, 4, true><<<tb, TS_THREADS, 0, s>>>(t.ptr, t.ent, us_in, mu_in, y_t, rs, na, wo, mu_out,
-                                                                    us_out, G, B, tgr);
+            tsweep_pf_kernel<WT, 4, true, 2, 4><<<tb, TS_THREADS, 0, s>>>(t.ptr, t.ent, us_in, mu_in, y_t, rs, na, wo,
+                                                                          mu_out, us_out, G, B);
         else
-            tsweep_pf_kernel<WT, 4, false><<<tb, TS_THREADS, 0, s>>>(t.ptr, t.ent, us_in, mu_in, y_t, rs, na, wo,
-                                                                     mu_out, us_out, G, B, tgr);
+            tsweep_pf_kernel<WT, 4, false, 4, 4><<<tb, TS_THREADS, 0, s>>>(t.ptr, t.ent, us_in, mu_in, y_t, rs, na, wo,
+                                                                           mu_out, us_out, G, B);
     };
     // mu_t lives in slice t of the history when one is kept, else ping-pong
     auto mu_slot = [&](int t) { return muhist ? muhist + (int64_t)t * stride : ((t & 1) ? mu_b : mu_a); };

@@ -130,8 +130,7 @@ template <int KP, typename WT, int NT, int MINB, int U, bool FRONT>
 __global__ void __launch_bounds__(NT, MINB) sweep_kernel(
     const int32_t *__restrict__ col, const WT *__restrict__ W, const float *__restrict__ rscale,
     const float *__restrict__ b, const float *__restrict__ yin, float *__restrict__ yout, int64_t n_active,
-    int32_t *__restrict__ ctrl, double2 *__restrict__ partials, double *__restrict__ resid, int t, double tol,
-    int tile_groups) {
+    int32_t *__restrict__ ctrl, double2 *__restrict__ partials, double *__restrict__ resid, int t, double tol) {
     if (*(volatile int32_t *)&ctrl[1]) return; // converged in an earlier sweep
     constexpr int LPR = KP / 4;
     constexpr bool W16 = WTraits<WT>::id != PG_W_F32;
@@ -149,8 +148,8 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(
     const int64_t r1 = FRONT ? n_active : min(n_active, r0 + chunk);
     auto step_base = [&](int64_t k) -> int64_t {
         if (!FRONT) return r0 + k * STEP;
-        const int64_t tile = k / tile_groups;
-        return (tile * gridDim.x + blockIdx.x) * (STEP * tile_groups) + (k - tile * tile_groups) * STEP;
+        const int64_t tile = k / TILE_GROUPS;
+        return (tile * gridDim.x + blockIdx.x) * (STEP * TILE_GROUPS) + (k - tile * TILE_GROUPS) * STEP;
     };
     float rd = 0.0f, rn = 0.0f;
     auto group = [&](int64_t base) { // uniform across the block
@@ -210,8 +209,7 @@ template <int KP, typename WT, int NT, int MINB, bool FRONT>
 __global__ void __launch_bounds__(NT, MINB) sweep_pf_kernel(
     const int32_t *__restrict__ col, const WT *__restrict__ W, const float *__restrict__ rscale,
     const float *__restrict__ b, const float *__restrict__ yin, float *__restrict__ yout, int64_t n_active,
-    int32_t *__restrict__ ctrl, double2 *__restrict__ partials, double *__restrict__ resid, int t, double tol,
-    int tile_groups) {
+    int32_t *__restrict__ ctrl, double2 *__restrict__ partials, double *__restrict__ resid, int t, double tol) {
     if (*(volatile int32_t *)&ctrl[1]) return; // converged in an earlier sweep
     constexpr int LPR = KP / 4;
     constexpr bool W16 = WTraits<WT>::id != PG_W_F32;
@@ -225,8 +223,8 @@ __global__ void __launch_bounds__(NT, MINB) sweep_pf_kernel(
     const int64_t r1 = FRONT ? n_active : min(n_active, r0 + chunk);
     auto group_base = [&](int64_t k) -> int64_t {
         if (!FRONT) return r0 + k * RPB;
-        const int64_t tile = k / tile_groups;
-        return (tile * gridDim.x + blockIdx.x) * ((int64_t)RPB * tile_groups) + (k - tile * tile_groups) * RPB;
+        const int64_t tile = k / TILE_GROUPS;
+        return (tile * gridDim.x + blockIdx.x) * ((int64_t)RPB * TILE_GROUPS) + (k - tile * TILE_GROUPS) * RPB;
     };
     const int32_t lr = threadIdx.x / LPR;
     auto load = [&](int64_t base, int4 &c4, float4 &w4, float &sv) {
@@ -277,7 +275,6 @@ __global__ void __launch_bounds__(NT, MINB) sweep_pf_kernel(
 // image size, 5-30 % faster in fronts).
 bool pg_sweep_front(int64_t n_active) { return n_active * 4 > ((int64_t)64 << 20); }
 static bool use_front(const pg_graph *g) { return pg_sweep_front(g->n_active); }
-static int tile_groups_fwd() { return TILE_GROUPS; }
 
 template <int KP, typename WT, int NT, int MINB>
 static void launch_pf_cfg(const pg_graph *g, const float *b, const float *yin, float *yout, int32_t *ctrl,
@@ -287,11 +284,11 @@ static void launch_pf_cfg(const pg_graph *g, const float *b, const float *yin, f
     int blocks = (int)std::max<int64_t>(1, std::min(need, cap));
     if (use_front(g))
         sweep_pf_kernel<KP, WT, NT, MINB, true><<<blocks, NT, 0, s>>>(g->col, (const WT *)g->W, g->rscale, b, yin,
-                                                                      yout, g->n_active, ctrl, partials, resid, t, tol, tile_groups_fwd());
+                                                                      yout, g->n_active, ctrl, partials, resid, t, tol);
     else
         sweep_pf_kernel<KP, WT, NT, MINB, false><<<blocks, NT, 0, s>>>(g->col, (const WT *)g->W, g->rscale, b, yin,
                                                                        yout, g->n_active, ctrl, partials, resid, t,
-                                                                       tol, tile_groups_fwd());
+                                                                       tol);
 }
 
 // slot n of each of `slices` vectors of n+1 floats
@@ -342,11 +339,11 @@ static void launch_sweep_cfg(const pg_graph *g, const float *b, const float *yin
     int blocks = (int)std::max<int64_t>(1, std::min(need, cap));
     if (use_front(g))
         sweep_kernel<KP, WT, NT, MINB, U, true><<<blocks, NT, 0, s>>>(g->col, (const WT *)g->W, g->rscale, b, yin,
-                                                                      yout, g->n_active, ctrl, partials, resid, t, tol, tile_groups_fwd());
+                                                                      yout, g->n_active, ctrl, partials, resid, t, tol);
     else
         sweep_kernel<KP, WT, NT, MINB, U, false><<<blocks, NT, 0, s>>>(g->col, (const WT *)g->W, g->rscale, b, yin,
                                                                        yout, g->n_active, ctrl, partials, resid, t,
-                                                                       tol, tile_groups_fwd());
+                                                                       tol);
 }
 
 // Launch shapes (measured on the 8.7M-vertex cloud, k = 16): FP32 rows in the
