@@ -338,11 +338,9 @@ extern "C" pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype w
         pg_count_launches(1);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     }
-    if (st == PG_OK && (cudaMemcpyAsync(&h_nact, d_nact, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                        cudaStreamSynchronize(s) != cudaSuccess))
-        st = PG_ERR_CUDA;
     int32_t hflags = 0;
-    if (st == PG_OK && (cudaMemcpyAsync(&hflags, g->flags, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    if (st == PG_OK && (cudaMemcpyAsync(&h_nact, d_nact, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                        cudaMemcpyAsync(&hflags, g->flags, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                         cudaStreamSynchronize(s) != cudaSuccess))
         st = PG_ERR_CUDA;
     if (st == PG_OK && (hflags & PG_FLAG_NONFINITE)) st = PG_ERR_NONFINITE;
