@@ -37,6 +37,7 @@ L2_BYTES = 129 * 2 ** 20
 
 WORKLOADS = ("cloud128", "dense256")
 EXTRA_M = 4  # extra emitter samples per path for the output-option timings
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # nominal FP32 FMA rate at the maximum SM clock
 
 
 def _scene(name):
@@ -364,6 +365,14 @@ def run_gpu(args):
         # two phase-function evaluations per neighbour entry in each of the two
         # aggregation passes, and two per row for the non-aggregated direct term
         "aggregate_hg_evals_per_s": (4 * info["k"] * n + 2 * n) / (stage_ms["aggregate"] / 1e3),
+        # the same against the FP32 rate: about 30 floating-point operations
+        # per phase-function evaluation (1 + o.d from |o + d|^2 and the
+        # vectors' norm errors, the Henyey-Greenstein power with a refined
+        # rsqrt); peak = 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz
+        "aggregate_alu": {"bound": "alu", "flop_per_hg_eval": 30, "peak_tflops": FP32_PEAK_TFLOPS,
+                          "achieved_tflops": 30 * (4 * info["k"] * n + 2 * n) / (stage_ms["aggregate"] / 1e3) / 1e12,
+                          "frac": 30 * (4 * info["k"] * n + 2 * n) / (stage_ms["aggregate"] / 1e3) / 1e12
+                          / FP32_PEAK_TFLOPS},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "sweep_kernel<16,%s,1024,2,2>" % wdtype if w16 else "sweep_pf_kernel<16,float,1024,1>",
