@@ -248,7 +248,7 @@ __device__ __forceinline__ unsigned long long pg_pm_fix(float x) {
     return __float2ull_rn(x * 17179869184.0f); // x * 2^34, exact scaling
 }
 __device__ __forceinline__ float pg_pm_float(unsigned long long a) {
-    return (float)((double)a * 5.820766091346740722656e-11); // * 2^-34
+    return __ull2float_rn(a) * 5.820766091346740722656e-11f; // rounded to float, then * 2^-34 (exact)
 }
 
 static inline size_t pg_wbytes(pg_wdtype t) { return t == PG_W_F32 ? 4 : 2; }
