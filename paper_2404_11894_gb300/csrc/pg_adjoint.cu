@@ -191,8 +191,8 @@ __global__ void seed_kernel(const int32_t *__restrict__ first, const float *__re
 // ------------------------------------------------------------------ reverse sweep (stored transpose)
 // Four lanes per column c: mu_out[c] = sum_e tW[e] us_in[trow[e]] over the
 // column's entries (rows ascending), two entries per 16-byte load, each block
-// walking one contiguous chunk of columns (neighbouring columns draw on
-// neighbouring rows). When y_t is given it also accumulates
+// walking its columns in order (neighbouring columns draw on neighbouring
+// rows). When y_t is given it also accumulates
 // G[c] += mu_in[c] y_t[c] (and B[c] += mu_in[c] when B is given); those
 // column scalars are loaded up front, one per lane, so they travel with the
 // entry loads. us_out (the next input, mu times the 16-bit row scale) is
@@ -200,9 +200,9 @@ __global__ void seed_kernel(const int32_t *__restrict__ first, const float *__re
 static constexpr int TS_THREADS = 256;
 
 // The sweep is software-pipelined: the first pass of entries
-// (up to 32) of the next column group is loaded before this group's gathers,
-// with the column extents two groups ahead, so a column's DRAM round trip
-// overlaps the previous one's L2 round trip. Columns longer than 32 entries
+// (2 LPC PAIRS of them) of the next column group is loaded before this
+// group's gathers, with the column extents two groups ahead, so a column's
+// DRAM round trip overlaps the previous one's L2 round trip. Longer columns
 // take their remaining passes unpipelined.
 // Column schedules as in the forward sweep: contiguous chunks per block, or
 // (FRONT) tiles of TS_TILE_GROUPS column groups dealt round-robin to the
@@ -635,23 +635,23 @@ static pg_status adjoint_store(pg_graph *g, float *us0, float *mu_a, float *mu_b
     const int64_t stride = n + 1;
     const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
     if (!g->tA.ptr) PG_TRY(build_transpose<WT>(g, s));
-    // four lanes per column (two with the round-robin tiles, where they were
-    // 11 % faster on the 151 M-column dense medium and 16 % slower on the
-    // 7.8 M-column cloud in chunks), software-pipelined (next group's first
-    // pass of entries in flight during this group's gathers); 64 registers,
-    // 4 blocks of 256 per SM
+    // four lanes per column with a first pass of 24 entries (8 more than the
+    // typical column of k = 16, so only ~0.2 % of the columns of a kNN graph
+    // take a second pass, and fewer registers than a 32-entry pass: 15 %
+    // faster on the 151 M-column dense medium, 2 % on the cloud),
+    // software-pipelined (next group's first pass in flight during this
+    // group's gathers); at most 64 registers, 4 blocks of 256 per SM
     const bool front = pg_sweep_front(na);
-    const int lpc = front ? 2 : 4;
-    int64_t need = (na * lpc + TS_THREADS - 1) / TS_THREADS;
+    int64_t need = (na * 4 + TS_THREADS - 1) / TS_THREADS;
     int64_t cap = (int64_t)pg_num_sms() * 4;
     const int tb = (int)(need < cap ? (need > 0 ? need : 1) : cap);
     auto tsweep = [&](const pg_tcsr &t, const float *us_in, const float *mu_in, const float *y_t, int wo,
                       float *mu_out, float *us_out) {
         if (front)
-            tsweep_pf_kernel<WT, 4, true, 2, 4><<<tb, TS_THREADS, 0, s>>>(t.ptr, t.ent, us_in, mu_in, y_t, rs, na, wo,
+            tsweep_pf_kernel<WT, 4, true, 4, 3><<<tb, TS_THREADS, 0, s>>>(t.ptr, t.ent, us_in, mu_in, y_t, rs, na, wo,
                                                                           mu_out, us_out, G, B);
         else
-            tsweep_pf_kernel<WT, 4, false, 4, 4><<<tb, TS_THREADS, 0, s>>>(t.ptr, t.ent, us_in, mu_in, y_t, rs, na, wo,
+            tsweep_pf_kernel<WT, 4, false, 4, 3><<<tb, TS_THREADS, 0, s>>>(t.ptr, t.ent, us_in, mu_in, y_t, rs, na, wo,
                                                                            mu_out, us_out, G, B);
     };
     // mu_t lives in slice t of the history when one is kept, else ping-pong
