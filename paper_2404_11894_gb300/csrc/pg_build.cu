@@ -111,7 +111,8 @@ template <int KP, bool D32>
 __global__ void __launch_bounds__(128, 4) knn_kernel(const int4 *__restrict__ qrec, const int2 *__restrict__ cell_se,
                                                   int64_t n, int k, int level, int64_t r2_max,
                                                   const int32_t *__restrict__ c2m, int32_t *__restrict__ nbr,
-                                                  int32_t *__restrict__ redo, int32_t *__restrict__ redo_count) {
+                                                  int32_t *__restrict__ redo, int32_t *__restrict__ redo_count,
+                                                  uint64_t *__restrict__ redo_keys, int64_t redo_cap) {
     constexpr int M = KP - 1;
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n) return;
@@ -215,7 +216,14 @@ __global__ void __launch_bounds__(128, 4) knn_kernel(const int4 *__restrict__ qr
             int32_t base = 0;
             if (lane == leader) base = atomicAdd(redo_count, __popc(need_mask));
             base = __shfl_sync(need_mask, base, leader);
-            redo[base + __popc(need_mask & ((1u << lane) - 1u))] = (int32_t)m;
+            const int32_t slot = base + __popc(need_mask & ((1u << lane) - 1u));
+            redo[slot] = (int32_t)m;
+            // with exact 32-bit distances the list holds the true k-1 nearest
+            // of the 27 cells: the exact kernel resumes from it at ring 2
+            if (D32 && slot < redo_cap) {
+#pragma unroll
+                for (int i = 0; i < M; i++) redo_keys[(int64_t)slot * M + i] = bk[i];
+            }
             return;
         }
     }
@@ -238,7 +246,8 @@ __global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__
                                                         const int2 *__restrict__ cell_se,
                                                         const int32_t *__restrict__ c2m, const int32_t *__restrict__ list,
                                                         const int32_t *__restrict__ d_count, int64_t nq, int k,
-                                                        int level, int64_t r2_max, int32_t *__restrict__ nbr) {
+                                                        int level, int64_t r2_max, int32_t *__restrict__ nbr,
+                                                        const uint64_t *__restrict__ saved_keys, int64_t saved_cap) {
     constexpr int M = KP - 1;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (QUERY ? nq : (int64_t)*d_count)) return;
@@ -270,9 +279,25 @@ __global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__
     int64_t worst_d = INT64_MAX;
     int32_t worst_i = INT32_MAX;
     int found = 0;
+    int r_start = 0;
+    if (!QUERY && saved_keys && t < saved_cap) {
+        // resume from the fast kernel's list of rings 0 and 1
+#pragma unroll
+        for (int i = 0; i < M; i++) {
+            const uint64_t key = saved_keys[t * M + i];
+            if (i >= pad && key != UINT64_MAX) {
+                bd[i] = (int64_t)(key >> 31);
+                bi[i] = (int32_t)(key & 0x7fffffffu);
+                found++;
+            }
+        }
+        worst_d = bd[M - 1];
+        worst_i = bi[M - 1];
+        r_start = 2;
+    }
 
     if (km1 > 0) {
-        for (int r = 0;; r++) {
+        for (int r = r_start;; r++) {
             // cells of ring r: r = 0 the own cell; r = 1 the 26 neighbours,
             // nearest first (faces, edges, corners) so the list fills with
             // good candidates early; r >= 2 the shell of the (2r+1)^3 block
@@ -366,17 +391,22 @@ template <int KP>
 static pg_status launch_knn_t(pg_graph *g, cudaStream_t s) {
     const int64_t n = g->n;
     int32_t *redo = nullptr, *cnt = nullptr;
+    uint64_t *redo_keys = nullptr;
+    // lists saved for the first redo_cap queued queries (usually all of them)
+    const int64_t redo_cap = g->level >= 7 ? n / 8 + 1024 : 0;
     PG_TRY(pg_alloc(nullptr, (void **)&redo, 4 * (size_t)(n > 0 ? n : 1), s));
     pg_status st = pg_alloc(nullptr, (void **)&cnt, 16, s);
+    if (st == PG_OK && redo_cap > 0)
+        st = pg_alloc(nullptr, (void **)&redo_keys, 8 * (size_t)redo_cap * (KP - 1 > 0 ? KP - 1 : 1), s);
     if (st == PG_OK && cudaMemsetAsync(cnt, 0, 4, s) != cudaSuccess) st = PG_ERR_CUDA;
     if (st == PG_OK) {
         if (g->level >= 7) {
             knn_kernel<KP, true><<<pg_blocks(n, 128), 128, 0, s>>>(g->qrec, g->cell_se, n, g->k, g->level, g->r2_max,
-                                                                  g->c2m, g->nbr, redo, cnt);
+                                                                  g->c2m, g->nbr, redo, cnt, redo_keys, redo_cap);
             pg_count_launches(1);
         } else {
             knn_kernel<KP, false><<<pg_blocks(n, 128), 128, 0, s>>>(g->qrec, g->cell_se, n, g->k, g->level,
-                                                                   g->r2_max, g->c2m, g->nbr, redo, cnt);
+                                                                   g->r2_max, g->c2m, g->nbr, redo, cnt, nullptr, 0);
             pg_count_launches(1);
         }
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
@@ -388,12 +418,14 @@ static pg_status launch_knn_t(pg_graph *g, cudaStream_t s) {
     g->knn_exact = h_cnt;
     if (st == PG_OK && h_cnt > 0) {
         knn_exact_kernel<KP, false><<<pg_blocks(h_cnt, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, redo, cnt, 0,
-                                                                         g->k, g->level, g->r2_max, g->nbr);
+                                                                         g->k, g->level, g->r2_max, g->nbr, redo_keys,
+                                                                         redo_cap);
         pg_count_launches(1);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     }
     cudaFreeAsync(redo, s);
     cudaFreeAsync(cnt, s);
+    if (redo_keys) cudaFreeAsync(redo_keys, s);
     return st;
 }
 
@@ -413,7 +445,7 @@ pg_status pg_launch_knn_queries(const pg_graph *g, const int32_t *qm, int64_t nq
     const int kp = pg_row_width(k);
 #define Q(KP)                                                                                                   \
     knn_exact_kernel<KP, true><<<pg_blocks(nq, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, qm, nullptr, nq, k, \
-                                                                 g->level, -1, out)
+                                                                 g->level, -1, out, nullptr, 0)
     switch (kp) {
         case 4: Q(4); break;
         case 8: Q(8); break;
