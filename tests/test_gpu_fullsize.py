@@ -169,6 +169,45 @@ def test_last_residual(full):
     assert full.res[-1] == pytest.approx(r, rel=1e-4)
 
 
+def test_output_options_full_size(pg, full):
+    """The output options at full size (1 M paths): final-gather neighbour
+    tables equal the graph's rows for k_fg = k (kNN graph: their prefix) and
+    brute force for sampled paths at k_fg = 24 (the exact search); the
+    extra-sample image minus the plain one equals the oracle's
+    (1/spp) sum_p (tau/p_t)_f (D^x_p - D_f) pixel by pixel."""
+    from pgrec import synthetic
+
+    rec, first_np = full.rec, full.rec["first"]
+    L, D = _tensor(full.L), _tensor(full.D)
+    has = first_np >= 0
+    _, fg = pg.pg_gather_ex(full.graph, L, D, full.first, full.bg, SC.spp, SC.width, SC.height, final_gather_k=16,
+                            want_fg_nbr=True)
+    fg = fg.cpu().numpy()
+    assert np.array_equal(fg[has], full.nbr[first_np[has]])
+    assert np.all(fg[~has] == -1)
+    _, fg24 = pg.pg_gather_ex(full.graph, L, D, full.first, full.bg, SC.spp, SC.width, SC.height, final_gather_k=24,
+                              want_fg_nbr=True)
+    fg24 = fg24.cpu().numpy()
+    rng = np.random.default_rng(5)
+    for p in rng.choice(np.nonzero(has)[0], 24, replace=False):
+        assert np.array_equal(fg24[p], _brute_row(full.q, int(first_np[p]), 24)), p
+    # extra first-vertex samples (random records, 2 per path)
+    M = 2
+    X = synthetic.random_extra(rec["n_paths"], M, seed=17)
+    img_x = pg.pg_gather_ex(full.graph, L, D, full.first, full.bg, SC.spp, SC.width, SC.height,
+                            extra=pg.extra_from_records(X)).cpu().numpy().astype(np.float64)
+    Dx = oracle.extra_direct(rec, first_np, X, M)
+    f = first_np[has].astype(np.int64)
+    Df = oracle.aggregate(rec, np.arange(rec["n"], dtype=np.int64)[:, None], rows=f)["D"]
+    w = rec["w_prop"].astype(np.float64)[f]
+    delta = np.zeros(rec["n_paths"])
+    delta[has] = w * (Dx[has] - Df)
+    want = delta.reshape(SC.height, SC.width, SC.spp).mean(axis=2)
+    got = img_x - full.img.astype(np.float64)
+    scale = np.maximum(np.abs(full.img.astype(np.float64)), 1e-3 * np.abs(full.img).mean())
+    assert (np.abs(got - want) / scale).max() <= FP32_TOL
+
+
 def test_pixels_rows(full):
     rng = np.random.default_rng(7)
     pix = rng.choice(SC.width * SC.height, 24, replace=False)
