@@ -252,7 +252,8 @@ typedef struct {
  * A^fg, and Dir_p = D_f or D^x_f; image as in pg_gather. D may be NULL when
  * extra samples are given. Synchronises `stream` once when extra samples are
  * given (to report their validation). Temporary device memory: n_paths *
- * (4 + 4 * row width) bytes for a final gather, 8 * n_paths otherwise.
+ * (8 + 4 * row width) bytes for a final gather (row width = final_gather_k
+ * rounded up to 4, 8, 16 or 32), plus 4 * n_paths with extra samples.
  * Errors: PG_ERR_STATE, PG_ERR_INVALID_ARG (sizes, NULL arrays, m < 1,
  * negative Le or pe_e), PG_ERR_UNSUPPORTED (final_gather_k > 32),
  * PG_ERR_NONFINITE (an extra sample). */
