@@ -197,6 +197,20 @@ def run_gpu(args):
     stage_ms = {nm: float(np.mean([m[nm][0].elapsed_time(m[nm][1]) for m in marks_all if m[nm][0].query()]))
                 for nm in stage_names if not (args.no_adjoint and nm == "adjoint")}
 
+    # ---- end to end through the public API: host records -> image on the host
+    # (measured right after the device-timed steps, in the same state)
+    e2e_t = []
+    h2d = sum(int(v.numel() * v.element_size()) for v in host.values()) + host_target.numel() * 4
+    d2h = sc.width * sc.height * 4
+    for i in range(args.steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        img = solver.solve_host(host, host_target, sc.spp, sc.width, sc.height)
+        t1 = time.perf_counter()
+        if i > 0:
+            e2e_t.append(t1 - t0)
+    e2e_value = edge_updates_step / float(np.mean(e2e_t))
+
     pt = rec["pt_image"].astype(np.float64)
     solver_img_ratio = float(solver.last_image.double().mean()) / float(pt.mean()) if pt.mean() > 0 else None
 
@@ -328,19 +342,6 @@ def run_gpu(args):
         torch.cuda.synchronize()
         recorder = {"gpu_ms": a.elapsed_time(b) / 3, "host_s": host_trace_s, "host_threads": os.cpu_count(),
                     "vertices": n, "extra_samples_per_path": EXTRA_M, "same_records_as_host": same}
-
-    # ---- end to end through the public API: host records -> image on the host
-    e2e_t = []
-    h2d = sum(int(v.numel() * v.element_size()) for v in host.values()) + host_target.numel() * 4
-    d2h = sc.width * sc.height * 4
-    for i in range(args.steps + 1):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        img = solver.solve_host(host, host_target, sc.spp, sc.width, sc.height)
-        t1 = time.perf_counter()
-        if i > 0:
-            e2e_t.append(t1 - t0)
-    e2e_value = edge_updates_step / float(np.mean(e2e_t))
 
     value = total_updates / t_dev
     out = {
