@@ -107,15 +107,24 @@ __device__ __forceinline__ bool knn_less(int64_t da, int32_t ia, int64_t db, int
 // list holding one is redone exactly.
 static constexpr uint64_t KNN_SAT = (1ull << 33) - 1;
 
-template <int KP, bool D32>
+// QUERY = false: query t is vertex t, row t of nbr. QUERY = true: n query
+// slots, slot t asks for Morton vertex qlist[t] (-1: none), row t of nbr.
+// A queued query is recorded by its slot.
+template <int KP, bool D32, bool QUERY = false>
 __global__ void __launch_bounds__(128, 4) knn_kernel(const int4 *__restrict__ qrec, const int2 *__restrict__ cell_se,
                                                   int64_t n, int k, int level, int64_t r2_max,
                                                   const int32_t *__restrict__ c2m, int32_t *__restrict__ nbr,
                                                   int32_t *__restrict__ redo, int32_t *__restrict__ redo_count,
-                                                  uint64_t *__restrict__ redo_keys, int64_t redo_cap) {
+                                                  uint64_t *__restrict__ redo_keys, int64_t redo_cap,
+                                                  const int32_t *__restrict__ qlist = nullptr) {
     constexpr int M = KP - 1;
-    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= n) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int64_t m = QUERY ? (int64_t)qlist[t] : t;
+    if (QUERY && m < 0) {
+        for (int i = 0; i < KP; i++) nbr[t * KP + i] = -1;
+        return;
+    }
     const int4 qr = qrec[m];
     const int32_t qx = qr.x, qy = qr.y, qz = qr.z;
     const int sh = PG_QBITS - level;
@@ -217,7 +226,7 @@ __global__ void __launch_bounds__(128, 4) knn_kernel(const int4 *__restrict__ qr
             if (lane == leader) base = atomicAdd(redo_count, __popc(need_mask));
             base = __shfl_sync(need_mask, base, leader);
             const int32_t slot = base + __popc(need_mask & ((1u << lane) - 1u));
-            redo[slot] = (int32_t)m;
+            redo[slot] = (int32_t)t;
             // with exact 32-bit distances the list holds the true k-1 nearest
             // of the 27 cells: the exact kernel resumes from it at ring 2
             if (D32 && slot < redo_cap) {
@@ -227,7 +236,7 @@ __global__ void __launch_bounds__(128, 4) knn_kernel(const int4 *__restrict__ qr
             return;
         }
     }
-    int32_t *row = nbr + m * KP;
+    int32_t *row = nbr + t * KP;
     row[0] = (int32_t)m;
 #pragma unroll
     for (int i = 0; i < M; i++) {
@@ -247,12 +256,17 @@ __global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__
                                                         const int32_t *__restrict__ c2m, const int32_t *__restrict__ list,
                                                         const int32_t *__restrict__ d_count, int64_t nq, int k,
                                                         int level, int64_t r2_max, int32_t *__restrict__ nbr,
-                                                        const uint64_t *__restrict__ saved_keys, int64_t saved_cap) {
+                                                        const uint64_t *__restrict__ saved_keys, int64_t saved_cap,
+                                                        const int32_t *__restrict__ qlist = nullptr) {
     constexpr int M = KP - 1;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (QUERY ? nq : (int64_t)*d_count)) return;
-    const int64_t m = list[t];
-    int32_t *row = nbr + (QUERY ? t : m) * KP;
+    if (t >= ((QUERY && !qlist) ? nq : (int64_t)*d_count)) return;
+    // build: list = queued vertices, rows by vertex; queries: list = the
+    // queries' vertices, rows by t; queued queries (qlist given): list = the
+    // queued slots, slot s asks for vertex qlist[s], rows by slot
+    const int64_t slot = !QUERY ? (int64_t)list[t] : (qlist ? (int64_t)list[t] : t);
+    const int64_t m = !QUERY ? slot : (qlist ? (int64_t)qlist[slot] : (int64_t)list[t]);
+    int32_t *row = nbr + slot * KP;
     if (QUERY && m < 0) {
         for (int i = 0; i < KP; i++) row[i] = -1;
         return;
@@ -280,7 +294,7 @@ __global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__
     int32_t worst_i = INT32_MAX;
     int found = 0;
     int r_start = 0;
-    if (!QUERY && saved_keys && t < saved_cap) {
+    if (saved_keys && t < saved_cap) {
         // resume from the fast kernel's list of rings 0 and 1
 #pragma unroll
         for (int i = 0; i < M; i++) {
@@ -443,20 +457,51 @@ pg_status pg_launch_knn_queries(const pg_graph *g, const int32_t *qm, int64_t nq
     if (nq <= 0) return PG_OK;
     PG_TRY(upload_ring1(s));
     const int kp = pg_row_width(k);
+    if (g->level < 7) { // 64-bit distances: every query through the exact search
 #define Q(KP)                                                                                                   \
     knn_exact_kernel<KP, true><<<pg_blocks(nq, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, qm, nullptr, nq, k, \
                                                                  g->level, -1, out, nullptr, 0)
-    switch (kp) {
-        case 4: Q(4); break;
-        case 8: Q(8); break;
-        case 16: Q(16); break;
-        case 32: Q(32); break;
-        default: return PG_ERR_UNSUPPORTED;
-    }
+        switch (kp) {
+            case 4: Q(4); break;
+            case 8: Q(8); break;
+            case 16: Q(16); break;
+            case 32: Q(32); break;
+            default: return PG_ERR_UNSUPPORTED;
+        }
 #undef Q
-    pg_count_launches(1);
-    PG_LAUNCH_CHECK();
-    return PG_OK;
+        pg_count_launches(1);
+        PG_LAUNCH_CHECK();
+        return PG_OK;
+    }
+    // first ring for every query; the queued ones resume from their saved
+    // lists at ring 2 (the exact kernel reads the queue length on the device)
+    int32_t *redo = nullptr, *cnt = nullptr;
+    uint64_t *keys = nullptr;
+    pg_status st = pg_alloc(nullptr, (void **)&redo, 4 * (size_t)nq, s);
+    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&cnt, 16, s);
+    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&keys, 8 * (size_t)nq * (kp - 1 > 0 ? kp - 1 : 1), s);
+    if (st == PG_OK && cudaMemsetAsync(cnt, 0, 4, s) != cudaSuccess) st = PG_ERR_CUDA;
+    if (st == PG_OK) {
+#define Q(KP)                                                                                                    \
+    knn_kernel<KP, true, true><<<pg_blocks(nq, 128), 128, 0, s>>>(g->qrec, g->cell_se, nq, k, g->level, -1, g->c2m, \
+                                                                 out, redo, cnt, keys, nq, qm);                  \
+    knn_exact_kernel<KP, true><<<pg_blocks(nq, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, redo, cnt, nq, k,   \
+                                                                 g->level, -1, out, keys, nq, qm)
+        switch (kp) {
+            case 4: Q(4); break;
+            case 8: Q(8); break;
+            case 16: Q(16); break;
+            case 32: Q(32); break;
+            default: st = PG_ERR_UNSUPPORTED;
+        }
+#undef Q
+        pg_count_launches(2);
+        if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
+    }
+    if (redo) cudaFreeAsync(redo, s);
+    if (cnt) cudaFreeAsync(cnt, s);
+    if (keys) cudaFreeAsync(keys, s);
+    return st;
 }
 
 pg_status pg_launch_knn(pg_graph *g, cudaStream_t s) {

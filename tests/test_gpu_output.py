@@ -109,6 +109,31 @@ def test_final_gather_with_extra_direct(case, pg):
     assert rel_err(img, vals.reshape(sc.height, sc.width, sc.spp).mean(axis=2)) <= FP32_TOL
 
 
+@pytest.mark.parametrize("level", [7, 8])
+def test_final_gather_first_ring_and_resume(pg, level):
+    """On grids of level 7 or more the final gather's queries run the
+    first-ring kernel; on the fine grid most of them are queued and resume
+    at ring 2 from their saved lists. A graph of k = 4 puts every kfg below
+    on the query path (no reuse of graph rows)."""
+    sc = pgrec.CLOUD128.with_(width=40, height=40, spp=4, k=4, iters=10)
+    rec = pgrec.trace(sc)
+    V = pg.Vertices.from_records(rec)
+    graph = pg.pg_build_graph(V, sc.k, grid_level=level)
+    assert graph.info()["grid_level"] == level
+    ref = oracle.forward(rec, rec["first"], rec["bg"], sc.spp, sc.width, sc.height, sc.k, sc.iters)
+    assert np.array_equal(graph.neighbors().cpu().numpy(), ref["nbr"])
+    q = oracle.quantize(rec["px"], rec["py"], rec["pz"], (0, 0, 0), (1, 1, 1))
+    _, D = pg.pg_aggregate(graph, V, "f32")
+    L = pg.pg_propagate(graph, torch.from_numpy(rec["L0"]).cuda(), sc.iters)
+    first, bg = torch.from_numpy(rec["first"]).cuda(), torch.from_numpy(rec["bg"]).cuda()
+    for kfg in (5, 16, 32):
+        img, fg = pg.pg_gather_ex(graph, L, D, first, bg, sc.spp, sc.width, sc.height, final_gather_k=kfg,
+                                  want_fg_nbr=True)
+        vals, nb = oracle.final_gather(rec, q, ref["L"], rec["first"], rec["bg"], kfg, D=ref["D"])
+        assert np.array_equal(fg.cpu().numpy(), nb), kfg
+        assert rel_err(img.cpu().numpy(), vals.reshape(sc.height, sc.width, sc.spp).mean(axis=2)) <= FP32_TOL
+
+
 def test_final_gather_on_cluster_graph(pg):
     """Cluster neighbourhoods in the iteration, a kNN final gather at output."""
     sc = pgrec.CLOUD128.with_(width=48, height=48, spp=4)
