@@ -12,6 +12,7 @@
 #include <stdlib.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "pg_internal.cuh"
 
@@ -142,17 +143,38 @@ __global__ void __launch_bounds__(128, 4) knn_kernel(const int4 *__restrict__ qr
     uint64_t worst = UINT64_MAX;
     uint32_t worst32 = UINT32_MAX; // worst's distance part, clamped (D32)
     int found = 0;
+    // squared distance from the query to the neighbour cell across each face
+    // of its own cell: low side (offset in cell + 1)^2, high side (cs - offset)^2
+    using GT = typename std::conditional<D32, uint32_t, uint64_t>::type;
+    GT glo[3], ghi[3];
+    {
+        const int32_t q3[3] = {qx, qy, qz};
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const GT o = (GT)(q3[a] & (int32_t)(cs - 1));
+            glo[a] = (o + 1) * (o + 1);
+            ghi[a] = ((GT)cs - o) * ((GT)cs - o);
+        }
+    }
     if (km1 > 0) {
-        for (int t = 0; t < 27; t++) {
+        for (int ci = 0; ci < 27; ci++) {
             int dx = 0, dy = 0, dz = 0;
-            if (t > 0) {
-                const int o = c_ring1[t - 1];
+            if (ci > 0) {
+                const int o = c_ring1[ci - 1];
                 dx = (o & 3) - 1;
                 dy = ((o >> 2) & 3) - 1;
                 dz = ((o >> 4) & 3) - 1;
             }
             const int x = cx + dx, y = cy + dy, z = cz + dz;
             if (x < 0 || x >= G || y < 0 || y >= G || z < 0 || z >= G) continue;
+            if (ci > 0) {
+                // no vertex of a cell whose nearest point is already farther
+                // than the (k-1)-th entry can enter the list
+                const GT lb = (dx < 0 ? glo[0] : (dx > 0 ? ghi[0] : (GT)0)) +
+                              (dy < 0 ? glo[1] : (dy > 0 ? ghi[1] : (GT)0)) +
+                              (dz < 0 ? glo[2] : (dz > 0 ? ghi[2] : (GT)0));
+                if (D32 ? lb > (GT)worst32 : ((worst >> 31) < KNN_SAT && (uint64_t)lb > (worst >> 31))) continue;
+            }
             const int2 se = cell_se[(int64_t)x + ((int64_t)y << level) + ((int64_t)z << (2 * level))];
             const int32_t p1 = se.x + se.y;
             for (int32_t p = se.x; p < p1; p++) {
@@ -277,6 +299,7 @@ __global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__
     const int G = 1 << level;
     const int64_t cs = (int64_t)1 << sh;
     const int cx = qx >> sh, cy = qy >> sh, cz = qz >> sh;
+    const int32_t q3o[3] = {qx & (int32_t)(cs - 1), qy & (int32_t)(cs - 1), qz & (int32_t)(cs - 1)};
     const int km1 = k - 1;
 
     // Ascending list of M slots. The lowest M - (k-1) slots hold a sentinel
@@ -317,23 +340,37 @@ __global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__
             // good candidates early; r >= 2 the shell of the (2r+1)^3 block
             const int span = 2 * r + 1;
             const int ncell = r == 0 ? 1 : (r == 1 ? 26 : span * span * span);
-            for (int t = 0; t < ncell; t++) {
+            for (int ci = 0; ci < ncell; ci++) {
                 int dx, dy, dz;
                 if (r == 0) {
                     dx = dy = dz = 0;
                 } else if (r == 1) {
-                    int o = c_ring1[t];
+                    int o = c_ring1[ci];
                     dx = (o & 3) - 1;
                     dy = ((o >> 2) & 3) - 1;
                     dz = ((o >> 4) & 3) - 1;
                 } else {
-                    dx = t % span - r;
-                    dy = (t / span) % span - r;
-                    dz = t / (span * span) - r;
+                    dx = ci % span - r;
+                    dy = (ci / span) % span - r;
+                    dz = ci / (span * span) - r;
                     if (abs(dx) != r && abs(dy) != r && abs(dz) != r) continue;
                 }
                 const int x = cx + dx, y = cy + dy, z = cz + dz;
                 if (x < 0 || x >= G || y < 0 || y >= G || z < 0 || z >= G) continue;
+                if (worst_d != INT64_MAX) {
+                    // skip a cell whose nearest point is farther than the
+                    // (k-1)-th entry: none of its vertices can enter the list
+                    const int d3[3] = {dx, dy, dz};
+                    int64_t lb = 0;
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        const int64_t o = q3o[a];
+                        const int64_t gap = d3[a] < 0 ? o + 1 + (int64_t)(-d3[a] - 1) * cs
+                                                      : (d3[a] > 0 ? cs - o + (int64_t)(d3[a] - 1) * cs : 0);
+                        lb += gap * gap;
+                    }
+                    if (lb > worst_d) continue;
+                }
                 const int2 se = cell_se[(int64_t)x + ((int64_t)y << level) + ((int64_t)z << (2 * level))];
                 const int32_t p0 = se.x, p1 = se.x + se.y;
                 for (int32_t p = p0; p < p1; p++) {
