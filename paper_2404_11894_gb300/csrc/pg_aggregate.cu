@@ -243,8 +243,19 @@ static pg_status launch_agg(pg_graph *g, float *c_out, float *D_out, unsigned lo
     marginal_kernel<KP><<<pg_blocks(threads, 256), 256, 0, s>>>(g->nbr, g->OG, g->DP, g->EP, g->n, g->pmd, g->pme,
                                                                 g->kin);
     succ_row_kernel<<<pg_blocks(g->n, 256), 256, 0, s>>>(g->succ_m, g->m2r, g->n, sr);
+    // a fixed grid of exactly the resident blocks: every block strides over
+    // the same share of rows, so a grid larger than one wave would leave a
+    // second, nearly empty wave
+    static const int per_sm = [] {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, aggregate_kernel<KP, WT>, 256, 0) != cudaSuccess) {
+            (void)cudaGetLastError();
+            b = 1;
+        }
+        return b < 1 ? 1 : b;
+    }();
     int64_t need = (g->n * KP + 255) / 256;
-    int64_t cap = (int64_t)pg_num_sms() * 6;
+    int64_t cap = (int64_t)pg_num_sms() * per_sm;
     aggregate_kernel<KP, WT><<<(int)(need < cap ? need : cap), 256, 0, s>>>(
         g->nbr, g->OG, g->DP, g->EP, g->LV, sr, g->pmd, g->pme, g->kin, g->m2r, g->m2c, g->n, g->n_active,
         (WT *)g->W, g->rscale, g->col, g->b, g->c_m, g->D_m, c_out, D_out, cnt);
