@@ -16,12 +16,22 @@
 // (or a missing neighbour) points at the zero slot n.
 #include "pg_internal.cuh"
 
-__global__ void pack_kernel(pg_vertices v, int64_t n, const int32_t *__restrict__ c2m, float4 *__restrict__ OG,
-                            float4 *__restrict__ DP, float4 *__restrict__ EP, float4 *__restrict__ LV,
-                            int32_t *__restrict__ succ_m, int32_t *__restrict__ predcnt, int32_t *__restrict__ flags) {
+// One vertex's records, 64 bytes: (o, g), (d, p_ph), (e, p_e or -1 for a
+// delta light), (Le, Lph, sigma_s, w).
+struct alignas(16) vrec64 {
+    float4 og, dp, ep, lv;
+};
+
+// Pass 1, caller order i: read and check the vertex's records (coalesced)
+// and write them as one 64-byte record, still in caller order, with the
+// Morton index of the vertex's successor. Writing the four Morton-ordered
+// arrays from here would scatter 16-byte pieces of 32-byte sectors; the
+// second pass gathers whole 64-byte records instead and writes in order.
+__global__ void pack_kernel(pg_vertices v, int64_t n, const int32_t *__restrict__ c2m, vrec64 *__restrict__ rec,
+                            int32_t *__restrict__ succ_c, int32_t *__restrict__ predcnt,
+                            int32_t *__restrict__ flags) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int32_t m = c2m[i];
     float ox = v.ox[i], oy = v.oy[i], oz = v.oz[i], g = v.g[i];
     float dx = v.dx[i], dy = v.dy[i], dz = v.dz[i], pph = v.pe_ph[i];
     float ex = v.ex[i], ey = v.ey[i], ez = v.ez[i], pe = v.pe_e[i];
@@ -46,11 +56,29 @@ __global__ void pack_kernel(pg_vertices v, int64_t n, const int32_t *__restrict_
         f |= PG_FLAG_BAD_INDEX;
     }
     if (f) atomicOr(flags, f);
-    OG[m] = make_float4(ox, oy, oz, g);
-    DP[m] = make_float4(dx, dy, dz, pph);
-    EP[m] = make_float4(ex, ey, ez, delta ? -1.0f : pe);
-    LV[m] = make_float4(Le, Lph, ss, w);
-    succ_m[m] = sm;
+    vrec64 r;
+    r.og = make_float4(ox, oy, oz, g);
+    r.dp = make_float4(dx, dy, dz, pph);
+    r.ep = make_float4(ex, ey, ez, delta ? -1.0f : pe);
+    r.lv = make_float4(Le, Lph, ss, w);
+    rec[i] = r;
+    succ_c[i] = sm;
+}
+
+// Pass 2, Morton order m: the four record arrays and the successor.
+__global__ void permute_records_kernel(const vrec64 *__restrict__ rec, const int32_t *__restrict__ succ_c,
+                                       const int32_t *__restrict__ m2c, int64_t n, float4 *__restrict__ OG,
+                                       float4 *__restrict__ DP, float4 *__restrict__ EP, float4 *__restrict__ LV,
+                                       int32_t *__restrict__ succ_m) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const int32_t i = m2c[m];
+    const vrec64 r = rec[i];
+    OG[m] = r.og;
+    DP[m] = r.dp;
+    EP[m] = r.ep;
+    LV[m] = r.lv;
+    succ_m[m] = succ_c[i];
 }
 
 __global__ void active_flag_kernel(const int32_t *__restrict__ predcnt, int64_t n, int32_t *__restrict__ act,
@@ -324,9 +352,12 @@ extern "C" pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype w
         g->nnz_swept = 0;
         return PG_OK;
     }
-    int32_t *predcnt = nullptr, *act = nullptr, *d_nact = nullptr;
+    int32_t *predcnt = nullptr, *act = nullptr, *d_nact = nullptr, *succ_c = nullptr;
     unsigned long long *d_cnt = nullptr;
+    vrec64 *rec = nullptr;
     st = pg_alloc(nullptr, (void **)&predcnt, 4 * (size_t)n, s);
+    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&rec, sizeof(vrec64) * (size_t)n, s);
+    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&succ_c, 4 * (size_t)n, s);
     if (st == PG_OK) st = pg_alloc(nullptr, (void **)&act, 4 * (size_t)n, s);
     if (st == PG_OK) st = pg_alloc(nullptr, (void **)&d_nact, 16, s);
     if (st == PG_OK) st = pg_alloc(nullptr, (void **)&d_cnt, 16, s);
@@ -335,9 +366,10 @@ extern "C" pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype w
                         cudaMemsetAsync(g->flags, 0, 16, s) != cudaSuccess))
         st = PG_ERR_CUDA;
     if (st == PG_OK) {
-        pack_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(*v, n, g->c2m, g->OG, g->DP, g->EP, g->LV, g->succ_m, predcnt,
-                                                      g->flags);
-        pg_count_launches(1);
+        pack_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(*v, n, g->c2m, rec, succ_c, predcnt, g->flags);
+        permute_records_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(rec, succ_c, g->m2c, n, g->OG, g->DP, g->EP,
+                                                                 g->LV, g->succ_m);
+        pg_count_launches(2);
         active_flag_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(predcnt, n, act, g->flags);
         pg_count_launches(1);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
@@ -372,6 +404,8 @@ extern "C" pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype w
                         cudaStreamSynchronize(s) != cudaSuccess))
         st = PG_ERR_CUDA;
     if (predcnt) cudaFreeAsync(predcnt, s);
+    if (rec) cudaFreeAsync(rec, s);
+    if (succ_c) cudaFreeAsync(succ_c, s);
     if (act) cudaFreeAsync(act, s);
     if (d_nact) cudaFreeAsync(d_nact, s);
     if (d_cnt) cudaFreeAsync(d_cnt, s);
