@@ -96,7 +96,7 @@ __global__ void tfill_kernel(const int32_t *__restrict__ col, const WT *__restri
     int32_t c = col[e];
     if (c >= ncols) return;
     int64_t pos = tptr[c] + atomicAdd(&fill[c], 1);
-    tent[pos] = make_int2((int32_t)(e / kp), wbits<WT>(W[e]));
+    tent[pos] = make_int2((int32_t)(e >> (__ffs(kp) - 1)), wbits<WT>(W[e])); // kp is a power of two
 }
 
 // Column lengths rounded up to even, so that every column starts on a
@@ -128,15 +128,29 @@ __device__ __forceinline__ void bitonic_rows(int2 (&kv)[N]) {
     }
 }
 
+// A column starts at an even entry (lengths are rounded up to even), so its
+// entries move in 16-byte pairs; an odd column's last pair ends in its pad
+// entry, which is read as a sentinel and not written back.
 template <int N>
 __device__ __forceinline__ void sort_column(int2 *__restrict__ tent, int64_t a, int32_t len) {
     int2 kv[N];
+    const int4 *src = reinterpret_cast<const int4 *>(tent + a);
 #pragma unroll
-    for (int i = 0; i < N; i++) kv[i] = i < len ? tent[a + i] : make_int2(INT32_MAX, 0);
+    for (int i = 0; i < N; i += 2) {
+        int4 u = make_int4(INT32_MAX, 0, INT32_MAX, 0);
+        if (i < len) u = src[i / 2];
+        kv[i] = make_int2(u.x, u.y);
+        kv[i + 1] = i + 1 < len ? make_int2(u.z, u.w) : make_int2(INT32_MAX, 0);
+    }
     bitonic_rows<N>(kv);
+    int4 *dst = reinterpret_cast<int4 *>(tent + a);
 #pragma unroll
-    for (int i = 0; i < N; i++)
-        if (i < len) tent[a + i] = kv[i];
+    for (int i = 0; i < N; i += 2) {
+        if (i + 1 < len)
+            dst[i / 2] = make_int4(kv[i].x, kv[i].y, kv[i + 1].x, kv[i + 1].y);
+        else if (i < len)
+            tent[a + i] = kv[i];
+    }
 }
 
 // Order each column's entries by source row (a row appears once per column),

@@ -109,8 +109,8 @@ __global__ void fg_prefix_kernel(const int32_t *__restrict__ qm, int64_t n_paths
                                  int kp, int kfg, int kpf, int32_t *__restrict__ fgn) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_paths * kpf) return;
-    const int64_t p = e / kpf;
-    const int i = (int)(e - p * kpf);
+    const int64_t p = e >> (__ffs(kpf) - 1); // kpf is a power of two
+    const int i = (int)(e & (kpf - 1));
     const int32_t m = qm[p];
     fgn[e] = (m >= 0 && i < kfg) ? nbr[(int64_t)m * kp + i] : -1;
 }
