@@ -352,12 +352,20 @@ extern "C" pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype w
         g->nnz_swept = 0;
         return PG_OK;
     }
-    int32_t *predcnt = nullptr, *act = nullptr, *d_nact = nullptr, *succ_c = nullptr;
+    int32_t *predcnt = nullptr, *act = nullptr, *d_nact = nullptr;
     unsigned long long *d_cnt = nullptr;
-    vrec64 *rec = nullptr;
+    // The caller-order records live in the entry-column array until the
+    // weight pass writes it (4 kp bytes per vertex, enough from kp = 16),
+    // else in a temporary; the successors' Morton indices live in act,
+    // which the active-row flags overwrite after the permutation.
+    vrec64 *rec = nullptr, *rec_tmp = nullptr;
     st = pg_alloc(nullptr, (void **)&predcnt, 4 * (size_t)n, s);
-    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&rec, sizeof(vrec64) * (size_t)n, s);
-    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&succ_c, 4 * (size_t)n, s);
+    if (st == PG_OK) {
+        if ((size_t)4 * kp >= sizeof(vrec64))
+            rec = reinterpret_cast<vrec64 *>(g->col);
+        else if ((st = pg_alloc(nullptr, (void **)&rec_tmp, sizeof(vrec64) * (size_t)n, s)) == PG_OK)
+            rec = rec_tmp;
+    }
     if (st == PG_OK) st = pg_alloc(nullptr, (void **)&act, 4 * (size_t)n, s);
     if (st == PG_OK) st = pg_alloc(nullptr, (void **)&d_nact, 16, s);
     if (st == PG_OK) st = pg_alloc(nullptr, (void **)&d_cnt, 16, s);
@@ -366,9 +374,9 @@ extern "C" pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype w
                         cudaMemsetAsync(g->flags, 0, 16, s) != cudaSuccess))
         st = PG_ERR_CUDA;
     if (st == PG_OK) {
-        pack_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(*v, n, g->c2m, rec, succ_c, predcnt, g->flags);
-        permute_records_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(rec, succ_c, g->m2c, n, g->OG, g->DP, g->EP,
-                                                                 g->LV, g->succ_m);
+        pack_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(*v, n, g->c2m, rec, act, predcnt, g->flags);
+        permute_records_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(rec, act, g->m2c, n, g->OG, g->DP, g->EP, g->LV,
+                                                                 g->succ_m);
         pg_count_launches(2);
         active_flag_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(predcnt, n, act, g->flags);
         pg_count_launches(1);
@@ -404,8 +412,7 @@ extern "C" pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype w
                         cudaStreamSynchronize(s) != cudaSuccess))
         st = PG_ERR_CUDA;
     if (predcnt) cudaFreeAsync(predcnt, s);
-    if (rec) cudaFreeAsync(rec, s);
-    if (succ_c) cudaFreeAsync(succ_c, s);
+    if (rec_tmp) cudaFreeAsync(rec_tmp, s);
     if (act) cudaFreeAsync(act, s);
     if (d_nact) cudaFreeAsync(d_nact, s);
     if (d_cnt) cudaFreeAsync(d_cnt, s);
