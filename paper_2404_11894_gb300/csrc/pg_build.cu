@@ -270,8 +270,11 @@ __global__ void __launch_bounds__(128, 4) knn_kernel(const int4 *__restrict__ qr
 
 // Exact path for queued queries: entries (int64 d2, caller id) compared
 // lexicographically. QUERY = false: the build's redo list (*d_count
-// entries), row m of nbr. QUERY = true: nq query points list[t] (Morton
-// index, or -1 for none), row t of nbr.
+// entries), row m of nbr. QUERY = true without qlist: nq query points
+// list[t] (Morton index, or -1 for none), row t of nbr; with qlist: the
+// first-ring kernel's queued query slots list[t] (*d_count entries), slot u
+// asking for vertex qlist[u], row u of nbr. With saved_keys, query t resumes
+// at ring 2 from the first-ring kernel's list (entry t of the queue).
 template <int KP, bool QUERY>
 __global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__ qrec,
                                                         const int2 *__restrict__ cell_se,
