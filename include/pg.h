@@ -55,7 +55,7 @@ typedef enum {
     PG_ERR_CUDA = 3,         /* CUDA runtime / launch error */
     PG_ERR_NONFINITE = 4,    /* NaN or Inf in an input array */
     PG_ERR_TIMEOUT = 5,      /* reserved: a bounded device wait ran out */
-    PG_ERR_UNSUPPORTED = 6,  /* parameter outside what this build supports */
+    PG_ERR_UNSUPPORTED = 6,  /* parameter outside what the library supports */
     PG_ERR_STATE = 7         /* call order: e.g. propagate before aggregate */
 } pg_status;
 
