@@ -34,8 +34,11 @@
  *    errors of earlier asynchronous work surface at the next synchronising
  *    call as PG_ERR_CUDA.
  *  - n = 0 is valid (empty outputs, PG_OK).
- *  - The library allocates its own device memory (stream-ordered allocator)
- *    for the graph object and temporaries; PG_ERR_OOM when that fails.
+ *  - The library allocates its own device memory for the graph object and
+ *    temporaries from a stream-ordered memory pool of its own on each device
+ *    (created at the first allocation on that device, never released to the
+ *    driver before exit, so repeated builds reuse it); the device's default
+ *    pool is left untouched. PG_ERR_OOM when an allocation fails.
  */
 #ifndef PG_H
 #define PG_H
@@ -159,15 +162,25 @@ typedef struct {
 
 pg_status pg_graph_get_info(const pg_graph *g, pg_graph_info *info);
 
-/* Aggregation (Section 3.5). For every vertex s with K = |N(s)|:
- *   A+_{s,j} = sigma_s(s) rho_s(o_s, d_j) / sum_{l in N(s)} rho_l(o_l, d_j)
- *     (Eq. ag-indirect with the marginal density of Eq. indirect-weight)
- *   c_s = sum_{j in N(s)} A°_{s,2j} Le_j + A°_{s,2j+1} Lph_j   (Eq. ag-direct)
- *     A°_{s,2j}   = sigma_s rho_s(o_s,e_j) / (sum_l rho_l(o_l,e_j) + K pe_e_j),
- *                   or sigma_s rho_s(o_s,e_j) / K for a delta light
- *     A°_{s,2j+1} = sigma_s rho_s(o_s,d_j) / (sum_l rho_l(o_l,d_j) + K pe_ph_j)
+/* Aggregation (Section 3.5). Each sample j (vertex j's phase sample d_j and
+ * emitter sample e_j) is shared by the vertices that hold j in their
+ * neighbourhood, R(j) = {r : j in N(r)}, K_j = |R(j)| (j itself included).
+ * Its marginal densities are summed over those vertices' phase strategies
+ * (Eq. indirect-weight's p_m; in the paper's clusters R(j) is the cluster):
+ *   pm_d(j) = sum_{r in R(j)} rho_r(o_r, d_j),  pm_e(j) = sum_{r in R(j)} rho_r(o_r, e_j)
+ * and for every vertex s and j in N(s):
+ *   A+_{s,j} = sigma_s(s) rho_s(o_s, d_j) / pm_d(j)           (Eq. ag-indirect)
+ *   c_s = sum_{j in N(s)} A°_{s,2j} Le_j + A°_{s,2j+1} Lph_j    (Eq. ag-direct)
+ *     A°_{s,2j}   = sigma_s rho_s(o_s,e_j) / (pm_e(j) + K_j pe_e_j),
+ *                   or sigma_s rho_s(o_s,e_j) / |N(s)| for a delta light
+ *     A°_{s,2j+1} = sigma_s rho_s(o_s,d_j) / (pm_d(j) + K_j pe_ph_j)
  *   D_s = the same direct term with N(s) = {s} (the non-aggregated direct
  *     light used at output, Section 4 "Handling direct light").
+ * So sample j's indirect weights over R(j) sum to sigma-weighted one (the
+ * balance heuristic of Eq. indirect-weight), and every column of P A+ sums
+ * to at most the largest albedo. The marginals are accumulated in 64-bit
+ * fixed point (34 fraction bits), so the weights do not depend on the order
+ * of the device's atomic additions.
  * The graph keeps the propagation matrix (P A+, Eq. rte-mff) in `wdtype` and
  * P c. c and D (caller order, n floats each, device) are written for the
  * caller; either may be NULL. Synchronises `stream` once.
@@ -326,10 +339,13 @@ pg_status pg_graph_release_weights(pg_graph *g);
  * exact Henyey-Greenstein phase sampling, no Russian roulette (max_depth
  * truncates). Records as described for pg_vertices, plus L0 (the path
  * tracer's incoming indirect radiance along d, the propagation's start) and
- * per path first / bg / the path tracer's value. Double precision inside,
- * deterministic: the same scene and seed give the same records on every run
- * (and the same as the repository's host recorder, which evaluates the same
- * operations in the same order). */
+ * per path first / bg / the path tracer's value. Paths are traced in single
+ * precision (positions, directions, free flights, transmittance; the records
+ * are float32 anyway); L0, L0_f64 and the per-path values are then summed in
+ * double from those records. Deterministic: the same scene and seed give the
+ * same records on every run (and the same as the repository's host
+ * recorder, which evaluates the same IEEE-rounded operations in the same
+ * order). */
 typedef struct {
     int32_t grid_res;        /* voxels per axis */
     const float *density;    /* device, grid_res^3 sigma_t >= 0, index x + G (y + G z) */

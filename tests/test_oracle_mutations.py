@@ -146,3 +146,43 @@ def test_final_gather_marginal_without_receiver_is_caught(monkeypatch):
     monkeypatch.setattr(opg, "hg", bad_hg)
     with pytest.raises(AssertionError):
         test_final_gather_expectation()
+
+
+def test_receiver_count_in_emitter_marginal_is_caught(monkeypatch):
+    """Multiplying the emitter pdf inside the direct marginals of Eq. ag-direct
+    by the receiver's |N(s)| instead of the sample's |R(j)| (the same count on
+    clusters) fails the identical-lobe closed form and biases the Monte Carlo
+    expectation of the direct term on a kNN graph."""
+    from test_oracle_direct_pins import (test_direct_term_unbiased_over_receivers_on_knn_graphs,
+                                         test_direct_weights_identical_lobes_closed_form_on_knn_graphs)
+
+    good = opg.aggregate
+
+    def bad_aggregate(V, nbr, sigma_s=None, g=None, rows=None, marginals=None):
+        out = good(V, nbr, sigma_s=sigma_s, g=g, rows=rows, marginals=marginals)
+        X = opg.vertex_arrays(V)
+        if sigma_s is not None:
+            X["sigma_s"] = np.asarray(sigma_s, np.float64)
+        if g is not None:
+            X["g"] = np.asarray(g, np.float64)
+        recv = np.arange(len(nbr)) if rows is None else np.asarray(rows)
+        nb = nbr[recv]
+        valid = nb >= 0
+        j = np.where(valid, nb, 0)
+        Ks = valid.sum(axis=1).astype(np.float64)[:, None]
+        sig, o, gs = X["sigma_s"][recv][:, None], X["o"][recv][:, None, :], X["g"][recv][:, None]
+        rho_se = opg.hg(o, X["e"][j], gs)
+        rho_sd = opg.hg(o, X["d"][j], gs)
+        Ae = np.where(X["delta"][j], out["Ae"], sig * rho_se / (out["pm_e"][j] + Ks * X["pe_e"][j]))
+        Aph = sig * rho_sd / (out["pm_d"][j] + Ks * X["pe_ph"][j])
+        out["Ae"] = np.where(valid, Ae, 0.0)
+        out["Aph"] = np.where(valid, Aph, 0.0)
+        return out
+
+    monkeypatch.setattr(opg, "aggregate", bad_aggregate)
+    monkeypatch.setattr(oracle, "aggregate", bad_aggregate)
+    for g in (0.0, 0.7):
+        with pytest.raises(AssertionError):
+            test_direct_weights_identical_lobes_closed_form_on_knn_graphs(g)
+    with pytest.raises(AssertionError):
+        test_direct_term_unbiased_over_receivers_on_knn_graphs()
