@@ -12,8 +12,7 @@ the direct term A°L° (Eq. ag-direct), the propagation matrix P
 (Eq. volume-propagation / rte-pg) and the per-path output (Section 4,
 "Final output", "Handling direct light").
 
-Readings where the paper is silent or garbled (each listed in the design
-notes):
+Readings where the paper is silent or garbled:
   * neighbourhoods are exact k-nearest-neighbour sets (self first, then the
     k-1 nearest others by squared integer distance, ties by smaller index) on
     21-bit quantised coordinates; the paper's clusters (Section 3.1) are the

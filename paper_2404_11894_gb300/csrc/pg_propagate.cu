@@ -6,7 +6,9 @@
 // evict-first so the gathered vector y stays in L2); KP/4 lanes share a row
 // and combine their four products with shuffles. The relative change of the
 // sweep is reduced in FP64 (per-block partials, then the last block), and a
-// sweep that finds the previous one converged returns at once.
+// sweep that finds the previous one converged returns at once. The squared
+// change and norm are accumulated in FP64 in every thread (the difference of
+// two float iterates is exact in double), then across the grid.
 #include <algorithm>
 #include <mutex>
 
@@ -68,7 +70,7 @@ __device__ __forceinline__ void block_sum2(double &a, double &b) {
 // Relative change of the sweep: per-block FP64 partials, then the last block
 // to finish (ticket in ctrl[2]) adds them up and sets the stop flag.
 template <int NT>
-__device__ __forceinline__ void sweep_residual(float rd, float rn, int32_t *ctrl, double2 *partials,
+__device__ __forceinline__ void sweep_residual(double rd, double rn, int32_t *ctrl, double2 *partials,
                                                double *resid, int t, double tol) {
     double a = rd, bb = rn;
     block_sum2<NT>(a, bb);
@@ -151,7 +153,7 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(
         const int64_t tile = k / TILE_GROUPS;
         return (tile * gridDim.x + blockIdx.x) * (STEP * TILE_GROUPS) + (k - tile * TILE_GROUPS) * STEP;
     };
-    float rd = 0.0f, rn = 0.0f;
+    double rd = 0.0, rn = 0.0;
     auto group = [&](int64_t base) { // uniform across the block
         int32_t row[U]; // row indices fit in 32 bits (n < 2^31); 64-bit only in element offsets
         bool ok[U];
@@ -183,10 +185,11 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(
             if (ok[u] && q == 0) {
                 const float sc = W16 ? rscale[row[u]] : 1.0f;
                 const float yn = fmaf(acc, sc, b[row[u]]);
-                const float d = yn - yin[row[u]];
                 yout[row[u]] = yn;
-                rd = fmaf(d, d, rd);
-                rn = fmaf(yn, yn, rn);
+                // the residual's sums in FP64 from the first term on
+                const double d = (double)yn - (double)yin[row[u]];
+                rd = fma(d, d, rd);
+                rn = fma((double)yn, (double)yn, rn);
             }
         }
     };
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(NT, MINB) sweep_pf_kernel(
             else if (W16 && q == 2) sv = __ldcs(rscale + row);
         }
     };
-    float rd = 0.0f, rn = 0.0f;
+    double rd = 0.0, rn = 0.0;
     int4 c4n;
     float4 w4n;
     float svn;
@@ -259,10 +262,11 @@ __global__ void __launch_bounds__(NT, MINB) sweep_pf_kernel(
         const int64_t row = base + lr;
         if (row < r1 && q == 0) {
             const float yn = fmaf(acc, sc, sv);
-            const float d = yn - yo;
             yout[row] = yn;
-            rd = fmaf(d, d, rd);
-            rn = fmaf(yn, yn, rn);
+            // the residual's sums in FP64 from the first term on
+            const double d = (double)yn - (double)yo;
+            rd = fma(d, d, rd);
+            rn = fma((double)yn, (double)yn, rn);
         }
         base = nb;
     }

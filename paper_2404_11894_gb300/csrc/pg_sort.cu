@@ -1,6 +1,7 @@
 // Device primitives: stream-ordered allocation, exclusive scan, and a stable
 // LSD radix sort of (uint32 key, int32 value) pairs.
 #include <atomic>
+#include <mutex>
 
 #include "pg_internal.cuh"
 
@@ -8,27 +9,46 @@ static std::atomic<long long> g_launches{0};
 void pg_count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 extern "C" int64_t pg_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
-// Keep freed blocks in the device's default stream-ordered pool instead of
-// returning them to the driver at every synchronisation, so a graph rebuilt
-// every frame reuses its memory.
-static void pool_keep_memory() {
-    static bool done = false;
-    if (done) return;
-    done = true;
-    int dev = 0;
-    cudaMemPool_t pool;
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+// The library's own stream-ordered memory pool on each device. Freed blocks
+// stay in it (release threshold: never) instead of going back to the driver
+// at every synchronisation, so a graph rebuilt every frame reuses its memory.
+// Being private, it leaves the device's default pool, which other code in the
+// process may share, exactly as the caller configured it.
+static cudaMemPool_t lib_pool(int dev) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
         uint64_t thr = UINT64_MAX;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        (void)cudaGetLastError();
+        pools[dev] = pool;
     }
-    (void)cudaGetLastError();
+    return pools[dev];
 }
 
 pg_status pg_alloc(pg_graph *g, void **p, size_t bytes, cudaStream_t s) {
-    pool_keep_memory();
     *p = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return PG_ERR_CUDA;
+    }
+    cudaMemPool_t pool = lib_pool(dev);
+    if (!pool) return PG_ERR_CUDA;
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         *p = nullptr;

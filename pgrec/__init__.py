@@ -167,7 +167,7 @@ class Scene:
 
 
 # The five workloads. Media are synthetic stand-ins for the paper's scenes
-# (clouds and smoke under sun/sky or area lighting); see the design notes.
+# (clouds and smoke under sun/sky or area lighting).
 CUBE_CONST = Scene(
     name="cube32_const_sigma2_a0.9_iso_64px_4spp_d8", grid_res=32, medium_kind=0,
     sigma_t_max=2.0, albedo=0.9, g=0.0, width=64, height=64, spp=4, max_depth=8,
