@@ -64,8 +64,16 @@ typedef enum {
 
 /* Storage type of the edge weights in the propagation sweep. 16-bit types
  * store each row as an FP32 scale times a 16-bit payload; accumulation is
- * FP32 in every case. */
-typedef enum { PG_W_F32 = 0, PG_W_BF16 = 1, PG_W_F16 = 2 } pg_wdtype;
+ * FP32 in every case.
+ *   PG_W_BF16, PG_W_F16  each weight divided by the row's largest weight,
+ *                        rounded to nearest in that format (8 or 11
+ *                        significant bits);
+ *   PG_W_U16             each weight as 16-bit unsigned fixed point,
+ *                        q = round(65535 w / max), scale max / 65535: the
+ *                        weights are non-negative and the scale carries the
+ *                        range, so every weight has an absolute error of at
+ *                        most max / 131070 (the most accurate 16-bit form). */
+typedef enum { PG_W_F32 = 0, PG_W_BF16 = 1, PG_W_F16 = 2, PG_W_U16 = 3 } pg_wdtype;
 
 typedef struct pg_graph pg_graph; /* opaque; owns its device buffers */
 
@@ -397,6 +405,80 @@ pg_status pg_record_count(const pg_scene *scene, int64_t *path_offsets, int64_t 
 pg_status pg_record_fill(const pg_scene *scene, const int64_t *path_offsets, const pg_recording *out,
                          pg_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Sharded sweeps (one shard per GPU). The Jacobi sweep of Eq. rte-mff
+ * updates every swept row from the previous iterate only, so the rows split
+ * into independent parts. A shard owns a contiguous range of the graph's
+ * sweep rows (sweep rows are in Morton order: a range is a spatial slab),
+ * cut so that all shards hold nearly the same number of live entries, and
+ * iterates a local vector z of local_len floats:
+ *     z = [ own rows (row_end - row_begin) | halo (n_halo) | zero slot ]
+ * The halo holds the sweep-vector entries its rows read but other shards
+ * own (neighbours across the slab boundary, continuation edges leaving the
+ * slab), in ascending global order, so the entries owned by shard q are the
+ * halo segment [recv_begin[q], recv_begin[q+1]). Shard q sends them, in the
+ * same order, as the segment [send_begin[p], send_begin[p+1]) of its packed
+ * send buffer. One sweep per shard: pg_shard_pack, exchange the segments
+ * (e.g. NCCL send/recv), copy each received segment into the halo, then
+ * pg_shard_sweep. Every row is summed in the same order as in pg_propagate,
+ * so T sharded sweeps give bitwise pg_propagate's iterate. The sweep vector
+ * y (n+1 floats, sweep-row order) relates to L+ by pg_graph_y_from_L and
+ * pg_graph_L_from_y; the shards' own rows, gathered into y, give L+. */
+typedef struct pg_shard pg_shard;
+
+typedef struct {
+    int32_t n_shards, shard, row_width;
+    int64_t row_begin, row_end; /* own sweep rows [row_begin, row_end) */
+    int64_t n_halo;             /* halo entries */
+    int64_t local_len;          /* floats of z: own rows + halo + 1 */
+    int64_t n_send;             /* floats of the packed send buffer (all peers) */
+} pg_shard_info;
+
+/* Shard `shard` of `n_shards` of an aggregated graph (its swept rows'
+ * column table is copied to the host to plan the partition; synchronises
+ * `stream`). The shard keeps a pointer to g: destroy it first. Errors:
+ * PG_ERR_STATE (no pg_aggregate, weights released), PG_ERR_INVALID_ARG. */
+pg_status pg_shard_create(const pg_graph *g, int32_t n_shards, int32_t shard, pg_stream_t stream, pg_shard **out);
+
+/* The same plan from a HOST column table (n_rows rows of row_width entries,
+ * entry values in [0, n_rows) or zero_slot >= n_rows for an empty entry),
+ * without a device: for inspecting and testing the partition. Such a shard
+ * supports only pg_shard_get_info / pg_shard_get_lists / pg_shard_destroy. */
+pg_status pg_shard_create_host(const int32_t *col, int64_t n_rows, int32_t row_width, int64_t zero_slot,
+                               int32_t n_shards, int32_t shard, pg_shard **out);
+
+pg_status pg_shard_get_info(const pg_shard *s, pg_shard_info *info);
+
+/* HOST copies of the plan, each optional (NULL skips): row_begin
+ * (n_shards + 1: shard q owns rows [row_begin[q], row_begin[q+1])),
+ * recv_begin (n_shards + 1, halo segments by owner), send_begin
+ * (n_shards + 1, send-buffer segments by receiver), halo (n_halo global
+ * rows), send_idx (n_send own local rows), local_col (own rows x row_width,
+ * the column table re-indexed into z). */
+pg_status pg_shard_get_lists(const pg_shard *s, int64_t *row_begin, int64_t *recv_begin, int64_t *send_begin,
+                             int32_t *halo, int32_t *send_idx, int32_t *local_col);
+
+/* z (device, local_len floats) from a global sweep vector y (device, n+1):
+ * own rows, halo entries, zero slot. */
+pg_status pg_shard_load(const pg_shard *s, const float *y, float *z, pg_stream_t stream);
+
+/* send[i] = z[send_idx[i]] for all peers (device, n_send floats). */
+pg_status pg_shard_pack(const pg_shard *s, const float *z, float *send, pg_stream_t stream);
+
+/* One sweep of the own rows: z_out[r] = sum_i W[r][i] z_in[local_col[r][i]]
+ * (times the row scale of 16-bit weights) + b[r] for r < own rows, with the
+ * graph's stored weights and P c of its last pg_aggregate. z_in's halo must
+ * hold the previous iterate's values of the peers' rows. z_out's halo and
+ * zero slot are not written. Asynchronous. */
+pg_status pg_shard_sweep(pg_shard *s, const float *z_in, float *z_out, pg_stream_t stream);
+
+void pg_shard_destroy(pg_shard *s);
+
+/* y (device, n+1 floats, sweep-row order) with y[row of succ(v)] = L[v] and
+ * 0 elsewhere; and back: L[v] = y[row of succ(v)], 0 at a path's end. */
+pg_status pg_graph_y_from_L(const pg_graph *g, const float *L, float *y, pg_stream_t stream);
+pg_status pg_graph_L_from_y(const pg_graph *g, const float *y, float *L, pg_stream_t stream);
+
 void pg_graph_destroy(pg_graph *g);
 const char *pg_status_string(pg_status s);
 
@@ -413,16 +495,21 @@ const char *pg_status_string(pg_status s);
  * and no residual output: `iters` sweeps from L0 (caller order, n floats),
  * stopping early on the device when tol > 0, writing L (caller order, n
  * floats). Its scratch (two iterates, residual partials and control words)
- * lives in one file-scope device array of 32 MiB + 96 KiB that every GPU
- * which loads the library holds until the process exits. The first call on
- * each device looks up that array's device address; make that first call
- * before any stream capture. Every call shares the array and the array keeps
+ * lives in one file-scope device array of 32 MiB + 96 KiB, reserved on a
+ * device when the library's device code is first loaded there and held
+ * until the process exits. Under CUDA's default lazy module loading that
+ * can be this call's first use on the device, which then reports PG_ERR_OOM
+ * if the device has no room for the array: make one call (or any other
+ * library call) on each device at set-up, or set CUDA_MODULE_LOADING=EAGER.
+ * The first call on each device also looks up that array's device address;
+ * make that first call before any stream capture. Every call shares the array and the array keeps
  * the previous call's contents (the call resets what must start at zero), so
  * calls whose work overlaps on the GPU -- on any stream, for any graph --
  * race and corrupt each other's results: serialise them.
  * Errors: PG_ERR_UNSUPPORTED when n > PG_NOALLOC_MAX_VERTICES or
  * iters > PG_NOALLOC_MAX_ITERS; PG_ERR_STATE (no pg_aggregate, or weights
- * released); PG_ERR_INVALID_ARG. It calls no allocation routine. */
+ * released); PG_ERR_INVALID_ARG; PG_ERR_OOM (the array could not be
+ * reserved, see above). It calls no allocation routine. */
 #define PG_NOALLOC_MAX_VERTICES 4194303
 #define PG_NOALLOC_MAX_ITERS 4096
 pg_status pg_propagate_noalloc(pg_graph *g, const float *L0, int32_t iters, double tol, float *L,

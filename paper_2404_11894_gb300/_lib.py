@@ -11,7 +11,7 @@ PG_STATUS = {
     0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
     4: "non-finite input", 5: "device wait timed out", 6: "unsupported parameter", 7: "invalid call order",
 }
-W_DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
+W_DTYPES = {"f32": 0, "bf16": 1, "f16": 2, "u16": 3}
 
 c_float_p = ctypes.POINTER(ctypes.c_float)
 
@@ -66,10 +66,18 @@ class PgRecording(ctypes.Structure):
                 + [(k, ctypes.c_void_p) for k in RECORD_EXTRA_F32 + ("x_delta",)])
 
 
+class PgShardInfo(ctypes.Structure):
+    _fields_ = [("n_shards", ctypes.c_int32), ("shard", ctypes.c_int32), ("row_width", ctypes.c_int32),
+                ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64), ("n_halo", ctypes.c_int64),
+                ("local_len", ctypes.c_int64), ("n_send", ctypes.c_int64)]
+
+
 EXPORTS = ("pg_build_graph", "pg_graph_neighbors", "pg_graph_get_info", "pg_aggregate", "pg_propagate",
            "pg_gather", "pg_propagate_adjoint", "pg_graph_release_weights", "pg_graph_destroy",
            "pg_status_string", "pg_launch_count", "pg_propagate_noalloc", "pg_gather_ex",
-           "pg_record_count", "pg_record_fill", "pg_prepare_adjoint")
+           "pg_record_count", "pg_record_fill", "pg_prepare_adjoint", "pg_shard_create", "pg_shard_create_host",
+           "pg_shard_get_info", "pg_shard_get_lists", "pg_shard_load", "pg_shard_pack", "pg_shard_sweep",
+           "pg_shard_destroy", "pg_graph_y_from_L", "pg_graph_L_from_y")
 
 _lib = None
 
@@ -101,10 +109,21 @@ def load(path: str = LIB_PATH):
     lib.pg_status_string.argtypes = [ctypes.c_int]
     lib.pg_status_string.restype = ctypes.c_char_p
     lib.pg_propagate_noalloc.argtypes = [vp, vp, i32, f64, vp, vp]
+    lib.pg_shard_create.argtypes = [vp, i32, i32, vp, ctypes.POINTER(vp)]
+    lib.pg_shard_create_host.argtypes = [vp, i64, i32, i64, i32, i32, ctypes.POINTER(vp)]
+    lib.pg_shard_get_info.argtypes = [vp, ctypes.POINTER(PgShardInfo)]
+    lib.pg_shard_get_lists.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.pg_shard_load.argtypes = [vp, vp, vp, vp]
+    lib.pg_shard_pack.argtypes = [vp, vp, vp, vp]
+    lib.pg_shard_sweep.argtypes = [vp, vp, vp, vp]
+    lib.pg_shard_destroy.argtypes = [vp]
+    lib.pg_shard_destroy.restype = None
+    lib.pg_graph_y_from_L.argtypes = [vp, vp, vp, vp]
+    lib.pg_graph_L_from_y.argtypes = [vp, vp, vp, vp]
     lib.pg_launch_count.argtypes = []
     lib.pg_launch_count.restype = ctypes.c_int64
     for name in EXPORTS:
-        if name not in ("pg_graph_destroy", "pg_status_string", "pg_launch_count"):
+        if name not in ("pg_graph_destroy", "pg_status_string", "pg_launch_count", "pg_shard_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

@@ -20,58 +20,6 @@
 // with atomic adds (no weight memory).
 #include "pg_internal.cuh"
 
-template <typename WT>
-__device__ __forceinline__ float wload(const WT *W, int64_t i);
-template <>
-__device__ __forceinline__ float wload<float>(const float *W, int64_t i) { return W[i]; }
-template <>
-__device__ __forceinline__ float wload<__nv_bfloat16>(const __nv_bfloat16 *W, int64_t i) { return __bfloat162float(W[i]); }
-template <>
-__device__ __forceinline__ float wload<__half>(const __half *W, int64_t i) { return __half2float(W[i]); }
-
-// weight <-> the 32-bit payload of a transposed entry
-template <typename WT>
-__device__ __forceinline__ int32_t wbits(WT w);
-template <>
-__device__ __forceinline__ int32_t wbits<float>(float w) { return __float_as_int(w); }
-template <>
-__device__ __forceinline__ int32_t wbits<__nv_bfloat16>(__nv_bfloat16 w) { return (int32_t)__bfloat16_as_ushort(w); }
-template <>
-__device__ __forceinline__ int32_t wbits<__half>(__half w) { return (int32_t)__half_as_ushort(w); }
-template <typename WT>
-__device__ __forceinline__ float wfrom(int32_t b);
-template <>
-__device__ __forceinline__ float wfrom<float>(int32_t b) { return __int_as_float(b); }
-template <>
-__device__ __forceinline__ float wfrom<__nv_bfloat16>(int32_t b) { return __bfloat162float(__ushort_as_bfloat16((unsigned short)b)); }
-template <>
-__device__ __forceinline__ float wfrom<__half>(int32_t b) { return __half2float(__ushort_as_half((unsigned short)b)); }
-
-template <typename WT>
-struct W4L;
-template <>
-struct W4L<float> {
-    static __device__ __forceinline__ float4 load(const float *p) { return __ldcs(reinterpret_cast<const float4 *>(p)); }
-};
-template <>
-struct W4L<__nv_bfloat16> {
-    static __device__ __forceinline__ float4 load(const __nv_bfloat16 *p) {
-        uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
-        __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162 *>(&u.x), b = *reinterpret_cast<__nv_bfloat162 *>(&u.y);
-        float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-        return make_float4(fa.x, fa.y, fb.x, fb.y);
-    }
-};
-template <>
-struct W4L<__half> {
-    static __device__ __forceinline__ float4 load(const __half *p) {
-        uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
-        __half2 a = *reinterpret_cast<__half2 *>(&u.x), b = *reinterpret_cast<__half2 *>(&u.y);
-        float2 fa = __half22float2(a), fb = __half22float2(b);
-        return make_float4(fa.x, fa.y, fb.x, fb.y);
-    }
-};
-
 __global__ void scale_rows_kernel(const float *__restrict__ mu, const float *__restrict__ rs, int64_t na,
                                   float *__restrict__ us) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -96,7 +44,7 @@ __global__ void tfill_kernel(const int32_t *__restrict__ col, const WT *__restri
     int32_t c = col[e];
     if (c >= ncols) return;
     int64_t pos = tptr[c] + atomicAdd(&fill[c], 1);
-    tent[pos] = make_int2((int32_t)(e >> (__ffs(kp) - 1)), wbits<WT>(W[e])); // kp is a power of two
+    tent[pos] = make_int2((int32_t)(e >> (__ffs(kp) - 1)), WTraits<WT>::bits(W[e])); // kp is a power of two
 }
 
 // Column lengths rounded up to even, so that every column starts on a
@@ -300,16 +248,16 @@ __global__ void __launch_bounds__(TS_THREADS, MINB) tsweep_pf_kernel(
         if (ok && write_out) {
 #pragma unroll
             for (int u = 0; u < PAIRS; u++) {
-                if (ent[u].x >= 0) acc = fmaf(wfrom<WT>(ent[u].y), __ldg(us_in + ent[u].x), acc);
-                if (ent[u].z >= 0) acc = fmaf(wfrom<WT>(ent[u].w), __ldg(us_in + ent[u].z), acc);
+                if (ent[u].x >= 0) acc = fmaf(WTraits<WT>::from_bits(ent[u].y), __ldg(us_in + ent[u].x), acc);
+                if (ent[u].z >= 0) acc = fmaf(WTraits<WT>::from_bits(ent[u].w), __ldg(us_in + ent[u].z), acc);
             }
             for (int64_t a = ca + 2 * LPC * PAIRS; a < cb; a += 2 * LPC * PAIRS) {
                 int4 more[PAIRS];
                 first_pass(a, cb, more);
 #pragma unroll
                 for (int u = 0; u < PAIRS; u++) {
-                    if (more[u].x >= 0) acc = fmaf(wfrom<WT>(more[u].y), __ldg(us_in + more[u].x), acc);
-                    if (more[u].z >= 0) acc = fmaf(wfrom<WT>(more[u].w), __ldg(us_in + more[u].z), acc);
+                    if (more[u].x >= 0) acc = fmaf(WTraits<WT>::from_bits(more[u].y), __ldg(us_in + more[u].x), acc);
+                    if (more[u].z >= 0) acc = fmaf(WTraits<WT>::from_bits(more[u].w), __ldg(us_in + more[u].z), acc);
                 }
             }
         }
@@ -351,7 +299,7 @@ __global__ void first_rows_kernel(const int32_t *__restrict__ first, int64_t n_p
     int32_t m = c2m[f];
     int64_t r = m2r[m];
     float sum = 0.0f;
-    for (int i = 0; i < kp; i++) sum = fmaf(wload<WT>(W, r * kp + i), yT[col[r * kp + i]], sum);
+    for (int i = 0; i < kp; i++) sum = fmaf(WTraits<WT>::dec(W[r * kp + i]), yT[col[r * kp + i]], sum);
     if (rscale) sum *= rscale[r];
     G[r] += nu[r] * (sum + LV[m].w * D_m[m]);
 }
@@ -374,7 +322,7 @@ __global__ void __launch_bounds__(256) scatter_sweep_kernel(
     const float u = us_in[row];
     if (write_out && u != 0.0f) {
         const int4 c4 = __ldcs(reinterpret_cast<const int4 *>(col + row * KP) + q);
-        const float4 w4 = W4L<WT>::load(W + row * KP + q * 4);
+        const float4 w4 = WTraits<WT>::load4(W + row * KP + q * 4);
         if (c4.x < n) atomicAdd(out + c4.x, w4.x * u);
         if (c4.y < n) atomicAdd(out + c4.y, w4.y * u);
         if (c4.z < n) atomicAdd(out + c4.z, w4.z * u);
@@ -799,12 +747,7 @@ extern "C" pg_status pg_prepare_adjoint(pg_graph *g, pg_stream_t stream) {
     if (!g->aggregated || !g->W) return PG_ERR_STATE;
     if (g->tA.ptr || g->n == 0) return PG_OK; // built for the current weights, or nothing to build
     cudaStream_t s = (cudaStream_t)stream;
-    switch (g->wdtype) {
-        case PG_W_F32: return build_transpose<float>(g, s);
-        case PG_W_BF16: return build_transpose<__nv_bfloat16>(g, s);
-        case PG_W_F16: return build_transpose<__half>(g, s);
-    }
-    return PG_ERR_INVALID_ARG;
+    return pg_dispatch_w(g->wdtype, [&](auto tag) { return build_transpose<typename decltype(tag)::type>(g, s); });
 }
 
 extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const int32_t *first, int64_t n_paths,
@@ -868,13 +811,9 @@ extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const in
     }
     if (st == PG_OK) {
         if (recompute_weights == 2) {
-            switch (g->wdtype) {
-                case PG_W_F32: st = adjoint_scatter_k<float>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s); break;
-                case PG_W_BF16:
-                    st = adjoint_scatter_k<__nv_bfloat16>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s);
-                    break;
-                case PG_W_F16: st = adjoint_scatter_k<__half>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s); break;
-            }
+            st = pg_dispatch_w(g->wdtype, [&](auto tag) {
+                return adjoint_scatter_k<typename decltype(tag)::type>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s);
+            });
         } else if (recompute_weights) {
             switch (g->kp) {
                 case 4: st = adjoint_recompute<4>(g, nu, mu_a, mu_b, G, B, muhist, s); break;
@@ -884,38 +823,21 @@ extern "C" pg_status pg_propagate_adjoint(pg_graph *g, const float *dI, const in
                 default: st = PG_ERR_UNSUPPORTED;
             }
         } else {
-            switch (g->wdtype) {
-                case PG_W_F32: st = adjoint_store<float>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s); break;
-                case PG_W_BF16:
-                    st = adjoint_store<__nv_bfloat16>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s);
-                    break;
-                case PG_W_F16: st = adjoint_store<__half>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s); break;
-            }
+            st = pg_dispatch_w(g->wdtype, [&](auto tag) {
+                return adjoint_store<typename decltype(tag)::type>(g, us0, mu_a, mu_b, us_a, us_b, G, B, muhist, s);
+            });
         }
         // output term of the first-vertex rows from the stored weights
         if (st == PG_OK && recompute_weights != 1 && n_paths > 0) {
             const float *rs = g->wdtype == PG_W_F32 ? nullptr : g->rscale;
             const float *yT = g->hist + (int64_t)g->hist_iters * (n + 1);
-            switch (g->wdtype) {
-                case PG_W_F32:
-                    first_rows_kernel<float><<<pg_blocks(n_paths, 256), 256, 0, s>>>(
-                        first, n_paths, n, g->c2m, g->m2r, g->col, (const float *)g->W, rs, yT, g->LV, g->D_m, nu,
-                        g->kp, G);
-                    pg_count_launches(1);
-                    break;
-                case PG_W_BF16:
-                    first_rows_kernel<__nv_bfloat16><<<pg_blocks(n_paths, 256), 256, 0, s>>>(
-                        first, n_paths, n, g->c2m, g->m2r, g->col, (const __nv_bfloat16 *)g->W, rs, yT, g->LV,
-                        g->D_m, nu, g->kp, G);
-                    pg_count_launches(1);
-                    break;
-                case PG_W_F16:
-                    first_rows_kernel<__half><<<pg_blocks(n_paths, 256), 256, 0, s>>>(
-                        first, n_paths, n, g->c2m, g->m2r, g->col, (const __half *)g->W, rs, yT, g->LV, g->D_m, nu,
-                        g->kp, G);
-                    pg_count_launches(1);
-                    break;
-            }
+            st = pg_dispatch_w(g->wdtype, [&](auto tag) {
+                using WT = typename decltype(tag)::type;
+                first_rows_kernel<WT><<<pg_blocks(n_paths, 256), 256, 0, s>>>(
+                    first, n_paths, n, g->c2m, g->m2r, g->col, (const WT *)g->W, rs, yT, g->LV, g->D_m, nu, g->kp, G);
+                pg_count_launches(1);
+                return PG_OK;
+            });
             if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
         }
     }

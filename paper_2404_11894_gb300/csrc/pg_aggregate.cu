@@ -111,23 +111,6 @@ __global__ void row_order_kernel(const int32_t *__restrict__ predcnt, const int3
     r2m[r] = (int32_t)m;
 }
 
-template <typename WT>
-__device__ __forceinline__ WT to_w(float x);
-template <>
-__device__ __forceinline__ float to_w<float>(float x) { return x; }
-template <>
-__device__ __forceinline__ __nv_bfloat16 to_w<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
-template <>
-__device__ __forceinline__ __half to_w<__half>(float x) { return __float2half_rn(x); }
-template <typename WT>
-__device__ __forceinline__ float from_w(WT x);
-template <>
-__device__ __forceinline__ float from_w<float>(float x) { return x; }
-template <>
-__device__ __forceinline__ float from_w<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
-template <>
-__device__ __forceinline__ float from_w<__half>(__half x) { return __half2float(x); }
-
 // Pass 1: the marginal densities of every sample over the rows that use it
 // (Eq. indirect-weight read on a neighbour graph: sample j is combined by the
 // strategies of R(j) = {r : j in N(r)}, so pm_d[j] = sum_{r in R(j)}
@@ -224,17 +207,18 @@ __global__ void __launch_bounds__(256) aggregate_kernel(
         }
         const float Wt = w_s * A;
         const int32_t r = row_ok ? m2r[m] : 0;
-        float scale = 1.0f;
+        float mx = 1.0f;
         if (WTraits<WT>::id != PG_W_F32) {
-            float mx = Wt;
+            mx = Wt;
     #pragma unroll
             for (int o = KP / 2; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            scale = mx > 0.0f ? mx : 1.0f;
+            mx = mx > 0.0f ? mx : 1.0f;
         }
         // 16-bit payload: the row's weights relative to its largest one, rounded
         // to nearest (error diffusion along the row was measured to be worse:
         // the gathered radiance of a row's columns is far from uniform)
-        const WT wq = to_w<WT>(WTraits<WT>::id == PG_W_F32 ? Wt : Wt / scale);
+        const WT wq = WTraits<WT>::enc(Wt, mx);
+        const float scale = WTraits<WT>::scale(mx);
         if (row_ok) {
             W[(int64_t)r * KP + j] = wq;
             col[(int64_t)r * KP + j] = cl;
@@ -312,7 +296,8 @@ static bool verts_ok(const pg_vertices *v) {
 extern "C" pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype wdtype, float *c, float *D,
                                   pg_stream_t stream) {
     if (!g) return PG_ERR_INVALID_ARG;
-    if (wdtype != PG_W_F32 && wdtype != PG_W_BF16 && wdtype != PG_W_F16) return PG_ERR_INVALID_ARG;
+    if (wdtype != PG_W_F32 && wdtype != PG_W_BF16 && wdtype != PG_W_F16 && wdtype != PG_W_U16)
+        return PG_ERR_INVALID_ARG;
     if (g->n > 0 && (!v || !verts_ok(v))) return PG_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     g->stream = s;
@@ -405,6 +390,7 @@ extern "C" pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype w
             case PG_W_F32: st = launch_agg_k<float>(g, c, D, d_cnt, s); break;
             case PG_W_BF16: st = launch_agg_k<__nv_bfloat16>(g, c, D, d_cnt, s); break;
             case PG_W_F16: st = launch_agg_k<__half>(g, c, D, d_cnt, s); break;
+            case PG_W_U16: st = launch_agg_k<pg_unorm16>(g, c, D, d_cnt, s); break;
         }
     }
     unsigned long long h_cnt = 0;

@@ -222,20 +222,111 @@ __device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) 
     return part1by2(x) | (part1by2(y) << 1) | (part1by2(z) << 2);
 }
 
+// ------------------------------------------------------------------ edge-weight storage
+// The sweep matrix stores W~ = (tau/p_t)_s A+_{s,j} as FP32, or per row as an
+// FP32 scale times a 16-bit payload: BF16 and FP16 hold each weight relative
+// to the row's largest one (payload w / max, scale max); U16 holds it as
+// 16-bit unsigned fixed point, q = round(65535 w / max), scale max / 65535
+// (the weights are non-negative and the scale carries the range, so all 16
+// bits resolve the weight: absolute error at most max / 131070). Every
+// reader forms weight = dec(payload) * scale.
+struct pg_unorm16 {
+    uint16_t q;
+};
+
+// exact float value of a 16-bit unsigned field of x: its bits placed in the
+// mantissa of 2^23 (one byte permute), minus 2^23
+__device__ __forceinline__ float u16_lo(uint32_t x) {
+    return __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7410)) - 8388608.0f;
+}
+__device__ __forceinline__ float u16_hi(uint32_t x) {
+    return __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7432)) - 8388608.0f;
+}
+
 template <typename T>
 struct WTraits;
 template <>
 struct WTraits<float> {
     static constexpr pg_wdtype id = PG_W_F32;
+    __device__ static float enc(float w, float) { return w; }
+    __device__ static float scale(float) { return 1.0f; }
+    __device__ static float dec(float w) { return w; }
+    __device__ static int32_t bits(float w) { return __float_as_int(w); }
+    __device__ static float from_bits(int32_t b) { return __int_as_float(b); }
+    // four consecutive weights, streamed (evict-first)
+    __device__ static float4 load4(const float *p) { return __ldcs(reinterpret_cast<const float4 *>(p)); }
+    // the same as raw bits, decoded later (fewer registers held across the gathers)
+    using raw4 = float4;
+    __device__ static raw4 load4_raw(const float *p) { return load4(p); }
+    __device__ static float4 dec4(raw4 r) { return r; }
 };
 template <>
 struct WTraits<__nv_bfloat16> {
     static constexpr pg_wdtype id = PG_W_BF16;
+    __device__ static __nv_bfloat16 enc(float w, float mx) { return __float2bfloat16_rn(w / mx); }
+    __device__ static float scale(float mx) { return mx; }
+    __device__ static float dec(__nv_bfloat16 w) { return __bfloat162float(w); }
+    __device__ static int32_t bits(__nv_bfloat16 w) { return (int32_t)__bfloat16_as_ushort(w); }
+    __device__ static float from_bits(int32_t b) { return __bfloat162float(__ushort_as_bfloat16((unsigned short)b)); }
+    __device__ static float4 load4(const __nv_bfloat16 *p) { return dec4(load4_raw(p)); }
+    using raw4 = uint2;
+    __device__ static raw4 load4_raw(const __nv_bfloat16 *p) { return __ldcs(reinterpret_cast<const uint2 *>(p)); }
+    __device__ static float4 dec4(uint2 u) {
+        float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&u.x));
+        float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
 };
 template <>
 struct WTraits<__half> {
     static constexpr pg_wdtype id = PG_W_F16;
+    __device__ static __half enc(float w, float mx) { return __float2half_rn(w / mx); }
+    __device__ static float scale(float mx) { return mx; }
+    __device__ static float dec(__half w) { return __half2float(w); }
+    __device__ static int32_t bits(__half w) { return (int32_t)__half_as_ushort(w); }
+    __device__ static float from_bits(int32_t b) { return __half2float(__ushort_as_half((unsigned short)b)); }
+    __device__ static float4 load4(const __half *p) { return dec4(load4_raw(p)); }
+    using raw4 = uint2;
+    __device__ static raw4 load4_raw(const __half *p) { return __ldcs(reinterpret_cast<const uint2 *>(p)); }
+    __device__ static float4 dec4(uint2 u) {
+        float2 a = __half22float2(*reinterpret_cast<__half2 *>(&u.x));
+        float2 b = __half22float2(*reinterpret_cast<__half2 *>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
 };
+template <>
+struct WTraits<pg_unorm16> {
+    static constexpr pg_wdtype id = PG_W_U16;
+    __device__ static pg_unorm16 enc(float w, float mx) {
+        pg_unorm16 r;
+        r.q = (uint16_t)__float2uint_rn(fminf(w / mx, 1.0f) * 65535.0f);
+        return r;
+    }
+    __device__ static float scale(float mx) { return mx / 65535.0f; }
+    __device__ static float dec(pg_unorm16 w) { return u16_lo(w.q); }
+    __device__ static int32_t bits(pg_unorm16 w) { return (int32_t)w.q; }
+    __device__ static float from_bits(int32_t b) { return u16_lo((uint32_t)b); }
+    __device__ static float4 load4(const pg_unorm16 *p) { return dec4(load4_raw(p)); }
+    using raw4 = uint2;
+    __device__ static raw4 load4_raw(const pg_unorm16 *p) { return __ldcs(reinterpret_cast<const uint2 *>(p)); }
+    __device__ static float4 dec4(uint2 u) { return make_float4(u16_lo(u.x), u16_hi(u.x), u16_lo(u.y), u16_hi(u.y)); }
+};
+
+template <typename T>
+struct pg_type_tag {
+    using type = T;
+};
+// f(pg_type_tag<WT>{}) for the storage type of weight format t
+template <typename F>
+static pg_status pg_dispatch_w(pg_wdtype t, F &&f) {
+    switch (t) {
+        case PG_W_F32: return f(pg_type_tag<float>{});
+        case PG_W_BF16: return f(pg_type_tag<__nv_bfloat16>{});
+        case PG_W_F16: return f(pg_type_tag<__half>{});
+        case PG_W_U16: return f(pg_type_tag<pg_unorm16>{});
+    }
+    return PG_ERR_UNSUPPORTED;
+}
 
 // Sample marginals are summed as unsigned 64-bit fixed point with 34
 // fraction bits: integer additions are exact, so the sums (and every weight
@@ -269,3 +360,9 @@ void pg_free_transposes(pg_graph *g); // releases both transposes (weights chang
 // tiles (a window of the Morton order at a time) rather than in chunks
 bool pg_sweep_front(int64_t n_active);
 pg_status pg_launch_aggregate(pg_graph *g, float *c_out, float *D_out, cudaStream_t s);
+// one propagation sweep over the rows [0, view->n_active) of a graph view:
+// yout[r] = sum_i W[r][i] yin[col[r][i]] (* rscale[r]) + b[r]
+pg_status pg_launch_sweep(const pg_graph *view, const float *b, const float *yin, float *yout, int32_t *ctrl,
+                          double2 *partials, double *resid, int t, double tol, cudaStream_t s);
+// grid size of one sweep launch (residual partials needed per sweep)
+int pg_sweep_blocks(const pg_graph *g);

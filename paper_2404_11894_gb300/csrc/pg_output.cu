@@ -9,15 +9,6 @@
 
 #include "pg_internal.cuh"
 
-template <typename WT>
-__device__ __forceinline__ float wdec(const WT *W, int64_t i);
-template <>
-__device__ __forceinline__ float wdec<float>(const float *W, int64_t i) { return W[i]; }
-template <>
-__device__ __forceinline__ float wdec<__nv_bfloat16>(const __nv_bfloat16 *W, int64_t i) { return __bfloat162float(W[i]); }
-template <>
-__device__ __forceinline__ float wdec<__half>(const __half *W, int64_t i) { return __half2float(W[i]); }
-
 // ------------------------------------------------------------------ gather over N(f)
 // One thread per pixel; its spp paths in order. Row f of the propagation
 // matrix already holds (tau/p_t)_f A+_{f,j}.
@@ -43,7 +34,7 @@ __global__ void gather_kernel(const int32_t *__restrict__ first, const float *__
             float sum = 0.0f;
             for (int i = 0; i < kp; i++) {
                 int32_t j = nbr[(int64_t)m * kp + i];
-                if (j >= 0) sum = fmaf(wdec<WT>(W, r * kp + i), L[m2c[j]], sum);
+                if (j >= 0) sum = fmaf(WTraits<WT>::dec(W[r * kp + i]), L[m2c[j]], sum);
             }
             val += fmaf(sum, sc, LV[m].w * (Dp ? Dp[p] : D[f]));
         }
@@ -281,6 +272,7 @@ extern "C" pg_status pg_gather_ex(const pg_graph *g, const float *L, const float
             case PG_W_F32: launch_gather<float>(g, L, D, Dp, first, bg, spp, npix, image, s); break;
             case PG_W_BF16: launch_gather<__nv_bfloat16>(g, L, D, Dp, first, bg, spp, npix, image, s); break;
             case PG_W_F16: launch_gather<__half>(g, L, D, Dp, first, bg, spp, npix, image, s); break;
+            case PG_W_U16: launch_gather<pg_unorm16>(g, L, D, Dp, first, bg, spp, npix, image, s); break;
         }
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     }

@@ -11,25 +11,29 @@ class Solver:
     """Runs the path-graph hot path on device-resident records.
 
     k: neighbours per vertex (self included); iters: propagation sweeps;
-    wdtype: 'f32' | 'bf16' | 'f16' edge weights; adjoint: also run
+    wdtype: 'f32' | 'bf16' | 'f16' | 'u16' edge weights; adjoint: also run
     pg_propagate_adjoint for the loss 1/2 |image - target|^2;
     cluster_size: 0 for kNN neighbourhoods, K > 0 for the paper's disjoint
-    clusters of expected size K (parts of at most k points).
+    clusters of expected size K (parts of at most k points); n_vox > 0: the
+    adjoint also forms the per-voxel albedo gradient (step() then takes the
+    vertices' voxel ids and sigma_t).
     """
 
     def __init__(self, k: int, iters: int, wdtype: str = "f32", adjoint: bool = True,
                  bbox_lo=(0.0, 0.0, 0.0), bbox_hi=(1.0, 1.0, 1.0), recompute_weights: int = 0,
-                 want_g: bool = True, cluster_size: int = 0, cluster_seed: int = 0):
+                 want_g: bool = True, cluster_size: int = 0, cluster_seed: int = 0, n_vox: int = 0):
         self.k, self.iters, self.wdtype, self.adjoint = k, iters, wdtype, adjoint
         self.cluster_size, self.cluster_seed = cluster_size, cluster_seed
         self.bbox_lo, self.bbox_hi = bbox_lo, bbox_hi
         self.recompute_weights = int(recompute_weights)
         self.want_g = want_g
+        self.n_vox = int(n_vox)
         self.graph = None
         self.last_image = None
         self.grads = None
 
-    def step(self, V: Vertices, L0, first, bg, spp, width, height, target=None, marks=None, ready=None):
+    def step(self, V: Vertices, L0, first, bg, spp, width, height, target=None, marks=None, ready=None,
+             voxel=None, sigma_t=None):
         """One pass; ``marks`` maps stage names to (start, end) CUDA events.
         ``ready``: a CUDA event the stream waits for after the graph build
         (the build reads only positions; everything else may still be in
@@ -61,7 +65,10 @@ class Solver:
         if use_adj:
             mark("adjoint", 0)
             dI = img - target
+            vox = voxel if self.n_vox > 0 else None
             self.grads = pg_propagate_adjoint(self.graph, dI, first, spp, width, height, want_g=self.want_g,
+                                              voxel=vox, sigma_t=sigma_t if vox is not None else None,
+                                              n_vox=self.n_vox if vox is not None else 0,
                                               recompute_weights=self.recompute_weights)
             mark("adjoint", 1)
         return img
@@ -135,8 +142,9 @@ class Solver:
                 t.record_stream(main)
         if tgt is not None:
             tgt.record_stream(main)
-        V = Vertices({k: dev[k] for k in dev if k not in ("L0", "first", "bg")})
-        img = self.step(V, dev["L0"], dev["first"], dev["bg"], spp, width, height, tgt, ready=ready)
+        V = Vertices({k: dev[k] for k in dev if k not in ("L0", "first", "bg", "voxel")})
+        img = self.step(V, dev["L0"], dev["first"], dev["bg"], spp, width, height, tgt, ready=ready,
+                        voxel=dev.get("voxel"), sigma_t=dev.get("sigma_t"))
         return img.to("cpu")
 
     def close(self):

@@ -257,7 +257,7 @@ def test_image_against_stored_oracle(full, golden):
     np.testing.assert_allclose(full.res, golden["residuals"], rtol=1e-3, atol=1e-7)
 
 
-@pytest.mark.parametrize("wdtype", ["f16", "bf16"])
+@pytest.mark.parametrize("wdtype", ["u16", "f16", "bf16"])
 def test_16bit_crop_against_stored_oracle(pg, full, golden, wdtype):
     """Per-pixel relative error of the 64 x 64 crop against the FP64 oracle."""
     _, _, _, img = _forward(pg, full, wdtype=wdtype, history=False)

@@ -2,13 +2,17 @@
 256^3 fBm medium (sigma_t max 60, albedo 0.999, HG g = 0.9), area light plus
 environment, 1024 x 1024 pixels, 8 spp, depth 256 -> 158.7 M vertices and
 2.3e9 swept entries (past 2^31, so every 64-bit index path is exercised);
-k = 16, BF16 weights, 50 sweeps, forward plus adjoint.
+k = 16, 16-bit weights (U16, the 16-bit format that meets 2e-3 per pixel at
+albedo 0.999), 50 sweeps, forward plus adjoint.
 
 The FP64 oracle checks, one by one: kNN rows by brute force, the direct terms
-of sampled rows, and one BF16 sweep of sampled rows, held to the rounding
-bound of their 16-bit weights. Properties: the residuals fall, and the
-reverse sweep from the stored transpose equals the atomic scatter of the
-stored rows.
+of sampled rows, and one U16 sweep of sampled rows, held to the rounding
+bound of their 16-bit weights. Against the FP64 oracle's full-size image
+(tests/golden/dense256_oracle_image.txt, the central 64 x 64 crop and every
+32nd pixel, written by make_dense256_reference.py from oracle/ only): U16
+and FP16 within 2e-3 per pixel; BF16's error is reported. Properties: the
+residuals fall, and the reverse sweep from the stored transpose equals the
+atomic scatter of the stored rows.
 """
 import numpy as np
 import pytest
@@ -42,7 +46,7 @@ def big():
     r.bg = torch.from_numpy(r.rec["bg"]).cuda()
     r.graph = pg.pg_build_graph(r.V, SC.k)
     r.nbr = r.graph.neighbors().cpu().numpy()
-    c, D = pg.pg_aggregate(r.graph, r.V, "bf16")
+    c, D = pg.pg_aggregate(r.graph, r.V, "u16")
     r.c, r.D = c.cpu().numpy(), D.cpu().numpy()
     r.Lp = pg.pg_propagate(r.graph, r.L0, SC.iters - 1).cpu().numpy()
     L, res, done = pg.pg_propagate(r.graph, r.L0, SC.iters, keep_history=True, want_residual=True)
@@ -74,12 +78,12 @@ def test_knn_rows_bruteforce(big):
         assert np.array_equal(big.nbr[s, 1:], cand), s
 
 
-def test_direct_terms_and_bf16_sweep_rows(big):
+def test_direct_terms_and_u16_sweep_rows(big):
     """Sampled rows s = succ(v): c_s and D_s within 1e-5 (they hold no 16-bit
     weight), and L_T[v] = w_s (sum_j W~_{s,j} L_{T-1}[j] / w_s + c_s) within
-    the bound of the row's BF16 payload: each weight is rounded to nearest on
-    8 significant bits relative to the row's largest, so it moves by at most
-    2^-9 of that largest weight."""
+    the bound of the row's U16 payload: each weight is rounded to nearest
+    on a 16-bit fixed-point grid of the row's largest weight, so it moves by
+    at most 1/131070 of that weight (plus float32 rounding of the scale)."""
     succ = big.rec["succ"].astype(np.int64)
     rows = np.concatenate([big.S, succ[big.S]])
     ref = oracle.aggregate(big.rec, big.nbr, rows=rows)
@@ -96,7 +100,7 @@ def test_direct_terms_and_bf16_sweep_rows(big):
     Lj = np.where(nb >= 0, big.Lp.astype(np.float64)[np.where(nb >= 0, nb, 0)], 0.0)
     Wt = w[:, None] * A
     expect = (Wt * Lj).sum(axis=1) + w * ref["c"][m:]
-    bound = 2.0 ** -9 * Wt.max(axis=1) * np.abs(Lj).sum(axis=1) + FP32_TOL * np.abs(expect) + 1e-30
+    bound = (1.0 / 131070 + 2.0 ** -22) * Wt.max(axis=1) * np.abs(Lj).sum(axis=1) + FP32_TOL * np.abs(expect) + 1e-30
     assert np.all(np.abs(big.L[big.S].astype(np.float64) - expect) <= bound)
 
 
@@ -124,6 +128,57 @@ def test_adjoint_modes_agree(big):
         grads.append(out["grad_sigma_s"].cpu().numpy().astype(np.float64))
     fl = 1e-3 * np.abs(grads[0]).max()
     assert (np.abs(grads[1] - grads[0]) / np.maximum(np.abs(grads[0]), fl)).max() <= 1e-4
+
+
+def _dense_golden(big):
+    import os
+    import sys
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "dense256_oracle_image.txt")
+    if not os.path.exists(path):
+        pytest.skip("no stored FP64 oracle image of the dense workload")
+    sys.path.insert(0, os.path.dirname(path))
+    import make_dense256_reference as mod
+
+    g = mod.load()
+    if g["trace_sha256"] != mod.trace_checksum(big.rec):
+        pytest.fail("the recorder's output differs from the one the stored oracle image was written from")
+    return g
+
+
+def _dense_image_error(img, g):
+    y0, x0, crop = g["crop"]
+    s_ = crop.shape[0]
+    st, strided = g["stride"]
+    floor = 1e-3 * np.abs(strided).mean()
+    e1 = np.abs(img[y0:y0 + s_, x0:x0 + s_] - crop) / np.maximum(np.abs(crop), floor)
+    e2 = np.abs(img[::st, ::st] - strided) / np.maximum(np.abs(strided), floor)
+    return max(e1.max(), e2.max()), np.concatenate([e1.ravel(), e2.ravel()]).mean()
+
+
+def test_u16_image_against_stored_oracle(big):
+    """The 16-bit (U16) image of the full-size dense workload against the FP64
+    oracle's, per pixel within 2e-3 on the crop and the strided grid."""
+    g = _dense_golden(big)
+    e_max, e_mean = _dense_image_error(big.img.cpu().numpy().astype(np.float64), g)
+    print(f"\nu16 image vs FP64 oracle: max {e_max:.3e} mean {e_mean:.3e}")
+    assert e_max <= 2e-3
+
+
+@pytest.mark.parametrize("wdtype", ["f16", "bf16"])
+def test_other_16bit_images_against_stored_oracle(big, wdtype):
+    """FP16 within 2e-3 per pixel; BF16's error is measured and reported (its
+    8-bit significand does not meet the bar at albedo 0.999)."""
+    g = _dense_golden(big)
+    pg = big.pg
+    _, D = pg.pg_aggregate(big.graph, big.V, wdtype)
+    L = pg.pg_propagate(big.graph, big.L0, SC.iters)
+    img = pg.pg_gather(big.graph, L, D, big.first, big.bg, SC.spp, SC.width, SC.height)
+    e_max, e_mean = _dense_image_error(img.cpu().numpy().astype(np.float64), g)
+    print(f"\n{wdtype} image vs FP64 oracle: max {e_max:.3e} mean {e_mean:.3e}")
+    if wdtype == "f16":
+        assert e_max <= 2e-3
+    del L, img
 
 
 def test_fp32_sweep_rows(big):

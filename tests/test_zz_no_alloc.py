@@ -60,3 +60,38 @@ def test_noalloc_matches_pg_propagate(wdtype):
     big = lib.pg_propagate_noalloc(graph.handle, ctypes.c_void_p(L0.data_ptr()), 4097, 0.0,
                                    ctypes.c_void_p(ref.data_ptr()), stream)
     assert big == 6  # PG_ERR_UNSUPPORTED
+
+
+def test_noalloc_early_stop_and_graph_change():
+    """The array keeps whatever the last call left: a call with a stopping
+    tolerance (which raises the device's stop flag) followed by calls without
+    one, and a smaller graph after a larger one, must each still equal
+    pg_propagate on the same graph and arguments."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2404_11894_gb300 as pg
+    from paper_2404_11894_gb300 import _lib
+
+    lib = _lib.load()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    graphs = []
+    for size in (64, 32):  # the larger graph first
+        sc = pgrec.CLOUD128.with_(width=size, height=size, spp=4)
+        rec = pgrec.trace(sc)
+        V = pg.Vertices.from_records(rec)
+        graph = pg.pg_build_graph(V, sc.k)
+        pg.pg_aggregate(graph, V, "f32")
+        graphs.append((sc, graph, torch.from_numpy(rec["L0"]).cuda()))
+    for sc, graph, L0 in graphs:
+        for tol in (0.05, 0.0, 0.05):
+            ref, _, done = pg.pg_propagate(graph, L0, sc.iters, tol=tol, want_residual=True)
+            if tol > 0:
+                assert done < sc.iters  # the stop flag was raised on the device
+            out = torch.full_like(ref, float("nan"))
+            st = lib.pg_propagate_noalloc(graph.handle, ctypes.c_void_p(L0.data_ptr()), sc.iters, tol,
+                                          ctypes.c_void_p(out.data_ptr()), stream)
+            assert st == 0, lib.pg_status_string(st)
+            torch.cuda.synchronize()
+            o = out.cpu().numpy()
+            assert np.isfinite(o).all()
+            assert rel_err(o, ref.cpu().numpy()) <= FP32_TOL, (sc.width, tol)
