@@ -6,38 +6,12 @@
 // evict-first so the gathered vector y stays in L2); KP/4 lanes share a row
 // and combine their four products with shuffles. The relative change of the
 // sweep is reduced in FP64 (per-block partials, then the last block), and a
-// sweep that finds the previous one converged returns at once. The squared
-// change and norm are accumulated in FP64 in every thread (the difference of
-// two float iterates is exact in double), then across the grid.
+// sweep that finds the previous one converged returns at once. Each thread
+// accumulates its squared changes and norms with a compensated float sum.
 #include <algorithm>
 #include <mutex>
 
 #include "pg_internal.cuh"
-
-template <typename WT>
-struct W4;
-template <>
-struct W4<float> {
-    static __device__ __forceinline__ float4 load(const float *p) { return __ldcs(reinterpret_cast<const float4 *>(p)); }
-};
-template <>
-struct W4<__nv_bfloat16> {
-    static __device__ __forceinline__ float4 load(const __nv_bfloat16 *p) {
-        uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
-        __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162 *>(&u.x), b = *reinterpret_cast<__nv_bfloat162 *>(&u.y);
-        float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-        return make_float4(fa.x, fa.y, fb.x, fb.y);
-    }
-};
-template <>
-struct W4<__half> {
-    static __device__ __forceinline__ float4 load(const __half *p) {
-        uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
-        __half2 a = *reinterpret_cast<__half2 *>(&u.x), b = *reinterpret_cast<__half2 *>(&u.y);
-        float2 fa = __half22float2(a), fb = __half22float2(b);
-        return make_float4(fa.x, fa.y, fb.x, fb.y);
-    }
-};
 
 static constexpr int SWEEP_THREADS = 256;
 
@@ -99,6 +73,23 @@ __device__ __forceinline__ void sweep_residual(double rd, double rn, int32_t *ct
     }
 }
 
+// A thread's share of the residual's sums of squares: float32 with a
+// compensation term (TwoSum), so its relative error stays near 2^-23
+// whatever the number of rows the thread sweeps (the terms are squares, so
+// nothing cancels); the grid then sums the threads' shares in FP64.
+// Per-thread FP64 accumulation measured 205 -> 312 us per FP32 sweep on
+// this GPU's FP64 rate, for no accuracy a convergence test can use.
+struct csum {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        float s, e;
+        two_sum(hi, x, s, e);
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // Compensated sum of one row's products, four per lane, then over the row's
 // LPR lanes (the kernel is memory-bound, so the extra additions are free;
 // they keep 30+ sweeps at albedo ~1 within float32 rounding of the exact
@@ -153,22 +144,34 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(
         const int64_t tile = k / TILE_GROUPS;
         return (tile * gridDim.x + blockIdx.x) * (STEP * TILE_GROUPS) + (k - tile * TILE_GROUPS) * STEP;
     };
-    double rd = 0.0, rn = 0.0;
+    csum rd, rn;
+    // with four or more lanes per row its scalars (b, the previous iterate,
+    // the 16-bit row scale) travel with the streamed loads, one per lane,
+    // and reach the row's first lane by shuffles after the gathers
+    constexpr bool PRE = LPR >= 4;
+    const int lead = lane & ~(LPR - 1);
     auto group = [&](int64_t base) { // uniform across the block
         int32_t row[U]; // row indices fit in 32 bits (n < 2^31); 64-bit only in element offsets
         bool ok[U];
         int4 c4[U];
-        float4 w4[U];
+        typename WTraits<WT>::raw4 w4[U];
+        float sv[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
             row[u] = (int32_t)(base + u * RPB + threadIdx.x / LPR);
             ok[u] = row[u] < r1;
+            sv[u] = 0.0f;
             if (ok[u]) {
                 c4[u] = __ldcs(reinterpret_cast<const int4 *>(col + (int64_t)row[u] * KP) + q);
-                w4[u] = W4<WT>::load(W + (int64_t)row[u] * KP + q * 4);
+                w4[u] = WTraits<WT>::load4_raw(W + (int64_t)row[u] * KP + q * 4);
+                if (PRE) {
+                    if (q == 0) sv[u] = __ldcs(b + row[u]);
+                    else if (q == 1) sv[u] = yin[row[u]];
+                    else if (W16 && q == 2) sv[u] = __ldcs(rscale + row[u]);
+                }
             } else {
                 c4[u] = make_int4(0, 0, 0, 0);
-                w4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                w4[u] = {};
             }
         }
         float g[U][4];
@@ -181,15 +184,23 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(
         }
 #pragma unroll
         for (int u = 0; u < U; u++) {
-            const float acc = row_dot<LPR>(w4[u], g[u][0], g[u][1], g[u][2], g[u][3]);
+            const float acc = row_dot<LPR>(WTraits<WT>::dec4(w4[u]), g[u][0], g[u][1], g[u][2], g[u][3]);
+            float yo = 0.0f, sc = 1.0f, bb = sv[u];
+            if (PRE) {
+                yo = __shfl_sync(0xffffffffu, sv[u], lead + 1);
+                if (W16) sc = __shfl_sync(0xffffffffu, sv[u], lead + 2);
+            }
             if (ok[u] && q == 0) {
-                const float sc = W16 ? rscale[row[u]] : 1.0f;
-                const float yn = fmaf(acc, sc, b[row[u]]);
+                if (!PRE) {
+                    sc = W16 ? rscale[row[u]] : 1.0f;
+                    bb = b[row[u]];
+                    yo = yin[row[u]];
+                }
+                const float yn = fmaf(acc, sc, bb);
                 yout[row[u]] = yn;
-                // the residual's sums in FP64 from the first term on
-                const double d = (double)yn - (double)yin[row[u]];
-                rd = fma(d, d, rd);
-                rn = fma((double)yn, (double)yn, rn);
+                const float d = yn - yo;
+                rd.add(d * d);
+                rn.add(yn * yn);
             }
         }
     };
@@ -198,7 +209,7 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(
     } else {
         for (int64_t base = r0; base < r1; base += STEP) group(base); // uniform across the block
     }
-    sweep_residual<NT>(rd, rn, ctrl, partials, resid, t, tol);
+    sweep_residual<NT>(rd.value(), rn.value(), ctrl, partials, resid, t, tol);
 }
 
 // The same sweep, software-pipelined: one row group per iteration, with the
@@ -237,13 +248,13 @@ __global__ void __launch_bounds__(NT, MINB) sweep_pf_kernel(
         sv = 0.0f;
         if (row < r1) {
             c4 = __ldcs(reinterpret_cast<const int4 *>(col + row * KP) + q);
-            w4 = W4<WT>::load(W + row * KP + q * 4);
+            w4 = WTraits<WT>::load4(W + row * KP + q * 4);
             if (q == 0) sv = __ldcs(b + row);
             else if (q == 1) sv = yin[row];
             else if (W16 && q == 2) sv = __ldcs(rscale + row);
         }
     };
-    double rd = 0.0, rn = 0.0;
+    csum rd, rn;
     int4 c4n;
     float4 w4n;
     float svn;
@@ -263,14 +274,13 @@ __global__ void __launch_bounds__(NT, MINB) sweep_pf_kernel(
         if (row < r1 && q == 0) {
             const float yn = fmaf(acc, sc, sv);
             yout[row] = yn;
-            // the residual's sums in FP64 from the first term on
-            const double d = (double)yn - (double)yo;
-            rd = fma(d, d, rd);
-            rn = fma((double)yn, (double)yn, rn);
+            const float d = yn - yo;
+            rd.add(d * d);
+            rn.add(yn * yn);
         }
         base = nb;
     }
-    sweep_residual<NT>(rd, rn, ctrl, partials, resid, t, tol);
+    sweep_residual<NT>(rd.value(), rn.value(), ctrl, partials, resid, t, tol);
 }
 
 // The front schedule pays off once the gathered vector no longer fits in L2
@@ -386,8 +396,16 @@ static pg_status launch_sweep_w(const pg_graph *g, const float *b, const float *
         case PG_W_F32: return launch_sweep_k<float>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
         case PG_W_BF16: return launch_sweep_k<__nv_bfloat16>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
         case PG_W_F16: return launch_sweep_k<__half>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
+        case PG_W_U16: return launch_sweep_k<pg_unorm16>(g, b, yin, yout, ctrl, partials, resid, t, tol, s);
     }
     return PG_ERR_UNSUPPORTED;
+}
+
+// One sweep over the rows of a graph view (a shard's rows with its own
+// column table, see pg_shard.cu).
+pg_status pg_launch_sweep(const pg_graph *view, const float *b, const float *yin, float *yout, int32_t *ctrl,
+                          double2 *partials, double *resid, int t, double tol, cudaStream_t s) {
+    return launch_sweep_w(view, b, yin, yout, ctrl, partials, resid, t, tol, s);
 }
 
 int pg_sweep_blocks(const pg_graph *g) {
@@ -522,10 +540,12 @@ static pg_status noalloc_scratch(unsigned char **out) {
     std::lock_guard<std::mutex> lock(mu);
     if (!addr[dev]) {
         void *p = nullptr;
+        // with lazy module loading this is where the array is reserved on
+        // the device, so a device without room for it reports PG_ERR_OOM
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             (void)cudaGetLastError();
-            return PG_ERR_CUDA;
+            return e == cudaErrorMemoryAllocation ? PG_ERR_OOM : PG_ERR_CUDA;
         }
         addr[dev] = (unsigned char *)p;
     }
