@@ -149,7 +149,7 @@ def run_gpu(args):
         t = torch.from_numpy(np.ascontiguousarray(a))
         return t.pin_memory()
 
-    host = {k: pinned(rec[k]) for k in pg.VERTEX_F32 + ("e_delta", "succ", "L0", "first", "bg")}
+    host = {k: pinned(rec[k]) for k in pg.VERTEX_F32 + ("e_delta", "succ", "L0", "first", "bg", "voxel")}
     rng = np.random.default_rng(0)
     target = rec["pt_image"].astype(np.float32) * rng.uniform(0.9, 1.1, rec["pt_image"].shape).astype(np.float32)
     host_target = pinned(target)
@@ -158,12 +158,13 @@ def run_gpu(args):
     V = pg.Vertices({k: dev_in[k] for k in pg.VERTEX_F32 + ("e_delta", "succ")})
     solver = pg.Solver(k=sc.k, iters=sc.iters, wdtype=wdtype, adjoint=not args.no_adjoint,
                        cluster_size=args.clusters, cluster_seed=sc.seed,
-                       recompute_weights=args.adjoint_mode, want_g=False)
+                       recompute_weights=args.adjoint_mode, want_g=False, n_vox=sc.grid_res ** 3)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     def step(V, L0, first, bg, tgt, marks=None):
-        return solver.step(V, L0, first, bg, sc.spp, sc.width, sc.height, tgt, marks=marks)
+        return solver.step(V, L0, first, bg, sc.spp, sc.width, sc.height, tgt, marks=marks,
+                           voxel=dev_in["voxel"], sigma_t=dev_in["sigma_t"])
 
     for _ in range(args.warmup):
         step(V, dev_in["L0"], dev_in["first"], dev_in["bg"], dev_target)
@@ -247,11 +248,9 @@ def run_gpu(args):
     if not args.no_adjoint and not args.quick:
         e2, e3 = ev(), ev()
         solver.want_g = True
-        solver.step(V, dev_in["L0"], dev_in["first"], dev_in["bg"], sc.spp, sc.width, sc.height, dev_target)
+        step(V, dev_in["L0"], dev_in["first"], dev_in["bg"], dev_target)
         torch.cuda.synchronize()
-        marks = {"adjoint": (e2, e3)}
-        solver.step(V, dev_in["L0"], dev_in["first"], dev_in["bg"], sc.spp, sc.width, sc.height, dev_target,
-                    marks=marks)
+        step(V, dev_in["L0"], dev_in["first"], dev_in["bg"], dev_target, marks={"adjoint": (e2, e3)})
         torch.cuda.synchronize()
         adj_g_ms = e2.elapsed_time(e3)
         solver.want_g = False
@@ -260,7 +259,8 @@ def run_gpu(args):
     prec = {}
     if not args.quick and not w16:
         img32 = solver.last_image.clone()
-        for wd in ("bf16", "f16"):
+        gold = _golden("cloud128") if sc.name == pgrec.CLOUD128.name and args.scale == 1.0 else None
+        for wd in ("bf16", "f16", "u16"):
             s16 = pg.Solver(k=sc.k, iters=sc.iters, wdtype=wd, adjoint=False)
             s16.step(V, dev_in["L0"], dev_in["first"], dev_in["bg"], sc.spp, sc.width, sc.height, None)
             torch.cuda.synchronize()
@@ -275,6 +275,11 @@ def run_gpu(args):
                         "speedup_vs_f32": round(sweep_ms / sw, 3),
                         "max_rel_err_vs_f32": float(((a - b).abs() / den).max()),
                         "mean_rel_err_vs_f32": float(((a - b).abs() / den).mean())}
+            if gold is not None:
+                y0, x0, crop = gold["crop"]
+                e = _pixel_err(b.cpu().numpy()[y0:y0 + crop.shape[0], x0:x0 + crop.shape[1]], crop,
+                               1e-3 * np.abs(gold["stride"][1]).mean())
+                prec[wd]["crop_64x64_vs_fp64_oracle"] = {"max_rel_err": float(e.max()), "mean_rel_err": float(e.mean())}
             s16.close()
 
     # ---- output options on the step's graph and L (not part of the step):
@@ -389,12 +394,178 @@ def run_gpu(args):
         "clocks": clk,
     }
     solver.close()
+    if world == 1 and not args.quick and args.scale == 1.0 and not args.clusters and args.workload == "cloud128":
+        out["configs"] = bench_configs(pg, args, peak)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(rec, sc, args)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _time_config(pg, sc, wdtype, dev, target, steps, warmup, adjoint, n_vox=0, peak=6800.0):
+    """Times ``steps`` whole steps (graph, aggregation, sweeps, output, and
+    the adjoint when ``adjoint``) of one workload on device-resident records
+    ``dev``; returns the solver (holding the last step) and the record."""
+    import torch
+
+    solver = pg.Solver(k=sc.k, iters=sc.iters, wdtype=wdtype, adjoint=adjoint, want_g=False, n_vox=n_vox)
+    V = pg.Vertices({k: dev[k] for k in pg.VERTEX_F32 + ("e_delta", "succ")})
+    kw = dict(voxel=dev["voxel"], sigma_t=dev["sigma_t"]) if n_vox else {}
+
+    def step(marks=None):
+        return solver.step(V, dev["L0"], dev["first"], dev["bg"], sc.spp, sc.width, sc.height, target,
+                           marks=marks, **kw)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    names = ["build", "aggregate", "propagate", "gather"] + (["adjoint"] if adjoint else [])
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    s = torch.cuda.current_stream()
+    e0, e1 = ev(), ev()
+    allm = []
+    e0.record(s)
+    for _ in range(steps):
+        m = {nm: (ev(), ev()) for nm in names}
+        step(marks=m)
+        allm.append(m)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    stage = {nm: float(np.mean([m[nm][0].elapsed_time(m[nm][1]) for m in allm])) for nm in names}
+    info = solver.graph.info()
+    nnz, na, n = info["nnz_swept"], info["n_active"], info["n"]
+    base = solver.time_propagate(0, reps=3, keep_history=adjoint, from_idle=True)
+    sweep_ms = (stage["propagate"] - base) / sc.iters
+    w16 = wdtype != "f32"
+    nbytes = nnz * (4 + (2 if w16 else 4)) + na * (16 if w16 else 12)
+    sweeps = sc.iters * (2 if adjoint else 1)
+    rec = {"workload": sc.name, "weights": wdtype, "vertices": n, "n_active": na, "k": sc.k, "iters": sc.iters,
+           "nnz_per_sweep": nnz, "sweeps_per_step": sweeps, "steps": steps, "warmup": warmup,
+           "step": "build+aggregate+propagate+gather" + ("+adjoint" + ("(per-voxel albedo)" if n_vox else "")
+                                                         if adjoint else ""),
+           "ms_per_step": ms, "edge_updates_per_s": nnz * sweeps / (ms / 1e3), "stages_ms": stage,
+           "propagate_edge_updates_per_s": nnz / (sweep_ms / 1e3),
+           "sweep_roofline": {"bound": "hbm", "launch_ms": sweep_ms, "algorithmic_bytes_per_launch": nbytes,
+                              "achieved": nbytes / (sweep_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                              "frac": nbytes / (sweep_ms / 1e3) / 1e9 / peak},
+           "build_vertices_per_s": n / (stage["build"] / 1e3)}
+    return solver, rec
+
+
+def bench_configs(pg, args, peak):
+    """Every other workload of the method at 1 GPU, each on its own stored
+    FP64 oracle values: the plain-method cube (FP32), the differentiation
+    cloud (FP32, forward + adjoint with the per-voxel albedo gradient), and
+    the large dense medium (U16 weights, forward + adjoint, records from the
+    GPU recorder)."""
+    import torch
+
+    import pgrec
+
+    out = {}
+    dev = torch.device("cuda")
+    tens = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    fields = pg.VERTEX_F32 + ("e_delta", "succ", "L0", "first", "bg", "voxel")
+
+    # plain method: 32^3 constant cube, k = 8, 10 sweeps, FP32
+    sc = pgrec.CUBE_CONST
+    rec = pgrec.trace(sc)
+    d = {k: tens(rec[k]) for k in fields}
+    solver, r = _time_config(pg, sc, "f32", d, None, 20, 3, False, peak=peak)
+    g = _golden("cube32")
+    if g is not None:
+        e = _pixel_err(solver.last_image.cpu().numpy(), g["image"], 1e-3 * np.abs(g["image"]).mean())
+        r["image_vs_fp64_oracle"] = {"max_rel_err": float(e.max()), "mean_rel_err": float(e.mean()), "bar": 1e-5,
+                                     "pixels": int(e.size)}
+    solver.close()
+    out["cube32"] = r
+    del d
+
+    # differentiation: 64^3 cloud, forward + adjoint, L2 loss against a seeded target render
+    sc = pgrec.CLOUD64_GRAD
+    rec = pgrec.trace(sc)
+    d = {k: tens(rec[k]) for k in fields}
+    g = _golden("cloud64")
+    st = rec["sigma_t"].astype(np.float64)
+    offs = g["module"].target_albedo_offsets(sc.grid_res) if g is not None else np.zeros(sc.grid_res ** 3)
+    sig_t = tens(((sc.albedo + offs[rec["voxel"]]) * st).astype(np.float32))
+    tsolver = pg.Solver(k=sc.k, iters=sc.iters, adjoint=False)
+    Vt = pg.Vertices({**{k: d[k] for k in pg.VERTEX_F32 + ("e_delta", "succ")}, "sigma_s": sig_t})
+    target = tsolver.step(Vt, d["L0"], d["first"], d["bg"], sc.spp, sc.width, sc.height).clone()
+    tsolver.close()
+    solver, r = _time_config(pg, sc, "f32", d, target, 10, 3, True, n_vox=sc.grid_res ** 3, peak=peak)
+    if g is not None:
+        img = solver.last_image.cpu().numpy()
+        s_ = g["stride"]
+        e = _pixel_err(img[::s_, ::s_], g["image"], 1e-3 * np.abs(g["image"]).mean())
+        r["image_vs_fp64_oracle"] = {"max_rel_err": float(e.max()), "mean_rel_err": float(e.mean()), "bar": 1e-5,
+                                     "pixels": int(e.size)}
+        ga = solver.grads["grad_albedo"].cpu().numpy().astype(np.float64)[g["voxels"]]
+        ef = _pixel_err(ga, g["fd"], 1e-3 * np.abs(g["fd"]).max())
+        ea = _pixel_err(ga, g["adjoint"], 1e-3 * np.abs(g["adjoint"]).max())
+        r["albedo_gradient"] = {"voxels": int(len(ga)), "bar": 1e-3,
+                                "max_rel_err_vs_fp64_central_differences_h1e-3": float(ef.max()),
+                                "max_rel_err_vs_fp64_oracle_adjoint": float(ea.max())}
+    solver.close()
+    out["cloud64_grad"] = r
+    del d, target, sig_t
+
+    # large dense medium: records from the GPU recorder, U16 weights, forward + adjoint
+    sc = pgrec.CLOUD256_DENSE
+    dens, alb = (torch.from_numpy(a).to(dev) for a in pgrec.medium(sc))
+    d = pg.pg_record(sc, dens, alb)
+    torch.cuda.synchronize()
+    pt = d["pt_value"].view(sc.height, sc.width, sc.spp).mean(dim=2).float()
+    target = (0.9 * pt).contiguous()
+    del dens, alb
+    solver, r = _time_config(pg, sc, "u16", d, target, 3, 3, True, peak=peak)
+    r["records"] = "GPU path recorder (pg_record_count, pg_record_fill)"
+    g = _golden("dense256")
+    if g is not None:
+        img = solver.last_image.cpu().numpy().astype(np.float64)
+        y0, x0, crop = g["crop"]
+        st_, strided = g["stride"]
+        fl = 1e-3 * np.abs(strided).mean()
+        e = np.concatenate([_pixel_err(img[y0:y0 + crop.shape[0], x0:x0 + crop.shape[1]], crop, fl).ravel(),
+                            _pixel_err(img[::st_, ::st_], strided, fl).ravel()])
+        r["image_vs_fp64_oracle"] = {"max_rel_err": float(e.max()), "mean_rel_err": float(e.mean()), "bar": 2e-3,
+                                     "pixels": int(e.size), "pixels_sampled": "central 64x64 crop and every "
+                                     f"{st_}th pixel"}
+    solver.close()
+    out["dense256"] = r
+    del d, target
+    torch.cuda.empty_cache()
+    return out
+
+
+def _golden(name):
+    """Parsed stored FP64 oracle values for workload ``name`` (written by
+    tests/golden/make_<name>_reference.py), or None when absent."""
+    import importlib.util
+
+    d = os.path.join(ROOT, "tests", "golden")
+    path = os.path.join(d, f"make_{name}_reference.py")
+    spec = importlib.util.spec_from_file_location(f"golden_{name}", path)
+    mod = importlib.util.module_from_spec(spec)
+    sys.path.insert(0, d)
+    try:
+        spec.loader.exec_module(mod)
+        if not os.path.exists(mod.OUT):
+            return None
+        g = mod.load()
+    finally:
+        sys.path.remove(d)
+    g["module"] = mod
+    return g
+
+
+def _pixel_err(got, ref, floor):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return np.abs(got - ref) / np.maximum(np.abs(ref), floor)
 
 
 def _profile_traffic(kind, n):
@@ -418,11 +589,11 @@ def _profile_traffic(kind, n):
 
 
 # ----------------------------------------------------------------------------- oracle arm
-def oracle_sample(rec, sc, stride):
-    """Every `stride`-th pixel in x and y, all of its paths."""
+def oracle_sample(rec, sc, stride, offset=(0, 0)):
+    """Every `stride`-th pixel in x and y from pixel ``offset``, all of its paths."""
     import pgrec
 
-    sub = pgrec.sample_pixels(rec, sc.width, sc.height, sc.spp, stride)
+    sub = pgrec.sample_pixels(rec, sc.width, sc.height, sc.spp, stride, offset)
     return sub, sub["n_paths"]
 
 
@@ -449,14 +620,63 @@ def oracle_step(sub, sc, npix, adjoint=True):
     return t, nnz * sc.iters * (2 if adjoint else 1)
 
 
+def _oracle_worker(args):
+    """One host core: `reps` oracle steps of its own pixel sample."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    sub, sc_name, adjoint, reps = args
+    import pgrec
+
+    sc = pgrec.SCENES[sc_name]
+    out = []
+    for _ in range(reps):
+        out.append(oracle_step(sub, sc, sub["n_paths"] // sc.spp, adjoint=adjoint))
+    return out
+
+
+class OraclePool:
+    """The FP64 oracle on every host core: one spawned process per core, each
+    running whole oracle steps on its own disjoint sample of the workload
+    (every `stride`-th pixel in x and y from its own pixel offset)."""
+
+    def __init__(self, rec, sc, stride, adjoint, cores=None):
+        import multiprocessing as mp
+
+        self.sc, self.adjoint = sc, adjoint
+        self.cores = cores or os.cpu_count() or 1
+        offs = [(i // stride % stride, i % stride) for i in range(self.cores)]
+        self.subs = [oracle_sample(rec, sc, stride, o)[0] for o in offs]
+        self.stride = stride
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+
+    def step(self, reps=1):
+        """Wall time of `reps` steps on every core, and the edge updates done."""
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_worker, [(s, self.sc.name, self.adjoint, reps) for s in self.subs])
+        t = time.perf_counter() - t0
+        return t, sum(u for r in res for _, u in r)
+
+    def describe(self, total_paths):
+        paths = sum(s["n_paths"] for s in self.subs)
+        verts = sum(s["n"] for s in self.subs)
+        return (f"{self.cores} disjoint samples, one per host core, each every {self.stride}th pixel in x and y "
+                f"from its own offset: {paths} of {total_paths} paths ({verts} vertices) of {self.sc.name}; "
+                f"whole oracle step (kNN, aggregation, {self.sc.iters} sweeps, output"
+                f"{', adjoint' if self.adjoint else ''}) per sample")
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 def cpu_baseline(rec, sc, args):
-    sub, hi = oracle_sample(rec, sc, args.oracle_stride)
-    t, updates = oracle_step(sub, sc, hi // sc.spp, adjoint=not args.no_adjoint)
-    return {"value": updates / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"every {args.oracle_stride}th pixel in x and y: {hi} of {rec['n_paths']} paths "
-                      f"({sub['n']} vertices) of the same workload; whole oracle step (kNN, aggregation, "
-                      f"{sc.iters} sweeps, output{', adjoint' if not args.no_adjoint else ''}) in {t:.1f} s "
-                      f"on one host core"}
+    pool = OraclePool(rec, sc, args.oracle_stride, not args.no_adjoint)
+    try:
+        pool.step()  # warm-up: process start and imports
+        t, updates = pool.step()
+    finally:
+        pool.close()
+    return {"value": updates / t, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+            "sample": pool.describe(rec["n_paths"]) + f"; one step on all cores took {t:.1f} s"}
 
 
 def run_reference(args):
@@ -467,23 +687,25 @@ def run_reference(args):
         return
     sc = pgrec.CLOUD128
     rec = pgrec.trace(sc)
-    sub, hi = oracle_sample(rec, sc, args.oracle_stride)
-    for _ in range(args.warmup):
-        oracle_step(sub, sc, hi // sc.spp, adjoint=not args.no_adjoint)
-    ts, ups = [], 0
-    for _ in range(args.steps):
-        t, u = oracle_step(sub, sc, hi // sc.spp, adjoint=not args.no_adjoint)
-        ts.append(t)
-        ups += u
+    pool = OraclePool(rec, sc, args.oracle_stride, not args.no_adjoint)
+    try:
+        for _ in range(args.warmup):
+            pool.step()
+        ts, ups = [], 0
+        for _ in range(args.steps):
+            t, u = pool.step()
+            ts.append(t)
+            ups += u
+    finally:
+        pool.close()
     value = ups / sum(ts)
-    sample = (f"every {args.oracle_stride}th pixel in x and y: {hi} of {rec['n_paths']} paths "
-              f"({sub['n']} vertices) of {sc.name}")
+    sample = pool.describe(rec["n_paths"])
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ts)) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": sc.name, "k": sc.k, "iters": sc.iters, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -510,7 +732,6 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
-        args.warmup = min(args.warmup, 3)
         run_reference(args)
     else:
         run_gpu(args)

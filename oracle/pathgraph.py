@@ -97,15 +97,16 @@ def knn_brute(q, k, r2_max=None):
     return nbr
 
 
-def knn(q, k, r2_max=None, workers=1, rows=None):
+def knn(q, k, r2_max=None, workers=1, rows=None, tree=None):
     """Same neighbourhoods as :func:`knn_brute`, found with a k-d tree.
 
     scipy's cKDTree (a library kNN primitive) proposes candidate sets; each is
     re-ordered with exact int64 squared distances and index ties, and widened
     until the candidate set provably holds every point that can tie with the
     last kept entry. With ``rows`` only those query points are answered (row i
-    of the result is point rows[i]'s neighbourhood among all points). Pinned
-    against :func:`knn_brute`.
+    of the result is point rows[i]'s neighbourhood among all points); ``tree``
+    may pass a cKDTree already built over q (as float64) for repeated calls
+    over row blocks. Pinned against :func:`knn_brute`.
     """
     from scipy.spatial import cKDTree
 
@@ -117,7 +118,8 @@ def knn(q, k, r2_max=None, workers=1, rows=None):
     nbr[:, 0] = qi
     if k == 1 or n == 1:
         return nbr
-    tree = cKDTree(q.astype(np.float64))
+    if tree is None:
+        tree = cKDTree(q.astype(np.float64))
     todo = np.arange(len(qi))
     kk = min(n, k + 8)
     while todo.size:

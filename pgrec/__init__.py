@@ -299,12 +299,13 @@ def subset_paths(rec: dict, path_lo: int, path_hi: int) -> dict:
     return out
 
 
-def sample_pixels(rec: dict, width: int, height: int, spp: int, stride: int) -> dict:
+def sample_pixels(rec: dict, width: int, height: int, spp: int, stride: int, offset=(0, 0)) -> dict:
     """Records of the paths of every `stride`-th pixel in x and y (all spp),
-    re-indexed from zero; the result is a (height/stride x width/stride)
-    image's worth of paths with every path's vertices still contiguous."""
-    ys = np.arange(0, height, stride)
-    xs = np.arange(0, width, stride)
+    starting at pixel ``offset`` = (y, x), re-indexed from zero; the result is
+    a (height/stride x width/stride) image's worth of paths with every path's
+    vertices still contiguous."""
+    ys = np.arange(offset[0], height, stride)
+    xs = np.arange(offset[1], width, stride)
     pix = (ys[:, None] * width + xs[None, :]).reshape(-1)
     paths = (pix[:, None] * spp + np.arange(spp)[None, :]).reshape(-1)
     first = rec["first"][paths]
