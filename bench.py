@@ -198,11 +198,13 @@ def run_gpu(args):
     stage_ms = {nm: float(np.mean([m[nm][0].elapsed_time(m[nm][1]) for m in marks_all if m[nm][0].query()]))
                 for nm in stage_names if not (args.no_adjoint and nm == "adjoint")}
 
-    # ---- end to end through the public API: host records -> image on the host
-    # (measured right after the device-timed steps, in the same state)
+    # ---- end to end through the C ABI's host-buffer entry point (pg_step_host):
+    # host records -> image and gradient on the host (measured right after the
+    # device-timed steps, in the same state)
     e2e_t = []
     h2d = sum(int(v.numel() * v.element_size()) for v in host.values()) + host_target.numel() * 4
-    d2h = sc.width * sc.height * 4
+    # the image, and with the adjoint the per-voxel albedo gradient
+    d2h = sc.width * sc.height * 4 + (0 if args.no_adjoint else 4 * sc.grid_res ** 3)
     for i in range(args.steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()

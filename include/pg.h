@@ -479,6 +479,37 @@ void pg_shard_destroy(pg_shard *s);
 pg_status pg_graph_y_from_L(const pg_graph *g, const float *L, float *y, pg_stream_t stream);
 pg_status pg_graph_L_from_y(const pg_graph *g, const float *y, float *L, pg_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * The whole hot path from HOST buffers (the path-graph solver of Section 4
+ * as one call): the records are copied to the device (positions first on
+ * `stream`, which builds the graph from them while the other records are
+ * copied on a second stream of the library's), then pg_build_graph,
+ * pg_aggregate, pg_propagate, pg_gather and, with a target, the adjoint of
+ * the loss 1/2 sum_p (image_p - target_p)^2 (pg_propagate_adjoint, stored
+ * transpose); the image and the requested gradients are copied back.
+ * Synchronises `stream` before returning; every device buffer it used is
+ * released (to the library's pool) and no graph outlives the call. */
+typedef struct {
+    int32_t k, iters;       /* neighbours per vertex (self included), sweeps */
+    pg_wdtype wdtype;
+    float bbox_lo[3], bbox_hi[3];
+    int32_t spp, width, height;
+    int32_t adjoint;        /* 1: run the adjoint when a target is given */
+    int64_t n_vox;          /* voxels of the per-voxel albedo gradient */
+} pg_step_params;
+
+/* hv: HOST pointers of the vertex records (pg_vertices fields; pinned host
+ * memory lets the copies overlap the graph build); L0: host, n floats;
+ * first, bg: host, n_paths; target: host width*height floats or NULL;
+ * voxel: host, n int32 voxel ids (needed only for grad_albedo_vox).
+ * Outputs (host): image (width*height floats), grad_sigma_s (n floats, or
+ * NULL), grad_albedo_vox (n_vox floats, or NULL): as in
+ * pg_propagate_adjoint. Errors: those of the calls it makes,
+ * PG_ERR_INVALID_ARG (sizes, NULL inputs, a gradient without a target). */
+pg_status pg_step_host(const pg_vertices *hv, int64_t n, const float *L0, const int32_t *first, const float *bg,
+                       int64_t n_paths, const float *target, const int32_t *voxel, const pg_step_params *params,
+                       float *image, float *grad_sigma_s, float *grad_albedo_vox, pg_stream_t stream);
+
 void pg_graph_destroy(pg_graph *g);
 const char *pg_status_string(pg_status s);
 

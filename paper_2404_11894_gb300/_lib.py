@@ -72,12 +72,19 @@ class PgShardInfo(ctypes.Structure):
                 ("local_len", ctypes.c_int64), ("n_send", ctypes.c_int64)]
 
 
+class PgStepParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("iters", ctypes.c_int32), ("wdtype", ctypes.c_int),
+                ("bbox_lo", ctypes.c_float * 3), ("bbox_hi", ctypes.c_float * 3), ("spp", ctypes.c_int32),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("adjoint", ctypes.c_int32),
+                ("n_vox", ctypes.c_int64)]
+
+
 EXPORTS = ("pg_build_graph", "pg_graph_neighbors", "pg_graph_get_info", "pg_aggregate", "pg_propagate",
            "pg_gather", "pg_propagate_adjoint", "pg_graph_release_weights", "pg_graph_destroy",
            "pg_status_string", "pg_launch_count", "pg_propagate_noalloc", "pg_gather_ex",
            "pg_record_count", "pg_record_fill", "pg_prepare_adjoint", "pg_shard_create", "pg_shard_create_host",
            "pg_shard_get_info", "pg_shard_get_lists", "pg_shard_load", "pg_shard_pack", "pg_shard_sweep",
-           "pg_shard_destroy", "pg_graph_y_from_L", "pg_graph_L_from_y")
+           "pg_shard_destroy", "pg_graph_y_from_L", "pg_graph_L_from_y", "pg_step_host")
 
 _lib = None
 
@@ -120,6 +127,8 @@ def load(path: str = LIB_PATH):
     lib.pg_shard_destroy.restype = None
     lib.pg_graph_y_from_L.argtypes = [vp, vp, vp, vp]
     lib.pg_graph_L_from_y.argtypes = [vp, vp, vp, vp]
+    lib.pg_step_host.argtypes = [ctypes.POINTER(PgVertices), i64, vp, vp, vp, i64, vp, vp,
+                                 ctypes.POINTER(PgStepParams), vp, vp, vp, vp]
     lib.pg_launch_count.argtypes = []
     lib.pg_launch_count.restype = ctypes.c_int64
     for name in EXPORTS:

@@ -6,8 +6,7 @@
 // evict-first so the gathered vector y stays in L2); KP/4 lanes share a row
 // and combine their four products with shuffles. The relative change of the
 // sweep is reduced in FP64 (per-block partials, then the last block), and a
-// sweep that finds the previous one converged returns at once. Each thread
-// accumulates its squared changes and norms with a compensated float sum.
+// sweep that finds the previous one converged returns at once.
 #include <algorithm>
 #include <mutex>
 
@@ -73,23 +72,14 @@ __device__ __forceinline__ void sweep_residual(double rd, double rn, int32_t *ct
     }
 }
 
-// A thread's share of the residual's sums of squares: float32 with a
-// compensation term (TwoSum), so its relative error stays near 2^-23
-// whatever the number of rows the thread sweeps (the terms are squares, so
-// nothing cancels); the grid then sums the threads' shares in FP64.
-// Per-thread FP64 accumulation measured 205 -> 312 us per FP32 sweep on
-// this GPU's FP64 rate, for no accuracy a convergence test can use.
-struct csum {
-    float hi = 0.0f, lo = 0.0f;
-    __device__ __forceinline__ void add(float x) {
-        float s, e;
-        two_sum(hi, x, s, e);
-        hi = s;
-        lo = __fadd_rn(lo, e);
-    }
-    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
-
+// A thread's share of the residual's sums of squares is a float32 sum
+// over its rows (a few hundred per thread; the terms are squares, so the
+// relative error stays below rows * 2^-24, about 1e-5, and nothing
+// cancels); the block and the grid add the threads' shares in FP64, where
+// millions of terms meet. Measured on the 8.7M-vertex cloud, FP32 sweep:
+// float 199 us; a compensated (TwoSum) float sum 209 us; float partials of
+// 32 row groups folded into FP64 245 us; FP64 per row 312 us (this GPU's
+// FP64 rate).
 // Compensated sum of one row's products, four per lane, then over the row's
 // LPR lanes (the kernel is memory-bound, so the extra additions are free;
 // they keep 30+ sweeps at albedo ~1 within float32 rounding of the exact
@@ -144,31 +134,19 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(
         const int64_t tile = k / TILE_GROUPS;
         return (tile * gridDim.x + blockIdx.x) * (STEP * TILE_GROUPS) + (k - tile * TILE_GROUPS) * STEP;
     };
-    csum rd, rn;
-    // with four or more lanes per row its scalars (b, the previous iterate,
-    // the 16-bit row scale) travel with the streamed loads, one per lane,
-    // and reach the row's first lane by shuffles after the gathers
-    constexpr bool PRE = LPR >= 4;
-    const int lead = lane & ~(LPR - 1);
+    float rd = 0.0f, rn = 0.0f;
     auto group = [&](int64_t base) { // uniform across the block
         int32_t row[U]; // row indices fit in 32 bits (n < 2^31); 64-bit only in element offsets
         bool ok[U];
         int4 c4[U];
         typename WTraits<WT>::raw4 w4[U];
-        float sv[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
             row[u] = (int32_t)(base + u * RPB + threadIdx.x / LPR);
             ok[u] = row[u] < r1;
-            sv[u] = 0.0f;
             if (ok[u]) {
                 c4[u] = __ldcs(reinterpret_cast<const int4 *>(col + (int64_t)row[u] * KP) + q);
                 w4[u] = WTraits<WT>::load4_raw(W + (int64_t)row[u] * KP + q * 4);
-                if (PRE) {
-                    if (q == 0) sv[u] = __ldcs(b + row[u]);
-                    else if (q == 1) sv[u] = yin[row[u]];
-                    else if (W16 && q == 2) sv[u] = __ldcs(rscale + row[u]);
-                }
             } else {
                 c4[u] = make_int4(0, 0, 0, 0);
                 w4[u] = {};
@@ -185,22 +163,14 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const float acc = row_dot<LPR>(WTraits<WT>::dec4(w4[u]), g[u][0], g[u][1], g[u][2], g[u][3]);
-            float yo = 0.0f, sc = 1.0f, bb = sv[u];
-            if (PRE) {
-                yo = __shfl_sync(0xffffffffu, sv[u], lead + 1);
-                if (W16) sc = __shfl_sync(0xffffffffu, sv[u], lead + 2);
-            }
             if (ok[u] && q == 0) {
-                if (!PRE) {
-                    sc = W16 ? rscale[row[u]] : 1.0f;
-                    bb = b[row[u]];
-                    yo = yin[row[u]];
-                }
+                const float sc = W16 ? rscale[row[u]] : 1.0f;
+                const float bb = b[row[u]], yo = yin[row[u]];
                 const float yn = fmaf(acc, sc, bb);
                 yout[row[u]] = yn;
                 const float d = yn - yo;
-                rd.add(d * d);
-                rn.add(yn * yn);
+                rd = fmaf(d, d, rd);
+                rn = fmaf(yn, yn, rn);
             }
         }
     };
@@ -209,7 +179,7 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(
     } else {
         for (int64_t base = r0; base < r1; base += STEP) group(base); // uniform across the block
     }
-    sweep_residual<NT>(rd.value(), rn.value(), ctrl, partials, resid, t, tol);
+    sweep_residual<NT>(rd, rn, ctrl, partials, resid, t, tol);
 }
 
 // The same sweep, software-pipelined: one row group per iteration, with the
@@ -254,7 +224,7 @@ __global__ void __launch_bounds__(NT, MINB) sweep_pf_kernel(
             else if (W16 && q == 2) sv = __ldcs(rscale + row);
         }
     };
-    csum rd, rn;
+    float rd = 0.0f, rn = 0.0f;
     int4 c4n;
     float4 w4n;
     float svn;
@@ -275,12 +245,12 @@ __global__ void __launch_bounds__(NT, MINB) sweep_pf_kernel(
             const float yn = fmaf(acc, sc, sv);
             yout[row] = yn;
             const float d = yn - yo;
-            rd.add(d * d);
-            rn.add(yn * yn);
+            rd = fmaf(d, d, rd);
+            rn = fmaf(yn, yn, rn);
         }
         base = nb;
     }
-    sweep_residual<NT>(rd.value(), rn.value(), ctrl, partials, resid, t, tol);
+    sweep_residual<NT>(rd, rn, ctrl, partials, resid, t, tol);
 }
 
 // The front schedule pays off once the gathered vector no longer fits in L2

@@ -116,36 +116,23 @@ class Solver:
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    POSITIONS = ("px", "py", "pz")
+    def solve_host(self, host: dict, host_target, spp, width, height, want_sigma_s: bool = False):
+        """End to end from pinned host records to the image on the host,
+        through the C ABI's host-buffer entry point (pg_step_host: the
+        positions are copied first and the graph built from them while the
+        other records are copied on a second stream). The per-voxel albedo
+        gradient is formed when the solver has n_vox > 0 and ``host`` holds
+        the voxel ids."""
+        from . import pg_step_host
 
-    def solve_host(self, host: dict, host_target, spp, width, height):
-        """End to end from pinned host records to the image on the host.
-
-        The positions are copied first on the compute stream; every other
-        record is copied on a side stream while the graph is built (the build
-        reads only positions), and the aggregation waits for those copies."""
-        main = torch.cuda.current_stream()
-        if getattr(self, "_copy_stream", None) is None:
-            self._copy_stream = torch.cuda.Stream()
-        side = self._copy_stream
-        side.wait_stream(main)  # the caller's earlier work on the host buffers' device copies is done
-        dev = {k: host[k].to("cuda", non_blocking=True) for k in self.POSITIONS}
-        with torch.cuda.stream(side):
-            for k, v in host.items():
-                if k not in self.POSITIONS:
-                    dev[k] = v.to("cuda", non_blocking=True)
-            tgt = host_target.to("cuda", non_blocking=True) if host_target is not None else None
-            ready = torch.cuda.Event()
-            ready.record(side)
-        for k, t in dev.items():
-            if k not in self.POSITIONS:
-                t.record_stream(main)
-        if tgt is not None:
-            tgt.record_stream(main)
-        V = Vertices({k: dev[k] for k in dev if k not in ("L0", "first", "bg", "voxel")})
-        img = self.step(V, dev["L0"], dev["first"], dev["bg"], spp, width, height, tgt, ready=ready,
-                        voxel=dev.get("voxel"), sigma_t=dev.get("sigma_t"))
-        return img.to("cpu")
+        if self.cluster_size or self.recompute_weights:
+            raise ValueError("solve_host runs kNN neighbourhoods with the stored transpose")
+        nv = self.n_vox if "voxel" in host else 0
+        out = pg_step_host(host, spp, width, height, self.k, self.iters, self.wdtype,
+                           target=host_target if self.adjoint else None, n_vox=nv, want_sigma_s=want_sigma_s,
+                           bbox_lo=self.bbox_lo, bbox_hi=self.bbox_hi)
+        self.host_grads = out
+        return out["image"]
 
     def close(self):
         if self.graph is not None:

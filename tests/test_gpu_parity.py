@@ -249,27 +249,29 @@ def test_bad_inputs_rejected(pg):
 
 
 def test_solver_host_path_equals_device_path(pg):
-    """Solver.solve_host (records copied from pinned host memory, all but the
-    positions on a side stream overlapping the graph build) gives the same
-    image and gradients as the step on device-resident records."""
+    """The host-buffer entry point (pg_step_host through Solver.solve_host:
+    records copied from pinned host memory, all but the positions on a side
+    stream overlapping the graph build) gives the same image, sigma_s
+    gradient and per-voxel albedo gradient as the step on device-resident
+    records."""
     sc = pgrec.CLOUD128.with_(width=48, height=48, spp=4)
     rec = pgrec.trace(sc)
-    keys = pg.VERTEX_F32 + ("e_delta", "succ", "L0", "first", "bg")
+    keys = pg.VERTEX_F32 + ("e_delta", "succ", "L0", "first", "bg", "voxel")
     host = {k: torch.from_numpy(np.ascontiguousarray(rec[k])).pin_memory() for k in keys}
     target = torch.from_numpy((rec["pt_image"] * 1.05).astype(np.float32)).pin_memory()
-    solver = pg.Solver(k=sc.k, iters=sc.iters, adjoint=True, want_g=True)
-    img_h = solver.solve_host(host, target, sc.spp, sc.width, sc.height)
-    torch.cuda.synchronize()
-    gh = {k: v.clone() for k, v in solver.grads.items() if v is not None}
+    nv = sc.grid_res ** 3
+    solver = pg.Solver(k=sc.k, iters=sc.iters, adjoint=True, want_g=False, n_vox=nv)
+    img_h = solver.solve_host(host, target, sc.spp, sc.width, sc.height, want_sigma_s=True)
+    gh = solver.host_grads
     dev = {k: v.cuda() for k, v in host.items()}
     V = pg.Vertices({k: dev[k] for k in pg.VERTEX_F32 + ("e_delta", "succ")})
-    img_d = solver.step(V, dev["L0"], dev["first"], dev["bg"], sc.spp, sc.width, sc.height, target.cuda())
+    img_d = solver.step(V, dev["L0"], dev["first"], dev["bg"], sc.spp, sc.width, sc.height, target.cuda(),
+                        voxel=dev["voxel"], sigma_t=dev["sigma_t"])
     torch.cuda.synchronize()
     assert torch.equal(img_h, img_d.cpu())
-    assert torch.equal(gh["grad_sigma_s"], solver.grads["grad_sigma_s"])
-    # the g gradient's marginal terms are summed with float atomics: equal to
-    # the rounding of sums whose terms cancel (measured 1e-8 of the largest)
-    a, b = gh["grad_g"].double(), solver.grads["grad_g"].double()
+    assert torch.equal(gh["grad_sigma_s"], solver.grads["grad_sigma_s"].cpu())
+    # the per-voxel sums are float atomics: equal to their rounding
+    a, b = gh["grad_albedo"].double(), solver.grads["grad_albedo"].cpu().double()
     assert float((a - b).abs().max()) <= 1e-5 * float(b.abs().max())
     solver.close()
 
