@@ -130,7 +130,7 @@ def run_gpu(args):
     from paper_2404_11894_gb300.dist import combine_throughput, rank_seed
 
     sc = _scene(args.workload)
-    wdtype = sc.weight_dtypes[0] if sc.weight_dtypes else "f32"
+    wdtype = args.weights or (sc.weight_dtypes[0] if sc.weight_dtypes else "f32")
     if args.scale != 1.0:  # smaller image of the same scene (profiling captures)
         sc = sc.with_(width=int(sc.width * args.scale), height=int(sc.height * args.scale))
     if world > 1:  # independent renders (replicas), one per rank
@@ -728,6 +728,8 @@ def main():
     ap.add_argument("--workload", default="cloud128", choices=WORKLOADS,
                     help="cloud128: the headline workload; dense256: the 158.7M-vertex BF16 workload "
                          "(stage times at scale, not the headline line)")
+    ap.add_argument("--weights", default=None, choices=["f32", "bf16", "f16", "u16"],
+                    help="edge-weight storage of the timed step (default: the workload's own)")
     ap.add_argument("--adjoint-mode", type=int, default=0, choices=[0, 1, 2],
                     help="reverse sweep: 0 transposed copy, 1 recomputed weights, 2 atomic scatter")
     args = ap.parse_args()
