@@ -231,7 +231,8 @@ def run_gpu(args):
     bytes_sweep = nnz * (4 + (2 if w16 else 4)) + info["n_active"] * (16 if w16 else 12)
     achieved = bytes_sweep / (sweep_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
-    traffic = _profile_traffic("sweep_f32", n) if not w16 else None
+    traffic = _profile_traffic("sweep_f32", n) if not w16 else (
+        _profile_traffic("sweep_u16", n) if wdtype == "u16" else None)
     others = {}
     if not args.no_adjoint and args.adjoint_mode == 0:
         # transposed (reverse) sweep: adjoint time after T and after 1 forward sweeps

@@ -182,12 +182,14 @@ SCENE_FIELDS = tuple(f for f, _ in _lib.PgScene._fields_ if f not in ("density",
 
 def pg_step_host(host: dict, spp: int, width: int, height: int, k: int, iters: int, wdtype: str = "f32",
                  target=None, n_vox: int = 0, want_sigma_s: bool = False, bbox_lo=(0.0, 0.0, 0.0),
-                 bbox_hi=(1.0, 1.0, 1.0), stream=None) -> dict:
+                 bbox_hi=(1.0, 1.0, 1.0), out: dict | None = None, stream=None) -> dict:
     """The whole hot path from HOST buffers through the C ABI (pg_step_host):
     ``host`` holds CPU tensors (pinned for overlapped copies) of the vertex
     records, ``L0``, ``first``, ``bg`` (and ``voxel`` with n_vox > 0); with a
     host ``target`` image the adjoint of the L2 loss runs too. Returns host
-    tensors: image, and grad_sigma_s / grad_albedo when requested."""
+    tensors: image, and grad_sigma_s / grad_albedo when requested (written
+    into ``out``'s tensors of those names when given: pinned buffers let the
+    device-to-host copies run asynchronously)."""
     def hp(t):
         return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
@@ -198,9 +200,19 @@ def pg_step_host(host: dict, spp: int, width: int, height: int, k: int, iters: i
                             adjoint=1 if target is not None else 0, n_vox=n_vox)
     for i in range(3):
         prm.bbox_lo[i], prm.bbox_hi[i] = bbox_lo[i], bbox_hi[i]
-    img = torch.empty((height, width), dtype=torch.float32)
-    gs = torch.empty(n, dtype=torch.float32) if (want_sigma_s and target is not None) else None
-    ga = torch.empty(n_vox, dtype=torch.float32) if (n_vox > 0 and target is not None) else None
+    out = out or {}
+
+    def buf(name, shape, want):
+        if not want:
+            return None
+        t = out.get(name)
+        if t is None or tuple(t.shape) != tuple(shape):
+            t = torch.empty(shape, dtype=torch.float32)
+        return t
+
+    img = buf("image", (height, width), True)
+    gs = buf("grad_sigma_s", (n,), want_sigma_s and target is not None)
+    ga = buf("grad_albedo", (n_vox,), n_vox > 0 and target is not None)
     check(_LIB.pg_step_host(ctypes.byref(vs), n, hp(host["L0"]), hp(host["first"]), hp(host["bg"]), P, hp(target),
                             hp(host.get("voxel")) if ga is not None else None, ctypes.byref(prm), hp(img), hp(gs),
                             hp(ga), _stream_ptr(stream)), "pg_step_host")

@@ -268,13 +268,22 @@ __global__ void __launch_bounds__(128, 4) knn_kernel(const int4 *__restrict__ qr
     for (int pos = km1; pos < M; pos++) row[1 + pos] = -1;
 }
 
-// Exact path for queued queries: entries (int64 d2, caller id) compared
-// lexicographically. QUERY = false: the build's redo list (*d_count
-// entries), row m of nbr. QUERY = true without qlist: nq query points
-// list[t] (Morton index, or -1 for none), row t of nbr; with qlist: the
-// first-ring kernel's queued query slots list[t] (*d_count entries), slot u
-// asking for vertex qlist[u], row u of nbr. With saved_keys, query t resumes
-// at ring 2 from the first-ring kernel's list (entry t of the queue).
+// Exact path for queued queries, one warp per query: entries (int64 d2,
+// caller id) compared lexicographically, held one per lane (lane i = slot i
+// of the ascending list; lanes below `pad` hold a sentinel that precedes
+// every entry, so the (k-1)-th real entry is always lane M-1). The lanes
+// scan a ring's cells in parallel, one cell each, and every candidate that
+// beats the current (k-1)-th entry is inserted by all lanes together: a lane
+// whose entry is larger takes its left neighbour's entry, or the candidate
+// where the neighbour's is smaller (the register list's insertion, spread
+// over the warp). The few queries that get here need long ring scans; one
+// thread per query left most lanes of a warp idle behind the longest one.
+// QUERY = false: the build's redo list (*d_count entries), row m of nbr.
+// QUERY = true without qlist: nq query points list[t] (Morton index, or -1
+// for none), row t of nbr; with qlist: the first-ring kernel's queued query
+// slots list[t] (*d_count entries), slot u asking for vertex qlist[u], row
+// u of nbr. With saved_keys, query t resumes at ring 2 from the first-ring
+// kernel's list (entry t of the queue).
 template <int KP, bool QUERY>
 __global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__ qrec,
                                                         const int2 *__restrict__ cell_se,
@@ -284,16 +293,15 @@ __global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__
                                                         const uint64_t *__restrict__ saved_keys, int64_t saved_cap,
                                                         const int32_t *__restrict__ qlist = nullptr) {
     constexpr int M = KP - 1;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ((QUERY && !qlist) ? nq : (int64_t)*d_count)) return;
-    // build: list = queued vertices, rows by vertex; queries: list = the
-    // queries' vertices, rows by t; queued queries (qlist given): list = the
-    // queued slots, slot s asks for vertex qlist[s], rows by slot
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; // one query per warp
+    if (t >= ((QUERY && !qlist) ? nq : (int64_t)*d_count)) return;        // uniform over the warp
     const int64_t slot = !QUERY ? (int64_t)list[t] : (qlist ? (int64_t)list[t] : t);
     const int64_t m = !QUERY ? slot : (qlist ? (int64_t)qlist[slot] : (int64_t)list[t]);
     int32_t *row = nbr + slot * KP;
     if (QUERY && m < 0) {
-        for (int i = 0; i < KP; i++) row[i] = -1;
+        if (lane < KP) row[lane] = -1;
         return;
     }
     const int4 qr = qrec[m];
@@ -304,141 +312,132 @@ __global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__
     const int cx = qx >> sh, cy = qy >> sh, cz = qz >> sh;
     const int32_t q3o[3] = {qx & (int32_t)(cs - 1), qy & (int32_t)(cs - 1), qz & (int32_t)(cs - 1)};
     const int km1 = k - 1;
-
-    // Ascending list of M slots. The lowest M - (k-1) slots hold a sentinel
-    // below every real entry, so the k-1 real entries occupy the top slots
-    // and the current worst one is always slot M-1 (constant register index).
     const int pad = M - km1;
-    int64_t bd[M > 0 ? M : 1];
-    int32_t bi[M > 0 ? M : 1];
-#pragma unroll
-    for (int i = 0; i < M; i++) {
-        bd[i] = i < pad ? (int64_t)-1 : INT64_MAX;
-        bi[i] = i < pad ? -1 : INT32_MAX;
-    }
-    int64_t worst_d = INT64_MAX;
-    int32_t worst_i = INT32_MAX;
+    int64_t bd = lane < pad ? (int64_t)-1 : INT64_MAX;
+    int32_t bi = lane < pad ? -1 : INT32_MAX;
     int found = 0;
     int r_start = 0;
     if (saved_keys && t < saved_cap) {
-        // resume from the fast kernel's list of rings 0 and 1
-#pragma unroll
-        for (int i = 0; i < M; i++) {
-            const uint64_t key = saved_keys[t * M + i];
-            if (i >= pad && key != UINT64_MAX) {
-                bd[i] = (int64_t)(key >> 31);
-                bi[i] = (int32_t)(key & 0x7fffffffu);
-                found++;
+        // resume from the first-ring kernel's list of rings 0 and 1
+        bool real = false;
+        if (lane >= pad && lane < M) {
+            const uint64_t key = saved_keys[t * M + lane];
+            if (key != UINT64_MAX) {
+                bd = (int64_t)(key >> 31);
+                bi = (int32_t)(key & 0x7fffffffu);
+                real = true;
             }
         }
-        worst_d = bd[M - 1];
-        worst_i = bi[M - 1];
+        found = __popc(__ballot_sync(FULL, real));
         r_start = 2;
     }
+    int64_t worst_d = __shfl_sync(FULL, bd, M - 1);
+    int32_t worst_i = __shfl_sync(FULL, bi, M - 1);
 
     if (km1 > 0) {
         for (int r = r_start;; r++) {
-            // cells of ring r: r = 0 the own cell; r = 1 the 26 neighbours,
-            // nearest first (faces, edges, corners) so the list fills with
-            // good candidates early; r >= 2 the shell of the (2r+1)^3 block
+            // ring r: the shell of the (2r+1)^3 block of cells around the own
             const int span = 2 * r + 1;
-            const int ncell = r == 0 ? 1 : (r == 1 ? 26 : span * span * span);
-            for (int ci = 0; ci < ncell; ci++) {
-                int dx, dy, dz;
-                if (r == 0) {
-                    dx = dy = dz = 0;
-                } else if (r == 1) {
-                    int o = c_ring1[ci];
-                    dx = (o & 3) - 1;
-                    dy = ((o >> 2) & 3) - 1;
-                    dz = ((o >> 4) & 3) - 1;
-                } else {
-                    dx = ci % span - r;
-                    dy = (ci / span) % span - r;
-                    dz = ci / (span * span) - r;
-                    if (abs(dx) != r && abs(dy) != r && abs(dz) != r) continue;
-                }
-                const int x = cx + dx, y = cy + dy, z = cz + dz;
-                if (x < 0 || x >= G || y < 0 || y >= G || z < 0 || z >= G) continue;
-                if (worst_d != INT64_MAX) {
-                    // skip a cell whose nearest point is farther than the
-                    // (k-1)-th entry: none of its vertices can enter the list
-                    const int d3[3] = {dx, dy, dz};
-                    int64_t lb = 0;
+            const int ncell = span * span * span;
+            for (int c0 = 0; c0 < ncell; c0 += 32) {
+                int32_t p = 0, p1 = 0; // this lane's cell
+                const int ci = c0 + lane;
+                if (ci < ncell) {
+                    const int dx = ci % span - r, dy = (ci / span) % span - r, dz = ci / (span * span) - r;
+                    const int x = cx + dx, y = cy + dy, z = cz + dz;
+                    bool use = (abs(dx) == r || abs(dy) == r || abs(dz) == r) && x >= 0 && x < G && y >= 0 &&
+                               y < G && z >= 0 && z < G;
+                    if (use && worst_d != INT64_MAX) {
+                        // a cell whose nearest point is farther than the
+                        // (k-1)-th entry cannot contribute
+                        const int d3[3] = {dx, dy, dz};
+                        int64_t lb = 0;
 #pragma unroll
-                    for (int a = 0; a < 3; a++) {
-                        const int64_t o = q3o[a];
-                        const int64_t gap = d3[a] < 0 ? o + 1 + (int64_t)(-d3[a] - 1) * cs
-                                                      : (d3[a] > 0 ? cs - o + (int64_t)(d3[a] - 1) * cs : 0);
-                        lb += gap * gap;
+                        for (int a = 0; a < 3; a++) {
+                            const int64_t o = q3o[a];
+                            const int64_t gap = d3[a] < 0 ? o + 1 + (int64_t)(-d3[a] - 1) * cs
+                                                          : (d3[a] > 0 ? cs - o + (int64_t)(d3[a] - 1) * cs : 0);
+                            lb += gap * gap;
+                        }
+                        use = lb <= worst_d;
                     }
-                    if (lb > worst_d) continue;
+                    if (use) {
+                        const int2 se = cell_se[(int64_t)x + ((int64_t)y << level) + ((int64_t)z << (2 * level))];
+                        p = se.x;
+                        p1 = se.x + se.y;
+                    }
                 }
-                const int2 se = cell_se[(int64_t)x + ((int64_t)y << level) + ((int64_t)z << (2 * level))];
-                const int32_t p0 = se.x, p1 = se.x + se.y;
-                for (int32_t p = p0; p < p1; p++) {
-                    if (p == m) continue;
-                    const int4 cq = qrec[p];
-                    const int64_t ex = cq.x - qx, ey = cq.y - qy, ez = cq.z - qz;
-                    const int64_t d2 = ex * ex + ey * ey + ez * ez;
-                    if (d2 > worst_d) continue;
-                    if (r2_max >= 0 && d2 > r2_max) continue;
-                    const int32_t id = cq.w;
-                    if (!knn_less(d2, id, worst_d, worst_i)) continue;
-                    // insert into the sorted list, shifting larger entries up
-#pragma unroll
-                    for (int i = M - 1; i > 0; --i) {
-                        if (knn_less(d2, id, bd[i], bi[i])) {
-                            if (knn_less(d2, id, bd[i - 1], bi[i - 1])) {
-                                bd[i] = bd[i - 1];
-                                bi[i] = bi[i - 1];
+                // the lanes walk their cells together, one candidate each per step
+                while (__any_sync(FULL, p < p1)) {
+                    int64_t d2 = INT64_MAX;
+                    int32_t id = INT32_MAX;
+                    bool cand = false;
+                    if (p < p1) {
+                        if (p != m) {
+                            const int4 cq = qrec[p];
+                            const int64_t ex = cq.x - qx, ey = cq.y - qy, ez = cq.z - qz;
+                            d2 = ex * ex + ey * ey + ez * ez;
+                            id = cq.w;
+                            cand = d2 <= worst_d && (r2_max < 0 || d2 <= r2_max) &&
+                                   knn_less(d2, id, worst_d, worst_i);
+                        }
+                        p++;
+                    }
+                    unsigned ins = __ballot_sync(FULL, cand);
+                    while (ins) {
+                        const int src = __ffs(ins) - 1;
+                        ins &= ins - 1;
+                        const int64_t cd = __shfl_sync(FULL, d2, src);
+                        const int32_t cid = __shfl_sync(FULL, id, src);
+                        if (!knn_less(cd, cid, worst_d, worst_i)) continue; // the list moved on
+                        const int64_t ud = __shfl_up_sync(FULL, bd, 1);
+                        const int32_t ui = __shfl_up_sync(FULL, bi, 1);
+                        if (lane < M && knn_less(cd, cid, bd, bi)) {
+                            if (lane > 0 && knn_less(cd, cid, ud, ui)) {
+                                bd = ud;
+                                bi = ui;
                             } else {
-                                bd[i] = d2;
-                                bi[i] = id;
+                                bd = cd;
+                                bi = cid;
                             }
                         }
+                        found++;
+                        worst_d = __shfl_sync(FULL, bd, M - 1);
+                        worst_i = __shfl_sync(FULL, bi, M - 1);
                     }
-                    if (knn_less(d2, id, bd[0], bi[0])) {
-                        bd[0] = d2;
-                        bi[0] = id;
-                    }
-                    found++;
-                    worst_d = bd[M - 1];
-                    worst_i = bi[M - 1];
                 }
             }
             // lower bound on the distance to any vertex outside the scanned
             // block of cells [c - r, c + r]^3
             int64_t bnd = INT64_MAX;
             {
-                int c[3] = {cx, cy, cz};
-                int32_t q[3] = {qx, qy, qz};
+                const int c[3] = {cx, cy, cz};
+                const int32_t q[3] = {qx, qy, qz};
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
-                    int lo_c = c[a] - r, hi_c = c[a] + r;
+                    const int lo_c = c[a] - r, hi_c = c[a] + r;
                     if (lo_c > 0) {
-                        int64_t dlo = (int64_t)q[a] - (int64_t)lo_c * cs + 1;
+                        const int64_t dlo = (int64_t)q[a] - (int64_t)lo_c * cs + 1;
                         bnd = dlo < bnd ? dlo : bnd;
                     }
                     if (hi_c < G - 1) {
-                        int64_t dhi = (int64_t)(hi_c + 1) * cs - q[a];
+                        const int64_t dhi = (int64_t)(hi_c + 1) * cs - q[a];
                         bnd = dhi < bnd ? dhi : bnd;
                     }
                 }
             }
             if (bnd == INT64_MAX) break;                       // whole grid scanned
-            int64_t bnd2 = bnd * bnd;
+            const int64_t bnd2 = bnd * bnd;
             if (found >= km1 && worst_d < bnd2) break;          // nothing outside can enter
             if (r2_max >= 0 && bnd2 > r2_max) break;            // nothing outside is in range
         }
     }
-    row[0] = (int32_t)m;
-#pragma unroll
-    for (int i = 0; i < M; i++) {
-        int pos = i - pad; // rank among the k-1 others
-        if (pos >= 0) row[1 + pos] = bi[i] != INT32_MAX ? c2m[bi[i]] : -1;
+    if (lane == 0) row[0] = (int32_t)m;
+    if (lane < M) {
+        const int pos = lane - pad; // rank among the k-1 others
+        if (pos >= 0) row[1 + pos] = bi != INT32_MAX ? c2m[bi] : -1;
+        if (lane >= km1) row[1 + lane] = -1;
     }
-    for (int pos = km1; pos < M; pos++) row[1 + pos] = -1;
 }
 
 template <int KP>
@@ -471,7 +470,7 @@ static pg_status launch_knn_t(pg_graph *g, cudaStream_t s) {
         st = PG_ERR_CUDA;
     g->knn_exact = h_cnt;
     if (st == PG_OK && h_cnt > 0) {
-        knn_exact_kernel<KP, false><<<pg_blocks(h_cnt, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, redo, cnt, 0,
+        knn_exact_kernel<KP, false><<<pg_blocks(32 * (int64_t)h_cnt, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, redo, cnt, 0,
                                                                          g->k, g->level, g->r2_max, g->nbr, redo_keys,
                                                                          redo_cap);
         pg_count_launches(1);
@@ -499,7 +498,7 @@ pg_status pg_launch_knn_queries(const pg_graph *g, const int32_t *qm, int64_t nq
     const int kp = pg_row_width(k);
     if (g->level < 7) { // 64-bit distances: every query through the exact search
 #define Q(KP)                                                                                                   \
-    knn_exact_kernel<KP, true><<<pg_blocks(nq, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, qm, nullptr, nq, k, \
+    knn_exact_kernel<KP, true><<<pg_blocks(32 * nq, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, qm, nullptr, nq, k, \
                                                                  g->level, -1, out, nullptr, 0)
         switch (kp) {
             case 4: Q(4); break;
@@ -525,7 +524,7 @@ pg_status pg_launch_knn_queries(const pg_graph *g, const int32_t *qm, int64_t nq
 #define Q(KP)                                                                                                    \
     knn_kernel<KP, true, true><<<pg_blocks(nq, 128), 128, 0, s>>>(g->qrec, g->cell_se, nq, k, g->level, -1, g->c2m, \
                                                                  out, redo, cnt, keys, nq, qm);                  \
-    knn_exact_kernel<KP, true><<<pg_blocks(nq, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, redo, cnt, nq, k,   \
+    knn_exact_kernel<KP, true><<<pg_blocks(32 * nq, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, redo, cnt, nq, k, \
                                                                  g->level, -1, out, keys, nq, qm)
         switch (kp) {
             case 4: Q(4); break;

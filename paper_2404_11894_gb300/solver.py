@@ -122,15 +122,25 @@ class Solver:
         positions are copied first and the graph built from them while the
         other records are copied on a second stream). The per-voxel albedo
         gradient is formed when the solver has n_vox > 0 and ``host`` holds
-        the voxel ids."""
+        the voxel ids. The image and gradients (``self.host_grads``) live in
+        pinned buffers the solver reuses: the next call overwrites them."""
         from . import pg_step_host
 
         if self.cluster_size or self.recompute_weights:
             raise ValueError("solve_host runs kNN neighbourhoods with the stored transpose")
         nv = self.n_vox if "voxel" in host else 0
+        # pinned output buffers, kept between calls
+        if getattr(self, "_host_out", None) is None:
+            self._host_out = {}
+        shapes = {"image": (height, width), "grad_sigma_s": (int(host["px"].numel()),), "grad_albedo": (nv,)}
+        for name, shape in shapes.items():
+            t = self._host_out.get(name)
+            if (t is None or tuple(t.shape) != shape) and (name != "grad_sigma_s" or want_sigma_s) and \
+                    (name != "grad_albedo" or nv > 0):
+                self._host_out[name] = torch.empty(shape, dtype=torch.float32).pin_memory()
         out = pg_step_host(host, spp, width, height, self.k, self.iters, self.wdtype,
                            target=host_target if self.adjoint else None, n_vox=nv, want_sigma_s=want_sigma_s,
-                           bbox_lo=self.bbox_lo, bbox_hi=self.bbox_hi)
+                           bbox_lo=self.bbox_lo, bbox_hi=self.bbox_hi, out=self._host_out)
         self.host_grads = out
         return out["image"]
 
