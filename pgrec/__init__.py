@@ -185,7 +185,7 @@ CLOUD256_DENSE = Scene(
     name="cloud256_fbm_sigma60_a0.999_g0.9_1024px_8spp_d256", grid_res=256, medium_kind=1,
     sigma_t_max=60.0, albedo=0.999, g=0.9, width=1024, height=1024, spp=8, max_depth=256,
     k=16, iters=50, area_radiance=5.0, sky_radiance=0.2, p_area=0.5, cloud_threshold=0.2,
-    weight_dtypes=("bf16",))
+    weight_dtypes=("u16",))
 
 SCENES = {s.name: s for s in (CUBE_CONST, CLOUD128, CLOUD64_GRAD, CLOUD256_DENSE)}
 
