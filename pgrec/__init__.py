@@ -176,7 +176,7 @@ CLOUD128 = Scene(
     name="cloud128_fbm_sigma20_a0.99_g0.8_256px_16spp_d64", grid_res=128, medium_kind=1,
     sigma_t_max=20.0, albedo=0.99, g=0.8, width=256, height=256, spp=16, max_depth=64,
     k=16, iters=30, sun_irradiance=2.0, sky_radiance=0.3, p_sun=0.5)
-CLOUD128_16BIT = CLOUD128.with_(weight_dtypes=("f32", "bf16", "f16"))
+CLOUD128_16BIT = CLOUD128.with_(weight_dtypes=("f32", "u16", "f16", "bf16"))
 CLOUD64_GRAD = Scene(
     name="cloud64_fbm_a0.95_g0.6_128px_8spp_d32", grid_res=64, medium_kind=1,
     sigma_t_max=20.0, albedo=0.95, g=0.6, width=128, height=128, spp=8, max_depth=32,
