@@ -205,7 +205,8 @@ pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype wdtype, floa
  *   L0     caller order, n floats
  *   L      out, caller order, n floats: L+ after the last sweep run
  *   tol    > 0: stop after the first sweep whose relative change
- *          ||L_t - L_{t-1}||_2 / ||L_t||_2 (accumulated in FP64) is < tol;
+ *          ||L_t - L_{t-1}||_2 / ||L_t||_2 is < tol (each thread sums its
+ *          rows' squares in float32, the threads' sums are added in FP64);
  *          later sweeps return at once on the device (no host round trip)
  *   keep_history  1: the graph keeps every iterate for pg_propagate_adjoint
  *   residual      HOST, `iters` doubles, or NULL (entries past the stop are 0)

@@ -72,3 +72,41 @@ def test_argument_errors_without_gpu(lib):
     assert lib.pg_graph_release_weights(None) == 1
     lib.pg_graph_destroy(None)
     assert lib.pg_status_string(4) == b"non-finite input"
+
+
+def test_host_step_and_shard_argument_errors_without_gpu(lib):
+    """pg_step_host and the shard calls refuse bad arguments before any CUDA
+    work; a host-only shard plan needs no device at all."""
+    import numpy as np
+
+    from paper_2404_11894_gb300._lib import PgShardInfo, PgStepParams, PgVertices
+
+    prm = PgStepParams(k=8, iters=3, wdtype=0, spp=1, width=2, height=2, adjoint=0, n_vox=0)
+    img = np.zeros(4, np.float32)
+    ip = img.ctypes.data_as(ctypes.c_void_p)
+    v = PgVertices()
+    assert lib.pg_step_host(None, 0, None, None, None, 4, None, None, ctypes.byref(prm), ip, None, None, None) == 1
+    assert lib.pg_step_host(ctypes.byref(v), 0, None, None, None, 5, None, None, ctypes.byref(prm), ip, None, None,
+                            None) == 1  # paths != width * height * spp
+    assert lib.pg_step_host(ctypes.byref(v), 10, None, None, None, 4, None, None, ctypes.byref(prm), ip, None, None,
+                            None) == 1  # NULL records
+    # a gradient needs a target
+    first = np.full(4, -1, np.int32)
+    fp = first.ctypes.data_as(ctypes.c_void_p)
+    assert lib.pg_step_host(ctypes.byref(v), 0, None, fp, ip, 4, None, None, ctypes.byref(prm), ip, ip, None,
+                            None) == 1
+    out = ctypes.c_void_p()
+    assert lib.pg_shard_create(None, 2, 0, None, ctypes.byref(out)) == 1
+    col = np.array([[1, 3], [0, 2], [3, 3]], np.int32)  # 3 rows, zero slot 3
+    cp = col.ctypes.data_as(ctypes.c_void_p)
+    assert lib.pg_shard_create_host(cp, 3, 2, 3, 2, 2, ctypes.byref(out)) == 1   # shard out of range
+    assert lib.pg_shard_create_host(cp, 3, 2, 2, 2, 0, ctypes.byref(out)) == 1   # zero slot inside the rows
+    bad = np.array([[1, 7], [0, 2], [3, 3]], np.int32)
+    assert lib.pg_shard_create_host(bad.ctypes.data_as(ctypes.c_void_p), 3, 2, 3, 2, 0, ctypes.byref(out)) == 1
+    assert lib.pg_shard_create_host(cp, 3, 2, 3, 2, 1, ctypes.byref(out)) == 0
+    info = PgShardInfo()
+    assert lib.pg_shard_get_info(out, ctypes.byref(info)) == 0
+    assert (info.n_shards, info.shard, info.row_end) == (2, 1, 3)
+    # device calls on a host-only shard are refused
+    assert lib.pg_shard_sweep(out, None, None, None) == 7
+    lib.pg_shard_destroy(out)
