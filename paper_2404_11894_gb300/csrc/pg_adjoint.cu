@@ -35,16 +35,48 @@ __global__ void tcount_kernel(const int32_t *__restrict__ col, int64_t r0, int64
     if (c < ncols) atomicAdd(reinterpret_cast<unsigned long long *>(cnt + c), 1ull);
 }
 
+// Four entries of one row per thread: their column offsets, slot atomics and
+// scattered writes are independent, so a thread keeps four of these chains
+// in flight instead of waiting on one (the pass is bound by their latency).
 template <typename WT>
 __global__ void tfill_kernel(const int32_t *__restrict__ col, const WT *__restrict__ W, int64_t r0, int64_t r1,
                              int kp, int64_t ncols, const int64_t *__restrict__ tptr, int32_t *__restrict__ fill,
                              int2 *__restrict__ tent) {
-    int64_t e = r0 * kp + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= r1 * kp) return;
-    int32_t c = col[e];
+    const int64_t q = r0 * (kp / 4) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; // kp is a power of two >= 4
+    if (q >= r1 * (kp / 4)) return;
+    const int4 c4 = reinterpret_cast<const int4 *>(col)[q];
+    const int32_t c[4] = {c4.x, c4.y, c4.z, c4.w};
+    const int64_t e = 4 * q;
+    const int32_t row = (int32_t)(e >> (__ffs(kp) - 1));
+    int64_t at[4];
+    int32_t wb[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        at[i] = c[i] < ncols ? tptr[c[i]] : 0;
+        wb[i] = WTraits<WT>::bits(W[e + i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+        if (c[i] < ncols) at[i] += atomicAdd(&fill[c[i]], 1);
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+        if (c[i] < ncols) tent[at[i]] = make_int2(row, wb[i]);
+}
+
+// The active rows' column lengths from the aggregation's counts: sample j's
+// column is the sweep row of its successor, and |R(j)| counts every row that
+// uses j, so the active rows' share is |R(j)| less the first-vertex rows'
+// count of the same column (already in cntF, before rounding).
+__global__ void tcount_active_kernel(const uint32_t *__restrict__ kin, const int32_t *__restrict__ succ_m,
+                                     const int32_t *__restrict__ m2r, int64_t n, int64_t ncols,
+                                     const int64_t *__restrict__ cntF, int64_t *__restrict__ cntA) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int32_t sj = succ_m[j];
+    if (sj < 0) return;
+    const int32_t c = m2r[sj];
     if (c >= ncols) return;
-    int64_t pos = tptr[c] + atomicAdd(&fill[c], 1);
-    tent[pos] = make_int2((int32_t)(e >> (__ffs(kp) - 1)), WTraits<WT>::bits(W[e])); // kp is a power of two
+    cntA[c] = (int64_t)kin[j] - cntF[c];
 }
 
 // Column lengths rounded up to even, so that every column starts on a
@@ -549,13 +581,24 @@ static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
         if (fill) cudaFreeAsync(fill, s);
         return st;
     }
+    // Column lengths: the first-vertex rows' by counting their entries, the
+    // active rows' (nine in ten entries) from |R(j)| less those.
+    for (int i = 0; i < 2; i++) PG_CUDA(cudaMemsetAsync(ts[i]->ptr, 0, 8 * (size_t)(na + 1), s));
+    if (n > na) {
+        tcount_kernel<<<pg_blocks((n - na) * kp, 256), 256, 0, s>>>(g->col, na, n, kp, na, g->tF.ptr);
+        pg_count_launches(1);
+        PG_LAUNCH_CHECK();
+    }
+    if (na > 0) {
+        tcount_active_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(g->kin, g->succ_m, g->m2r, n, na, g->tF.ptr,
+                                                                g->tA.ptr);
+        pg_count_launches(1);
+        PG_LAUNCH_CHECK();
+    }
     for (int i = 0; i < 2; i++) {
-        PG_CUDA(cudaMemsetAsync(ts[i]->ptr, 0, 8 * (size_t)(na + 1), s));
         if (r1[i] > r0[i]) {
-            tcount_kernel<<<pg_blocks((r1[i] - r0[i]) * kp, 256), 256, 0, s>>>(g->col, r0[i], r1[i], kp, na,
-                                                                               ts[i]->ptr);
             tround_kernel<<<pg_blocks(na, 256), 256, 0, s>>>(ts[i]->ptr, na);
-            pg_count_launches(2);
+            pg_count_launches(1);
             PG_LAUNCH_CHECK();
         }
         PG_TRY(pg_scan_exclusive64(g, ts[i]->ptr, na + 1, d_total + i, s));
@@ -568,7 +611,7 @@ static pg_status build_transpose(pg_graph *g, cudaStream_t s) {
         PG_TRY(pg_alloc(g, (void **)&ts[i]->ent, 8 * (size_t)ts[i]->nnz, s));
         if (r1[i] == r0[i]) continue;
         PG_CUDA(cudaMemsetAsync(fill, 0, 4 * (size_t)(na + 1), s));
-        tfill_kernel<WT><<<pg_blocks((r1[i] - r0[i]) * kp, 256), 256, 0, s>>>(
+        tfill_kernel<WT><<<pg_blocks((r1[i] - r0[i]) * (kp / 4), 256), 256, 0, s>>>(
             g->col, (const WT *)g->W, r0[i], r1[i], kp, na, ts[i]->ptr, fill, ts[i]->ent);
         pg_count_launches(1);
         PG_LAUNCH_CHECK();
