@@ -169,6 +169,31 @@ def test_neighbors_ties_radius(pg, k):
         assert np.array_equal(got, want), (k, r2)
 
 
+@pytest.mark.parametrize("k", [2, 4, 8, 13, 16])
+def test_neighbors_ties_first_ring_level7(pg, k):
+    """A level-7 grid (32-bit distances in the first ring): a full 12^3
+    lattice at 4 sites per cell and axis, each site repeated 1 to 3 times and
+    a few sites 40 times, so the first-ring lists meet many equal distances
+    and duplicate positions, and the queries the first ring cannot settle
+    resume in the exact kernel from their saved lists."""
+    rng = np.random.default_rng(200 + k)
+    g = np.stack(np.meshgrid(np.arange(12), np.arange(12), np.arange(12), indexing="ij"), -1).reshape(-1, 3)
+    reps = rng.integers(1, 4, size=len(g))
+    reps[rng.choice(len(g), size=10, replace=False)] = 40
+    pos = (np.repeat(g, reps, axis=0) / 512.0 + 0.375).astype(np.float32)
+    n = len(pos)
+    V = synthetic.random_records(n, seed=k)
+    V["px"], V["py"], V["pz"] = pos[:, 0].copy(), pos[:, 1].copy(), pos[:, 2].copy()
+    q = oracle.quantize(V["px"], V["py"], V["pz"], (0, 0, 0), (1, 1, 1))
+    for r2 in (-1, int((2 ** 21 / 512) ** 2 * 3)):
+        Vd = pg.Vertices.from_records(V)
+        graph = pg.pg_build_graph(Vd, k, r2_max=r2, grid_level=7)
+        assert graph.info()["grid_level"] == 7
+        got = graph.neighbors().cpu().numpy()
+        want = oracle.knn(q, k, None if r2 < 0 else r2)
+        assert np.array_equal(got, want), (k, r2)
+
+
 def test_random_records_all_paths(pg):
     """Synthetic records: random directions, delta and continuous lights,
     short paths, empty camera paths; non-multiple-of-tile sizes."""
