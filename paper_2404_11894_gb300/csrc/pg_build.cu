@@ -268,6 +268,203 @@ __global__ void __launch_bounds__(128, 4) knn_kernel(const int4 *__restrict__ qr
     for (int pos = km1; pos < M; pos++) row[1 + pos] = -1;
 }
 
+// Marker in a queued query's saved list: no list was kept, the exact kernel
+// starts from the query's own cell.
+static constexpr uint64_t KNN_FRESH = UINT64_MAX - 1;
+
+// First ring with 32-bit distances (grid level >= 7) and a threshold from
+// the local density. With one thread per query and the candidates of a
+// warp's queries met in step, some lane wanted an insertion into its sorted
+// list at almost every candidate, so the warp ran the insertion network for
+// nearly all of them (about 60 % of this kernel's time went to insertions).
+// Here each query
+//   1. reads the vertex counts N of its 27 cells from the cell table and
+//      takes the radius that would hold k - 1 of them at uniform density,
+//      r^2 = (81 cs^3 (k - 1) / (4 pi (N - 1)))^(2/3), times 1.44 (1.2 in
+//      radius) as its threshold T (any T gives the same list; this one
+//      buffers about 26 candidates per query on the cloud, and 1 % of the
+//      queries fall outside 15..48),
+//   2. scans the cells that have a point closer than T and appends the
+//      candidates with d2 < T to a shared-memory buffer (no insertion),
+//   3. inserts the buffered candidates into its sorted register list; the
+//      lanes of a warp now insert together, about as often as the largest
+//      buffer holds.
+// With at least k - 1 candidates below T the list is the k - 1 smallest
+// (d2, id) of the 27 cells, as inserting every candidate gives; a query with
+// fewer (and T below its radius limit) or with an overflowing buffer is
+// queued for the exact kernel, which starts from its own cell.
+constexpr int KE_THREADS = 128;
+
+template <int KP, bool QUERY>
+__global__ void __launch_bounds__(KE_THREADS, 4) knn_est_kernel(
+    const int4 *__restrict__ qrec, const int2 *__restrict__ cell_se, int64_t n, int k, int level, int64_t r2_max,
+    const int32_t *__restrict__ c2m, int32_t *__restrict__ nbr, int32_t *__restrict__ redo,
+    int32_t *__restrict__ redo_count, uint64_t *__restrict__ redo_keys, int64_t redo_cap,
+    const int32_t *__restrict__ qlist = nullptr) {
+    constexpr int M = KP - 1;
+    constexpr int CAP = 3 * KP;
+    __shared__ int32_t buf[CAP][KE_THREADS];
+    const int tx = threadIdx.x;
+    const int64_t t = (int64_t)blockIdx.x * KE_THREADS + tx;
+    if (t >= n) return; // no block-wide barrier below
+    const int64_t m = QUERY ? (int64_t)qlist[t] : t;
+    if (QUERY && m < 0) {
+        for (int i = 0; i < KP; i++) nbr[t * KP + i] = -1;
+        return;
+    }
+    const int4 qr = qrec[m];
+    const int32_t qx = qr.x, qy = qr.y, qz = qr.z;
+    const int sh = PG_QBITS - level;
+    const int G = 1 << level;
+    const uint32_t cs = 1u << sh;
+    const int cx = qx >> sh, cy = qy >> sh, cz = qz >> sh;
+    const int km1 = k - 1;
+    const int pad = M - km1;
+    uint32_t glo[3], ghi[3];
+    {
+        const int32_t q3[3] = {qx, qy, qz};
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const uint32_t o = (uint32_t)q3[a] & (cs - 1);
+            glo[a] = (o + 1) * (o + 1);
+            ghi[a] = (cs - o) * (cs - o);
+        }
+    }
+    uint64_t bk[M > 0 ? M : 1];
+#pragma unroll
+    for (int i = 0; i < M; i++) bk[i] = i < pad ? 0ull : UINT64_MAX;
+    int found = 0;
+    bool fresh = false;
+    if (km1 > 0) {
+        // 1. the threshold from the 27 cells' counts
+        int64_t nb = 0;
+        for (int ci = 0; ci < 27; ci++) {
+            const int x = cx + ci % 3 - 1, y = cy + (ci / 3) % 3 - 1, z = cz + ci / 9 - 1;
+            if (x < 0 || x >= G || y < 0 || y >= G || z < 0 || z >= G) continue;
+            nb += cell_se[(int64_t)x + ((int64_t)y << level) + ((int64_t)z << (2 * level))].y;
+        }
+        // d2 < 3 * (2 cs)^2 <= 3 * 2^30 inside the block (cs <= 2^14)
+        uint32_t T = 0xffffffffu;
+        if (nb - 1 > km1) {
+            const float c3 = (float)cs * (float)cs * (float)cs;
+            const float r2 = cbrtf(81.0f * c3 * (float)km1 / (12.566370614359172f * (float)(nb - 1)));
+            const float tf = 1.44f * r2 * r2;
+            if (tf < 3.3e9f) T = (uint32_t)tf;
+        }
+        // a radius limit caps the threshold; below the cap the list is exact
+        // whatever the count
+        bool capped = false;
+        if (r2_max >= 0 && (int64_t)T > r2_max) {
+            T = (uint32_t)(r2_max + 1);
+            capped = true;
+        }
+        if (T == 0xffffffffu) capped = true; // every candidate of the block is buffered
+        // 2. buffer the candidates closer than T
+        int cnt = 0;
+        for (int ci = 0; ci < 27; ci++) {
+            int dx = 0, dy = 0, dz = 0;
+            if (ci > 0) {
+                const int o = c_ring1[ci - 1];
+                dx = (o & 3) - 1;
+                dy = ((o >> 2) & 3) - 1;
+                dz = ((o >> 4) & 3) - 1;
+            }
+            const int x = cx + dx, y = cy + dy, z = cz + dz;
+            if (x < 0 || x >= G || y < 0 || y >= G || z < 0 || z >= G) continue;
+            if (ci > 0) {
+                const uint32_t lb = (dx < 0 ? glo[0] : (dx > 0 ? ghi[0] : 0u)) +
+                                    (dy < 0 ? glo[1] : (dy > 0 ? ghi[1] : 0u)) +
+                                    (dz < 0 ? glo[2] : (dz > 0 ? ghi[2] : 0u));
+                if (lb >= T) continue; // no point of the cell is closer than T
+            }
+            const int2 se = cell_se[(int64_t)x + ((int64_t)y << level) + ((int64_t)z << (2 * level))];
+            const int32_t p1 = se.x + se.y;
+            for (int32_t p = se.x; p < p1; p++) {
+                if (p == m) continue;
+                const int4 c = qrec[p];
+                const int32_t ex = c.x - qx, ey = c.y - qy, ez = c.z - qz;
+                const uint32_t d2 = (uint32_t)(ex * ex) + (uint32_t)(ey * ey) + (uint32_t)(ez * ez);
+                if (d2 >= T) continue;
+                if (cnt < CAP) buf[cnt][tx] = p;
+                cnt++;
+            }
+        }
+        // 3. select: the buffered candidates into the sorted list
+        fresh = cnt > CAP || (cnt < km1 && !capped);
+        found = fresh ? 0 : cnt;
+        for (int i = 0; i < found; i++) {
+            const int32_t p = buf[i][tx];
+            const int4 c = qrec[p];
+            const int32_t ex = c.x - qx, ey = c.y - qy, ez = c.z - qz;
+            const uint32_t d2 = (uint32_t)(ex * ex) + (uint32_t)(ey * ey) + (uint32_t)(ez * ez);
+            const uint64_t key = ((uint64_t)d2 << 31) | (uint64_t)(uint32_t)c.w;
+#pragma unroll
+            for (int j = M - 1; j > 0; --j) {
+                const uint64_t prev = bk[j - 1];
+                if (key < bk[j]) bk[j] = key < prev ? prev : key;
+            }
+            if (key < bk[0]) bk[0] = key;
+        }
+        // done iff the (k-1)-th entry is closer than anything outside the block
+        int64_t bnd = INT64_MAX;
+        {
+            const int cc[3] = {cx, cy, cz};
+            const int32_t q[3] = {qx, qy, qz};
+#pragma unroll
+            for (int a2 = 0; a2 < 3; a2++) {
+                if (cc[a2] - 1 > 0) {
+                    const int64_t dlo = (int64_t)q[a2] - (int64_t)(cc[a2] - 1) * cs + 1;
+                    bnd = dlo < bnd ? dlo : bnd;
+                }
+                if (cc[a2] + 1 < G - 1) {
+                    const int64_t dhi = (int64_t)(cc[a2] + 2) * cs - q[a2];
+                    bnd = dhi < bnd ? dhi : bnd;
+                }
+            }
+        }
+        bool done = bnd == INT64_MAX; // whole grid scanned
+        if (!done) {
+            const int64_t bnd2 = bnd * bnd;
+            const uint64_t worst = bk[M - 1];
+            const int64_t worst_d = worst == UINT64_MAX ? INT64_MAX : (int64_t)(worst >> 31);
+            done = (found >= km1 && worst_d < bnd2) || (r2_max >= 0 && bnd2 > r2_max);
+        }
+        // queue the query for the exact kernel; one counter atomic per
+        // converged group of lanes, not one per query (a single hot address)
+        const bool need = fresh || !done;
+        const unsigned am = __activemask();
+        const unsigned need_mask = __ballot_sync(am, need);
+        if (need) {
+            const int lane = tx & 31;
+            const int leader = __ffs(need_mask) - 1;
+            int32_t base = 0;
+            if (lane == leader) base = atomicAdd(redo_count, __popc(need_mask));
+            base = __shfl_sync(need_mask, base, leader);
+            const int32_t slot = base + __popc(need_mask & ((1u << lane) - 1u));
+            redo[slot] = (int32_t)t;
+            // the list holds the true k-1 nearest of the 27 cells: the exact
+            // kernel resumes from it at ring 2 (from ring 0 for a fresh query)
+            if (slot < redo_cap) {
+                if (fresh) {
+                    redo_keys[(int64_t)slot * M] = KNN_FRESH;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < M; i++) redo_keys[(int64_t)slot * M + i] = bk[i];
+                }
+            }
+            return;
+        }
+    }
+    int32_t *row = nbr + t * KP;
+    row[0] = (int32_t)m;
+#pragma unroll
+    for (int i = 0; i < M; i++) {
+        const int pos = i - pad; // rank among the k-1 others
+        if (pos >= 0) row[1 + pos] = bk[i] != UINT64_MAX ? c2m[(int32_t)(bk[i] & 0x7fffffffu)] : -1;
+    }
+    for (int pos = km1; pos < M; pos++) row[1 + pos] = -1;
+}
+
 // Exact path for queued queries, one warp per query: entries (int64 d2,
 // caller id) compared lexicographically, held one per lane (lane i = slot i
 // of the ascending list; lanes below `pad` hold a sentinel that precedes
@@ -317,7 +514,7 @@ __global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__
     int32_t bi = lane < pad ? -1 : INT32_MAX;
     int found = 0;
     int r_start = 0;
-    if (saved_keys && t < saved_cap) {
+    if (saved_keys && t < saved_cap && saved_keys[t * M] != KNN_FRESH) {
         // resume from the first-ring kernel's list of rings 0 and 1
         bool real = false;
         if (lane >= pad && lane < M) {
@@ -453,7 +650,11 @@ static pg_status launch_knn_t(pg_graph *g, cudaStream_t s) {
         st = pg_alloc(nullptr, (void **)&redo_keys, 8 * (size_t)redo_cap * (KP - 1 > 0 ? KP - 1 : 1), s);
     if (st == PG_OK && cudaMemsetAsync(cnt, 0, 4, s) != cudaSuccess) st = PG_ERR_CUDA;
     if (st == PG_OK) {
-        if (g->level >= 7) {
+        if (g->level >= 7 && KP <= 16) {
+            knn_est_kernel<KP, false><<<pg_blocks(n, KE_THREADS), KE_THREADS, 0, s>>>(
+                g->qrec, g->cell_se, n, g->k, g->level, g->r2_max, g->c2m, g->nbr, redo, cnt, redo_keys, redo_cap);
+            pg_count_launches(1);
+        } else if (g->level >= 7) {
             knn_kernel<KP, true><<<pg_blocks(n, 128), 128, 0, s>>>(g->qrec, g->cell_se, n, g->k, g->level, g->r2_max,
                                                                   g->c2m, g->nbr, redo, cnt, redo_keys, redo_cap);
             pg_count_launches(1);
@@ -522,8 +723,12 @@ pg_status pg_launch_knn_queries(const pg_graph *g, const int32_t *qm, int64_t nq
     if (st == PG_OK && cudaMemsetAsync(cnt, 0, 4, s) != cudaSuccess) st = PG_ERR_CUDA;
     if (st == PG_OK) {
 #define Q(KP)                                                                                                    \
-    knn_kernel<KP, true, true><<<pg_blocks(nq, 128), 128, 0, s>>>(g->qrec, g->cell_se, nq, k, g->level, -1, g->c2m, \
-                                                                 out, redo, cnt, keys, nq, qm);                  \
+    if (KP <= 16)                                                                                                \
+        knn_est_kernel<KP, true><<<pg_blocks(nq, KE_THREADS), KE_THREADS, 0, s>>>(                               \
+            g->qrec, g->cell_se, nq, k, g->level, -1, g->c2m, out, redo, cnt, keys, nq, qm);                     \
+    else                                                                                                         \
+        knn_kernel<KP, true, true><<<pg_blocks(nq, 128), 128, 0, s>>>(g->qrec, g->cell_se, nq, k, g->level, -1,  \
+                                                                     g->c2m, out, redo, cnt, keys, nq, qm);      \
     knn_exact_kernel<KP, true><<<pg_blocks(32 * nq, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, redo, cnt, nq, k, \
                                                                  g->level, -1, out, keys, nq, qm)
         switch (kp) {
