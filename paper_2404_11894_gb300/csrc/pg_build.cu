@@ -46,11 +46,13 @@ __global__ void quantize_kernel(const float *__restrict__ px, const float *__res
 }
 
 __global__ void permute_build_kernel(const int32_t *__restrict__ m2c, const int4 *__restrict__ qrec_c, int64_t n,
-                                     int4 *__restrict__ qrec, int32_t *__restrict__ c2m) {
+                                     int4 *__restrict__ qrec, uint64_t *__restrict__ qpos, int32_t *__restrict__ c2m) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n) return;
     int32_t c = m2c[m];
-    qrec[m] = qrec_c[c]; // .w is the caller index
+    const int4 r = qrec_c[c];
+    qrec[m] = r; // .w is the caller index
+    qpos[m] = (uint64_t)(uint32_t)r.x | ((uint64_t)(uint32_t)r.y << 21) | ((uint64_t)(uint32_t)r.z << 42);
     c2m[c] = (int32_t)m;
 }
 
@@ -297,7 +299,7 @@ constexpr int KE_THREADS = 128;
 
 template <int KP, bool QUERY>
 __global__ void __launch_bounds__(KE_THREADS, 4) knn_est_kernel(
-    const int4 *__restrict__ qrec, const int2 *__restrict__ cell_se, int64_t n, int k, int level, int64_t r2_max,
+    const uint64_t *__restrict__ qpos, const int32_t *__restrict__ m2c, const int2 *__restrict__ cell_se, int64_t n, int k, int level, int64_t r2_max,
     const int32_t *__restrict__ c2m, int32_t *__restrict__ nbr, int32_t *__restrict__ redo,
     int32_t *__restrict__ redo_count, uint64_t *__restrict__ redo_keys, int64_t redo_cap,
     const int32_t *__restrict__ qlist = nullptr) {
@@ -312,8 +314,8 @@ __global__ void __launch_bounds__(KE_THREADS, 4) knn_est_kernel(
         for (int i = 0; i < KP; i++) nbr[t * KP + i] = -1;
         return;
     }
-    const int4 qr = qrec[m];
-    const int32_t qx = qr.x, qy = qr.y, qz = qr.z;
+    const uint64_t qp = qpos[m];
+    const int32_t qx = (int32_t)(qp & PG_QMASK), qy = (int32_t)((qp >> 21) & PG_QMASK), qz = (int32_t)(qp >> 42);
     const int sh = PG_QBITS - level;
     const int G = 1 << level;
     const uint32_t cs = 1u << sh;
@@ -381,8 +383,9 @@ __global__ void __launch_bounds__(KE_THREADS, 4) knn_est_kernel(
             const int32_t p1 = se.x + se.y;
             for (int32_t p = se.x; p < p1; p++) {
                 if (p == m) continue;
-                const int4 c = qrec[p];
-                const int32_t ex = c.x - qx, ey = c.y - qy, ez = c.z - qz;
+                const uint64_t c = qpos[p];
+                const int32_t ex = (int32_t)(c & PG_QMASK) - qx, ey = (int32_t)((c >> 21) & PG_QMASK) - qy,
+                              ez = (int32_t)(c >> 42) - qz;
                 const uint32_t d2 = (uint32_t)(ex * ex) + (uint32_t)(ey * ey) + (uint32_t)(ez * ez);
                 if (d2 >= T) continue;
                 if (cnt < CAP) buf[cnt][tx] = p;
@@ -394,10 +397,11 @@ __global__ void __launch_bounds__(KE_THREADS, 4) knn_est_kernel(
         found = fresh ? 0 : cnt;
         for (int i = 0; i < found; i++) {
             const int32_t p = buf[i][tx];
-            const int4 c = qrec[p];
-            const int32_t ex = c.x - qx, ey = c.y - qy, ez = c.z - qz;
+            const uint64_t c = qpos[p];
+            const int32_t ex = (int32_t)(c & PG_QMASK) - qx, ey = (int32_t)((c >> 21) & PG_QMASK) - qy,
+                          ez = (int32_t)(c >> 42) - qz;
             const uint32_t d2 = (uint32_t)(ex * ex) + (uint32_t)(ey * ey) + (uint32_t)(ez * ez);
-            const uint64_t key = ((uint64_t)d2 << 31) | (uint64_t)(uint32_t)c.w;
+            const uint64_t key = ((uint64_t)d2 << 31) | (uint64_t)(uint32_t)m2c[p]; // caller id
 #pragma unroll
             for (int j = M - 1; j > 0; --j) {
                 const uint64_t prev = bk[j - 1];
@@ -652,7 +656,7 @@ static pg_status launch_knn_t(pg_graph *g, cudaStream_t s) {
     if (st == PG_OK) {
         if (g->level >= 7 && KP <= 16) {
             knn_est_kernel<KP, false><<<pg_blocks(n, KE_THREADS), KE_THREADS, 0, s>>>(
-                g->qrec, g->cell_se, n, g->k, g->level, g->r2_max, g->c2m, g->nbr, redo, cnt, redo_keys, redo_cap);
+                g->qpos, g->m2c, g->cell_se, n, g->k, g->level, g->r2_max, g->c2m, g->nbr, redo, cnt, redo_keys, redo_cap);
             pg_count_launches(1);
         } else if (g->level >= 7) {
             knn_kernel<KP, true><<<pg_blocks(n, 128), 128, 0, s>>>(g->qrec, g->cell_se, n, g->k, g->level, g->r2_max,
@@ -725,7 +729,7 @@ pg_status pg_launch_knn_queries(const pg_graph *g, const int32_t *qm, int64_t nq
 #define Q(KP)                                                                                                    \
     if (KP <= 16)                                                                                                \
         knn_est_kernel<KP, true><<<pg_blocks(nq, KE_THREADS), KE_THREADS, 0, s>>>(                               \
-            g->qrec, g->cell_se, nq, k, g->level, -1, g->c2m, out, redo, cnt, keys, nq, qm);                     \
+            g->qpos, g->m2c, g->cell_se, nq, k, g->level, -1, g->c2m, out, redo, cnt, keys, nq, qm);                     \
     else                                                                                                         \
         knn_kernel<KP, true, true><<<pg_blocks(nq, 128), 128, 0, s>>>(g->qrec, g->cell_se, nq, k, g->level, -1,  \
                                                                      g->c2m, out, redo, cnt, keys, nq, qm);      \
@@ -812,6 +816,7 @@ extern "C" pg_status pg_build_graph(const pg_vertices *v, int64_t n, const pg_bu
     A(g->m2c, sizeof(int32_t) * n);
     A(g->c2m, sizeof(int32_t) * n);
     A(g->qrec, sizeof(int4) * n);
+    A(g->qpos, sizeof(uint64_t) * n);
     A(g->cell_se, sizeof(int2) * ncells);
     A(g->nbr, sizeof(int32_t) * n * g->kp);
     if (st == PG_OK) st = pg_alloc(nullptr, (void **)&keys, sizeof(uint32_t) * (n > 0 ? n : 1), s);
@@ -828,7 +833,7 @@ extern "C" pg_status pg_build_graph(const pg_vertices *v, int64_t n, const pg_bu
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
         if (st == PG_OK) st = pg_radix_sort(g, keys, g->m2c, n, 3 * g->level, s);
         if (st == PG_OK) {
-            permute_build_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(g->m2c, qrec_c, n, g->qrec, g->c2m);
+            permute_build_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(g->m2c, qrec_c, n, g->qrec, g->qpos, g->c2m);
             pg_count_launches(1);
             if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
         }
@@ -914,6 +919,7 @@ static pg_status graph_free_all(pg_graph *g) {
     pg_free(g, (void **)&g->m2c, 4 * n);
     pg_free(g, (void **)&g->c2m, 4 * n);
     pg_free(g, (void **)&g->qrec, 16 * n);
+    pg_free(g, (void **)&g->qpos, 8 * n);
     pg_free(g, (void **)&g->cell_se, 8 * (ncells - 1));
     pg_free(g, (void **)&g->nbr, 4 * n * kp);
     pg_free(g, (void **)&g->m2r, 4 * n);

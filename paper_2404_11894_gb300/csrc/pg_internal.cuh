@@ -44,6 +44,7 @@ struct pg_graph {
     int32_t *m2c = nullptr;        // m -> caller index
     int32_t *c2m = nullptr;        // caller -> m
     int4 *qrec = nullptr;          // (qx, qy, qz, caller index), m order
+    uint64_t *qpos = nullptr;      // qx | qy << 21 | qz << 42, m order (half the bytes of qrec)
     int2 *cell_se = nullptr;       // (start, count) per cell, index x + G (y + G z)
     int32_t *nbr = nullptr;        // [n][kp], m-space neighbour ids, -1 padded; slot 0 = self
     int64_t knn_exact = 0;         // queries resolved by the exact neighbour kernel
