@@ -19,7 +19,7 @@
 __global__ void quantize_kernel(const float *__restrict__ px, const float *__restrict__ py,
                                 const float *__restrict__ pz, int64_t n, float lo0, float lo1, float lo2,
                                 float scale, int level, uint32_t *__restrict__ cellkey, int32_t *__restrict__ idx,
-                                int4 *__restrict__ qrec_c, int32_t *__restrict__ flags) {
+                                uint64_t *__restrict__ qpos_c, int32_t *__restrict__ flags) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     float p[3] = {px[v], py[v], pz[v]};
@@ -42,17 +42,15 @@ __global__ void quantize_kernel(const float *__restrict__ px, const float *__res
     int sh = PG_QBITS - level;
     cellkey[v] = morton3(q[0] >> sh, q[1] >> sh, q[2] >> sh);
     idx[v] = (int32_t)v;
-    qrec_c[v] = make_int4((int32_t)q[0], (int32_t)q[1], (int32_t)q[2], (int32_t)v);
+    qpos_c[v] = (uint64_t)q[0] | ((uint64_t)q[1] << 21) | ((uint64_t)q[2] << 42);
 }
 
-__global__ void permute_build_kernel(const int32_t *__restrict__ m2c, const int4 *__restrict__ qrec_c, int64_t n,
-                                     int4 *__restrict__ qrec, uint64_t *__restrict__ qpos, int32_t *__restrict__ c2m) {
+__global__ void permute_build_kernel(const int32_t *__restrict__ m2c, const uint64_t *__restrict__ qpos_c, int64_t n,
+                                     uint64_t *__restrict__ qpos, int32_t *__restrict__ c2m) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n) return;
     int32_t c = m2c[m];
-    const int4 r = qrec_c[c];
-    qrec[m] = r; // .w is the caller index
-    qpos[m] = (uint64_t)(uint32_t)r.x | ((uint64_t)(uint32_t)r.y << 21) | ((uint64_t)(uint32_t)r.z << 42);
+    qpos[m] = qpos_c[c];
     c2m[c] = (int32_t)m;
 }
 
@@ -114,7 +112,8 @@ static constexpr uint64_t KNN_SAT = (1ull << 33) - 1;
 // slots, slot t asks for Morton vertex qlist[t] (-1: none), row t of nbr.
 // A queued query is recorded by its slot.
 template <int KP, bool D32, bool QUERY = false>
-__global__ void __launch_bounds__(128, 4) knn_kernel(const int4 *__restrict__ qrec, const int2 *__restrict__ cell_se,
+__global__ void __launch_bounds__(128, 4) knn_kernel(const uint64_t *__restrict__ qpos, const int32_t *__restrict__ m2c,
+                                                  const int2 *__restrict__ cell_se,
                                                   int64_t n, int k, int level, int64_t r2_max,
                                                   const int32_t *__restrict__ c2m, int32_t *__restrict__ nbr,
                                                   int32_t *__restrict__ redo, int32_t *__restrict__ redo_count,
@@ -128,8 +127,8 @@ __global__ void __launch_bounds__(128, 4) knn_kernel(const int4 *__restrict__ qr
         for (int i = 0; i < KP; i++) nbr[t * KP + i] = -1;
         return;
     }
-    const int4 qr = qrec[m];
-    const int32_t qx = qr.x, qy = qr.y, qz = qr.z;
+    const uint64_t qp = qpos[m];
+    const int32_t qx = (int32_t)(qp & PG_QMASK), qy = (int32_t)((qp >> 21) & PG_QMASK), qz = (int32_t)(qp >> 42);
     const int sh = PG_QBITS - level;
     const int G = 1 << level;
     const int64_t cs = (int64_t)1 << sh;
@@ -181,21 +180,23 @@ __global__ void __launch_bounds__(128, 4) knn_kernel(const int4 *__restrict__ qr
             const int32_t p1 = se.x + se.y;
             for (int32_t p = se.x; p < p1; p++) {
                 if (p == m) continue;
-                const int4 c = qrec[p];
+                const uint64_t c = qpos[p];
+                const int32_t cx_ = (int32_t)(c & PG_QMASK), cy_ = (int32_t)((c >> 21) & PG_QMASK),
+                              cz_ = (int32_t)(c >> 42);
                 uint64_t key;
                 if (D32) {
-                    const int32_t ex = c.x - qx, ey = c.y - qy, ez = c.z - qz;
+                    const int32_t ex = cx_ - qx, ey = cy_ - qy, ez = cz_ - qz;
                     const uint32_t d2 = (uint32_t)(ex * ex) + (uint32_t)(ey * ey) + (uint32_t)(ez * ez);
                     if (d2 > worst32) continue;
                     if (r2_max >= 0 && (int64_t)d2 > r2_max) continue;
-                    key = ((uint64_t)d2 << 31) | (uint64_t)(uint32_t)c.w;
+                    key = ((uint64_t)d2 << 31) | (uint64_t)(uint32_t)m2c[p]; // the caller id breaks ties
                 } else {
-                    const int64_t ex = c.x - qx, ey = c.y - qy, ez = c.z - qz;
+                    const int64_t ex = cx_ - qx, ey = cy_ - qy, ez = cz_ - qz;
                     const int64_t d2 = ex * ex + ey * ey + ez * ez;
                     const uint64_t dk = d2 < (int64_t)KNN_SAT ? (uint64_t)d2 : KNN_SAT;
                     if ((dk << 31) > worst) continue;
                     if (r2_max >= 0 && d2 > r2_max) continue;
-                    key = (dk << 31) | (uint64_t)(uint32_t)c.w;
+                    key = (dk << 31) | (uint64_t)(uint32_t)m2c[p];
                 }
                 if (key >= worst) continue;
                 // insert, shifting larger keys up
@@ -486,7 +487,8 @@ __global__ void __launch_bounds__(KE_THREADS, 4) knn_est_kernel(
 // u of nbr. With saved_keys, query t resumes at ring 2 from the first-ring
 // kernel's list (entry t of the queue).
 template <int KP, bool QUERY>
-__global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__ qrec,
+__global__ void __launch_bounds__(128) knn_exact_kernel(const uint64_t *__restrict__ qpos,
+                                                        const int32_t *__restrict__ m2c,
                                                         const int2 *__restrict__ cell_se,
                                                         const int32_t *__restrict__ c2m, const int32_t *__restrict__ list,
                                                         const int32_t *__restrict__ d_count, int64_t nq, int k,
@@ -505,8 +507,8 @@ __global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__
         if (lane < KP) row[lane] = -1;
         return;
     }
-    const int4 qr = qrec[m];
-    const int32_t qx = qr.x, qy = qr.y, qz = qr.z;
+    const uint64_t qp = qpos[m];
+    const int32_t qx = (int32_t)(qp & PG_QMASK), qy = (int32_t)((qp >> 21) & PG_QMASK), qz = (int32_t)(qp >> 42);
     const int sh = PG_QBITS - level;
     const int G = 1 << level;
     const int64_t cs = (int64_t)1 << sh;
@@ -575,12 +577,15 @@ __global__ void __launch_bounds__(128) knn_exact_kernel(const int4 *__restrict__
                     bool cand = false;
                     if (p < p1) {
                         if (p != m) {
-                            const int4 cq = qrec[p];
-                            const int64_t ex = cq.x - qx, ey = cq.y - qy, ez = cq.z - qz;
+                            const uint64_t cq = qpos[p];
+                            const int64_t ex = (int64_t)(cq & PG_QMASK) - qx, ey = (int64_t)((cq >> 21) & PG_QMASK) - qy,
+                                          ez = (int64_t)(cq >> 42) - qz;
                             d2 = ex * ex + ey * ey + ez * ez;
-                            id = cq.w;
-                            cand = d2 <= worst_d && (r2_max < 0 || d2 <= r2_max) &&
-                                   knn_less(d2, id, worst_d, worst_i);
+                            cand = d2 <= worst_d && (r2_max < 0 || d2 <= r2_max);
+                            if (cand) { // the caller id breaks ties
+                                id = m2c[p];
+                                cand = knn_less(d2, id, worst_d, worst_i);
+                            }
                         }
                         p++;
                     }
@@ -659,11 +664,11 @@ static pg_status launch_knn_t(pg_graph *g, cudaStream_t s) {
                 g->qpos, g->m2c, g->cell_se, n, g->k, g->level, g->r2_max, g->c2m, g->nbr, redo, cnt, redo_keys, redo_cap);
             pg_count_launches(1);
         } else if (g->level >= 7) {
-            knn_kernel<KP, true><<<pg_blocks(n, 128), 128, 0, s>>>(g->qrec, g->cell_se, n, g->k, g->level, g->r2_max,
+            knn_kernel<KP, true><<<pg_blocks(n, 128), 128, 0, s>>>(g->qpos, g->m2c, g->cell_se, n, g->k, g->level, g->r2_max,
                                                                   g->c2m, g->nbr, redo, cnt, redo_keys, redo_cap);
             pg_count_launches(1);
         } else {
-            knn_kernel<KP, false><<<pg_blocks(n, 128), 128, 0, s>>>(g->qrec, g->cell_se, n, g->k, g->level,
+            knn_kernel<KP, false><<<pg_blocks(n, 128), 128, 0, s>>>(g->qpos, g->m2c, g->cell_se, n, g->k, g->level,
                                                                    g->r2_max, g->c2m, g->nbr, redo, cnt, nullptr, 0);
             pg_count_launches(1);
         }
@@ -675,7 +680,7 @@ static pg_status launch_knn_t(pg_graph *g, cudaStream_t s) {
         st = PG_ERR_CUDA;
     g->knn_exact = h_cnt;
     if (st == PG_OK && h_cnt > 0) {
-        knn_exact_kernel<KP, false><<<pg_blocks(32 * (int64_t)h_cnt, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, redo, cnt, 0,
+        knn_exact_kernel<KP, false><<<pg_blocks(32 * (int64_t)h_cnt, 128), 128, 0, s>>>(g->qpos, g->m2c, g->cell_se, g->c2m, redo, cnt, 0,
                                                                          g->k, g->level, g->r2_max, g->nbr, redo_keys,
                                                                          redo_cap);
         pg_count_launches(1);
@@ -703,7 +708,7 @@ pg_status pg_launch_knn_queries(const pg_graph *g, const int32_t *qm, int64_t nq
     const int kp = pg_row_width(k);
     if (g->level < 7) { // 64-bit distances: every query through the exact search
 #define Q(KP)                                                                                                   \
-    knn_exact_kernel<KP, true><<<pg_blocks(32 * nq, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, qm, nullptr, nq, k, \
+    knn_exact_kernel<KP, true><<<pg_blocks(32 * nq, 128), 128, 0, s>>>(g->qpos, g->m2c, g->cell_se, g->c2m, qm, nullptr, nq, k, \
                                                                  g->level, -1, out, nullptr, 0)
         switch (kp) {
             case 4: Q(4); break;
@@ -731,9 +736,9 @@ pg_status pg_launch_knn_queries(const pg_graph *g, const int32_t *qm, int64_t nq
         knn_est_kernel<KP, true><<<pg_blocks(nq, KE_THREADS), KE_THREADS, 0, s>>>(                               \
             g->qpos, g->m2c, g->cell_se, nq, k, g->level, -1, g->c2m, out, redo, cnt, keys, nq, qm);                     \
     else                                                                                                         \
-        knn_kernel<KP, true, true><<<pg_blocks(nq, 128), 128, 0, s>>>(g->qrec, g->cell_se, nq, k, g->level, -1,  \
+        knn_kernel<KP, true, true><<<pg_blocks(nq, 128), 128, 0, s>>>(g->qpos, g->m2c, g->cell_se, nq, k, g->level, -1,  \
                                                                      g->c2m, out, redo, cnt, keys, nq, qm);      \
-    knn_exact_kernel<KP, true><<<pg_blocks(32 * nq, 128), 128, 0, s>>>(g->qrec, g->cell_se, g->c2m, redo, cnt, nq, k, \
+    knn_exact_kernel<KP, true><<<pg_blocks(32 * nq, 128), 128, 0, s>>>(g->qpos, g->m2c, g->cell_se, g->c2m, redo, cnt, nq, k, \
                                                                  g->level, -1, out, keys, nq, qm)
         switch (kp) {
             case 4: Q(4); break;
@@ -808,19 +813,18 @@ extern "C" pg_status pg_build_graph(const pg_vertices *v, int64_t n, const pg_bu
     pg_status st = PG_OK;
     int64_t ncells = (int64_t)1 << (3 * g->level);
     uint32_t *keys = nullptr;
-    int4 *qrec_c = nullptr;
+    uint64_t *qpos_c = nullptr;
     int32_t *cell_start = nullptr;
 #define A(ptr, bytes) \
     if (st == PG_OK) st = pg_alloc(g, (void **)&(ptr), (bytes), s)
     A(g->flags, sizeof(int32_t) * 4);
     A(g->m2c, sizeof(int32_t) * n);
     A(g->c2m, sizeof(int32_t) * n);
-    A(g->qrec, sizeof(int4) * n);
     A(g->qpos, sizeof(uint64_t) * n);
     A(g->cell_se, sizeof(int2) * ncells);
     A(g->nbr, sizeof(int32_t) * n * g->kp);
     if (st == PG_OK) st = pg_alloc(nullptr, (void **)&keys, sizeof(uint32_t) * (n > 0 ? n : 1), s);
-    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&qrec_c, sizeof(int4) * (n > 0 ? n : 1), s);
+    if (st == PG_OK) st = pg_alloc(nullptr, (void **)&qpos_c, sizeof(uint64_t) * (n > 0 ? n : 1), s);
     if (st == PG_OK) st = pg_alloc(nullptr, (void **)&cell_start, sizeof(int32_t) * (ncells + 1), s);
 #undef A
     if (st == PG_OK) {
@@ -828,12 +832,12 @@ extern "C" pg_status pg_build_graph(const pg_vertices *v, int64_t n, const pg_bu
     }
     if (st == PG_OK && n > 0) {
         quantize_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(v->px, v->py, v->pz, n, g->lo[0], g->lo[1], g->lo[2],
-                                                          g->scale, g->level, keys, g->m2c, qrec_c, g->flags);
+                                                          g->scale, g->level, keys, g->m2c, qpos_c, g->flags);
         pg_count_launches(1);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
         if (st == PG_OK) st = pg_radix_sort(g, keys, g->m2c, n, 3 * g->level, s);
         if (st == PG_OK) {
-            permute_build_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(g->m2c, qrec_c, n, g->qrec, g->qpos, g->c2m);
+            permute_build_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(g->m2c, qpos_c, n, g->qpos, g->c2m);
             pg_count_launches(1);
             if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
         }
@@ -855,7 +859,7 @@ extern "C" pg_status pg_build_graph(const pg_vertices *v, int64_t n, const pg_bu
                                      : pg_launch_knn(g, s);
     }
     if (keys) cudaFreeAsync(keys, s);
-    if (qrec_c) cudaFreeAsync(qrec_c, s);
+    if (qpos_c) cudaFreeAsync(qpos_c, s);
     if (cell_start) cudaFreeAsync(cell_start, s);
     int32_t hflags = 0;
     if (st == PG_OK) {
@@ -918,7 +922,6 @@ static pg_status graph_free_all(pg_graph *g) {
     pg_free(g, (void **)&g->flags, sizeof(int32_t) * 4);
     pg_free(g, (void **)&g->m2c, 4 * n);
     pg_free(g, (void **)&g->c2m, 4 * n);
-    pg_free(g, (void **)&g->qrec, 16 * n);
     pg_free(g, (void **)&g->qpos, 8 * n);
     pg_free(g, (void **)&g->cell_se, 8 * (ncells - 1));
     pg_free(g, (void **)&g->nbr, 4 * n * kp);

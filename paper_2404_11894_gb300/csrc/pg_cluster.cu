@@ -23,11 +23,11 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
     return z ^ (z >> 31);
 }
 
-__global__ void centre_flag_kernel(const int4 *__restrict__ qrec, int64_t n, uint64_t seed, uint64_t thr,
+__global__ void centre_flag_kernel(const int32_t *__restrict__ m2c, int64_t n, uint64_t seed, uint64_t thr,
                                    int32_t *__restrict__ flag) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n) return;
-    flag[m] = splitmix64_at(seed, (uint64_t)(uint32_t)qrec[m].w) < thr ? 1 : 0;
+    flag[m] = splitmix64_at(seed, (uint64_t)(uint32_t)m2c[m]) < thr ? 1 : 0; // by caller index
 }
 
 __global__ void set_one_kernel(int32_t *__restrict__ flag, const int32_t *__restrict__ c2m) { flag[c2m[0]] = 1; }
@@ -48,13 +48,14 @@ __device__ __forceinline__ bool centre_less(int64_t da, int32_t ia, int64_t db, 
 
 // Nearest centre of every vertex: rings of cells around the vertex's own,
 // until the best distance is below the distance to any unscanned cell.
-__global__ void __launch_bounds__(128) nearest_centre_kernel(const int4 *__restrict__ qrec,
+__global__ void __launch_bounds__(128) nearest_centre_kernel(const uint64_t *__restrict__ qpos,
+                                                             const int32_t *__restrict__ m2c,
                                                              const int32_t *__restrict__ cent,
                                                              const int2 *__restrict__ c_se, int level, int64_t n,
                                                              int32_t *__restrict__ owner) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n) return;
-    const int4 qr = qrec[m];
+    const int3 qr = pg_qpos_unpack(qpos[m]);
     const int sh = PG_QBITS - level;
     const int G = 1 << level;
     const int64_t cs = (int64_t)1 << sh;
@@ -71,13 +72,17 @@ __global__ void __launch_bounds__(128) nearest_centre_kernel(const int4 *__restr
             if (x < 0 || x >= G || y < 0 || y >= G || z < 0 || z >= G) continue;
             const int2 se = c_se[(int64_t)x + ((int64_t)y << level) + ((int64_t)z << (2 * level))];
             for (int32_t i = se.x; i < se.x + se.y; i++) {
-                const int4 cq = qrec[cent[i]];
+                const int32_t cm = cent[i];
+                const int3 cq = pg_qpos_unpack(qpos[cm]);
                 const int64_t ex = cq.x - qr.x, ey = cq.y - qr.y, ez = cq.z - qr.z;
                 const int64_t d2 = ex * ex + ey * ey + ez * ez;
-                if (centre_less(d2, cq.w, best_d, best_id)) {
-                    best_d = d2;
-                    best_id = cq.w;
-                    best = i;
+                if (d2 <= best_d) { // the caller index breaks ties
+                    const int32_t cid = m2c[cm];
+                    if (centre_less(d2, cid, best_d, best_id)) {
+                        best_d = d2;
+                        best_id = cid;
+                        best = i;
+                    }
                 }
             }
         }
@@ -205,7 +210,7 @@ pg_status pg_launch_clusters(pg_graph *g, const uint32_t *keys, int32_t K, uint6
     const uint64_t thr = 0xFFFFFFFFFFFFFFFFull / (uint64_t)K;
     int32_t h_tot = 0;
     if (st == PG_OK) {
-        centre_flag_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(g->qrec, n, seed, thr, flag);
+        centre_flag_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(g->m2c, n, seed, thr, flag);
         pg_count_launches(1);
         PG_LAUNCH_CHECK();
         if (cudaMemcpyAsync(pos, flag, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) st = PG_ERR_CUDA;
@@ -234,7 +239,7 @@ pg_status pg_launch_clusters(pg_graph *g, const uint32_t *keys, int32_t K, uint6
     }
     if (st == PG_OK) {
         centre_cell_table_kernel<<<pg_blocks(ncells, 256), 256, 0, s>>>(cstart_cells, ncells, level, c_se);
-        nearest_centre_kernel<<<pg_blocks(n, 128), 128, 0, s>>>(g->qrec, cent, c_se, level, n, owner);
+        nearest_centre_kernel<<<pg_blocks(n, 128), 128, 0, s>>>(g->qpos, g->m2c, cent, c_se, level, n, owner);
         identity_kernel<<<pg_blocks(n, 256), 256, 0, s>>>(sorted_m, n);
         pg_count_launches(3);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;

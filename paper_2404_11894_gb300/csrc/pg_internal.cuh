@@ -43,8 +43,7 @@ struct pg_graph {
     // ---- graph build (Morton order m) ----
     int32_t *m2c = nullptr;        // m -> caller index
     int32_t *c2m = nullptr;        // caller -> m
-    int4 *qrec = nullptr;          // (qx, qy, qz, caller index), m order
-    uint64_t *qpos = nullptr;      // qx | qy << 21 | qz << 42, m order (half the bytes of qrec)
+    uint64_t *qpos = nullptr;      // quantised position qx | qy << 21 | qz << 42, m order
     int2 *cell_se = nullptr;       // (start, count) per cell, index x + G (y + G z)
     int32_t *nbr = nullptr;        // [n][kp], m-space neighbour ids, -1 padded; slot 0 = self
     int64_t knn_exact = 0;         // queries resolved by the exact neighbour kernel
@@ -209,6 +208,11 @@ __device__ __forceinline__ float hg_eval_dg(float g, float opd, float *rho_out) 
     float C = (1.0f - g * g) * inv4pi;
     *rho_out = C * r3;
     return -2.0f * g * inv4pi * r3 - 3.0f * C * ((g - 1.0f) + opd) * (r3 * r * r);
+}
+
+// quantised position packed as qx | qy << 21 | qz << 42
+__device__ __forceinline__ int3 pg_qpos_unpack(uint64_t c) {
+    return make_int3((int32_t)(c & PG_QMASK), (int32_t)((c >> 21) & PG_QMASK), (int32_t)(c >> 42));
 }
 
 __device__ __forceinline__ uint32_t part1by2(uint32_t x) {
