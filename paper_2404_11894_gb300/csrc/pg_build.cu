@@ -283,10 +283,11 @@ static constexpr uint64_t KNN_FRESH = UINT64_MAX - 1;
 // Here each query
 //   1. reads the vertex counts N of its 27 cells from the cell table and
 //      takes the radius that would hold k - 1 of them at uniform density,
-//      r^2 = (81 cs^3 (k - 1) / (4 pi (N - 1)))^(2/3), times 1.44 (1.2 in
-//      radius) as its threshold T (any T gives the same list; this one
-//      buffers about 26 candidates per query on the cloud, and 1 % of the
-//      queries fall outside 15..48),
+//      r^2 = (81 cs^3 (k - 1) / (4 pi (N - 1)))^(2/3), times 1.5625 (1.25
+//      in radius) as its threshold T (any T gives the same list; this one
+//      buffers about 29 candidates per query on the cloud, and 0.2 % of the
+//      queries fall outside 15..48; 1.2 in radius left 0.8 % with fewer
+//      than 15 and was 0.6 % slower, 1.1 in radius 37 % slower),
 //   2. scans the cells that have a point closer than T and appends the
 //      candidates with d2 < T to a shared-memory buffer (no insertion),
 //   3. inserts the buffered candidates into its sorted register list; the
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(KE_THREADS, 4) knn_est_kernel(
         if (nb - 1 > km1) {
             const float c3 = (float)cs * (float)cs * (float)cs;
             const float r2 = cbrtf(81.0f * c3 * (float)km1 / (12.566370614359172f * (float)(nb - 1)));
-            const float tf = 1.44f * r2 * r2;
+            const float tf = 1.5625f * r2 * r2;
             if (tf < 3.3e9f) T = (uint32_t)tf;
         }
         // a radius limit caps the threshold; below the cap the list is exact
