@@ -98,185 +98,17 @@ __device__ __forceinline__ bool knn_less(int64_t da, int32_t ia, int64_t db, int
     return da < db || (da == db && ia < ib);
 }
 
-// Fast path: one thread per query over its own cell and the 26 around it;
-// queries that need more rings go to the exact kernel. Each list entry is one
-// 64-bit key (d2 << 31) | caller id, which orders like (d2, id) while
-// d2 < 2^33. With cells of at most 2^14 quantisation units (grid level >= 7)
-// every candidate of the 3x3x3 block is closer than two cells per axis, so
-// d2 < 3 * 2^30 and the distance is computed in 32-bit arithmetic (D32);
-// otherwise in 64-bit, where a distance of 2^33 or more saturates and a final
-// list holding one is redone exactly.
+// A first-ring list entry is one 64-bit key (d2 << 31) | caller id, which
+// orders like (d2, id) while d2 < KNN_SAT.
 static constexpr uint64_t KNN_SAT = (1ull << 33) - 1;
-
-// QUERY = false: query t is vertex t, row t of nbr. QUERY = true: n query
-// slots, slot t asks for Morton vertex qlist[t] (-1: none), row t of nbr.
-// A queued query is recorded by its slot.
-template <int KP, bool D32, bool QUERY = false>
-__global__ void __launch_bounds__(128, 4) knn_kernel(const uint64_t *__restrict__ qpos, const int32_t *__restrict__ m2c,
-                                                  const int2 *__restrict__ cell_se,
-                                                  int64_t n, int k, int level, int64_t r2_max,
-                                                  const int32_t *__restrict__ c2m, int32_t *__restrict__ nbr,
-                                                  int32_t *__restrict__ redo, int32_t *__restrict__ redo_count,
-                                                  uint64_t *__restrict__ redo_keys, int64_t redo_cap,
-                                                  const int32_t *__restrict__ qlist = nullptr) {
-    constexpr int M = KP - 1;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const int64_t m = QUERY ? (int64_t)qlist[t] : t;
-    if (QUERY && m < 0) {
-        for (int i = 0; i < KP; i++) nbr[t * KP + i] = -1;
-        return;
-    }
-    const uint64_t qp = qpos[m];
-    const int32_t qx = (int32_t)(qp & PG_QMASK), qy = (int32_t)((qp >> 21) & PG_QMASK), qz = (int32_t)(qp >> 42);
-    const int sh = PG_QBITS - level;
-    const int G = 1 << level;
-    const int64_t cs = (int64_t)1 << sh;
-    const int cx = qx >> sh, cy = qy >> sh, cz = qz >> sh;
-    const int km1 = k - 1;
-    // ascending list; the lowest M - (k-1) slots hold key 0, which no
-    // candidate displaces (comparisons are strict), so the (k-1)-th real
-    // entry is always slot M-1
-    const int pad = M - km1;
-    uint64_t bk[M > 0 ? M : 1];
-#pragma unroll
-    for (int i = 0; i < M; i++) bk[i] = i < pad ? 0ull : UINT64_MAX;
-    uint64_t worst = UINT64_MAX;
-    uint32_t worst32 = UINT32_MAX; // worst's distance part, clamped (D32)
-    int found = 0;
-    // squared distance from the query to the neighbour cell across each face
-    // of its own cell: low side (offset in cell + 1)^2, high side (cs - offset)^2
-    using GT = typename std::conditional<D32, uint32_t, uint64_t>::type;
-    GT glo[3], ghi[3];
-    {
-        const int32_t q3[3] = {qx, qy, qz};
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const GT o = (GT)(q3[a] & (int32_t)(cs - 1));
-            glo[a] = (o + 1) * (o + 1);
-            ghi[a] = ((GT)cs - o) * ((GT)cs - o);
-        }
-    }
-    if (km1 > 0) {
-        for (int ci = 0; ci < 27; ci++) {
-            int dx = 0, dy = 0, dz = 0;
-            if (ci > 0) {
-                const int o = c_ring1[ci - 1];
-                dx = (o & 3) - 1;
-                dy = ((o >> 2) & 3) - 1;
-                dz = ((o >> 4) & 3) - 1;
-            }
-            const int x = cx + dx, y = cy + dy, z = cz + dz;
-            if (x < 0 || x >= G || y < 0 || y >= G || z < 0 || z >= G) continue;
-            if (ci > 0) {
-                // no vertex of a cell whose nearest point is already farther
-                // than the (k-1)-th entry can enter the list
-                const GT lb = (dx < 0 ? glo[0] : (dx > 0 ? ghi[0] : (GT)0)) +
-                              (dy < 0 ? glo[1] : (dy > 0 ? ghi[1] : (GT)0)) +
-                              (dz < 0 ? glo[2] : (dz > 0 ? ghi[2] : (GT)0));
-                if (D32 ? lb > (GT)worst32 : ((worst >> 31) < KNN_SAT && (uint64_t)lb > (worst >> 31))) continue;
-            }
-            const int2 se = cell_se[(int64_t)x + ((int64_t)y << level) + ((int64_t)z << (2 * level))];
-            const int32_t p1 = se.x + se.y;
-            for (int32_t p = se.x; p < p1; p++) {
-                if (p == m) continue;
-                const uint64_t c = qpos[p];
-                const int32_t cx_ = (int32_t)(c & PG_QMASK), cy_ = (int32_t)((c >> 21) & PG_QMASK),
-                              cz_ = (int32_t)(c >> 42);
-                uint64_t key;
-                if (D32) {
-                    const int32_t ex = cx_ - qx, ey = cy_ - qy, ez = cz_ - qz;
-                    const uint32_t d2 = (uint32_t)(ex * ex) + (uint32_t)(ey * ey) + (uint32_t)(ez * ez);
-                    if (d2 > worst32) continue;
-                    if (r2_max >= 0 && (int64_t)d2 > r2_max) continue;
-                    key = ((uint64_t)d2 << 31) | (uint64_t)(uint32_t)m2c[p]; // the caller id breaks ties
-                } else {
-                    const int64_t ex = cx_ - qx, ey = cy_ - qy, ez = cz_ - qz;
-                    const int64_t d2 = ex * ex + ey * ey + ez * ez;
-                    const uint64_t dk = d2 < (int64_t)KNN_SAT ? (uint64_t)d2 : KNN_SAT;
-                    if ((dk << 31) > worst) continue;
-                    if (r2_max >= 0 && d2 > r2_max) continue;
-                    key = (dk << 31) | (uint64_t)(uint32_t)m2c[p];
-                }
-                if (key >= worst) continue;
-                // insert, shifting larger keys up
-#pragma unroll
-                for (int i = M - 1; i > 0; --i) {
-                    const uint64_t prev = bk[i - 1];
-                    if (key < bk[i]) bk[i] = key < prev ? prev : key;
-                }
-                if (key < bk[0]) bk[0] = key;
-                found++;
-                worst = bk[M - 1];
-                const uint64_t wd = worst >> 31;
-                worst32 = wd > 0xffffffffull ? 0xffffffffu : (uint32_t)wd;
-            }
-        }
-        // done iff the (k-1)-th entry is closer than anything outside the block
-        int64_t bnd = INT64_MAX;
-        {
-            const int cc[3] = {cx, cy, cz};
-            const int32_t q[3] = {qx, qy, qz};
-#pragma unroll
-            for (int a2 = 0; a2 < 3; a2++) {
-                if (cc[a2] - 1 > 0) {
-                    const int64_t dlo = (int64_t)q[a2] - (int64_t)(cc[a2] - 1) * cs + 1;
-                    bnd = dlo < bnd ? dlo : bnd;
-                }
-                if (cc[a2] + 1 < G - 1) {
-                    const int64_t dhi = (int64_t)(cc[a2] + 2) * cs - q[a2];
-                    bnd = dhi < bnd ? dhi : bnd;
-                }
-            }
-        }
-        bool done = bnd == INT64_MAX; // whole grid scanned
-        if (!done) {
-            const int64_t bnd2 = bnd * bnd;
-            const int64_t worst_d = worst == UINT64_MAX ? INT64_MAX : (int64_t)(worst >> 31);
-            done = (found >= km1 && worst_d < bnd2) || (r2_max >= 0 && bnd2 > r2_max);
-        }
-        bool saturated = false;
-#pragma unroll
-        for (int i = 0; i < M; i++)
-            if (i >= pad && bk[i] != UINT64_MAX && (bk[i] >> 31) >= KNN_SAT) saturated = true;
-        // queue the query for the exact kernel; one counter atomic per
-        // converged group of lanes, not one per query (a single hot address)
-        const bool need = !done || saturated;
-        const unsigned am = __activemask();
-        const unsigned need_mask = __ballot_sync(am, need);
-        if (need) {
-            const int lane = threadIdx.x & 31;
-            const int leader = __ffs(need_mask) - 1;
-            int32_t base = 0;
-            if (lane == leader) base = atomicAdd(redo_count, __popc(need_mask));
-            base = __shfl_sync(need_mask, base, leader);
-            const int32_t slot = base + __popc(need_mask & ((1u << lane) - 1u));
-            redo[slot] = (int32_t)t;
-            // with exact 32-bit distances the list holds the true k-1 nearest
-            // of the 27 cells: the exact kernel resumes from it at ring 2
-            if (D32 && slot < redo_cap) {
-#pragma unroll
-                for (int i = 0; i < M; i++) redo_keys[(int64_t)slot * M + i] = bk[i];
-            }
-            return;
-        }
-    }
-    int32_t *row = nbr + t * KP;
-    row[0] = (int32_t)m;
-#pragma unroll
-    for (int i = 0; i < M; i++) {
-        const int pos = i - pad; // rank among the k-1 others
-        if (pos >= 0) row[1 + pos] = bk[i] != UINT64_MAX ? c2m[(int32_t)(bk[i] & 0x7fffffffu)] : -1;
-    }
-    for (int pos = km1; pos < M; pos++) row[1 + pos] = -1;
-}
 
 // Marker in a queued query's saved list: no list was kept, the exact kernel
 // starts from the query's own cell.
 static constexpr uint64_t KNN_FRESH = UINT64_MAX - 1;
 
-// First ring with 32-bit distances (grid level >= 7) and a threshold from
-// the local density. With one thread per query and the candidates of a
+// First ring: one thread per query over its own cell and the 26 around it,
+// with a threshold from the local density; queries that need more rings go
+// to the exact kernel. With one thread per query and the candidates of a
 // warp's queries met in step, some lane wanted an insertion into its sorted
 // list at almost every candidate, so the warp ran the insertion network for
 // nearly all of them (about 60 % of this kernel's time went to insertions).
@@ -297,19 +129,27 @@ static constexpr uint64_t KNN_FRESH = UINT64_MAX - 1;
 // (d2, id) of the 27 cells, as inserting every candidate gives; a query with
 // fewer (and T below its radius limit) or with an overflowing buffer is
 // queued for the exact kernel, which starts from its own cell.
-constexpr int KE_THREADS = 128;
+// D32: 32-bit squared distances (grid level >= 7: cells of at most 2^14
+// units, so d2 < 3 * (2 cs)^2 <= 3 * 2^30 inside the block); otherwise
+// 64-bit, and a buffered candidate at d2 >= 2^33 - 1 (whose key would
+// saturate) sends the query to the exact kernel.
+template <int KP>
+constexpr int ke_threads() { return KP <= 16 ? 128 : 64; } // the buffer is 3 KP entries a thread
 
-template <int KP, bool QUERY>
-__global__ void __launch_bounds__(KE_THREADS, 4) knn_est_kernel(
+template <int KP, bool QUERY, bool D32>
+__global__ void __launch_bounds__(ke_threads<KP>(), 4) knn_est_kernel(
     const uint64_t *__restrict__ qpos, const int32_t *__restrict__ m2c, const int2 *__restrict__ cell_se, int64_t n, int k, int level, int64_t r2_max,
     const int32_t *__restrict__ c2m, int32_t *__restrict__ nbr, int32_t *__restrict__ redo,
     int32_t *__restrict__ redo_count, uint64_t *__restrict__ redo_keys, int64_t redo_cap,
     const int32_t *__restrict__ qlist = nullptr) {
     constexpr int M = KP - 1;
     constexpr int CAP = 3 * KP;
-    __shared__ int32_t buf[CAP][KE_THREADS];
+    constexpr int NT = ke_threads<KP>();
+    using DT = typename std::conditional<D32, uint32_t, uint64_t>::type;
+    constexpr DT DT_MAX = (DT)~(DT)0;
+    __shared__ int32_t buf[CAP][NT];
     const int tx = threadIdx.x;
-    const int64_t t = (int64_t)blockIdx.x * KE_THREADS + tx;
+    const int64_t t = (int64_t)blockIdx.x * NT + tx;
     if (t >= n) return; // no block-wide barrier below
     const int64_t m = QUERY ? (int64_t)qlist[t] : t;
     if (QUERY && m < 0) {
@@ -320,16 +160,16 @@ __global__ void __launch_bounds__(KE_THREADS, 4) knn_est_kernel(
     const int32_t qx = (int32_t)(qp & PG_QMASK), qy = (int32_t)((qp >> 21) & PG_QMASK), qz = (int32_t)(qp >> 42);
     const int sh = PG_QBITS - level;
     const int G = 1 << level;
-    const uint32_t cs = 1u << sh;
+    const DT cs = (DT)1 << sh;
     const int cx = qx >> sh, cy = qy >> sh, cz = qz >> sh;
     const int km1 = k - 1;
     const int pad = M - km1;
-    uint32_t glo[3], ghi[3];
+    DT glo[3], ghi[3];
     {
         const int32_t q3[3] = {qx, qy, qz};
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            const uint32_t o = (uint32_t)q3[a] & (cs - 1);
+            const DT o = (DT)q3[a] & (cs - 1);
             glo[a] = (o + 1) * (o + 1);
             ghi[a] = (cs - o) * (cs - o);
         }
@@ -347,24 +187,24 @@ __global__ void __launch_bounds__(KE_THREADS, 4) knn_est_kernel(
             if (x < 0 || x >= G || y < 0 || y >= G || z < 0 || z >= G) continue;
             nb += cell_se[(int64_t)x + ((int64_t)y << level) + ((int64_t)z << (2 * level))].y;
         }
-        // d2 < 3 * (2 cs)^2 <= 3 * 2^30 inside the block (cs <= 2^14)
-        uint32_t T = 0xffffffffu;
+        DT T = DT_MAX;
         if (nb - 1 > km1) {
             const float c3 = (float)cs * (float)cs * (float)cs;
             const float r2 = cbrtf(81.0f * c3 * (float)km1 / (12.566370614359172f * (float)(nb - 1)));
             const float tf = 1.5625f * r2 * r2;
-            if (tf < 3.3e9f) T = (uint32_t)tf;
+            if (tf < (D32 ? 3.3e9f : 1.0e19f)) T = (DT)tf;
         }
         // a radius limit caps the threshold; below the cap the list is exact
         // whatever the count
         bool capped = false;
-        if (r2_max >= 0 && (int64_t)T > r2_max) {
-            T = (uint32_t)(r2_max + 1);
+        if (r2_max >= 0 && (uint64_t)T > (uint64_t)r2_max) {
+            T = (DT)(r2_max + 1);
             capped = true;
         }
-        if (T == 0xffffffffu) capped = true; // every candidate of the block is buffered
+        if (T == DT_MAX) capped = true; // every candidate of the block is buffered
         // 2. buffer the candidates closer than T
         int cnt = 0;
+        bool sat = false;
         for (int ci = 0; ci < 27; ci++) {
             int dx = 0, dy = 0, dz = 0;
             if (ci > 0) {
@@ -376,9 +216,9 @@ __global__ void __launch_bounds__(KE_THREADS, 4) knn_est_kernel(
             const int x = cx + dx, y = cy + dy, z = cz + dz;
             if (x < 0 || x >= G || y < 0 || y >= G || z < 0 || z >= G) continue;
             if (ci > 0) {
-                const uint32_t lb = (dx < 0 ? glo[0] : (dx > 0 ? ghi[0] : 0u)) +
-                                    (dy < 0 ? glo[1] : (dy > 0 ? ghi[1] : 0u)) +
-                                    (dz < 0 ? glo[2] : (dz > 0 ? ghi[2] : 0u));
+                const DT lb = (dx < 0 ? glo[0] : (dx > 0 ? ghi[0] : (DT)0)) +
+                              (dy < 0 ? glo[1] : (dy > 0 ? ghi[1] : (DT)0)) +
+                              (dz < 0 ? glo[2] : (dz > 0 ? ghi[2] : (DT)0));
                 if (lb >= T) continue; // no point of the cell is closer than T
             }
             const int2 se = cell_se[(int64_t)x + ((int64_t)y << level) + ((int64_t)z << (2 * level))];
@@ -388,22 +228,29 @@ __global__ void __launch_bounds__(KE_THREADS, 4) knn_est_kernel(
                 const uint64_t c = qpos[p];
                 const int32_t ex = (int32_t)(c & PG_QMASK) - qx, ey = (int32_t)((c >> 21) & PG_QMASK) - qy,
                               ez = (int32_t)(c >> 42) - qz;
-                const uint32_t d2 = (uint32_t)(ex * ex) + (uint32_t)(ey * ey) + (uint32_t)(ez * ez);
+                DT d2;
+                if (D32) {
+                    d2 = (DT)((uint32_t)(ex * ex) + (uint32_t)(ey * ey) + (uint32_t)(ez * ez));
+                } else {
+                    d2 = (DT)((int64_t)ex * ex + (int64_t)ey * ey + (int64_t)ez * ez);
+                    sat |= d2 < T && (uint64_t)d2 >= KNN_SAT;
+                }
                 if (d2 >= T) continue;
                 if (cnt < CAP) buf[cnt][tx] = p;
                 cnt++;
             }
         }
         // 3. select: the buffered candidates into the sorted list
-        fresh = cnt > CAP || (cnt < km1 && !capped);
+        fresh = sat || cnt > CAP || (cnt < km1 && !capped);
         found = fresh ? 0 : cnt;
         for (int i = 0; i < found; i++) {
             const int32_t p = buf[i][tx];
             const uint64_t c = qpos[p];
             const int32_t ex = (int32_t)(c & PG_QMASK) - qx, ey = (int32_t)((c >> 21) & PG_QMASK) - qy,
                           ez = (int32_t)(c >> 42) - qz;
-            const uint32_t d2 = (uint32_t)(ex * ex) + (uint32_t)(ey * ey) + (uint32_t)(ez * ez);
-            const uint64_t key = ((uint64_t)d2 << 31) | (uint64_t)(uint32_t)m2c[p]; // caller id
+            const uint64_t d2 = D32 ? (uint64_t)((uint32_t)(ex * ex) + (uint32_t)(ey * ey) + (uint32_t)(ez * ez))
+                                    : (uint64_t)((int64_t)ex * ex + (int64_t)ey * ey + (int64_t)ez * ez);
+            const uint64_t key = (d2 << 31) | (uint64_t)(uint32_t)m2c[p]; // caller id breaks ties
 #pragma unroll
             for (int j = M - 1; j > 0; --j) {
                 const uint64_t prev = bk[j - 1];
@@ -419,11 +266,11 @@ __global__ void __launch_bounds__(KE_THREADS, 4) knn_est_kernel(
 #pragma unroll
             for (int a2 = 0; a2 < 3; a2++) {
                 if (cc[a2] - 1 > 0) {
-                    const int64_t dlo = (int64_t)q[a2] - (int64_t)(cc[a2] - 1) * cs + 1;
+                    const int64_t dlo = (int64_t)q[a2] - (int64_t)(cc[a2] - 1) * (int64_t)cs + 1;
                     bnd = dlo < bnd ? dlo : bnd;
                 }
                 if (cc[a2] + 1 < G - 1) {
-                    const int64_t dhi = (int64_t)(cc[a2] + 2) * cs - q[a2];
+                    const int64_t dhi = (int64_t)(cc[a2] + 2) * (int64_t)cs - q[a2];
                     bnd = dhi < bnd ? dhi : bnd;
                 }
             }
@@ -653,26 +500,21 @@ static pg_status launch_knn_t(pg_graph *g, cudaStream_t s) {
     int32_t *redo = nullptr, *cnt = nullptr;
     uint64_t *redo_keys = nullptr;
     // lists saved for the first redo_cap queued queries (usually all of them)
-    const int64_t redo_cap = g->level >= 7 ? n / 8 + 1024 : 0;
+    const int64_t redo_cap = n / 8 + 1024;
     PG_TRY(pg_alloc(nullptr, (void **)&redo, 4 * (size_t)(n > 0 ? n : 1), s));
     pg_status st = pg_alloc(nullptr, (void **)&cnt, 16, s);
     if (st == PG_OK && redo_cap > 0)
         st = pg_alloc(nullptr, (void **)&redo_keys, 8 * (size_t)redo_cap * (KP - 1 > 0 ? KP - 1 : 1), s);
     if (st == PG_OK && cudaMemsetAsync(cnt, 0, 4, s) != cudaSuccess) st = PG_ERR_CUDA;
     if (st == PG_OK) {
-        if (g->level >= 7 && KP <= 16) {
-            knn_est_kernel<KP, false><<<pg_blocks(n, KE_THREADS), KE_THREADS, 0, s>>>(
+        constexpr int NT = ke_threads<KP>();
+        if (g->level >= 7)
+            knn_est_kernel<KP, false, true><<<pg_blocks(n, NT), NT, 0, s>>>(
                 g->qpos, g->m2c, g->cell_se, n, g->k, g->level, g->r2_max, g->c2m, g->nbr, redo, cnt, redo_keys, redo_cap);
-            pg_count_launches(1);
-        } else if (g->level >= 7) {
-            knn_kernel<KP, true><<<pg_blocks(n, 128), 128, 0, s>>>(g->qpos, g->m2c, g->cell_se, n, g->k, g->level, g->r2_max,
-                                                                  g->c2m, g->nbr, redo, cnt, redo_keys, redo_cap);
-            pg_count_launches(1);
-        } else {
-            knn_kernel<KP, false><<<pg_blocks(n, 128), 128, 0, s>>>(g->qpos, g->m2c, g->cell_se, n, g->k, g->level,
-                                                                   g->r2_max, g->c2m, g->nbr, redo, cnt, nullptr, 0);
-            pg_count_launches(1);
-        }
+        else
+            knn_est_kernel<KP, false, false><<<pg_blocks(n, NT), NT, 0, s>>>(
+                g->qpos, g->m2c, g->cell_se, n, g->k, g->level, g->r2_max, g->c2m, g->nbr, redo, cnt, redo_keys, redo_cap);
+        pg_count_launches(1);
         if (cudaGetLastError() != cudaSuccess) st = PG_ERR_CUDA;
     }
     int32_t h_cnt = 0;
@@ -707,22 +549,6 @@ pg_status pg_launch_knn_queries(const pg_graph *g, const int32_t *qm, int64_t nq
     if (nq <= 0) return PG_OK;
     PG_TRY(upload_ring1(s));
     const int kp = pg_row_width(k);
-    if (g->level < 7) { // 64-bit distances: every query through the exact search
-#define Q(KP)                                                                                                   \
-    knn_exact_kernel<KP, true><<<pg_blocks(32 * nq, 128), 128, 0, s>>>(g->qpos, g->m2c, g->cell_se, g->c2m, qm, nullptr, nq, k, \
-                                                                 g->level, -1, out, nullptr, 0)
-        switch (kp) {
-            case 4: Q(4); break;
-            case 8: Q(8); break;
-            case 16: Q(16); break;
-            case 32: Q(32); break;
-            default: return PG_ERR_UNSUPPORTED;
-        }
-#undef Q
-        pg_count_launches(1);
-        PG_LAUNCH_CHECK();
-        return PG_OK;
-    }
     // first ring for every query; the queued ones resume from their saved
     // lists at ring 2 (the exact kernel reads the queue length on the device)
     int32_t *redo = nullptr, *cnt = nullptr;
@@ -733,12 +559,12 @@ pg_status pg_launch_knn_queries(const pg_graph *g, const int32_t *qm, int64_t nq
     if (st == PG_OK && cudaMemsetAsync(cnt, 0, 4, s) != cudaSuccess) st = PG_ERR_CUDA;
     if (st == PG_OK) {
 #define Q(KP)                                                                                                    \
-    if (KP <= 16)                                                                                                \
-        knn_est_kernel<KP, true><<<pg_blocks(nq, KE_THREADS), KE_THREADS, 0, s>>>(                               \
-            g->qpos, g->m2c, g->cell_se, nq, k, g->level, -1, g->c2m, out, redo, cnt, keys, nq, qm);                     \
+    if (g->level >= 7)                                                                                           \
+        knn_est_kernel<KP, true, true><<<pg_blocks(nq, ke_threads<KP>()), ke_threads<KP>(), 0, s>>>(             \
+            g->qpos, g->m2c, g->cell_se, nq, k, g->level, -1, g->c2m, out, redo, cnt, keys, nq, qm);             \
     else                                                                                                         \
-        knn_kernel<KP, true, true><<<pg_blocks(nq, 128), 128, 0, s>>>(g->qpos, g->m2c, g->cell_se, nq, k, g->level, -1,  \
-                                                                     g->c2m, out, redo, cnt, keys, nq, qm);      \
+        knn_est_kernel<KP, true, false><<<pg_blocks(nq, ke_threads<KP>()), ke_threads<KP>(), 0, s>>>(            \
+            g->qpos, g->m2c, g->cell_se, nq, k, g->level, -1, g->c2m, out, redo, cnt, keys, nq, qm);             \
     knn_exact_kernel<KP, true><<<pg_blocks(32 * nq, 128), 128, 0, s>>>(g->qpos, g->m2c, g->cell_se, g->c2m, redo, cnt, nq, k, \
                                                                  g->level, -1, out, keys, nq, qm)
         switch (kp) {
