@@ -83,6 +83,10 @@ __global__ void cell_count_kernel(const uint32_t *__restrict__ sorted_keys, int6
 // The 26 neighbours of a cell, packed (dx+1) | (dy+1) << 2 | (dz+1) << 4 and
 // ordered by the number of non-zero offsets: faces, then edges, then corners.
 __constant__ int c_ring1[26];
+// the 98 cells of ring 2 (the shell of the 5x5x5 block), packed
+// (dx + 2) | (dy + 2) << 3 | (dz + 2) << 6, nearest classes first (by the
+// number of axes at distance 2, then the sum of |d|)
+__constant__ int c_ring2[98];
 
 static void ring1_table(int out[26]) {
     int n = 0;
@@ -91,6 +95,19 @@ static void ring1_table(int out[26]) {
             for (int dy = -1; dy <= 1; dy++)
                 for (int dx = -1; dx <= 1; dx++)
                     if ((dx != 0) + (dy != 0) + (dz != 0) == cls) out[n++] = (dx + 1) | ((dy + 1) << 2) | ((dz + 1) << 4);
+}
+
+static void ring2_table(int out[98]) {
+    int n = 0;
+    for (int far = 1; far <= 3; far++)
+        for (int sum = 2; sum <= 6; sum++)
+            for (int dz = -2; dz <= 2; dz++)
+                for (int dy = -2; dy <= 2; dy++)
+                    for (int dx = -2; dx <= 2; dx++) {
+                        const int f = (abs(dx) == 2) + (abs(dy) == 2) + (abs(dz) == 2);
+                        if (f == far && abs(dx) + abs(dy) + abs(dz) == sum)
+                            out[n++] = (dx + 2) | ((dy + 2) << 3) | ((dz + 2) << 6);
+                    }
 }
 
 // (d2, id) lexicographic order
@@ -388,15 +405,28 @@ __global__ void __launch_bounds__(128) knn_exact_kernel(const uint64_t *__restri
     if (km1 > 0) {
         for (int r = r_start;; r++) {
             // ring r: the shell of the (2r+1)^3 block of cells around the own
+            // (ring 2, where most queued queries end, from a table: no
+            // divisions, no interior cells)
             const int span = 2 * r + 1;
-            const int ncell = span * span * span;
+            const bool tab = r == 2;
+            const int ncell = tab ? 98 : span * span * span;
             for (int c0 = 0; c0 < ncell; c0 += 32) {
                 int32_t p = 0, p1 = 0; // this lane's cell
                 const int ci = c0 + lane;
                 if (ci < ncell) {
-                    const int dx = ci % span - r, dy = (ci / span) % span - r, dz = ci / (span * span) - r;
+                    int dx, dy, dz;
+                    if (tab) {
+                        const int o = c_ring2[ci];
+                        dx = (o & 7) - 2;
+                        dy = ((o >> 3) & 7) - 2;
+                        dz = ((o >> 6) & 7) - 2;
+                    } else {
+                        dx = ci % span - r;
+                        dy = (ci / span) % span - r;
+                        dz = ci / (span * span) - r;
+                    }
                     const int x = cx + dx, y = cy + dy, z = cz + dz;
-                    bool use = (abs(dx) == r || abs(dy) == r || abs(dz) == r) && x >= 0 && x < G && y >= 0 &&
+                    bool use = (tab || abs(dx) == r || abs(dy) == r || abs(dz) == r) && x >= 0 && x < G && y >= 0 &&
                                y < G && z >= 0 && z < G;
                     if (use && worst_d != INT64_MAX) {
                         // a cell whose nearest point is farther than the
@@ -537,10 +567,14 @@ static pg_status launch_knn_t(pg_graph *g, cudaStream_t s) {
 
 static pg_status upload_ring1(cudaStream_t s) {
     static std::once_flag once;
-    static int ring[26];
-    std::call_once(once, [] { ring1_table(ring); });
-    // the constant lives per device: copy it before every launch (26 ints)
+    static int ring[26], ring2[98];
+    std::call_once(once, [] {
+        ring1_table(ring);
+        ring2_table(ring2);
+    });
+    // the constants live per device: copy them before every launch
     PG_CUDA(cudaMemcpyToSymbolAsync(c_ring1, ring, sizeof(ring), 0, cudaMemcpyHostToDevice, s));
+    PG_CUDA(cudaMemcpyToSymbolAsync(c_ring2, ring2, sizeof(ring2), 0, cudaMemcpyHostToDevice, s));
     return PG_OK;
 }
 
