@@ -240,9 +240,8 @@ __global__ void __launch_bounds__(ke_threads<KP>(), 4) knn_est_kernel(
             }
             const int2 se = cell_se[(int64_t)x + ((int64_t)y << level) + ((int64_t)z << (2 * level))];
             const int32_t p1 = se.x + se.y;
-            for (int32_t p = se.x; p < p1; p++) {
-                if (p == m) continue;
-                const uint64_t c = qpos[p];
+            auto visit = [&](int32_t p, uint64_t c) {
+                if (p == m) return;
                 const int32_t ex = (int32_t)(c & PG_QMASK) - qx, ey = (int32_t)((c >> 21) & PG_QMASK) - qy,
                               ez = (int32_t)(c >> 42) - qz;
                 DT d2;
@@ -252,10 +251,22 @@ __global__ void __launch_bounds__(ke_threads<KP>(), 4) knn_est_kernel(
                     d2 = (DT)((int64_t)ex * ex + (int64_t)ey * ey + (int64_t)ez * ez);
                     sat |= d2 < T && (uint64_t)d2 >= KNN_SAT;
                 }
-                if (d2 >= T) continue;
+                if (d2 >= T) return;
                 if (cnt < CAP) buf[cnt][tx] = p;
                 cnt++;
+            };
+            // two positions per 16-byte load
+            int32_t p = se.x;
+            if ((p & 1) && p < p1) {
+                visit(p, qpos[p]);
+                p++;
             }
+            for (; p + 1 < p1; p += 2) {
+                const ulonglong2 two = __ldg(reinterpret_cast<const ulonglong2 *>(qpos + p));
+                visit(p, two.x);
+                visit(p + 1, two.y);
+            }
+            if (p < p1) visit(p, qpos[p]);
         }
         // 3. select: the buffered candidates into the sorted list
         fresh = sat || cnt > CAP || (cnt < km1 && !capped);
