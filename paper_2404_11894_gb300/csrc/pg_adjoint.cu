@@ -136,9 +136,11 @@ __device__ __forceinline__ void sort_column(int2 *__restrict__ tent, int64_t a, 
 // Order each column's entries by source row (a row appears once per column),
 // which makes the reverse sweep's summation order deterministic, and write
 // the column's pad entry (source row pad_row < 0, skipped by the sweep) when
-// its length was rounded up. Columns of up to 16 or 32 entries (all of them
-// for k <= 16 in practice) are sorted in registers by a bitonic network;
-// longer ones by insertion sort in memory.
+// its length was rounded up. Columns of up to 32 entries (all of them for
+// k <= 16 in practice) are sorted in registers by one 32-entry bitonic
+// network (a 16-entry one for the shorter columns made nearly every warp
+// run both, as 30 % of a kNN graph's columns hold more than 16); longer
+// ones by insertion sort in memory.
 __global__ void __launch_bounds__(128) tsort_kernel(const int64_t *__restrict__ tptr,
                                                     const int32_t *__restrict__ fill, int64_t ncols,
                                                     int32_t pad_row, int2 *__restrict__ tent) {
@@ -148,10 +150,6 @@ __global__ void __launch_bounds__(128) tsort_kernel(const int64_t *__restrict__ 
     const int32_t len = fill[c];
     if (a + len < tptr[c + 1]) tent[a + len] = make_int2(pad_row, 0);
     if (len <= 1) return;
-    if (len <= 16) {
-        sort_column<16>(tent, a, len);
-        return;
-    }
     if (len <= 32) {
         sort_column<32>(tent, a, len);
         return;
