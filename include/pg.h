@@ -277,9 +277,9 @@ typedef struct {
  * (8 + 4 * row width) bytes for a final gather (row width = final_gather_k
  * rounded up to 4, 8, 16 or 32), plus 4 * n_paths with extra samples. A
  * final gather that searches its neighbourhoods (final_gather_k above the
- * graph's k, a cluster graph or a radius limit) on a grid of level 7 or more
- * adds n_paths * (4 + 8 * (row width - 1)) + 16 bytes for the first-ring
- * search's queue and the saved lists its queued queries resume from.
+ * graph's k, a cluster graph or a radius limit) adds n_paths * (4 + 8 *
+ * (row width - 1)) + 16 bytes for the first-ring search's queue and the
+ * saved lists its queued queries resume from.
  * Errors: PG_ERR_STATE, PG_ERR_INVALID_ARG (sizes, NULL arrays, m < 1,
  * negative Le or pe_e), PG_ERR_UNSUPPORTED (final_gather_k > 32),
  * PG_ERR_NONFINITE (an extra sample). */
