@@ -139,7 +139,9 @@ typedef struct {
  * quantised coordinates q = min(2^21-1, floor((p - lo) * 2^21 / max_extent)),
  * ties broken by the smaller caller index; entries beyond r2_max are
  * dropped. Exact (bit-identical to brute force).
- * Synchronises `stream` once (to report non-finite positions).
+ * Synchronises `stream` twice (to size the exact search of the queries the
+ * first ring around each vertex leaves open, and to report non-finite
+ * positions; cluster mode synchronises more often to size its lists).
  * Errors: PG_ERR_INVALID_ARG (NULL, n < 0, n >= 2^31-1, bad box),
  * PG_ERR_UNSUPPORTED (k outside 1..32, grid_level > 10), PG_ERR_NONFINITE.
  * *out is freed with pg_graph_destroy. */
