@@ -193,7 +193,9 @@ pg_status pg_graph_get_info(const pg_graph *g, pg_graph_info *info);
  * of the device's atomic additions.
  * The graph keeps the propagation matrix (P A+, Eq. rte-mff) in `wdtype` and
  * P c. c and D (caller order, n floats each, device) are written for the
- * caller; either may be NULL. Synchronises `stream` once.
+ * caller; either may be NULL. Synchronises `stream` twice (for the count
+ * of rows with a predecessor and the input checks, then for the count of
+ * swept entries).
  * Errors: PG_ERR_NONFINITE, PG_ERR_INVALID_ARG (succ out of range, a vertex
  * with two predecessors, |g| >= 1, negative coefficients or pdfs). */
 pg_status pg_aggregate(pg_graph *g, const pg_vertices *v, pg_wdtype wdtype, float *c, float *D, pg_stream_t stream);
