@@ -169,7 +169,7 @@ def test_neighbors_ties_radius(pg, k):
         assert np.array_equal(got, want), (k, r2)
 
 
-@pytest.mark.parametrize("k", [2, 4, 8, 13, 16])
+@pytest.mark.parametrize("k", [2, 4, 8, 13, 16, 17, 32])
 def test_neighbors_ties_first_ring_level7(pg, k):
     """A level-7 grid (32-bit distances in the first ring): a full 12^3
     lattice at 4 sites per cell and axis, each site repeated 1 to 3 times and
