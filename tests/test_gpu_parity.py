@@ -301,7 +301,8 @@ def test_solver_host_path_equals_device_path(pg):
     solver.close()
 
 
-def test_prepared_transpose_on_a_side_stream(pg):
+@pytest.mark.parametrize("wdtype", ["f32", "u16", "bf16"])
+def test_prepared_transpose_on_a_side_stream(pg, wdtype):
     """pg_prepare_adjoint on a second stream, concurrent with the forward
     sweeps, gives the same reverse sweeps as the transpose built inside
     pg_propagate_adjoint (bitwise: mode 0 sums in a fixed order)."""
@@ -314,7 +315,7 @@ def test_prepared_transpose_on_a_side_stream(pg):
     grads = []
     for prepared in (False, True):
         graph = pg.pg_build_graph(V, sc.k)
-        pg.pg_aggregate(graph, V, "bf16")
+        pg.pg_aggregate(graph, V, wdtype)
         main = torch.cuda.current_stream()
         side = torch.cuda.Stream()
         if prepared:

@@ -23,7 +23,7 @@ def pg():
     return pg
 
 
-@pytest.mark.parametrize("world,wdtype", [(2, "f32"), (3, "f32"), (2, "u16"), (4, "bf16")])
+@pytest.mark.parametrize("world,wdtype", [(2, "f32"), (3, "f32"), (2, "u16"), (4, "bf16"), (8, "f32"), (8, "u16")])
 def test_shards_on_one_device_equal_pg_propagate(pg, world, wdtype):
     from paper_2404_11894_gb300 import _lib, _ptr, _stream_ptr
     from paper_2404_11894_gb300.dist import ShardLists
